@@ -1,0 +1,433 @@
+#!/usr/bin/env python
+"""Throughput of the BG-Triangle differentiable rasterizer on one node.
+
+Workload (the batched configuration of the metric): 20,000 degree-2
+BG-triangles (icosphere + three ellipsoids, control-point noise N(0, 0.02)),
+64 views of mixed size {256, 512, 800, 1024}^2 on a radius 3.5..5 sphere,
+boundary scale r_b = 1e-2. One step = forward of all 64 views in one batched
+call, L1 loss gradient against a fixed target, backward to the primitive
+parameters. Metric: renders/s, one render = one view forward + backward.
+The step's inputs (~0.5 GB of pixels and pairs) exceed the 129 MB L2.
+
+Beside it: the plain single-view path on the same 64 views, one 800^2 view,
+an end-to-end number with the parameters copied from pinned host memory and
+the gradients read back every step, per-stage device times (CUDA events) for
+the roofline of the dominant kernel, SM clocks sampled during the timed
+region, and the FP64 CPU oracle timed on a bounded sample of views.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "fwd+bwd renders/s at 800² (20k BG-triangles) batched vs plain; % HBM peak"
+WORKLOAD = ("20k degree-2 BG-triangles (icosphere f20 + 3 ellipsoids, noise 0.02), 64 views mixed "
+            "{256,512,800,1024}^2, radius U[3.5,5], r_b=1e-2, batched fwd+L1+bwd")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--rb", type=float, default=1e-2)
+    ap.add_argument("--tile", type=int, default=0, help="0 = autotune")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else f"/tmp/bgt_clocks_{os.getpid()}.csv"
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() in ("active", "1", "yes"):
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def stage_bytes(stage, c, M, ncp, V):
+    """Algorithmic bytes a stage must move per call (per unit x units)."""
+    P, F, Nb, K, Kb = c["P"], c["F"], c["Nb"], c["K"], c["Kb"]
+    return {
+        # control points per view + one 64-bit depth key per pixel
+        "raster": 12 * ncp * M * V + 8 * P,
+        # depth key read, I_id + I_uv write
+        "resolve": 8 * P + 12 * P,
+        # I_id (+ neighbours) and I_uv read, Gaussian (48 B) and boundary (16 B) records written
+        "generate": 4 * P + 8 * F + 48 * F + 16 * Nb,
+        # pair keys written once, read + written by the per-tile sort
+        "binning": 3 * 8 * K + 3 * 8 * Kb + 20 * Kb,
+        # per tile: keys + 48-B records of its pairs, 20-B boundary entries; image, T, n, I_id per pixel
+        "composite_fwd": 56 * K + 20 * Kb + 12 * P + 8 * P + 4 * P,
+        # as forward + dl/dC read + per-Gaussian gradient accumulation (36 B)
+        "composite_bwd": 56 * K + 20 * Kb + 12 * P + 12 * P + 36 * F,
+        # per-Gaussian / boundary gradients read, parameter gradients written
+        "chain": 48 * F + 16 * Nb + 8 * F + 4 * (2 * 3 * ncp + 2) * M,
+        "prep": 8 * P,
+    }[stage]
+
+
+def build_workload(seed_views, rb):
+    from paper_2503_13961_gb300 import scenes
+    sc, cams = scenes.config_scene(4, r_b=rb)
+    if seed_views:
+        # other ranks render their own 64 views of the same scene (weak scaling)
+        rng = np.random.default_rng(1000 + seed_views)
+        sizes = [(c["width"], c["height"]) for c in cams]
+        cams = scenes.make_views(rng, sizes, 3.5, 5.0)
+    return sc, cams
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2503_13961_gb300 import render as R
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    sc, cams = build_workload(rank, args.rb)
+    V = len(cams)
+    P = sum(c["width"] * c["height"] for c in cams)
+    M, ncp = sc["ctrl"].shape[0], sc["ctrl"].shape[1]
+    rd = R.Renderer(degree=2, max_prims=M, max_views=V, max_pixels=P, max_pairs=6 * P, max_boundary_pairs=6 * P,
+                    tile_size=16, graph=True)
+    dev = R.scene_to_device(sc)
+    stream = torch.cuda.Stream()
+    gen = torch.Generator(device="cuda").manual_seed(1234 + rank)
+    with torch.cuda.stream(stream):
+        images = torch.empty((P, 3), device="cuda")
+        target = torch.rand((P, 3), device="cuda", generator=gen)
+        dimg = torch.zeros((P, 3), device="cuda")
+        grads = {k: torch.empty_like(dev[k]) for k in R.GRAD_KEYS}
+        loss = torch.zeros(1, device="cuda")
+    torch.cuda.synchronize()  # scene tensors were filled on the default stream
+    scale = 1.0 / (3 * P)
+    tune_ms = None
+    if args.tile:
+        rd.set_tile_size(args.tile)
+    else:
+        _, tune_ms = rd.autotune(dev, cams, images, dimg, grads, iters=2, stream=stream)
+
+    def step():
+        rd.forward(dev, cams, images, stream=stream)
+        rd.l1_loss_grad(images, target, scale, dimg, loss, stream=stream)
+        rd.backward(dev, cams, dimg, grads, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    rd.sync_status(stream)
+    counts = rd.counts(stream)
+    counts["P"] = P
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    e1.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    rd.sync_status(stream)
+    value = world * V * args.steps / (ms / 1e3)
+
+    # per-stage device time of the same step: a second handle (no graph, same
+    # tile size) records CUDA events between the stages on the same stream
+    prof_rd = R.Renderer(degree=2, max_prims=M, max_views=V, max_pixels=P, max_pairs=6 * P,
+                         max_boundary_pairs=6 * P, tile_size=rd.tile_size, graph=False)
+    prof_rd.set_profiling(True)
+    stage_ms = {}
+    nprof = max(3, min(args.steps, 8))
+    for i in range(nprof + 1):
+        prof_rd.forward(dev, cams, images, stream=stream)
+        prof_rd.l1_loss_grad(images, target, scale, dimg, loss, stream=stream)
+        prof_rd.backward(dev, cams, dimg, grads, stream=stream)
+        stream.synchronize()
+        prof, kf, kb = prof_rd.profile()
+        if i == 0:
+            continue  # warm-up
+        for k, v in prof.items():
+            stage_ms[k] = stage_ms.get(k, 0.0) + v / nprof
+    prof_rd.sync_status(stream)
+    prof_rd.close()
+    del prof_rd
+    launches_per_step = kf + kb + 1  # + the L1 loss-gradient kernel
+
+    # end to end: parameters from pinned host memory in, gradients + loss out, every step
+    host_in = {k: dev[k].cpu().pin_memory() for k in R.SCENE_KEYS}
+    host_out = {k: torch.empty(grads[k].shape, dtype=torch.float32).pin_memory() for k in R.GRAD_KEYS}
+    host_loss = torch.empty(1).pin_memory()
+    h2d = sum(t.numel() * 4 for t in host_in.values())
+    d2h = sum(t.numel() * 4 for t in host_out.values()) + 4
+
+    def e2e_step():
+        for k in R.SCENE_KEYS:
+            dev[k].copy_(host_in[k], non_blocking=True)
+        step()
+        for k in R.GRAD_KEYS:
+            host_out[k].copy_(grads[k], non_blocking=True)
+        host_loss.copy_(loss, non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            e2e_step()
+        stream.synchronize()
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        e1.synchronize()
+        wall = time.perf_counter() - t0
+    e2e_ms = max(e0.elapsed_time(e1), wall * 1e3)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * V * args.steps / (e2e_ms / 1e3)
+    rd.sync_status(stream)
+
+    out = None
+    if rank == 0:
+        dom = max(("composite_fwd", "composite_bwd", "raster", "generate", "binning", "chain", "resolve"),
+                  key=lambda s: stage_ms.get(s, 0.0))
+        peak, peak_kind = peaks()
+        per_stage = {}
+        for s_name, s_ms in stage_ms.items():
+            b = stage_bytes(s_name, counts, M, ncp, V)
+            per_stage[s_name] = {"ms": round(s_ms, 4), "alg_bytes": int(b),
+                                 "GBps": round(b / (s_ms * 1e-3) / 1e9, 1) if s_ms > 0 else None}
+        dom_bytes = stage_bytes(dom, counts, M, ncp, V)
+        achieved = dom_bytes / (stage_ms[dom] * 1e-3) / 1e9
+        out = {
+            "metric": METRIC, "value": round(value, 2), "unit": "renders/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded scene generator; stands in for Lego / NeRF-Synthetic)",
+            "config": {"workload": WORKLOAD, "views": V, "pixels": P, "prims": M, "degree": 2,
+                       "tile": rd.tile_size, "tile_autotune_ms": tune_ms, "graph": True,
+                       "counts": {k: int(v) for k, v in counts.items()},
+                       "l2": "inputs larger than L2 (no flush needed)", "parallelism": f"replicas x{world}"},
+            "clocks": clk,
+            "e2e": {"value": round(e2e_value, 2), "unit": "renders/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches_per_step * args.steps),
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "traffic": None, "alg_bytes_per_launch": int(dom_bytes),
+                         "ms_per_launch": round(stage_ms[dom], 4)},
+            "stages": per_stage,
+        }
+    return out, (rd, dev, cams, sc, stream)
+
+
+def run_plain(rd_ctx, args):
+    """The single-view path: each view rendered and differentiated on its own."""
+    import torch
+    from paper_2503_13961_gb300 import render as R
+    _, dev, cams, sc, stream = rd_ctx
+    M = sc["ctrl"].shape[0]
+    Pmax = max(c["width"] * c["height"] for c in cams)
+    rd = R.Renderer(degree=2, max_prims=M, max_views=1, max_pixels=Pmax, max_pairs=6 * Pmax,
+                    max_boundary_pairs=6 * Pmax, tile_size=16, graph=False)
+    bufs = []
+    gen = torch.Generator(device="cuda").manual_seed(99)
+    with torch.cuda.stream(stream):
+        for c in cams:
+            n = c["width"] * c["height"]
+            bufs.append((torch.empty((n, 3), device="cuda"), torch.rand((n, 3), device="cuda", generator=gen),
+                         torch.zeros((n, 3), device="cuda")))
+        grads = {k: torch.empty_like(dev[k]) for k in R.GRAD_KEYS}
+
+    def step():
+        for c, (img, tgt, d) in zip(cams, bufs):
+            rd.forward(dev, [c], img, stream=stream)
+            rd.l1_loss_grad(img, tgt, 1.0 / img.numel(), d, stream=stream)
+            rd.backward(dev, [c], d, grads, stream=stream)
+
+    step()
+    rd.sync_status(stream)
+    steps = max(2, args.steps // 2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    rd.sync_status(stream)
+    plain = {"value": round(len(cams) * steps / (ms / 1e3), 2), "unit": "renders/s",
+             "ms_per_64_views": round(ms / steps, 3), "graph": False, "tile": 16}
+    # one 800^2 view, plain
+    c800 = [c for c in cams if c["width"] == 800][:1]
+    v800 = None
+    if c800:
+        img, tgt, d = bufs[cams.index(c800[0])]
+        for _ in range(3):
+            rd.forward(dev, c800, img, stream=stream)
+            rd.l1_loss_grad(img, tgt, 1.0 / img.numel(), d, stream=stream)
+            rd.backward(dev, c800, d, grads, stream=stream)
+        n = 20
+        e0.record(stream)
+        for _ in range(n):
+            rd.forward(dev, c800, img, stream=stream)
+            rd.l1_loss_grad(img, tgt, 1.0 / img.numel(), d, stream=stream)
+            rd.backward(dev, c800, d, grads, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        v800 = {"value": round(n / (e0.elapsed_time(e1) / 1e3), 2), "unit": "renders/s",
+                "ms_per_render": round(e0.elapsed_time(e1) / n, 4)}
+    rd.close()
+    return plain, v800
+
+
+def cpu_baseline(budget_s, rb):
+    """The FP64 oracle on the host cores: whole views of the workload (forward +
+    backward) until the time budget is used; renders/s."""
+    from oracle import oracle
+    from paper_2503_13961_gb300 import scenes
+    sc, cams = scenes.config_scene(4, r_b=rb)
+    order = sorted(range(len(cams)), key=lambda i: cams[i]["width"])
+    rng = np.random.default_rng(0)
+    done, t0, pix = 0, time.perf_counter(), 0
+    for i in order:
+        c = cams[i]
+        idm, uv, _ = oracle.raster(sc, c)
+        oracle.render(sc, c, idm, uv)
+        dl = rng.normal(size=(c["height"], c["width"], 3)) / (3 * c["width"] * c["height"])
+        oracle.backward(sc, c, dl, idm, uv)
+        done += 1
+        pix += c["width"] * c["height"]
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(done / dt, 4), "unit": "renders/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{done} whole views ({pix} px) of the 64-view workload, smallest first, fwd+bwd, "
+                      f"FP64, {dt:.1f} s"}
+
+
+def main():
+    args = parse()
+    world, rank, _ = dist_env()
+    if args.impl == "reference":
+        # the reference arm is the FP64 oracle (the paper publishes no code)
+        if rank != 0:
+            return
+        from oracle import oracle
+        oracle.build()
+        ms_steps = []
+        base = None
+        for _ in range(args.warmup):
+            cpu_baseline(1.0, args.rb)
+        for _ in range(args.steps):
+            base = cpu_baseline(args.cpu_seconds / max(args.steps, 1), args.rb)
+            ms_steps.append(base["value"])
+        val = statistics.mean(ms_steps)
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": "renders/s",
+                          "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "config": {"workload": WORKLOAD},
+                          "cpu_baseline": {"kind": "oracle", "cores": base["cores"], "sample": base["sample"],
+                                           "value": round(val, 4), "unit": "renders/s"},
+                          "e2e": {"value": round(val, 4), "unit": "renders/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}), flush=True)
+        return
+    out, ctx = run_ours(args)
+    if rank == 0:
+        if world == 1 and not args.no_plain:
+            plain, v800 = run_plain(ctx, args)
+            out["plain"] = plain
+            out["batched_over_plain"] = round(out["value"] / plain["value"], 3)
+            out["view_800"] = v800
+        if world == 1:
+            out["cpu_baseline"] = cpu_baseline(args.cpu_seconds, args.rb)
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * bgt.h -- C ABI of the GB300 BG-Triangle differentiable rasterizer.
+ *
+ * Renders Bezier Gaussian Triangles (Wu et al., "BG-Triangle: Bezier Gaussian
+ * Triangle for 3D Vectorization and Rendering", CVPR 2025) into images and
+ * back-propagates image gradients to their parameters. The forward pass is
+ * the pipeline of Sec. 3.2 / Fig. 2: tessellation + rasterization with a
+ * depth test (I_id, I_uv, boundary set B), sub-primitive generation (Eq. 3-5)
+ * and discontinuity-aware alpha blending (Eq. 6-8). The backward pass follows
+ * the supplementary "Backward Derivative" with the rasterizer outputs held
+ * fixed, as the paper does.
+ *
+ * Conventions
+ *   - All pointers inside bgt_scene, bgt_grads and every image buffer are
+ *     DEVICE pointers owned by the caller. Cameras are HOST memory.
+ *   - Streams are passed as `void *` holding a cudaStream_t (NULL = default).
+ *     All work is asynchronous on that stream; one handle must not be used
+ *     from two streams at once.
+ *   - Images of a call with n views are packed back to back in view order;
+ *     view v occupies pixels [off_v, off_v + W_v H_v), row-major, 3 floats
+ *     (R, G, B) per pixel, off_v = sum of the earlier views' W H.
+ *   - Control points of primitive g are ctrl[g][idx][3] with idx running over
+ *     (i, j, k), i + j + k = n, in the order i = n..0, then j = n-i..0; the
+ *     corner p_n00 is barycentric u = 1, p_0n0 is v = 1, p_00n is w = 1.
+ *   - Errors are returned, never trapped. Errors detected on the device
+ *     (capacity overflow, non-finite values) set a status word that
+ *     bgt_sync_status() reports; outputs of such a call are unspecified.
+ *
+ * The library allocates its whole workspace in bgt_create() from the
+ * capacities in bgt_config and never allocates afterwards, so a sequence of
+ * calls can be captured in a CUDA graph.
+ */
+#ifndef BGT_H
+#define BGT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BGT_OK = 0,
+  BGT_ERR_INVALID_ARG = 1, /* bad pointer, size or configuration */
+  BGT_ERR_CAPACITY = 2,    /* a call or a device-side count exceeded a capacity */
+  BGT_ERR_CUDA = 3,        /* a CUDA runtime call failed; see bgt_last_error */
+  BGT_ERR_TIMEOUT = 4,     /* reserved: a bounded device wait gave up */
+  BGT_ERR_NONFINITE = 5,   /* non-finite projected Gaussian detected */
+  BGT_ERR_STATE = 6        /* backward called without a matching forward */
+} bgt_status;
+
+typedef struct bgt_handle bgt_handle;
+
+/* Flags of bgt_config.flags */
+#define BGT_FLAG_NO_BOUNDARY 1 /* w = 1 everywhere: the paper's "w/o B" ablation (Table 3) */
+#define BGT_FLAG_GRAPH 2       /* capture forward and backward in CUDA graphs, replay when shapes repeat */
+
+typedef struct {
+  int degree;                   /* n of the Bezier triangles, 1..4 (paper: 2) */
+  int max_prims;                /* capacity: primitives per scene */
+  int max_views;                /* capacity: views per call (<= 4096) */
+  long long max_pixels;         /* capacity: sum of W*H over the views of one call */
+  long long max_pairs;          /* capacity: (Gaussian, tile) pairs per call */
+  long long max_boundary_pairs; /* capacity: (boundary point, tile) pairs per call */
+  int tess_level;               /* L: each primitive becomes L^2 flat triangles (1..16) */
+  int tile_size;                /* screen tile edge: 8, 16 or 32 pixels */
+  float k_b;                    /* boundary radius sigma = k_b fx r_b / z (Sec. 3.2) */
+  float alpha_min;              /* pairs with alpha below are skipped (1/255) */
+  float alpha_max;              /* alpha = min(alpha_max, o w G) (0.99) */
+  float t_stop;                 /* blending stops before T would fall below (1e-4) */
+  float dilation;               /* added to the diagonal of every 2D covariance, px^2 (0.3) */
+  float near_z;                 /* flat triangles with a vertex nearer than this are culled */
+  int flags;                    /* BGT_FLAG_* */
+} bgt_config;
+
+typedef struct {
+  float R[9];           /* world -> camera rotation, row-major; camera x right, y down, z forward */
+  float t[3];           /* world -> camera translation */
+  float fx, fy, cx, cy; /* pinhole intrinsics in pixels; pixel (x, y) has its centre at (x, y) */
+  int width, height;
+} bgt_camera;
+
+typedef struct {
+  const float *ctrl;      /* [M][Ncp][3] control points p_ijk (Eq. 1), Ncp = (n+1)(n+2)/2 */
+  const float *color;     /* [M][Ncp][3] colour control points p^c_ijk (Eq. 4) */
+  const float *opacity;   /* [M] opacity o (Eq. 8) */
+  const float *r_b;       /* [M] boundary scale r_b (Sec. 3.2) */
+  const float *log_scale; /* [M][3] log scales of the sub-primitive Gaussians (Eq. 5, one texel) */
+  const float *quat;      /* [M][4] rotation (w, x, y, z) of the sub-primitive Gaussians */
+  int num_prims;          /* M */
+  float bg[3];            /* background colour c_bg */
+} bgt_scene;
+
+typedef struct {
+  float *ctrl;    /* [M][Ncp][3] dl/dp_ijk */
+  float *color;   /* [M][Ncp][3] dl/dp^c_ijk */
+  float *opacity; /* [M] dl/do */
+  float *r_b;     /* [M] dl/dr_b */
+} bgt_grads;
+
+/* Fill *cfg with the defaults named above (n = 2, L = 8, tile 16, 1/255, 0.99,
+ * 1e-4, 0.3, k_b = 3, near 0.2) and capacities for one 1024x1024 view of
+ * 100k primitives. Returns BGT_ERR_INVALID_ARG if cfg is NULL. */
+bgt_status bgt_default_config(bgt_config *cfg);
+
+/* Create a handle on the current CUDA device and allocate its workspace from
+ * the capacities in *cfg. On success *out owns the workspace until
+ * bgt_destroy. BGT_ERR_INVALID_ARG for an out-of-range field, BGT_ERR_CUDA if
+ * the allocation fails. */
+bgt_status bgt_create(const bgt_config *cfg, bgt_handle **out);
+
+/* Release the handle and its workspace (synchronizes the device). NULL is a no-op. */
+void bgt_destroy(bgt_handle *h);
+
+/* Forward pass (Sec. 3.2 pipeline) of n_views cameras (host array) on
+ * `stream`. images: device [sum W H][3], written entirely. The handle keeps
+ * the rasterizer outputs, sorted lists and per-pixel final transmittance for
+ * bgt_render_bwd (valid until the next bgt_render_fwd on the handle).
+ * BGT_ERR_INVALID_ARG / BGT_ERR_CAPACITY for bad or oversized inputs (checked
+ * on the host before any launch), BGT_ERR_CUDA if a launch fails. */
+bgt_status bgt_render_fwd(bgt_handle *h, const bgt_scene *scene, const bgt_camera *cams, int n_views,
+                          float *images, void *stream);
+
+/* Backward pass for the last forward on this handle: d_images is dl/dC in
+ * the image layout (device). Overwrites the four gradient arrays of *grads
+ * (device, zeroed first) with dl/dparameters summed over all views, holding
+ * I_id, I_uv, B and the per-pixel survivor lists of the forward fixed
+ * (supplementary "Backward Derivative"). The scene and cameras must be those
+ * of the forward; BGT_ERR_STATE otherwise or without a forward. */
+bgt_status bgt_render_bwd(bgt_handle *h, const bgt_scene *scene, const bgt_camera *cams, int n_views,
+                          const float *d_images, const bgt_grads *grads, void *stream);
+
+/* Wait for `stream`, then report and clear the device status word:
+ * BGT_ERR_CAPACITY (pairs or boundary pairs exceeded their capacity),
+ * BGT_ERR_NONFINITE, or BGT_OK. */
+bgt_status bgt_sync_status(bgt_handle *h, void *stream);
+
+/* Text of the last error on this handle ("" if none). Owned by the handle. */
+const char *bgt_last_error(const bgt_handle *h);
+
+/* Counts of the last forward, after a synchronize: out[0] = foreground
+ * pixels F (= Gaussians), out[1] = boundary points |B|, out[2] = Gaussian
+ * tile pairs K, out[3] = boundary tile pairs Kb, out[4] = total tiles. */
+bgt_status bgt_get_counts(bgt_handle *h, long long out[5], void *stream);
+
+/* Change the tile size (8, 16 or 32) used by later calls. Images do not
+ * depend on it (every pixel composites the same pairs in the same order). */
+bgt_status bgt_set_tile_size(bgt_handle *h, int tile_size);
+int bgt_get_tile_size(const bgt_handle *h);
+
+/* Per-stage timing: when on, forward and backward record CUDA events on their
+ * stream between stages (also inside captured graphs). bgt_get_profile
+ * waits for the last backward and returns device milliseconds of the last
+ * forward + backward: ms[0] clears + per-primitive prep, [1] tessellation +
+ * raster, [2] resolve, [3] sub-primitive generation, [4] binning + sort,
+ * [5] forward blending, [6] backward blending, [7] chain to parameters;
+ * *kernels_fwd / *kernels_bwd receive the kernels each pass enqueues.
+ * BGT_ERR_STATE if profiling is off or no profiled pair has run. */
+bgt_status bgt_set_profiling(bgt_handle *h, int on);
+bgt_status bgt_get_profile(bgt_handle *h, float ms[8], int *kernels_fwd, int *kernels_bwd);
+
+/* Autotuner: time `iters` forward + backward passes of this workload at each
+ * tile size in {8, 16, 32} with CUDA events on `stream`, keep the fastest and
+ * return it in *best (ms per pass of each size in ms_out[3] if non-NULL).
+ * Buffers as for bgt_render_fwd / bgt_render_bwd. */
+bgt_status bgt_autotune(bgt_handle *h, const bgt_scene *scene, const bgt_camera *cams, int n_views,
+                        float *images, const float *d_images, const bgt_grads *grads, int iters,
+                        int *best, float *ms_out, void *stream);
+
+/* Loss helper for training loops and benchmarks: L1 loss
+ * l = scale * sum |images - target| over n floats; writes dl/dC =
+ * scale * sign(images - target) to d_images and atomically adds l to *loss
+ * (device, may be NULL). */
+bgt_status bgt_l1_loss_grad(const float *images, const float *target, long long n, float scale,
+                            float *d_images, float *loss, void *stream);
+
+/* Intermediate buffers of the last forward, copied to host memory for stage
+ * tests. `which`: 0 I_id int32[P]; 1 I_uv float[P][2]; 2 Gaussian records
+ * float[F][12] (off_x, off_y, K_a, K_b, K_c, o, bits(qx|qy<<16), bits(prim),
+ * r, g, b, depth); 3 boundary records float[Nb][8] (pixel, prim, off_x,
+ * off_y, sigma, z, 0, 0 with pixel and prim as int32 bits); 4 per-tile
+ * Gaussian ranges int64[tiles+1]; 5 sorted Gaussian keys uint64[K]; 6 per-tile
+ * boundary ranges int64[tiles+1]; 7 sorted boundary keys uint64[Kb];
+ * 8 final transmittance float[P]; 9 per-pixel count of list entries
+ * processed int32[P]; 10 per-Gaussian gradients float[F][12];
+ * 11 per-boundary-point gradients float[Nb][4]. `bytes` is the size of dst;
+ * *written receives the bytes copied. Synchronizes `stream`. */
+bgt_status bgt_get_stage(bgt_handle *h, int which, void *dst, long long bytes, long long *written,
+                         void *stream);
+
+/* Binning + sort stage on its own (Sec. 3.2 "Rendering Acceleration"; the
+ * (tile, depth) sort): `count` projected Gaussians of one W x H view given
+ * as device arrays qxy int32[count] (qx | qy << 16), off float[count][2],
+ * conic float[count][3], opacity float[count], depth float[count]. The
+ * Gaussians are binned to tiles of the handle's tile size by their support
+ * o exp(-1/2 d^T K d) >= alpha_min and sorted inside each tile by
+ * (depth, index); read the result with bgt_get_stage(4) and (5). */
+bgt_status bgt_bin_sort(bgt_handle *h, int width, int height, int count, const int *qxy, const float *off,
+                        const float *conic, const float *opacity, const float *depth, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BGT_H */

@@ -1,0 +1,343 @@
+// Internal declarations of the BG-Triangle CUDA library (sm_103a).
+//
+// Data layout in HBM (one call renders V views of mixed size):
+//   pixels   the views' pixels concatenated in view order, row-major inside a
+//            view; global pixel index p = view.pix_off + y * W + x.
+//   tiles    t x t screen tiles, concatenated the same way (view.tile_off).
+//   gaussians one per foreground pixel (Sec. 3.2, sub-primitive generation),
+//            compacted in global pixel order; gaussian index = rank.
+//   boundary  one point per pixel of B, compacted in global pixel order.
+//   pairs    (tile, gaussian) and (tile, boundary point) pairs bucketed by
+//            tile, then sorted inside each tile (see binning.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bgt {
+
+constexpr int kMaxDegree = 4;
+constexpr int kMaxCp = 15;
+constexpr int kMaxTess = 16;
+constexpr int kMaxViews = 4096;
+constexpr int kGuardPx = 1 << 20;  // vertices beyond +-2^20 px cull their flat triangles
+
+// status word bits (device-side errors, reported by bgt_sync_status)
+constexpr int kStatusPairOverflow = 1;
+constexpr int kStatusBoundaryOverflow = 2;
+constexpr int kStatusTileOverflow = 4;
+constexpr int kStatusNonFinite = 8;
+constexpr int kStatusBadPrim = 16;
+
+struct View {                 // one camera and its place in the batch (128 B)
+  float R[9];                 // world -> camera rotation, row-major
+  float t[3];
+  float fx, fy, cx, cy;
+  int W, H;
+  int pix_off;                // first global pixel of the view
+  int tile_off;               // first global tile of the view
+  int tiles_x, tiles_y;
+  int pad[10];
+};
+static_assert(sizeof(View) == 128, "View is 128 bytes");
+
+struct Params {
+  int n, ncp, M, L;
+  float near_z, k_b, alpha_min, alpha_max, t_stop, dilation;
+  float log_alpha_min;
+  int use_boundary;
+  int tile;                   // tile edge in pixels (8, 16 or 32)
+  int V, P, tiles;            // views, total pixels, total tiles of this call
+  float bg[3];
+  long long max_pairs, max_bpairs;
+};
+
+struct Scene {                // device pointers, caller-owned
+  const float *ctrl, *color, *opacity, *r_b, *log_scale, *quat;
+};
+
+struct Grads {                // device pointers, caller-owned outputs
+  float *ctrl, *color, *opacity, *r_b;
+};
+
+// Gaussian record (one per foreground pixel), three float4 per Gaussian:
+//   A = (off_x, off_y, K_a, K_b)   mean = pixel centre + off; conic (a, b, c)
+//   B = (K_c, opacity, bits(qx | qy << 16), bits(prim))
+//   C = (r, g, b, depth)
+// Boundary record (one per pixel of B):
+//   R = (bits(qx | qy << 16), off_x, off_y, 1 / sigma)
+struct Work {
+  const View *views;
+  const int *view_pix_off;    // V + 1 entries
+  const int *view_tile_off;   // V + 1 entries
+  unsigned long long *zbuf;   // [P] depth key of the nearest flat triangle
+  int *pid;                   // [P] I_id, -1 background
+  float2 *puv;                // [P] I_uv (u, v)
+  int *pix_gidx;              // [P] gaussian index of a foreground pixel, else -1
+  int *blk_cnt;               // [2][nblk] per-block foreground / boundary counts
+  int *counters;              // [16] F, Nb, K, Kb, queue heads...
+  int *status;                // [1]
+  // per primitive
+  float *sig3;                // [M][6] 3D covariance (xx, xy, xz, yy, yz, zz)
+  // gaussians
+  float4 *gA, *gB, *gC;       // [Fcap]
+  int *g_pix;                 // [Fcap] global pixel index
+  int *g_view;                // [Fcap]
+  float2 *g_uv;               // [Fcap]
+  uint2 *g_rect;              // [Fcap] tile rect x0 | y0 << 16, x1 | y1 << 16 (view-local tiles)
+  // boundary points
+  float4 *bR;                 // [Fcap]
+  int *b_pix, *b_prim, *b_view;
+  float2 *b_uv;
+  float *b_sigma, *b_z;
+  uint2 *b_rect;
+  // tiles
+  int *g_tcount, *g_tfill;    // [tiles + 1] per-tile pair counts / fill cursors
+  int *b_tcount, *b_tfill;
+  long long *g_tstart, *b_tstart;  // [tiles + 1] exclusive prefix sums (64-bit: no wrap)
+  long long *scan_aux, *scan_aux2; // scratch of the two tile-count scans
+  // pairs
+  unsigned long long *gkeys;  // [Kcap] (depth bits << 32) | gaussian index
+  unsigned long long *bkeys;  // [Kbcap] (prim << 32) | boundary index
+  int *bl_prim;               // [Kbcap] prim of each sorted boundary entry
+  float4 *bl_rec;             // [Kbcap] boundary record of each sorted entry
+  // forward state for the backward pass
+  float *T_final;             // [P]
+  int *n_contrib;             // [P] tile-list position after the last composited pair
+  // intermediate gradients
+  float *gg;                  // [Fcap][12]: dmu x,y; dK a,b,c; do; dcol r,g,b; pad
+  float4 *bg_grad;            // [Fcap] (db x, db y, dsigma, 0)
+  long long Fcap;
+  int nblk;
+};
+
+enum Counter { kF = 0, kNb = 1, kK = 2, kKb = 3, kQueueFwd = 4, kQueueBwd = 5, kQueueSort = 6 };
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+
+__host__ __device__ inline int ncp_of(int n) { return (n + 1) * (n + 2) / 2; }
+
+__device__ inline int find_view(const int *off, int V, int idx) {
+  int lo = 0, hi = V;  // off[lo] <= idx < off[hi]
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (__ldg(off + mid) <= idx) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ inline float multinom(int n, int i, int j, int k) {
+  // n! / (i! j! k!) for n <= 4, exact in FP32
+  const float f[5] = {1.f, 1.f, 2.f, 6.f, 24.f};
+  return f[n] / (f[i] * f[j] * f[k]);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 lattice vertex with one fixed sequence of IEEE-rounded operations.
+// Coverage and the depth test are integer decisions taken from these values,
+// so every operation is an explicit correctly rounded intrinsic (no
+// contraction): Bernstein weights ((coef u^i) v^j) w^k, fused multiply-add
+// accumulation in control-point order, world->camera rows as
+// fma(r2, z, fma(r1, y, r0 * x)) + t, projection fma(f, X / Z, c), and a
+// snap to the 1/256-pixel grid with round-to-nearest-even.
+// ---------------------------------------------------------------------------
+struct RVert {
+  int X, Y;     // 1/256-pixel fixed point
+  float Z, iz;  // camera depth and its reciprocal
+  bool valid;
+};
+
+__device__ inline RVert raster_vertex(int n, const float *cp, int a, int b, int L, const View &v,
+                                      float near_z) {
+  RVert o;
+  const float fL = (float)L;
+  const float u = __fdiv_rn((float)a, fL);
+  const float vv = __fdiv_rn((float)b, fL);
+  const float w = __fdiv_rn((float)(L - a - b), fL);
+  float pu[kMaxDegree + 1], pv[kMaxDegree + 1], pw[kMaxDegree + 1];
+  pu[0] = pv[0] = pw[0] = 1.0f;
+#pragma unroll
+  for (int m = 1; m <= kMaxDegree; m++) {
+    pu[m] = __fmul_rn(pu[m - 1], u);
+    pv[m] = __fmul_rn(pv[m - 1], vv);
+    pw[m] = __fmul_rn(pw[m - 1], w);
+  }
+  float Sx = 0.f, Sy = 0.f, Sz = 0.f;
+  int idx = 0;
+  for (int i = n; i >= 0; i--)
+    for (int j = n - i; j >= 0; j--) {
+      const int k = n - i - j;
+      const float B = __fmul_rn(__fmul_rn(__fmul_rn(multinom(n, i, j, k), pu[i]), pv[j]), pw[k]);
+      Sx = __fmaf_rn(B, cp[3 * idx + 0], Sx);
+      Sy = __fmaf_rn(B, cp[3 * idx + 1], Sy);
+      Sz = __fmaf_rn(B, cp[3 * idx + 2], Sz);
+      idx++;
+    }
+  float Xc = __fmul_rn(v.R[0], Sx); Xc = __fmaf_rn(v.R[1], Sy, Xc); Xc = __fmaf_rn(v.R[2], Sz, Xc); Xc = __fadd_rn(Xc, v.t[0]);
+  float Yc = __fmul_rn(v.R[3], Sx); Yc = __fmaf_rn(v.R[4], Sy, Yc); Yc = __fmaf_rn(v.R[5], Sz, Yc); Yc = __fadd_rn(Yc, v.t[1]);
+  float Zc = __fmul_rn(v.R[6], Sx); Zc = __fmaf_rn(v.R[7], Sy, Zc); Zc = __fmaf_rn(v.R[8], Sz, Zc); Zc = __fadd_rn(Zc, v.t[2]);
+  o.valid = (Zc >= near_z);
+  o.Z = Zc;
+  o.iz = __fdiv_rn(1.0f, Zc);
+  const float x = __fmaf_rn(v.fx, __fmul_rn(Xc, o.iz), v.cx);
+  const float y = __fmaf_rn(v.fy, __fmul_rn(Yc, o.iz), v.cy);
+  if (!(fabsf(x) <= (float)kGuardPx && fabsf(y) <= (float)kGuardPx)) o.valid = false;
+  if (o.valid) {
+    o.X = __float2int_rn(__fmul_rn(x, 256.0f));
+    o.Y = __float2int_rn(__fmul_rn(y, 256.0f));
+  } else {
+    o.X = o.Y = 0;
+  }
+  return o;
+}
+
+// exact edge function (b - a) x (P - a) on the fixed-point grid
+__device__ inline long long edge_fn(int ax, int ay, int bx, int by, int px, int py) {
+  return (long long)(bx - ax) * (long long)(py - ay) - (long long)(by - ay) * (long long)(px - ax);
+}
+
+// fill rule: a zero edge function counts as inside on edges with dy < 0 or (dy == 0, dx > 0)
+__device__ inline bool owns_zero_edge(int ax, int ay, int bx, int by) {
+  const int dx = bx - ax, dy = by - ay;
+  return (dy < 0) || (dy == 0 && dx > 0);
+}
+
+// sub-triangle s = 2 (a L + b) + down of the level-L lattice
+__device__ inline void subtri_verts(int L, int s, int *va, int *vb) {
+  const int down = s & 1, cell = s >> 1;
+  const int a = cell / L, b = cell - a * L;
+  if (!down) {
+    va[0] = a; vb[0] = b; va[1] = a + 1; vb[1] = b; va[2] = a; vb[2] = b + 1;
+  } else {
+    va[0] = a + 1; vb[0] = b; va[1] = a + 1; vb[1] = b + 1; va[2] = a; vb[2] = b + 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// double-float arithmetic (Dekker 1971 / Knuth TAOCP vol. 2, 4.2.2): a value
+// is hi + lo with |lo| <= ulp(hi) / 2. Used to place Gaussian means and
+// boundary points to ~1e-12 px before storing them relative to their pixel.
+// ---------------------------------------------------------------------------
+struct df {
+  float hi, lo;
+};
+
+__device__ inline df df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ inline df df_fast_two_sum(float a, float b) {  // requires |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ inline df df_two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ inline df df_add(df a, df b) {
+  const df s = df_two_sum(a.hi, b.hi);
+  const df t = df_two_sum(a.lo, b.lo);
+  df r = df_fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return df_fast_two_sum(r.hi, __fadd_rn(r.lo, t.lo));
+}
+__device__ inline df df_add_f(df a, float b) {
+  const df s = df_two_sum(a.hi, b);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+__device__ inline df df_mul_f(df a, float b) {
+  const df p = df_two_prod(a.hi, b);
+  return df_fast_two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
+}
+__device__ inline df df_div(df a, df b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const df r = df_add(a, df_mul_f(b, -q1));
+  const float q2 = __fdiv_rn(r.hi, b.hi);
+  return df_fast_two_sum(q1, q2);
+}
+
+// Surface point S(u, v) of Eq. 1 and its camera-space position, accurate to
+// a few 1e-9 world units: S = p_ref + sum_ijk B_ijk (p_ijk - p_ref) (the
+// weights sum to one), p_ref = first control point; the camera transform of
+// p_ref is taken in double-float.
+struct SurfPoint {
+  df t[3];        // camera-space position
+  float S[3];     // world position (FP32, for derivatives)
+  float B[kMaxCp];
+};
+
+__device__ inline void bernstein_f32(int n, float u, float v, float *B) {
+  const float w = 1.0f - u - v;
+  float pu[kMaxDegree + 1], pv[kMaxDegree + 1], pw[kMaxDegree + 1];
+  pu[0] = pv[0] = pw[0] = 1.0f;
+#pragma unroll
+  for (int m = 1; m <= kMaxDegree; m++) {
+    pu[m] = pu[m - 1] * u;
+    pv[m] = pv[m - 1] * v;
+    pw[m] = pw[m - 1] * w;
+  }
+  int idx = 0;
+  for (int i = n; i >= 0; i--)
+    for (int j = n - i; j >= 0; j--) {
+      const int k = n - i - j;
+      B[idx++] = multinom(n, i, j, k) * pu[i] * pv[j] * pw[k];
+    }
+}
+
+__device__ inline void surface_point(int n, const float *__restrict__ cp, float u, float v,
+                                     const View &vw, SurfPoint &sp) {
+  const int m = ncp_of(n);
+  bernstein_f32(n, u, v, sp.B);
+  const float r0 = __ldg(cp + 0), r1 = __ldg(cp + 1), r2 = __ldg(cp + 2);
+  float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+  for (int a = 1; a < m; a++) {
+    d0 = fmaf(sp.B[a], __ldg(cp + 3 * a + 0) - r0, d0);
+    d1 = fmaf(sp.B[a], __ldg(cp + 3 * a + 1) - r1, d1);
+    d2 = fmaf(sp.B[a], __ldg(cp + 3 * a + 2) - r2, d2);
+  }
+  sp.S[0] = r0 + d0;
+  sp.S[1] = r1 + d1;
+  sp.S[2] = r2 + d2;
+#pragma unroll
+  for (int r = 0; r < 3; r++) {
+    df acc = df_two_prod(vw.R[3 * r + 0], r0);
+    acc = df_add(acc, df_two_prod(vw.R[3 * r + 1], r1));
+    acc = df_add(acc, df_two_prod(vw.R[3 * r + 2], r2));
+    acc = df_add_f(acc, vw.t[r]);
+    const float delta = vw.R[3 * r + 0] * d0 + vw.R[3 * r + 1] * d1 + vw.R[3 * r + 2] * d2;
+    sp.t[r] = df_add_f(acc, delta);
+  }
+}
+
+// projected position of a camera-space point relative to pixel centre (qx, qy)
+__device__ inline float2 project_offset(const df *t, const View &vw, int qx, int qy) {
+  const df xz = df_div(t[0], t[2]);
+  const df yz = df_div(t[1], t[2]);
+  df mx = df_add_f(df_mul_f(xz, vw.fx), vw.cx);
+  df my = df_add_f(df_mul_f(yz, vw.fy), vw.cy);
+  mx = df_add_f(mx, -(float)qx);
+  my = df_add_f(my, -(float)qy);
+  return make_float2(mx.hi + mx.lo, my.hi + my.lo);
+}
+
+// ---------------------------------------------------------------------------
+// host-side launchers (one per kernel family)
+// ---------------------------------------------------------------------------
+// host-side launchers; each returns the number of kernels it enqueued
+int launch_prim_prep(const Params &p, const Scene &s, const Work &w, cudaStream_t st);
+int launch_raster(const Params &p, const Scene &s, const Work &w, cudaStream_t st);
+int launch_resolve(const Params &p, const Scene &s, const Work &w, cudaStream_t st);
+int launch_generate(const Params &p, const Scene &s, const Work &w, cudaStream_t st);
+int launch_binning(const Params &p, const Work &w, cudaStream_t st);
+int launch_composite_fwd(const Params &p, const Work &w, float *image, cudaStream_t st);
+int launch_composite_bwd(const Params &p, const Work &w, const float *dimage, cudaStream_t st);
+int launch_chain(const Params &p, const Scene &s, const Work &w, const Grads &g, cudaStream_t st);
+int launch_l1_grad(const float *img, const float *target, long long n, float scale, float *dimg,
+                   float *loss, cudaStream_t st);
+int launch_exclusive_scan(const int *in, long long *out, int n, long long *aux, cudaStream_t st);
+int launch_bin_sort_only(const Params &p, const Work &w, cudaStream_t st);
+
+}  // namespace bgt

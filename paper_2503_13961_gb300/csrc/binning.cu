@@ -1,0 +1,305 @@
+// Tile binning and the (tile, depth) sort of the Gaussians, and the per-tile
+// boundary-point lists sorted by primitive id (Sec. 3.2, "Rendering
+// Acceleration": precomputed tile range of each boundary point, per-tile
+// lists sorted by ID so that a binary search finds a primitive's points).
+//
+// The sort is a most-significant-digit radix sort of the key (tile, depth,
+// index): the first digit is the whole tile id (a counting sort: per-tile
+// counts from the generation pass, an exclusive scan, one scatter), the
+// remaining 64 bits (FP32 depth bits, Gaussian index) are sorted inside each
+// tile in shared memory. Keys are unique, so the order is fully determined.
+// Boundary keys are (primitive, boundary index).
+#include "bgt_internal.cuh"
+
+namespace bgt {
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+
+// block-wide exclusive scan of one value per thread; returns the block total
+__device__ inline long long block_excl_scan(long long v, long long &total, long long *s_warp) {
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  long long x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[wp] = x;
+  __syncthreads();
+  if (wp == 0) {
+    long long a = lane < nw ? s_warp[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, a, o);
+      if (lane >= o) a += y;
+    }
+    s_warp[lane] = a;
+  }
+  __syncthreads();
+  total = s_warp[nw - 1];
+  const long long res = (wp ? s_warp[wp - 1] : 0) + x - v;
+  __syncthreads();
+  return res;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int *in, int n, long long *aux) {
+  __shared__ long long s_warp[32];
+  const int base = blockIdx.x * kScanChunk;
+  long long sum = 0;
+  for (int k = 0; k < kScanItems; k++) {
+    const int i = base + k * kScanThreads + threadIdx.x;
+    if (i < n) sum += in[i];
+  }
+  long long total;
+  block_excl_scan(sum, total, s_warp);
+  if (threadIdx.x == 0) aux[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(long long *aux, int nb) {
+  __shared__ long long s_warp[32];
+  __shared__ long long s_carry;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nb; base += kScanThreads) {
+    const int i = base + threadIdx.x;
+    const long long v = i < nb ? aux[i] : 0;
+    long long tot;
+    const long long ex = block_excl_scan(v, tot, s_warp);
+    if (i < nb) aux[i] = ex + s_carry;
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry += tot;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const int *in, long long *out, int n,
+                                                            const long long *aux) {
+  __shared__ long long s_warp[32];
+  // each thread owns kScanItems consecutive elements
+  const int base = blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
+  int v[kScanItems];
+  long long sum = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; k++) {
+    v[k] = (base + k < n) ? in[base + k] : 0;
+    sum += v[k];
+  }
+  long long total;
+  long long run = block_excl_scan(sum, total, s_warp) + aux[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; k++) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+  // the thread holding element n - 1 also writes out[n] = grand total
+  if (base < n && base + kScanItems >= n) out[n] = run;
+}
+
+__device__ inline void emit_rect(unsigned long long *keys, int *fill, const long long *start, long long cap,
+                                 int tile_off, int tiles_x, uint2 rect, unsigned long long hi,
+                                 unsigned lo) {
+  const int x0 = rect.x & 0xffff, y0 = rect.x >> 16, x1 = rect.y & 0xffff, y1 = rect.y >> 16;
+  for (int ty = y0; ty <= y1; ty++)
+    for (int tx = x0; tx <= x1; tx++) {
+      const int t = tile_off + ty * tiles_x + tx;
+      const long long pos = start[t] + atomicAdd(fill + t, 1);
+      if (pos >= 0 && pos < cap) keys[pos] = (hi << 32) | (unsigned long long)lo;
+    }
+}
+
+__global__ void k_emit(Params p, Work w) {
+  const int F = w.counters[kF], Nb = w.counters[kNb];
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < F; i += stride) {
+    const uint2 rect = w.g_rect[i];
+    if ((rect.x & 0xffff) > (rect.y & 0xffff)) continue;
+    const View *vw = w.views + w.g_view[i];
+    const unsigned dbits = __float_as_uint(w.gC[i].w);
+    emit_rect(w.gkeys, w.g_tfill, w.g_tstart, p.max_pairs, __ldg(&vw->tile_off), __ldg(&vw->tiles_x),
+              rect, dbits, (unsigned)i);
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Nb; i += stride) {
+    const uint2 rect = w.b_rect[i];
+    if ((rect.x & 0xffff) > (rect.y & 0xffff)) continue;
+    const View *vw = w.views + w.b_view[i];
+    emit_rect(w.bkeys, w.b_tfill, w.b_tstart, p.max_bpairs, __ldg(&vw->tile_off), __ldg(&vw->tiles_x),
+              rect, (unsigned)w.b_prim[i], (unsigned)i);
+  }
+}
+
+__global__ void k_check_capacity(Params p, Work w) {
+  const long long K = w.g_tstart[p.tiles], Kb = w.b_tstart[p.tiles];
+  w.counters[kK] = (int)(K < 0x7fffffffll ? K : 0x7fffffffll);
+  w.counters[kKb] = (int)(Kb < 0x7fffffffll ? Kb : 0x7fffffffll);
+  if (K > p.max_pairs) atomicOr(w.status, kStatusPairOverflow);
+  if (Kb > p.max_bpairs) atomicOr(w.status, kStatusBoundaryOverflow);
+}
+
+// ---------------------------------------------------------------------------
+// per-tile sort
+// ---------------------------------------------------------------------------
+constexpr int kSortThreads = 256;
+constexpr int kSortCap = 4096;  // keys sorted in shared memory (32 KB)
+
+__device__ void bitonic_smem(unsigned long long *s, int n) {
+  int N = 1;
+  while (N < n) N <<= 1;
+  for (int i = n + threadIdx.x; i < N; i += blockDim.x) s[i] = ~0ull;
+  __syncthreads();
+  for (int k = 2; k <= N; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const unsigned long long a = s[i], b = s[ixj];
+          const bool up = (i & k) == 0;
+          if ((a > b) == up) {
+            s[i] = b;
+            s[ixj] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+}
+
+// Stable block-wide LSD radix sort (8-bit digits) of a segment in global
+// memory, for segments larger than the shared-memory capacity. Digits that
+// are equal across the whole segment are skipped.
+__device__ void radix_global(unsigned long long *keys, unsigned long long *tmp, int n, int *s_hist,
+                             int *s_base, int *s_wcnt, unsigned long long *s_red) {
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = kSortThreads / 32;
+  // OR / AND over the segment to find constant digits
+  unsigned long long vor = 0ull, vand = ~0ull;
+  for (int i = threadIdx.x; i < n; i += kSortThreads) {
+    vor |= keys[i];
+    vand &= keys[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    vor |= __shfl_xor_sync(0xffffffffu, vor, o);
+    vand &= __shfl_xor_sync(0xffffffffu, vand, o);
+  }
+  if (lane == 0) { s_red[wp] = vor; s_red[nw + wp] = vand; }
+  __syncthreads();
+  vor = 0ull; vand = ~0ull;
+  for (int i = 0; i < nw; i++) { vor |= s_red[i]; vand &= s_red[nw + i]; }
+  __syncthreads();
+  const unsigned long long varying = vor ^ vand;
+  unsigned long long *src = keys, *dst = tmp;
+  for (int shift = 0; shift < 64; shift += 8) {
+    if (((varying >> shift) & 0xffull) == 0ull) continue;
+    for (int d = threadIdx.x; d < 256; d += kSortThreads) s_hist[d] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += kSortThreads) atomicAdd(&s_hist[(src[i] >> shift) & 0xff], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int run = 0;
+      for (int d = 0; d < 256; d++) { s_base[d] = run; run += s_hist[d]; }
+    }
+    for (int d = threadIdx.x; d < nw * 256; d += kSortThreads) s_wcnt[d] = 0;
+    __syncthreads();
+    for (int chunk = 0; chunk < n; chunk += kSortThreads) {
+      const int i = chunk + threadIdx.x;
+      const bool valid = i < n;
+      const unsigned long long key = valid ? src[i] : 0ull;
+      const int dig = valid ? (int)((key >> shift) & 0xff) : 256 + wp;
+      const unsigned peers = __match_any_sync(0xffffffffu, dig);
+      const int rank = __popc(peers & ((1u << lane) - 1u));
+      if (valid && rank == 0) s_wcnt[wp * 256 + dig] = __popc(peers);
+      __syncthreads();
+      if (valid) {
+        int pos = s_base[dig] + rank;
+        for (int q = 0; q < wp; q++) pos += s_wcnt[q * 256 + dig];
+        dst[pos] = key;
+      }
+      __syncthreads();
+      for (int d = threadIdx.x; d < 256; d += kSortThreads) {
+        int add = 0;
+        for (int q = 0; q < nw; q++) { add += s_wcnt[q * 256 + d]; s_wcnt[q * 256 + d] = 0; }
+        s_base[d] += add;
+      }
+      __syncthreads();
+    }
+    unsigned long long *t = src; src = dst; dst = t;
+  }
+  if (src != keys)
+    for (int i = threadIdx.x; i < n; i += kSortThreads) keys[i] = src[i];
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_tile_sort(Params p, Work w, unsigned long long *gtmp,
+                                                           unsigned long long *btmp) {
+  __shared__ unsigned long long s_keys[kSortCap];
+  __shared__ int s_hist[256], s_base[256];
+  __shared__ int s_wcnt[(kSortThreads / 32) * 256];
+  __shared__ unsigned long long s_red[2 * (kSortThreads / 32)];
+  const int items = 2 * p.tiles;
+  // an overflowed call leaves key slots unwritten: treat its lists as empty
+  const bool g_over = w.g_tstart[p.tiles] > p.max_pairs, b_over = w.b_tstart[p.tiles] > p.max_bpairs;
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const bool bnd = item >= p.tiles;
+    const int tile = bnd ? item - p.tiles : item;
+    if (bnd ? b_over : g_over) continue;
+    const long long *start = bnd ? w.b_tstart : w.g_tstart;
+    const long long cap = bnd ? p.max_bpairs : p.max_pairs;
+    unsigned long long *keys = bnd ? w.bkeys : w.gkeys;
+    unsigned long long *tmp = bnd ? btmp : gtmp;
+    long long s0 = start[tile], s1 = start[tile + 1];
+    s0 = s0 < 0 ? 0 : (s0 > cap ? cap : s0);
+    s1 = s1 < s0 ? s0 : (s1 > cap ? cap : s1);
+    const int n = (int)(s1 - s0);
+    if (n > 1) {
+      if (n <= kSortCap) {
+        for (int i = threadIdx.x; i < n; i += kSortThreads) s_keys[i] = keys[s0 + i];
+        __syncthreads();
+        bitonic_smem(s_keys, n);
+        for (int i = threadIdx.x; i < n; i += kSortThreads) keys[s0 + i] = s_keys[i];
+      } else {
+        radix_global(keys + s0, tmp + s0, n, s_hist, s_base, s_wcnt, s_red);
+      }
+      __syncthreads();
+    }
+    if (bnd) {
+      for (int i = threadIdx.x; i < n; i += kSortThreads) {
+        const unsigned long long k = keys[s0 + i];
+        w.bl_prim[s0 + i] = (int)(k >> 32);
+        w.bl_rec[s0 + i] = w.bR[(unsigned)(k & 0xffffffffu)];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+int launch_exclusive_scan(const int *in, long long *out, int n, long long *aux, cudaStream_t st) {
+  // out[0..n) = exclusive prefix sums of in, out[n] = total
+  if (n <= 0) {
+    cudaMemsetAsync(out, 0, sizeof(long long), st);
+    return 0;
+  }
+  const int nb = (n + kScanChunk - 1) / kScanChunk;
+  k_scan_reduce<<<nb, kScanThreads, 0, st>>>(in, n, aux);
+  k_scan_top<<<1, kScanThreads, 0, st>>>(aux, nb);
+  k_scan_down<<<nb, kScanThreads, 0, st>>>(in, out, n, aux);
+  return 3;
+}
+
+int launch_bin_sort_only(const Params &p, const Work &w, cudaStream_t st) {
+  k_emit<<<4 * 152, 256, 0, st>>>(p, w);
+  int grid = 2 * p.tiles;
+  if (grid > 8 * 152) grid = 8 * 152;
+  if (grid > 0) k_tile_sort<<<grid, kSortThreads, 0, st>>>(p, w, w.gkeys + p.max_pairs, w.bkeys + p.max_bpairs);
+  return grid > 0 ? 2 : 1;
+}
+
+int launch_binning(const Params &p, const Work &w, cudaStream_t st) {
+  int k = launch_exclusive_scan(w.g_tcount, w.g_tstart, p.tiles, w.scan_aux, st);
+  k += launch_exclusive_scan(w.b_tcount, w.b_tstart, p.tiles, w.scan_aux2, st);
+  k_check_capacity<<<1, 1, 0, st>>>(p, w);
+  return k + 1 + launch_bin_sort_only(p, w, st);
+}
+
+}  // namespace bgt

@@ -1,0 +1,225 @@
+// Chain rule from the per-Gaussian and per-boundary-point gradients of the
+// blending pass to the primitive parameters (supplementary "Backward
+// Derivative": dl/dp_ijk = dl/dS_q B_ijk(I_uv(q)); the projection and EWA
+// factors that the paper leaves to 3DGS are derived here).
+//
+// Gaussian of primitive g at S_q, camera point t = W S_q + t_cam:
+//   mean  mu = (fx tx/tz + cx, fy ty/tz + cy)
+//   conic K = Sigma2D^-1, Sigma2D = (J W) Sigma3D (J W)^T + dilation I
+//   dl/dSigma2D = -K (dl/dK) K, dl/d(JW) = 2 dl/dSigma2D (JW) Sigma3D,
+//   dl/dJ = dl/d(JW) W^T, J depends on t; dl/dS_q = W^T dl/dt.
+// Boundary point b = projection of S_b, sigma = k_b fx r_b / z_b.
+// Control-point, colour and opacity gradients of consecutive Gaussians (which
+// mostly share a primitive, being compacted in pixel order) are summed with a
+// warp-segmented scan before one atomic per run.
+#include "bgt_internal.cuh"
+
+namespace bgt {
+
+namespace {
+
+struct Seg {
+  int start;
+  bool tail;
+};
+
+__device__ inline Seg seg_info(int key) {
+  const int lane = threadIdx.x & 31;
+  const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+  const int next = __shfl_down_sync(0xffffffffu, key, 1);
+  const bool head = lane == 0 || prev != key;
+  const unsigned heads = __ballot_sync(0xffffffffu, head);
+  const unsigned upto = (lane == 31) ? 0xffffffffu : ((2u << lane) - 1u);
+  Seg s;
+  s.start = 31 - __clz(heads & upto);
+  s.tail = lane == 31 || next != key;
+  return s;
+}
+
+__device__ inline float seg_sum(float v, const Seg &s) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane - o >= s.start) v += y;
+  }
+  return v;
+}
+
+__device__ inline void camera_point_f32(int n, const float *cp, float u, float v, const View &vw,
+                                        float *B, float *t) {
+  bernstein_f32(n, u, v, B);
+  float S[3] = {0.f, 0.f, 0.f};
+  const int m = ncp_of(n);
+  for (int a = 0; a < m; a++)
+#pragma unroll
+    for (int c = 0; c < 3; c++) S[c] = fmaf(B[a], __ldg(cp + 3 * a + c), S[c]);
+#pragma unroll
+  for (int r = 0; r < 3; r++) t[r] = vw.R[3 * r] * S[0] + vw.R[3 * r + 1] * S[1] + vw.R[3 * r + 2] * S[2] + vw.t[r];
+}
+
+// scatter sum_run B[a] * v[c] into dst[(g * m + a) * 3 + c] (runs of equal g)
+__device__ inline void scatter_cp(float *dst, int g, int m, const float *B, const float *v, const Seg &sg,
+                                  bool active) {
+  for (int a = 0; a < m; a++)
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      const float s = seg_sum(active ? B[a] * v[c] : 0.f, sg);
+      if (sg.tail && active && s != 0.f) atomicAdd(dst + ((size_t)g * m + a) * 3 + c, s);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_chain_gauss(Params p, Scene s, Work w, Grads out) {
+  const int F = w.counters[kF];
+  const int lane = threadIdx.x & 31;
+  const int warps_total = gridDim.x * (blockDim.x >> 5);
+  const int m = p.ncp;
+  for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < F; base += warps_total * 32) {
+    const int i = base + lane;
+    bool active = i < F;
+    int g = -1;
+    float gS[3] = {0.f, 0.f, 0.f}, gcol[3] = {0.f, 0.f, 0.f}, gop = 0.f;
+    float B[kMaxCp];
+    if (active) {
+      const float *gg = w.gg + 12 * (size_t)i;
+      const float4 q0 = reinterpret_cast<const float4 *>(gg)[0];
+      const float4 q1 = reinterpret_cast<const float4 *>(gg)[1];
+      const float4 q2 = reinterpret_cast<const float4 *>(gg)[2];
+      const float gmx = q0.x, gmy = q0.y, gKa = q0.z, gKb = q0.w, gKc = q1.x;
+      gop = q1.y;
+      gcol[0] = q1.z; gcol[1] = q1.w; gcol[2] = q2.x;
+      const float4 A = w.gA[i], Bq = w.gB[i];
+      g = __float_as_int(Bq.w);
+      const View vw = w.views[w.g_view[i]];
+      const float2 uv = w.g_uv[i];
+      float t[3];
+      camera_point_f32(p.n, s.ctrl + (size_t)g * m * 3, uv.x, uv.y, vw, B, t);
+      const bool any = gmx != 0.f || gmy != 0.f || gKa != 0.f || gKb != 0.f || gKc != 0.f;
+      if (any) {
+        const float Ka = A.z, Kb = A.w, Kc = Bq.x;
+        const float tx = t[0], ty = t[1], tz = t[2];
+        const float iz = 1.0f / tz, iz2 = iz * iz;
+        // dl/dSigma2D = -K GK K, GK = [[gKa, gKb/2], [gKb/2, gKc]]
+        const float hb = 0.5f * gKb;
+        const float a00 = Ka * gKa + Kb * hb, a01 = Ka * hb + Kb * gKc;
+        const float a10 = Kb * gKa + Kc * hb, a11 = Kb * hb + Kc * gKc;
+        const float GS00 = -(a00 * Ka + a01 * Kb);
+        const float GS01 = -0.5f * ((a00 * Kb + a01 * Kc) + (a10 * Ka + a11 * Kb));
+        const float GS11 = -(a10 * Kb + a11 * Kc);
+        const float j00 = vw.fx * iz, j02 = -vw.fx * tx * iz2;
+        const float j11 = vw.fy * iz, j12 = -vw.fy * ty * iz2;
+        float T0[3], T1[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+          T0[k] = j00 * vw.R[k] + j02 * vw.R[6 + k];
+          T1[k] = j11 * vw.R[3 + k] + j12 * vw.R[6 + k];
+        }
+        const float *S3 = w.sig3 + 6 * g;
+        const float Sg[9] = {S3[0], S3[1], S3[2], S3[1], S3[3], S3[4], S3[2], S3[4], S3[5]};
+        float TS0[3], TS1[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+          TS0[k] = T0[0] * Sg[k] + T0[1] * Sg[3 + k] + T0[2] * Sg[6 + k];
+          TS1[k] = T1[0] * Sg[k] + T1[1] * Sg[3 + k] + T1[2] * Sg[6 + k];
+        }
+        float GT0[3], GT1[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+          GT0[k] = 2.0f * (GS00 * TS0[k] + GS01 * TS1[k]);
+          GT1[k] = 2.0f * (GS01 * TS0[k] + GS11 * TS1[k]);
+        }
+        // dl/dJ = dl/dT W^T (only the entries J00, J02, J11, J12 vary with t)
+        const float GJ00 = GT0[0] * vw.R[0] + GT0[1] * vw.R[1] + GT0[2] * vw.R[2];
+        const float GJ02 = GT0[0] * vw.R[6] + GT0[1] * vw.R[7] + GT0[2] * vw.R[8];
+        const float GJ11 = GT1[0] * vw.R[3] + GT1[1] * vw.R[4] + GT1[2] * vw.R[5];
+        const float GJ12 = GT1[0] * vw.R[6] + GT1[1] * vw.R[7] + GT1[2] * vw.R[8];
+        float gt0 = GJ02 * (-vw.fx * iz2);
+        float gt1 = GJ12 * (-vw.fy * iz2);
+        float gt2 = GJ00 * (-vw.fx * iz2) + GJ02 * (2.0f * vw.fx * tx * iz2 * iz) +
+                    GJ11 * (-vw.fy * iz2) + GJ12 * (2.0f * vw.fy * ty * iz2 * iz);
+        gt0 += gmx * vw.fx * iz;
+        gt1 += gmy * vw.fy * iz;
+        gt2 += -gmx * vw.fx * tx * iz2 - gmy * vw.fy * ty * iz2;
+#pragma unroll
+        for (int k = 0; k < 3; k++) gS[k] = vw.R[k] * gt0 + vw.R[3 + k] * gt1 + vw.R[6 + k] * gt2;
+      }
+    }
+    const bool nz = active && (gS[0] != 0.f || gS[1] != 0.f || gS[2] != 0.f || gcol[0] != 0.f ||
+                               gcol[1] != 0.f || gcol[2] != 0.f || gop != 0.f);
+    if (!__any_sync(0xffffffffu, nz)) continue;
+    const Seg sg = seg_info(nz ? g : -1 - lane);
+    scatter_cp(out.ctrl, g, m, B, gS, sg, nz);
+    scatter_cp(out.color, g, m, B, gcol, sg, nz);
+    const float so = seg_sum(nz ? gop : 0.f, sg);
+    if (sg.tail && nz && so != 0.f) atomicAdd(out.opacity + g, so);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_chain_bnd(Params p, Scene s, Work w, Grads out) {
+  const int Nb = w.counters[kNb];
+  const int lane = threadIdx.x & 31;
+  const int warps_total = gridDim.x * (blockDim.x >> 5);
+  const int m = p.ncp;
+  for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < Nb; base += warps_total * 32) {
+    const int i = base + lane;
+    bool nz = false;
+    int g = -1;
+    float gS[3] = {0.f, 0.f, 0.f}, grb = 0.f;
+    float B[kMaxCp];
+    if (i < Nb) {
+      const float4 gb = w.bg_grad[i];
+      nz = gb.x != 0.f || gb.y != 0.f || gb.z != 0.f;
+      if (nz) {
+        g = w.b_prim[i];
+        const View vw = w.views[w.b_view[i]];
+        const float2 uv = w.b_uv[i];
+        float t[3];
+        camera_point_f32(p.n, s.ctrl + (size_t)g * m * 3, uv.x, uv.y, vw, B, t);
+        const float tz = w.b_z[i], sigma = w.b_sigma[i];
+        const float iz = 1.0f / tz, iz2 = iz * iz;
+        const float gt0 = gb.x * vw.fx * iz;
+        const float gt1 = gb.y * vw.fy * iz;
+        const float gt2 = -gb.x * vw.fx * t[0] * iz2 - gb.y * vw.fy * t[1] * iz2 - gb.z * sigma * iz;
+        grb = gb.z * p.k_b * vw.fx * iz;
+#pragma unroll
+        for (int k = 0; k < 3; k++) gS[k] = vw.R[k] * gt0 + vw.R[3 + k] * gt1 + vw.R[6 + k] * gt2;
+      }
+    }
+    if (!__any_sync(0xffffffffu, nz)) continue;
+    const Seg sg = seg_info(nz ? g : -1 - lane);
+    scatter_cp(out.ctrl, g, m, B, gS, sg, nz);
+    const float sr = seg_sum(nz ? grb : 0.f, sg);
+    if (sg.tail && nz && sr != 0.f) atomicAdd(out.r_b + g, sr);
+  }
+}
+
+__global__ void k_l1_grad(const float *img, const float *tgt, long long n, float scale, float *d, float *loss) {
+  float acc = 0.f;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float diff = img[i] - tgt[i];
+    d[i] = diff > 0.f ? scale : (diff < 0.f ? -scale : 0.f);
+    acc += fabsf(diff);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, acc * scale);
+}
+
+}  // namespace
+
+int launch_chain(const Params &p, const Scene &s, const Work &w, const Grads &g, cudaStream_t st) {
+  const int grid = 152 * 8;
+  k_chain_gauss<<<grid, 256, 0, st>>>(p, s, w, g);
+  k_chain_bnd<<<grid, 256, 0, st>>>(p, s, w, g);
+  return 2;
+}
+
+int launch_l1_grad(const float *img, const float *target, long long n, float scale, float *dimg, float *loss,
+                   cudaStream_t st) {
+  if (n <= 0) return 0;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_l1_grad<<<(int)blocks, 256, 0, st>>>(img, target, n, scale, dimg, loss);
+  return 1;
+}
+
+}  // namespace bgt

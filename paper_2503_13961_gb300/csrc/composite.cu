@@ -1,0 +1,433 @@
+// Discontinuity-aware alpha blending, forward and backward (Sec. 3.2, Eq. 6-8;
+// supplementary "Backward Derivative").
+//
+// One CTA per screen tile, persistent over a work queue of tiles. The tile's
+// Gaussian list (sorted by depth, index) is staged in shared memory in
+// batches; its boundary list (sorted by primitive, index) is staged once. For
+// pixel q and a Gaussian of primitive g, the coefficient w (Eq. 6) is
+// gamma* = min over g's boundary points b of gamma(|q - b|; sigma_b) (Eq. 7),
+// found by a binary search for g in the tile's list; w = gamma* if I_id(q) = g
+// else 1 - gamma*. alpha = min(alpha_max, o w G) (Eq. 8); pairs with
+// alpha < alpha_min are skipped; blending stops before the pair that would
+// take T below t_stop. Pair evaluation uses explicit IEEE-rounded intrinsics
+// so that the backward pass reproduces the forward decisions exactly.
+//
+// The backward pass re-traverses each pixel's list back to front from its
+// last composited entry, recovering T_i = T_{i+1} / (1 - alpha_i), and
+// accumulates per-Gaussian gradients (mean, conic, opacity, colour; warp-
+// reduced before the atomics) and per-boundary-point gradients (position,
+// radius).
+#include "bgt_internal.cuh"
+
+namespace bgt {
+
+namespace {
+
+constexpr int kBCap = 1536;  // boundary entries staged in shared memory
+
+template <int T>
+struct TileCfg {
+  static constexpr int NT = (T * T < 256) ? T * T : 256;
+  static constexpr int PPT = T * T / NT;
+};
+
+struct WRes {
+  float w, gamma, rho;
+  int best;  // position in the tile's boundary list, -1 if none within range
+};
+
+// Eq. 6-7 for pixel (px, py) and primitive g over the tile's boundary list.
+__device__ __forceinline__ WRes w_search(int g, int px, int py, int idq, const int *bprim,
+                                         const float4 *brec, int bn, int use_boundary) {
+  WRes r;
+  r.best = -1;
+  r.rho = 3.0e38f;
+  r.gamma = 1.0f;
+  if (use_boundary) {
+    int lo = 0, hi = bn;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (bprim[mid] < g) lo = mid + 1; else hi = mid;
+    }
+    float best = 3.0e38f;
+    for (int i = lo; i < bn && bprim[i] == g; i++) {
+      const float4 b = brec[i];
+      const unsigned qxy = __float_as_uint(b.x);
+      const float dx = __fsub_rn((float)(px - (int)(qxy & 0xffffu)), b.y);
+      const float dy = __fsub_rn((float)(py - (int)(qxy >> 16)), b.z);
+      const float r2 = __fmul_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)), __fmul_rn(b.w, b.w));
+      if (r2 < best) {
+        best = r2;
+        r.best = i;
+      }
+    }
+    if (r.best >= 0) {
+      r.rho = __fsqrt_rn(best);
+      if (best < 1.0f) r.gamma = exp2f(__fsub_rn(r.rho, 1.0f));
+    }
+  }
+  r.w = (idq == g) ? r.gamma : __fsub_rn(1.0f, r.gamma);
+  return r;
+}
+
+struct PairGeo {
+  float dx, dy, power;
+};
+
+__device__ __forceinline__ PairGeo pair_geo(int px, int py, const float4 &A, const float4 &B) {
+  PairGeo p;
+  const unsigned qxy = __float_as_uint(B.z);
+  p.dx = __fsub_rn((float)(px - (int)(qxy & 0xffffu)), A.x);
+  p.dy = __fsub_rn((float)(py - (int)(qxy >> 16)), A.y);
+  const float q = __fmaf_rn(A.z, __fmul_rn(p.dx, p.dx), __fmul_rn(B.x, __fmul_rn(p.dy, p.dy)));
+  p.power = __fsub_rn(__fmul_rn(-0.5f, q), __fmul_rn(A.w, __fmul_rn(p.dx, p.dy)));
+  return p;
+}
+
+// two-entry cache of (primitive -> coefficient) per pixel
+struct WCache {
+  int g[2];
+  WRes r[2];
+  int next;
+  __device__ void reset() {
+    g[0] = g[1] = -2;
+    next = 0;
+  }
+};
+
+__device__ __forceinline__ WRes w_cached(WCache &c, int g, int px, int py, int idq,
+                                                const int *bprim, const float4 *brec, int bn,
+                                                int use_boundary) {
+  if (c.g[0] == g) return c.r[0];
+  if (c.g[1] == g) return c.r[1];
+  const int k = c.next;
+  c.next ^= 1;
+  c.g[k] = g;
+  c.r[k] = w_search(g, px, py, idq, bprim, brec, bn, use_boundary);
+  return c.r[k];
+}
+
+struct TileInfo {
+  int view, W, H, pix_off, x0, y0;
+  long long gs, gn, bs, bn;
+};
+
+__device__ inline TileInfo tile_info(const Params &p, const Work &w, int tile, int T) {
+  TileInfo t;
+  t.view = find_view(w.view_tile_off, p.V, tile);
+  const View *vw = w.views + t.view;
+  t.W = __ldg(&vw->W);
+  t.H = __ldg(&vw->H);
+  t.pix_off = __ldg(&vw->pix_off);
+  const int lt = tile - __ldg(&vw->tile_off);
+  const int tx = __ldg(&vw->tiles_x);
+  t.y0 = (lt / tx) * T;
+  t.x0 = (lt - (lt / tx) * tx) * T;
+  // an overflowed call (reported through the status word) leaves key slots
+  // unwritten: its lists are treated as empty so that no slot is read
+  const bool g_over = w.g_tstart[p.tiles] > p.max_pairs, b_over = w.b_tstart[p.tiles] > p.max_bpairs;
+  t.gs = g_over ? 0 : w.g_tstart[tile];
+  t.gn = g_over ? 0 : w.g_tstart[tile + 1] - t.gs;
+  t.bs = b_over ? 0 : w.b_tstart[tile];
+  t.bn = b_over ? 0 : w.b_tstart[tile + 1] - t.bs;
+  return t;
+}
+
+template <int T>
+__global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work w, float *image) {
+  constexpr int NT = TileCfg<T>::NT, PPT = TileCfg<T>::PPT;
+  __shared__ float4 sA[NT], sB[NT], sC[NT];
+  __shared__ int s_bprim[kBCap];
+  __shared__ float4 s_brec[kBCap];
+  __shared__ int s_tile;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_tile = atomicAdd(w.counters + kQueueFwd, 1);
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= p.tiles) break;
+    const TileInfo ti = tile_info(p, w, tile, T);
+    const bool bsm = ti.bn <= kBCap;
+    if (bsm) {
+      for (int i = threadIdx.x; i < ti.bn; i += NT) {
+        s_bprim[i] = w.bl_prim[ti.bs + i];
+        s_brec[i] = w.bl_rec[ti.bs + i];
+      }
+    }
+    const int *bprim = bsm ? s_bprim : w.bl_prim + ti.bs;
+    const float4 *brec = bsm ? s_brec : w.bl_rec + ti.bs;
+    const int bn = (int)ti.bn;
+
+    float C[PPT][3], Tr[PPT];
+    int last[PPT], idq[PPT], px[PPT], py[PPT];
+    bool done[PPT];
+    WCache cache[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+      const int li = threadIdx.x + k * NT;
+      px[k] = ti.x0 + li % T;
+      py[k] = ti.y0 + li / T;
+      const bool inside = px[k] < ti.W && py[k] < ti.H;
+      done[k] = !inside;
+      idq[k] = inside ? w.pid[ti.pix_off + py[k] * ti.W + px[k]] : -1;
+      C[k][0] = C[k][1] = C[k][2] = 0.f;
+      Tr[k] = 1.0f;
+      last[k] = 0;
+      cache[k].reset();
+    }
+    const int gn = (int)ti.gn;
+    for (int b0 = 0; b0 < gn; b0 += NT) {
+      int alldone = 1;
+#pragma unroll
+      for (int k = 0; k < PPT; k++) alldone &= done[k] ? 1 : 0;
+      if (__syncthreads_and(alldone)) break;
+      const int i = b0 + threadIdx.x;
+      if (i < gn) {
+        const unsigned gi = (unsigned)(w.gkeys[ti.gs + i] & 0xffffffffull);
+        sA[threadIdx.x] = w.gA[gi];
+        sB[threadIdx.x] = w.gB[gi];
+        sC[threadIdx.x] = w.gC[gi];
+      }
+      __syncthreads();
+      const int nb = min(NT, gn - b0);
+#pragma unroll
+      for (int k = 0; k < PPT; k++) {
+        if (done[k]) continue;
+        for (int j = 0; j < nb; j++) {
+          const float4 A = sA[j], B = sB[j];
+          const PairGeo pg = pair_geo(px[k], py[k], A, B);
+          const float G = __expf(pg.power);
+          const float og = __fmul_rn(B.y, G);
+          if (og < p.alpha_min) continue;  // w <= 1: alpha < alpha_min
+          const int g = __float_as_int(B.w);
+          const WRes wr = w_cached(cache[k], g, px[k], py[k], idq[k], bprim, brec, bn, p.use_boundary);
+          const float alpha = fminf(p.alpha_max, __fmul_rn(og, wr.w));
+          if (alpha < p.alpha_min) continue;
+          const float testT = __fmul_rn(Tr[k], __fsub_rn(1.0f, alpha));
+          if (testT < p.t_stop) {
+            done[k] = true;
+            break;
+          }
+          const float4 Cc = sC[j];
+          const float ta = __fmul_rn(Tr[k], alpha);
+          C[k][0] = __fmaf_rn(ta, Cc.x, C[k][0]);
+          C[k][1] = __fmaf_rn(ta, Cc.y, C[k][1]);
+          C[k][2] = __fmaf_rn(ta, Cc.z, C[k][2]);
+          Tr[k] = testT;
+          last[k] = b0 + j + 1;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+      if (px[k] < ti.W && py[k] < ti.H) {
+        const int pix = ti.pix_off + py[k] * ti.W + px[k];
+        image[3 * (size_t)pix + 0] = __fmaf_rn(Tr[k], p.bg[0], C[k][0]);
+        image[3 * (size_t)pix + 1] = __fmaf_rn(Tr[k], p.bg[1], C[k][1]);
+        image[3 * (size_t)pix + 2] = __fmaf_rn(Tr[k], p.bg[2], C[k][2]);
+        w.T_final[pix] = Tr[k];
+        w.n_contrib[pix] = last[k];
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int T>
+__global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work w, const float *dimage) {
+  constexpr int NT = TileCfg<T>::NT, PPT = TileCfg<T>::PPT;
+  __shared__ float4 sA[NT], sB[NT], sC[NT];
+  __shared__ int sG[NT];
+  __shared__ int s_bprim[kBCap];
+  __shared__ float4 s_brec[kBCap];
+  __shared__ int s_tile, s_maxlast;
+  const float LN2 = 0.69314718055994531f;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_tile = atomicAdd(w.counters + kQueueBwd, 1);
+      s_maxlast = 0;
+    }
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= p.tiles) break;
+    const TileInfo ti = tile_info(p, w, tile, T);
+    const bool bsm = ti.bn <= kBCap;
+    if (bsm) {
+      for (int i = threadIdx.x; i < ti.bn; i += NT) {
+        s_bprim[i] = w.bl_prim[ti.bs + i];
+        s_brec[i] = w.bl_rec[ti.bs + i];
+      }
+    }
+    const int *bprim = bsm ? s_bprim : w.bl_prim + ti.bs;
+    const float4 *brec = bsm ? s_brec : w.bl_rec + ti.bs;
+    const unsigned long long *bkeys = w.bkeys + ti.bs;
+    const int bn = (int)ti.bn;
+
+    float Tr[PPT], S[PPT][3], dC[PPT][3];
+    int last[PPT], idq[PPT], px[PPT], py[PPT];
+    WCache cache[PPT];
+    int mylast = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+      const int li = threadIdx.x + k * NT;
+      px[k] = ti.x0 + li % T;
+      py[k] = ti.y0 + li / T;
+      last[k] = 0;
+      idq[k] = -1;
+      Tr[k] = 1.f;
+      cache[k].reset();
+      S[k][0] = S[k][1] = S[k][2] = 0.f;
+      dC[k][0] = dC[k][1] = dC[k][2] = 0.f;
+      if (px[k] < ti.W && py[k] < ti.H) {
+        const int pix = ti.pix_off + py[k] * ti.W + px[k];
+        idq[k] = w.pid[pix];
+        last[k] = w.n_contrib[pix];
+        Tr[k] = w.T_final[pix];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          dC[k][c] = dimage[3 * (size_t)pix + c];
+          S[k][c] = Tr[k] * p.bg[c];
+        }
+      }
+      mylast = max(mylast, last[k]);
+    }
+    atomicMax(&s_maxlast, mylast);
+    __syncthreads();
+    const int maxlast = s_maxlast;
+    for (int b1 = maxlast; b1 > 0; b1 -= NT) {
+      const int b0 = max(0, b1 - NT);
+      const int i = b0 + threadIdx.x;
+      __syncthreads();
+      if (i < b1) {
+        const unsigned gi = (unsigned)(w.gkeys[ti.gs + i] & 0xffffffffull);
+        sG[threadIdx.x] = (int)gi;
+        sA[threadIdx.x] = w.gA[gi];
+        sB[threadIdx.x] = w.gB[gi];
+        sC[threadIdx.x] = w.gC[gi];
+      }
+      __syncthreads();
+      for (int j = b1 - 1; j >= b0; j--) {
+        const int sj = j - b0;
+        const float4 A = sA[sj], B = sB[sj], Cc = sC[sj];
+        const int g = __float_as_int(B.w);
+        float acc[9];
+#pragma unroll
+        for (int q = 0; q < 9; q++) acc[q] = 0.f;
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < PPT; k++) {
+          if (j >= last[k]) continue;
+          const PairGeo pg = pair_geo(px[k], py[k], A, B);
+          const float G = __expf(pg.power);
+          const float og = __fmul_rn(B.y, G);
+          if (og < p.alpha_min) continue;
+          const WRes wr = w_cached(cache[k], g, px[k], py[k], idq[k], bprim, brec, bn, p.use_boundary);
+          const float raw = __fmul_rn(og, wr.w);
+          const float alpha = fminf(p.alpha_max, raw);
+          if (alpha < p.alpha_min) continue;
+          any = true;
+          const float oma = 1.0f - alpha;
+          Tr[k] = Tr[k] / oma;  // T_i
+          const float ta = Tr[k] * alpha;
+          float dl_da = 0.f;
+          const float col[3] = {Cc.x, Cc.y, Cc.z};
+#pragma unroll
+          for (int c = 0; c < 3; c++) {
+            acc[6 + c] += ta * dC[k][c];
+            dl_da += dC[k][c] * (Tr[k] * col[c] - S[k][c] / oma);
+            S[k][c] += ta * col[c];
+          }
+          if (raw >= p.alpha_max) continue;  // clamped: alpha is constant
+          acc[5] += dl_da * wr.w * G;
+          const float dl_dw = dl_da * B.y * G;
+          const float dl_dpow = dl_da * og * wr.w;
+          const float dx = pg.dx, dy = pg.dy;  // q - mu
+          acc[2] += dl_dpow * (-0.5f * dx * dx);
+          acc[3] += dl_dpow * (-dx * dy);
+          acc[4] += dl_dpow * (-0.5f * dy * dy);
+          acc[0] += dl_dpow * (A.z * dx + A.w * dy);
+          acc[1] += dl_dpow * (A.w * dx + B.x * dy);
+          if (wr.best >= 0 && wr.rho < 1.0f) {
+            const float4 b = brec[wr.best];
+            const unsigned qxy = __float_as_uint(b.x);
+            const float bx = (float)(px[k] - (int)(qxy & 0xffffu)) - b.y;
+            const float by = (float)(py[k] - (int)(qxy >> 16)) - b.z;
+            const float d = sqrtf(bx * bx + by * by);
+            if (d > 0.f) {
+              const float sgn = (idq[k] == g) ? 1.0f : -1.0f;
+              const float dl_drho = sgn * dl_dw * LN2 * wr.gamma;
+              const float isig = b.w;
+              const unsigned bidx = (unsigned)(bkeys[wr.best] & 0xffffffffull);
+              float *gb = reinterpret_cast<float *>(w.bg_grad + bidx);
+              atomicAdd(gb + 0, dl_drho * (-bx / d) * isig);
+              atomicAdd(gb + 1, dl_drho * (-by / d) * isig);
+              atomicAdd(gb + 2, dl_drho * (-wr.rho) * isig);
+            }
+          }
+        }
+        const unsigned ballot = __ballot_sync(0xffffffffu, any);
+        if (ballot) {
+#pragma unroll
+          for (int q = 0; q < 9; q++) acc[q] = warp_sum(acc[q]);
+          if ((threadIdx.x & 31) == 0) {
+            float *gg = w.gg + 12 * (size_t)sG[sj];
+#pragma unroll
+            for (int q = 0; q < 9; q++)
+              if (acc[q] != 0.f) atomicAdd(gg + q, acc[q]);
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int T>
+int launch_fwd_t(const Params &p, const Work &w, float *image, cudaStream_t st, int sms) {
+  int grid = p.tiles < sms * 8 ? p.tiles : sms * 8;
+  if (grid > 0) k_composite_fwd<T><<<grid, TileCfg<T>::NT, 0, st>>>(p, w, image);
+  return grid > 0 ? 1 : 0;
+}
+
+template <int T>
+int launch_bwd_t(const Params &p, const Work &w, const float *dimage, cudaStream_t st, int sms) {
+  int grid = p.tiles < sms * 8 ? p.tiles : sms * 8;
+  if (grid > 0) k_composite_bwd<T><<<grid, TileCfg<T>::NT, 0, st>>>(p, w, dimage);
+  return grid > 0 ? 1 : 0;
+}
+
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  return sms;
+}
+
+}  // namespace
+
+int launch_composite_fwd(const Params &p, const Work &w, float *image, cudaStream_t st) {
+  cudaMemsetAsync(w.counters + kQueueFwd, 0, sizeof(int), st);
+  const int sms = num_sms();
+  if (p.tile == 8) return launch_fwd_t<8>(p, w, image, st, sms);
+  if (p.tile == 32) return launch_fwd_t<32>(p, w, image, st, sms);
+  return launch_fwd_t<16>(p, w, image, st, sms);
+}
+
+int launch_composite_bwd(const Params &p, const Work &w, const float *dimage, cudaStream_t st) {
+  cudaMemsetAsync(w.counters + kQueueBwd, 0, sizeof(int), st);
+  const int sms = num_sms();
+  if (p.tile == 8) return launch_bwd_t<8>(p, w, dimage, st, sms);
+  if (p.tile == 32) return launch_bwd_t<32>(p, w, dimage, st, sms);
+  return launch_bwd_t<16>(p, w, dimage, st, sms);
+}
+
+}  // namespace bgt

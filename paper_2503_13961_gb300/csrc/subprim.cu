@@ -1,0 +1,301 @@
+// Sub-primitive generation (Sec. 3.2, "Sub-Primitive Generation") and the
+// boundary points of discontinuity-aware blending (same section, first
+// paragraph of "Discontinuity-Aware Alpha Blending").
+//
+// For every foreground pixel q (I_id(q) = g >= 0) one Gaussian is placed at
+// S_q = S(I_uv(q)) of primitive g (Eq. 3) with colour c_q (Eq. 4), the
+// primitive's rotation / scale (Eq. 5 at attribute-map resolution 1) and the
+// primitive's opacity; it is projected with the EWA approximation (J W
+// Sigma3D W^T J^T + dilation) as in 3DGS. Pixels of B (a 4-neighbour with a
+// different id) also yield a boundary point b = projection of the same S_q
+// with radius sigma = k_b fx r_b / z.
+//
+// Gaussians and boundary points are compacted in global pixel order with a
+// two-pass block scan (count, scan of block counts, generate), so indices do
+// not depend on scheduling. Each record counts its screen tiles into
+// per-tile counters for the binning pass.
+#include "bgt_internal.cuh"
+
+namespace bgt {
+
+namespace {
+
+constexpr int kGenThreads = 256;
+constexpr int kGenRounds = 4;  // pixels per thread; block covers 1024 pixels
+constexpr int kGenPixels = kGenThreads * kGenRounds;
+
+__global__ void k_prim_prep(Params p, Scene s, Work w) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= p.M) return;
+  const float q0 = s.quat[4 * g], q1 = s.quat[4 * g + 1], q2 = s.quat[4 * g + 2], q3 = s.quat[4 * g + 3];
+  const float nq = rsqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+  const float r = q0 * nq, x = q1 * nq, y = q2 * nq, z = q3 * nq;
+  const float R[9] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - r * z), 2.f * (x * z + r * y),
+                      2.f * (x * y + r * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - r * x),
+                      2.f * (x * z - r * y), 2.f * (y * z + r * x), 1.f - 2.f * (x * x + y * y)};
+  const float sc[3] = {expf(s.log_scale[3 * g]), expf(s.log_scale[3 * g + 1]), expf(s.log_scale[3 * g + 2])};
+  float Mx[9];
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) Mx[3 * i + j] = R[3 * i + j] * sc[j];
+  float S[6];
+  int k = 0;
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int j = i; j < 3; j++) S[k++] = Mx[3 * i] * Mx[3 * j] + Mx[3 * i + 1] * Mx[3 * j + 1] + Mx[3 * i + 2] * Mx[3 * j + 2];
+#pragma unroll
+  for (int i = 0; i < 6; i++) w.sig3[6 * g + i] = S[i];
+}
+
+// foreground / boundary flags of global pixel `pix`
+__device__ inline void pixel_flags(const Params &p, const Work &w, int pix, bool &fg, bool &bnd,
+                                   int &view) {
+  fg = false;
+  bnd = false;
+  view = 0;
+  if (pix >= p.P) return;
+  const int id = w.pid[pix];
+  if (id < 0) return;
+  fg = true;
+  view = find_view(w.view_pix_off, p.V, pix);
+  const int W = __ldg(&w.views[view].W), H = __ldg(&w.views[view].H);
+  const int local = pix - __ldg(&w.views[view].pix_off);
+  const int y = local / W, x = local - y * W;
+  bnd = (x > 0 && w.pid[pix - 1] != id) || (x < W - 1 && w.pid[pix + 1] != id) ||
+        (y > 0 && w.pid[pix - W] != id) || (y < H - 1 && w.pid[pix + W] != id);
+}
+
+__global__ void __launch_bounds__(kGenThreads) k_count(Params p, Work w) {
+  __shared__ int s_cnt[2][kGenThreads / 32];
+  const int base = blockIdx.x * kGenPixels;
+  int cf = 0, cb = 0;
+  for (int r = 0; r < kGenRounds; r++) {
+    bool fg, bnd;
+    int view;
+    pixel_flags(p, w, base + r * kGenThreads + threadIdx.x, fg, bnd, view);
+    cf += fg;
+    cb += bnd;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    cf += __shfl_xor_sync(0xffffffffu, cf, o);
+    cb += __shfl_xor_sync(0xffffffffu, cb, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_cnt[0][threadIdx.x >> 5] = cf;
+    s_cnt[1][threadIdx.x >> 5] = cb;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int a = 0, b = 0;
+    for (int i = 0; i < kGenThreads / 32; i++) {
+      a += s_cnt[0][i];
+      b += s_cnt[1][i];
+    }
+    w.blk_cnt[blockIdx.x] = a;
+    w.blk_cnt[w.nblk + blockIdx.x] = b;
+  }
+}
+
+// exclusive scan of the two block-count arrays in one block; totals -> F, Nb
+__global__ void __launch_bounds__(1024) k_scan_blocks(Work w, int nblk) {
+  __shared__ int s_w[2][32];
+  __shared__ int s_carry[2];
+  if (threadIdx.x < 2) s_carry[threadIdx.x] = 0;
+  __syncthreads();
+  for (int base = 0; base < nblk; base += 1024) {
+    const int i = base + threadIdx.x;
+    int v0 = i < nblk ? w.blk_cnt[i] : 0;
+    int v1 = i < nblk ? w.blk_cnt[w.nblk + i] : 0;
+    int x0 = v0, x1 = v1;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y0 = __shfl_up_sync(0xffffffffu, x0, o);
+      const int y1 = __shfl_up_sync(0xffffffffu, x1, o);
+      if (lane >= o) { x0 += y0; x1 += y1; }
+    }
+    if (lane == 31) { s_w[0][wp] = x0; s_w[1][wp] = x1; }
+    __syncthreads();
+    if (wp == 0) {
+      int a = s_w[0][lane], b = s_w[1][lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int ya = __shfl_up_sync(0xffffffffu, a, o);
+        const int yb = __shfl_up_sync(0xffffffffu, b, o);
+        if (lane >= o) { a += ya; b += yb; }
+      }
+      s_w[0][lane] = a;
+      s_w[1][lane] = b;
+    }
+    __syncthreads();
+    const int pre0 = (wp ? s_w[0][wp - 1] : 0) + x0 - v0 + s_carry[0];
+    const int pre1 = (wp ? s_w[1][wp - 1] : 0) + x1 - v1 + s_carry[1];
+    if (i < nblk) {
+      w.blk_cnt[i] = pre0;
+      w.blk_cnt[w.nblk + i] = pre1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_carry[0] += s_w[0][31];
+      s_carry[1] += s_w[1][31];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    w.counters[kF] = s_carry[0];
+    w.counters[kNb] = s_carry[1];
+  }
+}
+
+__device__ inline void count_tiles(int *cnt, int tile_off, int tiles_x, uint2 rect) {
+  const int x0 = rect.x & 0xffff, y0 = rect.x >> 16, x1 = rect.y & 0xffff, y1 = rect.y >> 16;
+  for (int ty = y0; ty <= y1; ty++)
+    for (int tx = x0; tx <= x1; tx++) atomicAdd(cnt + tile_off + ty * tiles_x + tx, 1);
+}
+
+// tile rect of the pixel box [cx - rx, cx + rx] x [cy - ry, cy + ry]; empty -> x0 > x1
+__device__ inline uint2 tile_rect(float cx, float cy, float rx, float ry, const View &vw, int t) {
+  int x0 = (int)ceilf(cx - rx), x1 = (int)floorf(cx + rx);
+  int y0 = (int)ceilf(cy - ry), y1 = (int)floorf(cy + ry);
+  x0 = max(x0, 0); y0 = max(y0, 0);
+  x1 = min(x1, vw.W - 1); y1 = min(y1, vw.H - 1);
+  if (x0 > x1 || y0 > y1) return make_uint2(1u, 0u);  // x0 = 1 > x1 = 0: empty
+  x0 /= t; x1 /= t; y0 /= t; y1 /= t;
+  return make_uint2((unsigned)x0 | ((unsigned)y0 << 16), (unsigned)x1 | ((unsigned)y1 << 16));
+}
+
+__global__ void __launch_bounds__(kGenThreads) k_generate(Params p, Scene s, Work w) {
+  __shared__ int s_wf[kGenThreads / 32], s_wb[kGenThreads / 32];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  int base_f = w.blk_cnt[blockIdx.x];
+  int base_b = w.blk_cnt[w.nblk + blockIdx.x];
+  const int base = blockIdx.x * kGenPixels;
+  for (int r = 0; r < kGenRounds; r++) {
+    const int pix = base + r * kGenThreads + threadIdx.x;
+    bool fg, bnd;
+    int view;
+    pixel_flags(p, w, pix, fg, bnd, view);
+    const unsigned mf = __ballot_sync(0xffffffffu, fg), mb = __ballot_sync(0xffffffffu, bnd);
+    const unsigned lt = (1u << lane) - 1u;
+    if (lane == 0) { s_wf[wp] = __popc(mf); s_wb[wp] = __popc(mb); }
+    __syncthreads();
+    int off_f = base_f, off_b = base_b, tot_f = 0, tot_b = 0;
+    for (int i = 0; i < kGenThreads / 32; i++) {
+      if (i < wp) { off_f += s_wf[i]; off_b += s_wb[i]; }
+      tot_f += s_wf[i];
+      tot_b += s_wb[i];
+    }
+    __syncthreads();
+    base_f += tot_f;
+    base_b += tot_b;
+    if (pix < p.P) w.pix_gidx[pix] = fg ? off_f + __popc(mf & lt) : -1;
+    if (!fg) continue;
+    const int gi = off_f + __popc(mf & lt);
+    const int bi = off_b + __popc(mb & lt);
+    const View vw = w.views[view];
+    const int prim = w.pid[pix];
+    const float2 uv = w.puv[pix];
+    const int local = pix - vw.pix_off;
+    const int qy = local / vw.W, qx = local - qy * vw.W;
+    const float *cp = s.ctrl + (size_t)prim * p.ncp * 3;
+    SurfPoint sp;
+    surface_point(p.n, cp, uv.x, uv.y, vw, sp);
+    const float2 off = project_offset(sp.t, vw, qx, qy);
+    const float tx = sp.t[0].hi + sp.t[0].lo, ty = sp.t[1].hi + sp.t[1].lo, tz = sp.t[2].hi + sp.t[2].lo;
+    // EWA: T = J W, Sigma2D = T Sigma3D T^T + dilation I
+    const float iz = 1.0f / tz;
+    const float j00 = vw.fx * iz, j02 = -vw.fx * tx * iz * iz;
+    const float j11 = vw.fy * iz, j12 = -vw.fy * ty * iz * iz;
+    float T0[3], T1[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      T0[k] = j00 * vw.R[k] + j02 * vw.R[6 + k];
+      T1[k] = j11 * vw.R[3 + k] + j12 * vw.R[6 + k];
+    }
+    const float *S3 = w.sig3 + 6 * prim;
+    const float Sxx = S3[0], Sxy = S3[1], Sxz = S3[2], Syy = S3[3], Syz = S3[4], Szz = S3[5];
+    const float a0 = T0[0] * Sxx + T0[1] * Sxy + T0[2] * Sxz;
+    const float a1 = T0[0] * Sxy + T0[1] * Syy + T0[2] * Syz;
+    const float a2 = T0[0] * Sxz + T0[1] * Syz + T0[2] * Szz;
+    const float b0 = T1[0] * Sxx + T1[1] * Sxy + T1[2] * Sxz;
+    const float b1 = T1[0] * Sxy + T1[1] * Syy + T1[2] * Syz;
+    const float b2 = T1[0] * Sxz + T1[1] * Syz + T1[2] * Szz;
+    const float cA = a0 * T0[0] + a1 * T0[1] + a2 * T0[2] + p.dilation;
+    const float cB = a0 * T1[0] + a1 * T1[1] + a2 * T1[2];
+    const float cC = b0 * T1[0] + b1 * T1[1] + b2 * T1[2] + p.dilation;
+    const float det = cA * cC - cB * cB;
+    const float idet = 1.0f / det;
+    const float Ka = cC * idet, Kb = -cB * idet, Kc = cA * idet;
+    float col[3] = {0.f, 0.f, 0.f};
+    const float *cc = s.color + (size_t)prim * p.ncp * 3;
+    for (int a = 0; a < p.ncp; a++) {
+      col[0] = fmaf(sp.B[a], __ldg(cc + 3 * a + 0), col[0]);
+      col[1] = fmaf(sp.B[a], __ldg(cc + 3 * a + 1), col[1]);
+      col[2] = fmaf(sp.B[a], __ldg(cc + 3 * a + 2), col[2]);
+    }
+    const float o = __ldg(s.opacity + prim);
+    const bool finite = isfinite(off.x) && isfinite(off.y) && isfinite(Ka) && isfinite(Kb) &&
+                        isfinite(Kc) && det > 0.f && tz > 0.f;
+    if (!finite) atomicOr(w.status, kStatusNonFinite);
+    uint2 rect = make_uint2(1u, 0u);
+    if (finite && o > p.alpha_min) {
+      // support {o G >= alpha_min} lies in the box |dx| <= sqrt(lvl Sigma_xx),
+      // |dy| <= sqrt(lvl Sigma_yy), lvl = 2 ln(o / alpha_min); widened slightly
+      const float lvl = 2.0f * (logf(o) - p.log_alpha_min);
+      const float rx = sqrtf(lvl * cA) * 1.0001f + 1e-3f;
+      const float ry = sqrtf(lvl * cC) * 1.0001f + 1e-3f;
+      rect = tile_rect((float)qx + off.x, (float)qy + off.y, rx, ry, vw, p.tile);
+      if ((rect.x & 0xffff) <= (rect.y & 0xffff)) count_tiles(w.g_tcount, vw.tile_off, vw.tiles_x, rect);
+    }
+    const unsigned qxy = (unsigned)qx | ((unsigned)qy << 16);
+    w.gA[gi] = make_float4(off.x, off.y, Ka, Kb);
+    w.gB[gi] = make_float4(Kc, o, __uint_as_float(qxy), __int_as_float(prim));
+    w.gC[gi] = make_float4(col[0], col[1], col[2], tz);
+    w.g_pix[gi] = pix;
+    w.g_view[gi] = view;
+    w.g_uv[gi] = uv;
+    w.g_rect[gi] = rect;
+    float4 *ggz = reinterpret_cast<float4 *>(w.gg + 12 * (size_t)gi);
+    ggz[0] = ggz[1] = ggz[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!bnd) continue;
+    // boundary point: the same surface point, radius sigma = k_b fx r_b / z
+    const float sigma = p.k_b * vw.fx * __ldg(s.r_b + prim) / tz;
+    uint2 brect = make_uint2(1u, 0u);
+    if (finite && sigma > 0.f && isfinite(sigma)) {
+      const float rr = sigma * 1.0001f + 1e-3f;
+      brect = tile_rect((float)qx + off.x, (float)qy + off.y, rr, rr, vw, p.tile);
+      if ((brect.x & 0xffff) <= (brect.y & 0xffff)) count_tiles(w.b_tcount, vw.tile_off, vw.tiles_x, brect);
+    }
+    w.bR[bi] = make_float4(__uint_as_float(qxy), off.x, off.y, 1.0f / sigma);
+    w.b_pix[bi] = pix;
+    w.b_prim[bi] = prim;
+    w.b_view[bi] = view;
+    w.b_uv[bi] = uv;
+    w.b_sigma[bi] = sigma;
+    w.b_z[bi] = tz;
+    w.b_rect[bi] = brect;
+    w.bg_grad[bi] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+}  // namespace
+
+int launch_prim_prep(const Params &p, const Scene &s, const Work &w, cudaStream_t st) {
+  if (p.M == 0) return 0;
+  k_prim_prep<<<(p.M + 127) / 128, 128, 0, st>>>(p, s, w);
+  return 1;
+}
+
+int launch_generate(const Params &p, const Scene &s, const Work &w, cudaStream_t st) {
+  const int nblk = (p.P + kGenPixels - 1) / kGenPixels;
+  if (nblk == 0) {
+    cudaMemsetAsync(w.counters, 0, 2 * sizeof(int), st);
+    return 0;
+  }
+  k_count<<<nblk, kGenThreads, 0, st>>>(p, w);
+  k_scan_blocks<<<1, 1024, 0, st>>>(w, nblk);
+  k_generate<<<nblk, kGenThreads, 0, st>>>(p, s, w);
+  return 3;
+}
+
+}  // namespace bgt

@@ -1,0 +1,252 @@
+"""PyTorch front end of the BG-Triangle CUDA rasterizer.
+
+`Renderer` owns one library handle (workspace sized at construction) and
+marshals torch CUDA tensors into the C ABI of include/bgt.h; `render()`
+wraps forward + backward in a torch.autograd.Function. PyTorch only provides
+device memory and the stream: every stage runs in the library's kernels.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _abi
+
+SCENE_KEYS = ("ctrl", "color", "opacity", "r_b", "log_scale", "quat")
+GRAD_KEYS = ("ctrl", "color", "opacity", "r_b")
+
+STAGE_ID = {"id": 0, "uv": 1, "gauss": 2, "bnd": 3, "g_ranges": 4, "g_keys": 5, "b_ranges": 6,
+            "b_keys": 7, "T": 8, "n": 9, "ggrad": 10, "bgrad": 11}
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def scene_to_device(scene, device="cuda"):
+    """Numpy scene dict (see scenes.py) -> dict of contiguous float32 CUDA tensors."""
+    out = {k: torch.as_tensor(np.ascontiguousarray(scene[k]), dtype=torch.float32, device=device)
+           for k in SCENE_KEYS}
+    out["degree"] = int(scene["degree"])
+    out["bg"] = [float(x) for x in np.asarray(scene["bg"]).ravel()]
+    return out
+
+
+def view_pixels(cams):
+    return int(sum(int(c["width"]) * int(c["height"]) for c in cams))
+
+
+class Renderer:
+    """One handle of the BG-Triangle library on the current CUDA device.
+
+    Capacities: max_prims, max_views, max_pixels (sum of W*H of one call),
+    max_pairs / max_boundary_pairs ((Gaussian, tile) and (boundary point,
+    tile) pairs; default 8 per pixel). Options: tess_level L, tile_size
+    (8/16/32), use_boundary (False = the paper's "w/o B" ablation), graph
+    (capture forward / backward in CUDA graphs) and the blending cutoffs.
+    """
+
+    def __init__(self, degree=2, max_prims=100_000, max_views=64, max_pixels=1 << 20, max_pairs=None,
+                 max_boundary_pairs=None, tess_level=8, tile_size=16, use_boundary=True, graph=False,
+                 k_b=3.0, alpha_min=1.0 / 255.0, alpha_max=0.99, t_stop=1e-4, dilation=0.3, near_z=0.2):
+        self.lib = _abi.load()
+        cfg = _abi.Config()
+        _abi.check(self.lib.bgt_default_config(ctypes.byref(cfg)))
+        cfg.degree = degree
+        cfg.max_prims = max_prims
+        cfg.max_views = max_views
+        cfg.max_pixels = max_pixels
+        cfg.max_pairs = max_pairs if max_pairs is not None else 8 * max_pixels
+        cfg.max_boundary_pairs = max_boundary_pairs if max_boundary_pairs is not None else 8 * max_pixels
+        cfg.tess_level = tess_level
+        cfg.tile_size = tile_size
+        cfg.k_b, cfg.alpha_min, cfg.alpha_max = k_b, alpha_min, alpha_max
+        cfg.t_stop, cfg.dilation, cfg.near_z = t_stop, dilation, near_z
+        cfg.flags = (0 if use_boundary else _abi.FLAG_NO_BOUNDARY) | (_abi.FLAG_GRAPH if graph else 0)
+        self.cfg = cfg
+        h = ctypes.c_void_p()
+        _abi.check(self.lib.bgt_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.h = h
+        self._last_pixels = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bgt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- marshalling -----------------------------------------------------
+    def _scene(self, sc):
+        s = _abi.Scene()
+        for k in SCENE_KEYS:
+            t = sc[k]
+            assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous(), k
+            setattr(s, k, t.data_ptr())
+        s.num_prims = int(sc["ctrl"].shape[0])
+        s.bg[:] = [float(x) for x in sc["bg"]]
+        return s
+
+    def _check(self, st):
+        _abi.check(st, self.h)
+
+    # -- calls -----------------------------------------------------------
+    def forward(self, scene, cams, images=None, stream=None):
+        """Images [sum W*H, 3] (views packed in order) of `scene` seen by `cams`."""
+        P = view_pixels(cams)
+        self._last_pixels = P
+        if images is None:
+            images = torch.empty((P, 3), dtype=torch.float32, device=scene["ctrl"].device)
+        cam_arr = _abi.camera_array(cams)
+        sc = self._scene(scene)
+        self._check(self.lib.bgt_render_fwd(self.h, ctypes.byref(sc), cam_arr, len(cams), _ptr(images),
+                                            _stream(stream)))
+        return images
+
+    def backward(self, scene, cams, d_images, grads=None, stream=None):
+        """dl/d(ctrl, color, opacity, r_b) for the last forward, given dl/dimages."""
+        if grads is None:
+            grads = {k: torch.empty_like(scene[k]) for k in GRAD_KEYS}
+        d_images = d_images.contiguous()
+        g = _abi.Grads(*(grads[k].data_ptr() for k in GRAD_KEYS))
+        sc = self._scene(scene)
+        cam_arr = _abi.camera_array(cams)
+        self._check(self.lib.bgt_render_bwd(self.h, ctypes.byref(sc), cam_arr, len(cams), _ptr(d_images),
+                                            ctypes.byref(g), _stream(stream)))
+        return grads
+
+    def sync_status(self, stream=None):
+        self._check(self.lib.bgt_sync_status(self.h, _stream(stream)))
+
+    def status_code(self, stream=None):
+        return int(self.lib.bgt_sync_status(self.h, _stream(stream)))
+
+    def counts(self, stream=None):
+        out = (ctypes.c_longlong * 5)()
+        self._check(self.lib.bgt_get_counts(self.h, out, _stream(stream)))
+        return {"F": out[0], "Nb": out[1], "K": out[2], "Kb": out[3], "tiles": out[4]}
+
+    def set_tile_size(self, t):
+        self._check(self.lib.bgt_set_tile_size(self.h, int(t)))
+
+    @property
+    def tile_size(self):
+        return int(self.lib.bgt_get_tile_size(self.h))
+
+    def autotune(self, scene, cams, images, d_images, grads, iters=3, stream=None):
+        best = ctypes.c_int(0)
+        ms = (ctypes.c_float * 3)()
+        g = _abi.Grads(*(grads[k].data_ptr() for k in GRAD_KEYS))
+        self._check(self.lib.bgt_autotune(self.h, ctypes.byref(self._scene(scene)), _abi.camera_array(cams),
+                                          len(cams), _ptr(images), _ptr(d_images), ctypes.byref(g), iters,
+                                          ctypes.byref(best), ms, _stream(stream)))
+        return best.value, {8: ms[0], 16: ms[1], 32: ms[2]}
+
+    STAGES = ("prep", "raster", "resolve", "generate", "binning", "composite_fwd", "composite_bwd", "chain")
+
+    def set_profiling(self, on=True):
+        self._check(self.lib.bgt_set_profiling(self.h, 1 if on else 0))
+
+    def profile(self):
+        """Device ms per stage of the last profiled forward + backward, and kernel counts."""
+        ms = (ctypes.c_float * 8)()
+        kf, kb = ctypes.c_int(0), ctypes.c_int(0)
+        self._check(self.lib.bgt_get_profile(self.h, ms, ctypes.byref(kf), ctypes.byref(kb)))
+        return dict(zip(self.STAGES, list(ms))), kf.value, kb.value
+
+    def l1_loss_grad(self, images, target, scale, d_images=None, loss=None, stream=None):
+        if d_images is None:
+            d_images = torch.empty_like(images)
+        _abi.check(self.lib.bgt_l1_loss_grad(_ptr(images), _ptr(target), images.numel(), float(scale),
+                                             _ptr(d_images), _ptr(loss), _stream(stream)))
+        return d_images
+
+    def stage(self, name, stream=None):
+        """Copy an intermediate buffer of the last forward to a numpy array."""
+        which = STAGE_ID[name]
+        c = self.counts(stream)
+        P = int(self.lib_last_pixels())
+        size = {0: 4 * P, 1: 8 * P, 2: 48 * c["F"], 3: 32 * c["Nb"], 4: 8 * (c["tiles"] + 1),
+                5: 8 * c["K"], 6: 8 * (c["tiles"] + 1), 7: 8 * c["Kb"], 8: 4 * P, 9: 4 * P,
+                10: 48 * c["F"], 11: 16 * c["Nb"]}[which]
+        buf = np.empty(max(size, 8), np.uint8)
+        written = ctypes.c_longlong(0)
+        self._check(self.lib.bgt_get_stage(self.h, which, buf.ctypes.data_as(ctypes.c_void_p), buf.nbytes,
+                                           ctypes.byref(written), _stream(stream)))
+        raw = buf[: written.value]
+        if which == 0:
+            return raw.view(np.int32)
+        if which in (1, 8):
+            return raw.view(np.float32).reshape(-1, 2) if which == 1 else raw.view(np.float32)
+        if which == 2:
+            return raw.view(np.float32).reshape(-1, 12)
+        if which == 3:
+            return raw.view(np.float32).reshape(-1, 8)
+        if which in (4, 6):
+            return raw.view(np.int64)
+        if which == 9:
+            return raw.view(np.int32)
+        if which in (5, 7):
+            return raw.view(np.uint64)
+        if which == 10:
+            return raw.view(np.float32).reshape(-1, 12)
+        return raw.view(np.float32).reshape(-1, 4)
+
+    def lib_last_pixels(self):
+        return self._last_pixels
+
+    def bin_sort(self, g, width, height, stream=None):
+        """Binning + per-tile sort of synthetic projected Gaussians (scenes.random_gaussians)."""
+        dev = torch.device("cuda")
+        qxy = torch.as_tensor((g["qx"].astype(np.int64) | (g["qy"].astype(np.int64) << 16)).astype(np.int32),
+                              device=dev)
+        off = torch.as_tensor(np.ascontiguousarray(g["off"], np.float32), device=dev)
+        conic = torch.as_tensor(np.ascontiguousarray(g["conic"], np.float32), device=dev)
+        op = torch.as_tensor(g["opacity"], device=dev)
+        dp = torch.as_tensor(g["depth"], device=dev)
+        self._check(self.lib.bgt_bin_sort(self.h, int(width), int(height), len(g["qx"]), _ptr(qxy), _ptr(off),
+                                          _ptr(conic), _ptr(op), _ptr(dp), _stream(stream)))
+        torch.cuda.synchronize()
+        self._last_pixels = width * height
+        return {"ranges": self.stage("g_ranges", stream), "keys": self.stage("g_keys", stream)}
+
+
+class _RenderFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, renderer, cams, scene_meta, ctrl, color, opacity, r_b, log_scale, quat):
+        scene = dict(scene_meta, ctrl=ctrl, color=color, opacity=opacity, r_b=r_b, log_scale=log_scale, quat=quat)
+        img = renderer.forward(scene, cams)
+        ctx.renderer, ctx.cams, ctx.scene = renderer, cams, scene
+        return img
+
+    @staticmethod
+    def backward(ctx, d_img):
+        g = ctx.renderer.backward(ctx.scene, ctx.cams, d_img.contiguous())
+        return None, None, None, g["ctrl"], g["color"], g["opacity"], g["r_b"], None, None
+
+
+def render(renderer, scene, cams):
+    """Differentiable render: images [sum W*H, 3]; gradients flow to
+    scene['ctrl'], ['color'], ['opacity'], ['r_b']."""
+    meta = {"degree": scene["degree"], "bg": scene["bg"]}
+    return _RenderFn.apply(renderer, cams, meta, scene["ctrl"], scene["color"], scene["opacity"], scene["r_b"],
+                           scene["log_scale"], scene["quat"])
+
+
+def split_views(images, cams):
+    """Packed images [sum W*H, 3] -> list of [H, W, 3] views."""
+    out, off = [], 0
+    for c in cams:
+        n = int(c["width"]) * int(c["height"])
+        out.append(images[off: off + n].view(int(c["height"]), int(c["width"]), 3))
+        off += n
+    return out

@@ -1,0 +1,195 @@
+"""GPU backward pass vs the FP64 oracle (supplementary "Backward Derivative").
+
+Upstream gradients dl/dC are seeded normals, set to zero at pixels the oracle
+flags as within rounding distance of a discrete decision (cutoffs, stop,
+depth order, gamma saturation, a near-tie of the most influential boundary
+point, or |q - b*| ~ 0 where the direction of dl/db is ill-conditioned), so
+both sides differentiate the same piecewise-smooth function. Gradients are
+compared to the oracle's analytic gradient (relative 1e-3 in norm, plus an
+elementwise bound) and to central finite differences of the oracle.
+"""
+import numpy as np
+import pytest
+
+from tests.gpu_util import GRAD_TOL, gpu_forward, grad_rel, make_renderer, split_flat
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(oracle, sc, cams, seed=0, tile=16, use_boundary=True):
+    import torch
+    g = gpu_forward(sc, cams, tile=tile, use_boundary=use_boundary, stages=())
+    rd, dev = g["renderer"], g["dev"]
+    rng = np.random.default_rng(seed)
+    opts = {"use_boundary": 1 if use_boundary else 0}
+    dls, refs = [], []
+    for c in cams:
+        ref = oracle.render(sc, c, opts=opts)
+        dl = rng.normal(size=(c["height"], c["width"], 3))
+        dl[ref["flags"] != 0] = 0.0
+        dls.append(dl)
+        refs.append(ref)
+    dl_flat = np.concatenate([d.reshape(-1, 3) for d in dls])
+    grads = rd.backward(dev, cams, torch.as_tensor(dl_flat, dtype=torch.float32, device="cuda"))
+    rd.sync_status()
+    out = {k: v.cpu().numpy().astype(np.float64) for k, v in grads.items()}
+    ref_g = None
+    inter = []
+    for c, dl in zip(cams, dls):
+        r = oracle.backward(sc, c, dl, opts=opts, intermediates=True)
+        inter.append(r)
+        if ref_g is None:
+            ref_g = {k: r[k].copy() for k in ("ctrl", "color", "opacity", "r_b")}
+        else:
+            for k in ref_g:
+                ref_g[k] += r[k]
+    return g, out, ref_g, inter, dls
+
+
+def _assert_close(got, ref, name):
+    rel = grad_rel(got, ref)
+    assert rel < GRAD_TOL, f"{name}: relative error {rel}"
+    scale = np.abs(ref).max()
+    assert np.all(np.abs(got - ref) <= GRAD_TOL * np.abs(ref) + 1e-4 * scale), name
+
+
+CASES = [
+    ("config1", lambda S: S.config_scene(1)[:2]),
+    ("two_wide_boundary", lambda S: S.tiny_scene("two", size=(72, 64), r_b=0.08)),
+    ("ico1_ragged", lambda S: S.tiny_scene("ico1", noise=0.04, size=(90, 70), r_b=0.04)),
+    ("degree3", lambda S: S.tiny_scene("ico1", n=3, noise=0.03, size=(70, 66), r_b=0.04)),
+]
+
+
+@pytest.mark.parametrize("name,make", CASES)
+def test_gradients_match_oracle_analytic(oracle, scenes, name, make):
+    sc, cams = make(scenes)
+    g, got, ref, inter, _ = _run(oracle, sc, cams)
+    for k in ("ctrl", "color", "opacity", "r_b"):
+        if np.abs(ref[k]).max() == 0:
+            assert np.abs(got[k]).max() < 1e-6, k
+            continue
+        _assert_close(got[k], ref[k], k)
+    # intermediate per-Gaussian and per-boundary-point gradients
+    rd = g["renderer"]
+    gg = rd.stage("ggrad").astype(np.float64)
+    og = inter[0]["ggrad"]
+    # GPU layout: dmu x,y, dK a,b,c, do, dcol r,g,b ; oracle: dmu, dK, dcol, do
+    assert grad_rel(gg[:, 0:5], og[:, 0:5]) < GRAD_TOL
+    assert grad_rel(gg[:, 5], og[:, 8]) < GRAD_TOL
+    assert grad_rel(gg[:, 6:9], og[:, 5:8]) < GRAD_TOL
+    bg = rd.stage("bgrad").astype(np.float64)
+    ob = inter[0]["bgrad"][: len(bg)]
+    if np.abs(ob).max() > 0:
+        assert grad_rel(bg[:, :3], ob) < GRAD_TOL
+
+
+def test_gradients_multiview_batch(oracle, scenes):
+    sc, cams = scenes.config_scene(4)
+    crops = [scenes.crop_camera(cams[0], 60, 70, 90, 70), scenes.crop_camera(cams[5], 200, 180, 80, 97)]
+    _, got, ref, _, _ = _run(oracle, sc, crops, seed=3)
+    for k in ("ctrl", "color", "opacity", "r_b"):
+        _assert_close(got[k], ref[k], k)
+
+
+def test_gradients_without_boundary_term(oracle, scenes):
+    sc, cams = scenes.tiny_scene("ico1", noise=0.04, size=(64, 60), r_b=0.04)
+    _, got, ref, _, _ = _run(oracle, sc, cams, use_boundary=False)
+    for k in ("ctrl", "color", "opacity"):
+        _assert_close(got[k], ref[k], k)
+    assert np.abs(got["r_b"]).max() == 0.0
+
+
+@pytest.mark.parametrize("tile", [8, 32])
+def test_gradients_other_tile_sizes(oracle, scenes, tile):
+    sc, cams = scenes.tiny_scene("ico1", noise=0.04, size=(90, 70), r_b=0.04)
+    _, got, ref, _, _ = _run(oracle, sc, cams, tile=tile)
+    for k in ("ctrl", "color", "opacity", "r_b"):
+        _assert_close(got[k], ref[k], k)
+
+
+def test_gradients_vs_finite_differences_config3_crop(oracle, scenes):
+    """Config 3: 20k triangles, 1024^2 view; 256^2 centre crop; 50 random
+    parameters (control points, colours, opacities, boundary scales); FP64
+    central differences of the oracle with h = 1e-6, relative error <= 1e-3."""
+    import torch
+    sc, cams = scenes.config_scene(3)
+    cam = scenes.crop_camera(cams[0], 384, 384, 256, 256)
+    opts = {"tol_d": 1e-2}
+    idm, uv, _ = oracle.raster(sc, cam)
+    base = oracle.render(sc, cam, idm, uv, opts=opts, records=True)
+    rng = np.random.default_rng(11)
+    dl = rng.normal(size=(256, 256, 3))
+    dl[base["flags"] != 0] = 0.0
+    g = gpu_forward(sc, [cam], stages=())
+    grads = g["renderer"].backward(g["dev"], [cam], torch.as_tensor(dl.reshape(-1, 3), dtype=torch.float32,
+                                                                    device="cuda"))
+    g["renderer"].sync_status()
+    got = {k: v.cpu().numpy().astype(np.float64) for k, v in grads.items()}
+    s64 = oracle.scene_to64(sc)
+    visible = np.unique(idm[idm >= 0])
+    rmax = int(np.ceil(max(base["gauss"][:, 12].max(), base["gauss"][:, 13].max()))) + 2
+    kinds = ["ctrl", "color", "opacity", "r_b"]
+    m = s64["ctrl"].shape[1]
+    results = []
+    tries = 0
+    while len(results) < 50 and tries < 400:
+        kind = kinds[tries % 4]
+        tries += 1
+        prim = int(rng.choice(visible))
+        idx = (prim, int(rng.integers(m)), int(rng.integers(3))) if kind in ("ctrl", "color") else (prim,)
+        # only pixels within the support of this primitive's Gaussians can change
+        near = np.zeros_like(idm, bool)
+        ys, xs = np.nonzero(idm == prim)
+        for y, x in zip(ys, xs):
+            near[max(0, y - rmax):y + rmax + 1, max(0, x - rmax):x + rmax + 1] = True
+        vals = []
+        for sgn in (1.0, -1.0):
+            s2 = {k: v.copy() for k, v in s64.items()}
+            s2[kind][idx] += sgn * 1e-6
+            r = oracle.render(sc, cam, idm, uv, opts=opts, scene64=s2, pixels=near)
+            vals.append(float((r["image"][near] * dl[near]).sum()))
+        fd = (vals[0] - vals[1]) / 2e-6
+        results.append((kind, idx, got[kind][idx], fd))
+    fds = np.array([r[3] for r in results])
+    scale = np.abs(fds).max()
+    assert scale > 0
+    bad = [(k, i, a, f) for k, i, a, f in results if abs(a - f) > GRAD_TOL * max(abs(f), 1e-2 * scale)]
+    assert len(results) == 50
+    assert not bad, bad[:5]
+
+
+def test_autograd_function_matches_backward(scenes):
+    import torch
+    from paper_2503_13961_gb300 import render as R
+    sc, cams = scenes.tiny_scene("ico1", noise=0.04, size=(64, 48), r_b=0.04)
+    rd = make_renderer(sc, cams)
+    dev = R.scene_to_device(sc)
+    leaf = {k: dev[k].clone().requires_grad_(k in ("ctrl", "color", "opacity", "r_b")) for k in R.SCENE_KEYS}
+    leaf.update(degree=dev["degree"], bg=dev["bg"])
+    img = R.render(rd, leaf, cams)
+    target = torch.rand_like(img)
+    loss = (img - target).abs().mean()
+    loss.backward()
+    dimg = torch.sign(img.detach() - target) / img.numel()
+    rd.forward(dev, cams)
+    ref = rd.backward(dev, cams, dimg)
+    rd.sync_status()
+    for k in ("ctrl", "color", "opacity", "r_b"):
+        a, b = leaf[k].grad.cpu().numpy(), ref[k].cpu().numpy()
+        assert np.allclose(a, b, rtol=1e-4, atol=1e-7 * np.abs(b).max()), k
+
+
+def test_l1_loss_helper(scenes):
+    import torch
+    from paper_2503_13961_gb300 import render as R
+    sc, cams = scenes.tiny_scene("ico1", size=(16, 16))
+    rd = make_renderer(sc, cams)
+    a = torch.rand(256, 3, device="cuda")
+    b = torch.rand(256, 3, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    d = rd.l1_loss_grad(a, b, 0.5, loss=loss)
+    torch.cuda.synchronize()
+    assert torch.allclose(d, 0.5 * torch.sign(a - b))
+    assert torch.allclose(loss, 0.5 * (a - b).abs().sum(), rtol=1e-5)
+    del R

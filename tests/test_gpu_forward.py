@@ -1,0 +1,302 @@
+"""GPU forward pass vs the FP64 oracle, through the C ABI.
+
+Raster outputs I_id and the boundary set B are integer results and must be
+bit-exact; I_uv, sub-primitive records and images are compared within the
+tolerances of the FP32 path (images: 1e-4 absolute per channel on pixels the
+oracle does not flag as within rounding distance of a discontinuity).
+"""
+import numpy as np
+import pytest
+
+from tests.gpu_util import (FWD_TOL, UNSTABLE_MAX, compare_images, gpu_forward, make_renderer, oracle_opts,
+                            split_flat)
+
+pytestmark = pytest.mark.gpu
+
+
+def _cases():
+    from paper_2503_13961_gb300 import scenes as S
+    out = []
+    sc, cams = S.config_scene(1)
+    out.append(("config1_64", sc, cams))
+    sc, cams = S.tiny_scene("two", size=(75, 53), r_b=0.05)
+    out.append(("two_ragged", sc, cams))
+    sc, cams = S.tiny_scene("ico1", noise=0.04, size=(100, 75), r_b=0.03)
+    out.append(("ico1_100x75", sc, cams))
+    sc, cams = S.tiny_scene("ico1", n=3, noise=0.03, size=(67, 61), r_b=0.03)
+    out.append(("degree3", sc, cams))
+    sc, cams = S.tiny_scene("octa", n=1, size=(48, 40), r_b=0.03)
+    out.append(("degree1", sc, cams))
+    sc, cams, _ = S.config_scene(2)
+    out.append(("config2_crop", sc, [S.crop_camera(cams[0], 300, 330, 160, 121)]))
+    sc, cams = S.config_scene(4)
+    crops = [S.crop_camera(cams[0], 60, 70, 90, 70), S.crop_camera(cams[5], 200, 180, 130, 97),
+             S.crop_camera(cams[9], 10, 20, 33, 150)]
+    out.append(("config4_multiview", sc, crops))
+    return out
+
+
+CASES = None
+
+
+def cases():
+    global CASES
+    if CASES is None:
+        CASES = {name: (sc, cams) for name, sc, cams in _cases()}
+    return CASES
+
+
+CASE_NAMES = ["config1_64", "two_ragged", "ico1_100x75", "degree3", "degree1", "config2_crop", "config4_multiview"]
+
+
+@pytest.fixture(scope="module")
+def forward_results(oracle):
+    res = {}
+    for name in CASE_NAMES:
+        sc, cams = cases()[name]
+        g = gpu_forward(sc, cams, stages=("id", "uv", "gauss", "bnd"))
+        refs = [oracle.render(sc, c, records=True) for c in cams]
+        res[name] = (sc, cams, g, refs)
+        g["renderer"].close()
+    return res
+
+
+@pytest.mark.parametrize("name", CASE_NAMES)
+def test_raster_index_map_bit_exact(forward_results, name):
+    sc, cams, g, refs = forward_results[name]
+    ids = split_flat(g["id"], cams)
+    for v, ref in enumerate(refs):
+        assert np.array_equal(ids[v], ref["id"]), f"view {v}: {np.sum(ids[v] != ref['id'])} pixels differ"
+    assert any((r["id"] >= 0).any() for r in refs)
+
+
+@pytest.mark.parametrize("name", CASE_NAMES)
+def test_raster_uv(forward_results, name):
+    sc, cams, g, refs = forward_results[name]
+    uvs = split_flat(g["uv"].ravel(), cams, width=2)
+    for v, ref in enumerate(refs):
+        fg = ref["id"] >= 0
+        assert np.abs(uvs[v][fg] - ref["uv"][fg]).max(initial=0) < 2e-5
+
+
+@pytest.mark.parametrize("name", CASE_NAMES)
+def test_boundary_set_bit_exact(forward_results, name):
+    sc, cams, g, refs = forward_results[name]
+    bpix = g["bnd"][:, 0].copy().view(np.int32).astype(np.int64)
+    off = 0
+    ref_all = []
+    for c, ref in zip(cams, refs):
+        ref_all.append(ref["bnd"][:, 0].astype(np.int64) + off)
+        off += c["width"] * c["height"]
+    ref_all = np.concatenate(ref_all)
+    assert np.array_equal(bpix, ref_all)
+    assert np.array_equal(g["bnd"][:, 1].copy().view(np.int32), np.concatenate([r["bnd"][:, 1] for r in refs]).astype(np.int32))
+
+
+@pytest.mark.parametrize("name", CASE_NAMES)
+def test_subprimitive_records(forward_results, name):
+    sc, cams, g, refs = forward_results[name]
+    ga = g["gauss"].astype(np.float64)
+    ref = np.concatenate([r["gauss"] for r in refs])
+    assert len(ga) == len(ref)
+    qxy = g["gauss"][:, 6].copy().view(np.uint32)
+    qx, qy = (qxy & 0xFFFF).astype(np.float64), (qxy >> 16).astype(np.float64)
+    mu = np.stack([qx + ga[:, 0], qy + ga[:, 1]], 1)
+    assert np.abs(mu - ref[:, 2:4]).max() < 2e-5
+    assert np.allclose(ga[:, 2:5], ref[:, 4:7], rtol=2e-4, atol=1e-6 * np.abs(ref[:, 4:7]).max())
+    assert np.allclose(ga[:, 11], ref[:, 7], rtol=1e-6)
+    assert np.abs(ga[:, 8:11] - ref[:, 8:11]).max() < 1e-5
+    assert np.array_equal(g["gauss"][:, 7].copy().view(np.int32), ref[:, 1].astype(np.int32))
+    bref = np.concatenate([r["bnd"] for r in refs])
+    gb = g["bnd"].astype(np.float64)
+    if len(bref):
+        assert np.allclose(gb[:, 4], bref[:, 4], rtol=1e-5)
+
+
+@pytest.mark.parametrize("name", CASE_NAMES)
+def test_image_matches_oracle(forward_results, oracle, name):
+    sc, cams, g, refs = forward_results[name]
+    for v, ref in enumerate(refs):
+        err, unstable = compare_images(g["images"][v], ref, ref["flags"], oracle)
+        assert err < FWD_TOL, f"view {v}: max abs err {err}"
+        assert unstable <= UNSTABLE_MAX, f"view {v}: {unstable:.4%} unstable pixels"
+
+
+def test_without_boundary_term(oracle, scenes):
+    sc, cams = scenes.tiny_scene("ico1", noise=0.04, size=(90, 70), r_b=0.05)
+    g = gpu_forward(sc, cams, use_boundary=False)
+    ref = oracle.render(sc, cams[0], opts=oracle_opts(use_boundary=False))
+    err, unstable = compare_images(g["images"][0], ref, ref["flags"], oracle)
+    assert err < FWD_TOL and unstable <= UNSTABLE_MAX
+    g2 = gpu_forward(sc, cams, use_boundary=True, stages=())
+    assert np.abs(g2["images"][0] - g["images"][0]).max() > 1e-3  # the boundary term matters here
+
+
+def test_tile_size_does_not_change_images(scenes):
+    sc, cams = scenes.config_scene(4)
+    crops = [scenes.crop_camera(cams[1], 100, 100, 150, 130), scenes.crop_camera(cams[2], 0, 0, 77, 201)]
+    imgs = [gpu_forward(sc, crops, tile=t, stages=())["images_flat"].cpu().numpy() for t in (8, 16, 32)]
+    assert np.array_equal(imgs[0], imgs[1]) and np.array_equal(imgs[1], imgs[2])
+
+
+def test_batch_equals_single_views(scenes):
+    sc, cams = scenes.config_scene(4)
+    crops = [scenes.crop_camera(cams[k], 40 * k, 30 * k, 60 + 13 * k, 50 + 7 * k) for k in range(5)]
+    batch = gpu_forward(sc, crops, stages=())["images"]
+    for k, c in enumerate(crops):
+        single = gpu_forward(sc, [c], stages=())["images"][0]
+        assert np.array_equal(single, batch[k])
+
+
+def test_graph_replay_matches_direct(scenes):
+    import torch
+    from paper_2503_13961_gb300 import render as R
+    sc, cams = scenes.tiny_scene("ico1", noise=0.04, size=(96, 80), r_b=0.03)
+    direct = gpu_forward(sc, cams, stages=())["images_flat"].cpu().numpy()
+    rd = make_renderer(sc, cams, graph=True)
+    dev = R.scene_to_device(sc)
+    img = torch.empty((96 * 80, 3), device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            rd.forward(dev, cams, images=img, stream=s)
+    s.synchronize()
+    rd.sync_status(stream=s)
+    assert np.array_equal(img.cpu().numpy(), direct)
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+
+def test_empty_scene_gives_background(scenes):
+    import torch
+    from paper_2503_13961_gb300 import render as R
+    sc, cams = scenes.tiny_scene("two", size=(33, 17))
+    empty = {k: (v[:0] if isinstance(v, np.ndarray) and v.ndim >= 1 and k != "bg" else v) for k, v in sc.items()}
+    empty["bg"] = np.array([0.25, 0.5, 0.75], np.float32)
+    rd = make_renderer(sc, cams)
+    dev = R.scene_to_device(empty)
+    img = rd.forward(dev, cams)
+    rd.sync_status()
+    assert np.array_equal(img.cpu().numpy(), np.tile(empty["bg"], (33 * 17, 1)))
+    assert rd.counts()["F"] == 0
+    grads = rd.backward(dev, cams, torch.ones_like(img))
+    rd.sync_status()
+    assert all(v.numel() == 0 for v in grads.values())
+
+
+def test_view_without_foreground(scenes):
+    sc, cams = scenes.tiny_scene("ico1", size=(40, 30))
+    away = scenes.look_at_camera((4.0, 0.0, 0.0), (8.0, 0.0, 0.0), 40, 30)
+    g = gpu_forward(sc, [away], stages=("id",))
+    assert (g["id"] == -1).all()
+    assert np.array_equal(g["images"][0], np.broadcast_to(sc["bg"].astype(np.float64), (30, 40, 3)))
+
+
+@pytest.mark.parametrize("size", [(1, 1), (1, 37), (41, 1), (17, 33)])
+def test_degenerate_view_sizes(oracle, scenes, size):
+    sc, cams = scenes.tiny_scene("ico1", noise=0.02, size=(64, 64))
+    cam = scenes.crop_camera(cams[0], 30, 28, *size)
+    g = gpu_forward(sc, [cam])
+    ref = oracle.render(sc, cam)
+    assert np.array_equal(g["id"].reshape(size[1], size[0]), ref["id"])
+    err, _ = compare_images(g["images"][0], ref, ref["flags"], oracle)
+    assert err < FWD_TOL
+
+
+def test_opacity_zero_gives_background(scenes):
+    sc, cams = scenes.tiny_scene("octa", noise=0.05, size=(40, 40))
+    sc = dict(sc)
+    sc["opacity"] = np.zeros_like(sc["opacity"])
+    sc["bg"] = np.array([0.3, 0.1, 0.7], np.float32)
+    g = gpu_forward(sc, cams, stages=())
+    assert np.array_equal(g["images"][0], np.broadcast_to(sc["bg"].astype(np.float64), (40, 40, 3)))
+
+
+def test_pair_capacity_overflow_is_reported(scenes):
+    import torch
+    from paper_2503_13961_gb300 import _abi
+    from paper_2503_13961_gb300 import render as R
+    sc, cams = scenes.tiny_scene("ico1", noise=0.02, size=(64, 64))
+    rd = R.Renderer(degree=2, max_prims=64, max_views=1, max_pixels=64 * 64, max_pairs=50, max_boundary_pairs=50)
+    dev = R.scene_to_device(sc)
+    rd.forward(dev, cams)
+    with pytest.raises(_abi.BGTError) as e:
+        rd.sync_status()
+    assert e.value.status == 2
+    torch.cuda.synchronize()
+    # the handle stays usable after the error
+    rd2 = make_renderer(sc, cams)
+    rd2.forward(dev, cams)
+    rd2.sync_status()
+
+
+def test_host_side_argument_errors(scenes):
+    import torch
+    from paper_2503_13961_gb300 import _abi
+    from paper_2503_13961_gb300 import render as R
+    sc, cams = scenes.tiny_scene("ico1", size=(32, 32))
+    rd = make_renderer(sc, cams)
+    dev = R.scene_to_device(sc)
+    with pytest.raises(_abi.BGTError) as e:
+        rd.backward(dev, cams, torch.zeros((32 * 32, 3), device="cuda"))
+    assert e.value.status == 6  # no forward yet
+    with pytest.raises(_abi.BGTError) as e:
+        rd.forward(dev, cams + cams)
+    assert e.value.status == 2  # more views than max_views
+    big = scenes.crop_camera(cams[0], 0, 0, 64, 64)
+    with pytest.raises(_abi.BGTError) as e:
+        rd.forward(dev, [big])
+    assert e.value.status == 2  # more pixels than max_pixels
+    bad = dict(cams[0])
+    bad["fx"] = np.float32(np.nan)
+    with pytest.raises(_abi.BGTError) as e:
+        rd.forward(dev, [bad])
+    assert e.value.status == 1
+    rd.forward(dev, cams)
+    rd.sync_status()
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads, sampled pixels
+# ---------------------------------------------------------------------------
+
+def _sampled_check(oracle, sc, cam, img, ids, n=1500, seed=0):
+    rng = np.random.default_rng(seed)
+    H, W = cam["height"], cam["width"]
+    ref_id, ref_uv, _ = oracle.raster(sc, cam)
+    assert np.array_equal(ids, ref_id)
+    fg = np.flatnonzero(ref_id.ravel() >= 0)
+    pick = np.concatenate([rng.choice(fg, size=min(n, len(fg)), replace=False),
+                           rng.integers(0, H * W, size=n // 4)])
+    mask = np.zeros(H * W, np.int32)
+    mask[pick] = 1
+    ref = oracle.render(sc, cam, ref_id, ref_uv, pixels=mask.reshape(H, W))
+    sel = mask.reshape(H, W).astype(bool) & ((ref["flags"] & oracle.FWD_UNSTABLE) == 0)
+    err = np.abs(img - ref["image"])[sel].max()
+    assert err < FWD_TOL, err
+    assert sel.sum() > 0.95 * mask.sum()
+
+
+def test_full_size_1024_view_20k_triangles(oracle, scenes):
+    sc, cams = scenes.config_scene(3)
+    g = gpu_forward(sc, cams, stages=("id",), tile=16)
+    _sampled_check(oracle, sc, cams[0], g["images"][0], g["id"].reshape(1024, 1024))
+
+
+def test_full_size_batched_64_views(oracle, scenes):
+    import torch
+    from paper_2503_13961_gb300 import render as R
+    sc, cams = scenes.config_scene(4)
+    rd = make_renderer(sc, cams, graph=True, tile=16)
+    dev = R.scene_to_device(sc)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        img = rd.forward(dev, cams, stream=s)
+    s.synchronize()
+    rd.sync_status(stream=s)
+    ids = split_flat(rd.stage("id", stream=s), cams)
+    views = R.split_views(img, cams)
+    for v in (0, 17, 63):
+        _sampled_check(oracle, sc, cams[v], views[v].cpu().numpy().astype(np.float64), ids[v], n=600, seed=v)
