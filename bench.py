@@ -341,10 +341,11 @@ def run_plain(rd_ctx, args):
     plain = {"value": round(len(cams) * steps / (ms / 1e3), 2), "unit": "renders/s",
              "ms_per_64_views": round(ms / steps, 3), "graph": False, "tile": 16}
     # one 800^2 view, plain
-    c800 = [c for c in cams if c["width"] == 800][:1]
+    i800 = [i for i, c in enumerate(cams) if c["width"] == 800][:1]
+    c800 = [cams[i] for i in i800]
     v800 = None
     if c800:
-        img, tgt, d = bufs[cams.index(c800[0])]
+        img, tgt, d = bufs[i800[0]]
         for _ in range(3):
             rd.forward(dev, c800, img, stream=stream)
             rd.l1_loss_grad(img, tgt, 1.0 / img.numel(), d, stream=stream)

@@ -57,7 +57,7 @@ typedef struct {
   int degree;                   /* n of the Bezier triangles, 1..4 (paper: 2) */
   int max_prims;                /* capacity: primitives per scene */
   int max_views;                /* capacity: views per call (<= 4096) */
-  long long max_pixels;         /* capacity: sum of W*H over the views of one call */
+  long long max_pixels;         /* capacity: sum of W*H over the views of one call (<= 2^27) */
   long long max_pairs;          /* capacity: (Gaussian, tile) pairs per call */
   long long max_boundary_pairs; /* capacity: (boundary point, tile) pairs per call */
   int tess_level;               /* L: each primitive becomes L^2 flat triangles (1..16) */
@@ -177,8 +177,9 @@ bgt_status bgt_l1_loss_grad(const float *images, const float *target, long long 
  * float[F][12] (off_x, off_y, K_a, K_b, K_c, o, bits(qx|qy<<16), bits(prim),
  * r, g, b, depth); 3 boundary records float[Nb][8] (pixel, prim, off_x,
  * off_y, sigma, z, 0, 0 with pixel and prim as int32 bits); 4 per-tile
- * Gaussian ranges int64[tiles+1]; 5 sorted Gaussian keys uint64[K]; 6 per-tile
- * boundary ranges int64[tiles+1]; 7 sorted boundary keys uint64[Kb];
+ * Gaussian ranges int64[tiles+1]; 5 sorted Gaussian keys uint64[K] (bits 63..32 FP32 depth, 31..27 finer
+ * depth, 26..0 Gaussian index); 6 per-tile
+ * boundary ranges int64[tiles+1]; 7 sorted boundary keys uint64[Kb] (primitive << 32 | boundary index);
  * 8 final transmittance float[P]; 9 per-pixel count of list entries
  * processed int32[P]; 10 per-Gaussian gradients float[F][12];
  * 11 per-boundary-point gradients float[Nb][4]. `bytes` is the size of dst;

@@ -72,6 +72,7 @@
 #define F_SAT 16
 #define F_ARGMIN 32
 #define F_DZERO 64 /* |q - b*| below tol_d: direction of dl/db ill-conditioned */
+#define F_DEPTHG 128 /* depth near-tie of equal-colour neighbours: C unchanged, gradient attribution not */
 
 /* record widths of the optional stage outputs */
 #define GREC 14 /* pix, prim, mux, muy, Ka, Kb, Kc, depth, r, g, b, o, rx, ry */
@@ -684,6 +685,18 @@ static int collect(const oprep *pr, const oparams *pa, const int32_t *id, int W,
   return cnt;
 }
 
+/* Survivors a (first in FP64 depth order) and b can be composited in the
+ * other order by a renderer whose depth keys resolve 1/32 of an FP32 ulp
+ * (then the index) only if the depths are that close and b has the smaller
+ * index; the band is widened by `tol` relative for the FP32 inputs of the
+ * renderer's depth. */
+static int depth_swappable(const pair_t *a, const pair_t *b, double tol) {
+  if (a->gi < b->gi) return 0;
+  float fa = (float)a->depth;
+  double ulp = (double)nextafterf(fa, INFINITY) - (double)fa;
+  return (b->depth - a->depth) <= ulp / 32.0 + tol * a->depth;
+}
+
 static uint64_t mix64(uint64_t h, uint64_t x) {
   h ^= x + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
   h *= 0xff51afd7ed558ccdull;
@@ -703,9 +716,18 @@ static int composite(const pair_t *s, int cnt, const oprep *pr, const oparams *p
     const pair_t *e = &s[k];
     double test_T = T * (1.0 - e->alpha);
     if (fabs(test_T - pa->t_stop) <= pa->tol_T * pa->t_stop) *flags |= F_TSTOP;
-    if (k + 1 < cnt && fabs(s[k + 1].depth - e->depth) <= pa->tol_z * e->depth) *flags |= F_DEPTH;
     *flags |= e->wr.flags;
-    if (test_T < pa->t_stop) break;
+    const int stop_here = test_T < pa->t_stop;
+    if (k + 1 < cnt && depth_swappable(e, &s[k + 1], pa->tol_z)) {
+      /* Two adjacent survivors that FP32 depth keys may order the other way.
+       * Swapping them leaves C unchanged when their colours are equal and the
+       * stop does not fall between them (C is symmetric in the pair). */
+      const double *c0 = pr->G[e->gi].col, *c1 = pr->G[s[k + 1].gi].col;
+      const int same = fabs(c0[0] - c1[0]) <= 1e-9 && fabs(c0[1] - c1[1]) <= 1e-9 && fabs(c0[2] - c1[2]) <= 1e-9;
+      const int next_stops = T * (1.0 - e->alpha) * (1.0 - s[k + 1].alpha) < pa->t_stop;
+      *flags |= (same && !stop_here && !next_stops) ? F_DEPTHG : F_DEPTH;
+    }
+    if (stop_here) break;
     const ogauss *G = &pr->G[e->gi];
     for (int c = 0; c < 3; c++) C[c] += T * e->alpha * G->col[c];
     if (Ti) Ti[k] = T;

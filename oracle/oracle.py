@@ -25,7 +25,7 @@ GREC = 14
 BREC = 6
 GGRAD = 9
 
-F_AMIN, F_AMAX, F_TSTOP, F_DEPTH, F_SAT, F_ARGMIN, F_DZERO = 1, 2, 4, 8, 16, 32, 64
+F_AMIN, F_AMAX, F_TSTOP, F_DEPTH, F_SAT, F_ARGMIN, F_DZERO, F_DEPTHG = 1, 2, 4, 8, 16, 32, 64, 128
 FWD_UNSTABLE = F_AMIN | F_AMAX | F_TSTOP | F_DEPTH
 
 # Defaults shared by name (not by code) with the CUDA library's config.
@@ -41,7 +41,7 @@ DEFAULTS = {
     "all_pairs": 0,
     "tol_alpha": 2e-5,
     "tol_T": 1e-4,
-    "tol_z": 1e-6,
+    "tol_z": 3e-9,
     "tol_rho": 1e-5,
     "tol_d": 1e-4,
 }

@@ -91,6 +91,7 @@ void carve(bgt_handle *h, char *base, size_t *total) {
   w.g_view = c.take<int>(F);
   w.g_uv = c.take<float2>(F);
   w.g_rect = c.take<uint2>(F);
+  w.g_dsub = c.take<unsigned char>(F);
   w.bR = c.take<float4>(F);
   w.b_pix = c.take<int>(F);
   w.b_prim = c.take<int>(F);
@@ -124,7 +125,7 @@ void carve(bgt_handle *h, char *base, size_t *total) {
 bool cfg_ok(const bgt_config *c, const char **why) {
   if (c->degree < 1 || c->degree > bgt::kMaxDegree) return *why = "degree must be 1..4", false;
   if (c->max_prims < 0 || c->max_views < 1 || c->max_views > bgt::kMaxViews) return *why = "max_views must be 1..4096", false;
-  if (c->max_pixels < 1 || c->max_pixels > (1ll << 30)) return *why = "max_pixels must be 1..2^30", false;
+  if (c->max_pixels < 1 || c->max_pixels > (1ll << bgt::kIndexBits)) return *why = "max_pixels must be 1..2^27", false;
   if (c->max_pairs < 1 || c->max_pairs > (1ll << 31) - 1) return *why = "max_pairs must be 1..2^31-1", false;
   if (c->max_boundary_pairs < 1 || c->max_boundary_pairs > (1ll << 31) - 1) return *why = "max_boundary_pairs must be 1..2^31-1", false;
   if (c->tess_level < 1 || c->tess_level > bgt::kMaxTess) return *why = "tess_level must be 1..16", false;
@@ -602,6 +603,7 @@ __global__ void k_load_gaussians(bgt::Params p, bgt::Work w, int count, const in
   w.gB[i] = make_float4(Kc, o, __uint_as_float(q), __int_as_float(0));
   w.gC[i] = make_float4(0.f, 0.f, 0.f, depth[i]);
   w.g_view[i] = 0;
+  w.g_dsub[i] = 16;
   uint2 rect = make_uint2(1u, 0u);
   const float det = Ka * Kc - Kb * Kb;
   if (o > p.alpha_min && det > 0.f) {

@@ -85,6 +85,8 @@ struct Work {
   int *g_view;                // [Fcap]
   float2 *g_uv;               // [Fcap]
   uint2 *g_rect;              // [Fcap] tile rect x0 | y0 << 16, x1 | y1 << 16 (view-local tiles)
+  unsigned char *g_dsub;      // [Fcap] 5 extra depth-key bits (position of the exact depth
+                              //        inside the rounding interval of its FP32 value)
   // boundary points
   float4 *bR;                 // [Fcap]
   int *b_pix, *b_prim, *b_view;
@@ -97,7 +99,7 @@ struct Work {
   long long *g_tstart, *b_tstart;  // [tiles + 1] exclusive prefix sums (64-bit: no wrap)
   long long *scan_aux, *scan_aux2; // scratch of the two tile-count scans
   // pairs
-  unsigned long long *gkeys;  // [Kcap] (depth bits << 32) | gaussian index
+  unsigned long long *gkeys;  // [Kcap] depth key (FP32 bits << 5 | sub) << 27 | gaussian index
   unsigned long long *bkeys;  // [Kbcap] (prim << 32) | boundary index
   int *bl_prim;               // [Kbcap] prim of each sorted boundary entry
   float4 *bl_rec;             // [Kbcap] boundary record of each sorted entry
@@ -110,6 +112,9 @@ struct Work {
   long long Fcap;
   int nblk;
 };
+
+constexpr int kIndexBits = 27;  // Gaussian index field of a pair key (<= 134M Gaussians per call)
+constexpr unsigned long long kIndexMask = (1ull << kIndexBits) - 1ull;
 
 enum Counter { kF = 0, kNb = 1, kK = 2, kKb = 3, kQueueFwd = 4, kQueueBwd = 5, kQueueSort = 6 };
 

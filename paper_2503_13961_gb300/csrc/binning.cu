@@ -6,8 +6,9 @@
 // The sort is a most-significant-digit radix sort of the key (tile, depth,
 // index): the first digit is the whole tile id (a counting sort: per-tile
 // counts from the generation pass, an exclusive scan, one scatter), the
-// remaining 64 bits (FP32 depth bits, Gaussian index) are sorted inside each
-// tile in shared memory. Keys are unique, so the order is fully determined.
+// remaining 64 bits (36-bit depth key = FP32 depth bits and 5 finer bits,
+// 27-bit Gaussian index) are sorted inside each tile in shared memory. Keys
+// are unique, so the order is fully determined.
 // Boundary keys are (primitive, boundary index).
 #include "bgt_internal.cuh"
 
@@ -105,7 +106,7 @@ __device__ inline void emit_rect(unsigned long long *keys, int *fill, const long
     for (int tx = x0; tx <= x1; tx++) {
       const int t = tile_off + ty * tiles_x + tx;
       const long long pos = start[t] + atomicAdd(fill + t, 1);
-      if (pos >= 0 && pos < cap) keys[pos] = (hi << 32) | (unsigned long long)lo;
+      if (pos >= 0 && pos < cap) keys[pos] = hi | (unsigned long long)lo;
     }
 }
 
@@ -116,16 +117,17 @@ __global__ void k_emit(Params p, Work w) {
     const uint2 rect = w.g_rect[i];
     if ((rect.x & 0xffff) > (rect.y & 0xffff)) continue;
     const View *vw = w.views + w.g_view[i];
-    const unsigned dbits = __float_as_uint(w.gC[i].w);
+    const unsigned long long dkey =
+        ((unsigned long long)__float_as_uint(w.gC[i].w) << 5) | (unsigned long long)w.g_dsub[i];
     emit_rect(w.gkeys, w.g_tfill, w.g_tstart, p.max_pairs, __ldg(&vw->tile_off), __ldg(&vw->tiles_x),
-              rect, dbits, (unsigned)i);
+              rect, dkey << kIndexBits, (unsigned)i);
   }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Nb; i += stride) {
     const uint2 rect = w.b_rect[i];
     if ((rect.x & 0xffff) > (rect.y & 0xffff)) continue;
     const View *vw = w.views + w.b_view[i];
     emit_rect(w.bkeys, w.b_tfill, w.b_tstart, p.max_bpairs, __ldg(&vw->tile_off), __ldg(&vw->tiles_x),
-              rect, (unsigned)w.b_prim[i], (unsigned)i);
+              rect, (unsigned long long)(unsigned)w.b_prim[i] << 32, (unsigned)i);
   }
 }
 

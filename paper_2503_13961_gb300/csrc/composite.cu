@@ -43,7 +43,11 @@ __device__ __forceinline__ WRes w_search(int g, int px, int py, int idq, const i
   r.best = -1;
   r.rho = 3.0e38f;
   r.gamma = 1.0f;
-  if (use_boundary) {
+  if (!use_boundary) {  // the paper's "w/o B" ablation: no blending coefficient
+    r.w = 1.0f;
+    return r;
+  }
+  {
     int lo = 0, hi = bn;
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
@@ -183,7 +187,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work
       if (__syncthreads_and(alldone)) break;
       const int i = b0 + threadIdx.x;
       if (i < gn) {
-        const unsigned gi = (unsigned)(w.gkeys[ti.gs + i] & 0xffffffffull);
+        const unsigned gi = (unsigned)(w.gkeys[ti.gs + i] & kIndexMask);
         sA[threadIdx.x] = w.gA[gi];
         sB[threadIdx.x] = w.gB[gi];
         sC[threadIdx.x] = w.gC[gi];
@@ -269,7 +273,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
     const unsigned long long *bkeys = w.bkeys + ti.bs;
     const int bn = (int)ti.bn;
 
-    float Tr[PPT], S[PPT][3], dC[PPT][3];
+    float Tr[PPT], S[PPT][3], dC[PPT][3];  // S: colour behind, normalised by T (3DGS-style)
     int last[PPT], idq[PPT], px[PPT], py[PPT];
     WCache cache[PPT];
     int mylast = 0;
@@ -292,7 +296,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
 #pragma unroll
         for (int c = 0; c < 3; c++) {
           dC[k][c] = dimage[3 * (size_t)pix + c];
-          S[k][c] = Tr[k] * p.bg[c];
+          S[k][c] = p.bg[c];
         }
       }
       mylast = max(mylast, last[k]);
@@ -305,7 +309,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
       const int i = b0 + threadIdx.x;
       __syncthreads();
       if (i < b1) {
-        const unsigned gi = (unsigned)(w.gkeys[ti.gs + i] & 0xffffffffull);
+        const unsigned gi = (unsigned)(w.gkeys[ti.gs + i] & kIndexMask);
         sG[threadIdx.x] = (int)gi;
         sA[threadIdx.x] = w.gA[gi];
         sB[threadIdx.x] = w.gB[gi];
@@ -335,14 +339,19 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
           const float oma = 1.0f - alpha;
           Tr[k] = Tr[k] / oma;  // T_i
           const float ta = Tr[k] * alpha;
+          // dl/dalpha_i = dl/dC . (T_i c_i - S_i / (1 - alpha_i)) with
+          // S_i / (1 - alpha_i) = T_i R_i, R_i = colour behind i seen through
+          // the pairs behind it: R <- alpha_i c_i + (1 - alpha_i) R. The form
+          // T_i (c_i - R_i) avoids amplifying rounding by 1 / (1 - alpha_i).
           float dl_da = 0.f;
           const float col[3] = {Cc.x, Cc.y, Cc.z};
 #pragma unroll
           for (int c = 0; c < 3; c++) {
             acc[6 + c] += ta * dC[k][c];
-            dl_da += dC[k][c] * (Tr[k] * col[c] - S[k][c] / oma);
-            S[k][c] += ta * col[c];
+            dl_da += dC[k][c] * (col[c] - S[k][c]);
+            S[k][c] = alpha * col[c] + oma * S[k][c];
           }
+          dl_da *= Tr[k];
           if (raw >= p.alpha_max) continue;  // clamped: alpha is constant
           acc[5] += dl_da * wr.w * G;
           const float dl_dw = dl_da * B.y * G;

@@ -202,6 +202,19 @@ __global__ void __launch_bounds__(kGenThreads) k_generate(Params p, Scene s, Wor
     surface_point(p.n, cp, uv.x, uv.y, vw, sp);
     const float2 off = project_offset(sp.t, vw, qx, qy);
     const float tx = sp.t[0].hi + sp.t[0].lo, ty = sp.t[1].hi + sp.t[1].lo, tz = sp.t[2].hi + sp.t[2].lo;
+    // depth sort key refinement: the exact depth hi + lo lies in the rounding
+    // interval of tz; its position there, in 1/32 ulp, extends the FP32 bits
+    // by 5 monotone bits (|lo| <= ulp / 2 maps to 0..31)
+    unsigned char dsub = 16;
+    {
+      const df z = df_fast_two_sum(sp.t[2].hi, sp.t[2].lo);
+      const float r = __fsub_rn(z.hi, tz) + z.lo;  // exact depth minus tz
+      const float ulp = __int_as_float(__float_as_int(tz) & 0x7f800000) * 1.1920928955078125e-7f;
+      if (ulp > 0.f) {
+        const float c = floorf(r / ulp * 32.0f) + 16.0f;
+        dsub = (unsigned char)fminf(fmaxf(c, 0.0f), 31.0f);
+      }
+    }
     // EWA: T = J W, Sigma2D = T Sigma3D T^T + dilation I
     const float iz = 1.0f / tz;
     const float j00 = vw.fx * iz, j02 = -vw.fx * tx * iz * iz;
@@ -255,6 +268,7 @@ __global__ void __launch_bounds__(kGenThreads) k_generate(Params p, Scene s, Wor
     w.g_view[gi] = view;
     w.g_uv[gi] = uv;
     w.g_rect[gi] = rect;
+    w.g_dsub[gi] = dsub;
     float4 *ggz = reinterpret_cast<float4 *>(w.gg + 12 * (size_t)gi);
     ggz[0] = ggz[1] = ggz[2] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (!bnd) continue;

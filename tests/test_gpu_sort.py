@@ -25,10 +25,11 @@ def _check_lists(g, W, H, tile, ranges, keys, ptr, idx, alpha_min):
     tx = (W + tile - 1) // tile
     ty = (H + tile - 1) // tile
     assert len(ranges) == tx * ty + 1
-    gi = (keys & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    gi = (keys & np.uint64((1 << 27) - 1)).astype(np.int64)
     dbits = (keys >> np.uint64(32)).astype(np.uint32)
-    # keys are the Gaussians' depth bits
+    # keys carry the Gaussians' FP32 depth bits; FP32 inputs sit mid-interval (sub = 16)
     assert np.array_equal(dbits, g["depth"].view(np.uint32)[gi])
+    assert np.all(((keys >> np.uint64(27)) & np.uint64(31)) == 16)
     lists = []
     for t in range(tx * ty):
         seg = keys[ranges[t]:ranges[t + 1]]
