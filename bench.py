@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--tile", type=int, default=0, help="0 = autotune")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", default="config4", choices=["config4", "view800"],
+                    help="view800: one 800^2 view of the same scene (small case for profilers)")
     return ap.parse_args()
 
 
@@ -138,9 +140,11 @@ def stage_bytes(stage, c, M, ncp, V):
     }[stage]
 
 
-def build_workload(seed_views, rb):
+def build_workload(seed_views, rb, workload="config4"):
     from paper_2503_13961_gb300 import scenes
     sc, cams = scenes.config_scene(4, r_b=rb)
+    if workload == "view800":
+        return sc, [c for c in cams if c["width"] == 800][:1]
     if seed_views:
         # other ranks render their own 64 views of the same scene (weak scaling)
         rng = np.random.default_rng(1000 + seed_views)
@@ -158,7 +162,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    sc, cams = build_workload(rank, args.rb)
+    sc, cams = build_workload(rank, args.rb, args.workload)
     V = len(cams)
     P = sum(c["width"] * c["height"] for c in cams)
     M, ncp = sc["ctrl"].shape[0], sc["ctrl"].shape[1]
@@ -286,7 +290,8 @@ def run_ours(args):
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms / args.steps, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded scene generator; stands in for Lego / NeRF-Synthetic)",
-            "config": {"workload": WORKLOAD, "views": V, "pixels": P, "prims": M, "degree": 2,
+            "config": {"workload": WORKLOAD if args.workload == "config4" else "one 800^2 view of: " + WORKLOAD,
+                       "views": V, "pixels": P, "prims": M, "degree": 2,
                        "tile": rd.tile_size, "tile_autotune_ms": tune_ms, "graph": True,
                        "counts": {k: int(v) for k, v in counts.items()},
                        "l2": "inputs larger than L2 (no flush needed)", "parallelism": f"replicas x{world}"},

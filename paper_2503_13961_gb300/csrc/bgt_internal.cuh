@@ -63,7 +63,8 @@ struct Grads {                // device pointers, caller-owned outputs
 // Gaussian record (one per foreground pixel), three float4 per Gaussian:
 //   A = (off_x, off_y, K_a, K_b)   mean = pixel centre + off; conic (a, b, c)
 //   B = (K_c, opacity, bits(qx | qy << 16), bits(prim))
-//   C = (r, g, b, depth)
+//   C = (r, g, b, support radius)  the support {o G >= alpha_min} lies inside
+//                                  the square of this half-width around the mean
 // Boundary record (one per pixel of B):
 //   R = (bits(qx | qy << 16), off_x, off_y, 1 / sigma)
 struct Work {
@@ -85,6 +86,7 @@ struct Work {
   int *g_view;                // [Fcap]
   float2 *g_uv;               // [Fcap]
   uint2 *g_rect;              // [Fcap] tile rect x0 | y0 << 16, x1 | y1 << 16 (view-local tiles)
+  float *g_depth;             // [Fcap] camera depth (FP32)
   unsigned char *g_dsub;      // [Fcap] 5 extra depth-key bits (position of the exact depth
                               //        inside the rounding interval of its FP32 value)
   // boundary points

@@ -118,7 +118,7 @@ __global__ void k_emit(Params p, Work w) {
     if ((rect.x & 0xffff) > (rect.y & 0xffff)) continue;
     const View *vw = w.views + w.g_view[i];
     const unsigned long long dkey =
-        ((unsigned long long)__float_as_uint(w.gC[i].w) << 5) | (unsigned long long)w.g_dsub[i];
+        ((unsigned long long)__float_as_uint(w.g_depth[i]) << 5) | (unsigned long long)w.g_dsub[i];
     emit_rect(w.gkeys, w.g_tfill, w.g_tstart, p.max_pairs, __ldg(&vw->tile_off), __ldg(&vw->tiles_x),
               rect, dkey << kIndexBits, (unsigned)i);
   }

@@ -25,11 +25,25 @@ namespace {
 
 constexpr int kBCap = 1536;  // boundary entries staged in shared memory
 
+// Block layout: NT threads; every warp owns a WX x WY block of the tile's
+// pixels (PPT pixels per lane), so that a chunk of 32 staged Gaussians can be
+// culled against the warp's block with one ballot.
 template <int T>
 struct TileCfg {
-  static constexpr int NT = (T * T < 256) ? T * T : 256;
-  static constexpr int PPT = T * T / NT;
+  static constexpr int NT = (T == 8) ? 64 : 256;
+  static constexpr int NW = NT / 32;
+  static constexpr int PPT = T * T / NT;     // 1, 1, 4
+  static constexpr int WX = (T == 32) ? 16 : 8;
+  static constexpr int WY = (T == 32) ? 8 : 4;
+  static constexpr int WPR = T / WX;         // warp blocks per tile row
 };
+
+template <int T>
+__device__ __forceinline__ void lane_pixel(int warp, int lane, int k, int &lx, int &ly) {
+  using C = TileCfg<T>;
+  lx = (warp % C::WPR) * C::WX + (lane & 7) + 8 * (k & 1);
+  ly = (warp / C::WPR) * C::WY + (lane >> 3) + 4 * (k >> 1);
+}
 
 struct WRes {
   float w, gamma, rho;
@@ -47,28 +61,26 @@ __device__ __forceinline__ WRes w_search(int g, int px, int py, int idq, const i
     r.w = 1.0f;
     return r;
   }
-  {
-    int lo = 0, hi = bn;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (bprim[mid] < g) lo = mid + 1; else hi = mid;
+  int lo = 0, hi = bn;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (bprim[mid] < g) lo = mid + 1; else hi = mid;
+  }
+  float best = 3.0e38f;
+  for (int i = lo; i < bn && bprim[i] == g; i++) {
+    const float4 b = brec[i];
+    const unsigned qxy = __float_as_uint(b.x);
+    const float dx = __fsub_rn((float)(px - (int)(qxy & 0xffffu)), b.y);
+    const float dy = __fsub_rn((float)(py - (int)(qxy >> 16)), b.z);
+    const float r2 = __fmul_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)), __fmul_rn(b.w, b.w));
+    if (r2 < best) {
+      best = r2;
+      r.best = i;
     }
-    float best = 3.0e38f;
-    for (int i = lo; i < bn && bprim[i] == g; i++) {
-      const float4 b = brec[i];
-      const unsigned qxy = __float_as_uint(b.x);
-      const float dx = __fsub_rn((float)(px - (int)(qxy & 0xffffu)), b.y);
-      const float dy = __fsub_rn((float)(py - (int)(qxy >> 16)), b.z);
-      const float r2 = __fmul_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)), __fmul_rn(b.w, b.w));
-      if (r2 < best) {
-        best = r2;
-        r.best = i;
-      }
-    }
-    if (r.best >= 0) {
-      r.rho = __fsqrt_rn(best);
-      if (best < 1.0f) r.gamma = exp2f(__fsub_rn(r.rho, 1.0f));
-    }
+  }
+  if (r.best >= 0) {
+    r.rho = __fsqrt_rn(best);
+    if (best < 1.0f) r.gamma = exp2f(__fsub_rn(r.rho, 1.0f));
   }
   r.w = (idq == g) ? r.gamma : __fsub_rn(1.0f, r.gamma);
   return r;
@@ -88,28 +100,25 @@ __device__ __forceinline__ PairGeo pair_geo(int px, int py, const float4 &A, con
   return p;
 }
 
-// two-entry cache of (primitive -> coefficient) per pixel
+// two-entry cache of (primitive -> coefficient) per pixel, in registers
 struct WCache {
-  int g[2];
-  WRes r[2];
-  int next;
-  __device__ void reset() {
-    g[0] = g[1] = -2;
-    next = 0;
+  int g0, g1;
+  WRes r0, r1;
+  bool flip;
+  __device__ __forceinline__ void reset() {
+    g0 = g1 = -2;
+    flip = false;
+  }
+  __device__ __forceinline__ WRes get(int g, int px, int py, int idq, const int *bprim, const float4 *brec,
+                                      int bn, int use_boundary) {
+    if (g == g0) return r0;
+    if (g == g1) return r1;
+    const WRes r = w_search(g, px, py, idq, bprim, brec, bn, use_boundary);
+    if (flip) { g1 = g; r1 = r; } else { g0 = g; r0 = r; }
+    flip = !flip;
+    return r;
   }
 };
-
-__device__ __forceinline__ WRes w_cached(WCache &c, int g, int px, int py, int idq,
-                                                const int *bprim, const float4 *brec, int bn,
-                                                int use_boundary) {
-  if (c.g[0] == g) return c.r[0];
-  if (c.g[1] == g) return c.r[1];
-  const int k = c.next;
-  c.next ^= 1;
-  c.g[k] = g;
-  c.r[k] = w_search(g, px, py, idq, bprim, brec, bn, use_boundary);
-  return c.r[k];
-}
 
 struct TileInfo {
   int view, W, H, pix_off, x0, y0;
@@ -137,13 +146,24 @@ __device__ inline TileInfo tile_info(const Params &p, const Work &w, int tile, i
   return t;
 }
 
+// does the support square of the Gaussian cover any pixel of [x0,x1] x [y0,y1]?
+__device__ __forceinline__ bool covers(const float4 &A, const float4 &B, const float4 &C, int x0, int x1,
+                                       int y0, int y1) {
+  const unsigned qxy = __float_as_uint(B.z);
+  const float cx = (float)(int)(qxy & 0xffffu) + A.x, cy = (float)(int)(qxy >> 16) + A.y;
+  const float r = C.w;
+  return r >= 0.f && cx + r >= (float)x0 && cx - r <= (float)x1 && cy + r >= (float)y0 && cy - r <= (float)y1;
+}
+
 template <int T>
 __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work w, float *image) {
-  constexpr int NT = TileCfg<T>::NT, PPT = TileCfg<T>::PPT;
+  using Cfg = TileCfg<T>;
+  constexpr int NT = Cfg::NT, PPT = Cfg::PPT;
   __shared__ float4 sA[NT], sB[NT], sC[NT];
   __shared__ int s_bprim[kBCap];
   __shared__ float4 s_brec[kBCap];
   __shared__ int s_tile;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_tile = atomicAdd(w.counters + kQueueFwd, 1);
@@ -161,6 +181,9 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work
     const int *bprim = bsm ? s_bprim : w.bl_prim + ti.bs;
     const float4 *brec = bsm ? s_brec : w.bl_rec + ti.bs;
     const int bn = (int)ti.bn;
+    // the warp's pixel block
+    const int wx0 = ti.x0 + (warp % Cfg::WPR) * Cfg::WX, wy0 = ti.y0 + (warp / Cfg::WPR) * Cfg::WY;
+    const int wx1 = wx0 + Cfg::WX - 1, wy1 = wy0 + Cfg::WY - 1;
 
     float C[PPT][3], Tr[PPT];
     int last[PPT], idq[PPT], px[PPT], py[PPT];
@@ -168,9 +191,10 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work
     WCache cache[PPT];
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
-      const int li = threadIdx.x + k * NT;
-      px[k] = ti.x0 + li % T;
-      py[k] = ti.y0 + li / T;
+      int lx, ly;
+      lane_pixel<T>(warp, lane, k, lx, ly);
+      px[k] = ti.x0 + lx;
+      py[k] = ti.y0 + ly;
       const bool inside = px[k] < ti.W && py[k] < ti.H;
       done[k] = !inside;
       idq[k] = inside ? w.pid[ti.pix_off + py[k] * ti.W + px[k]] : -1;
@@ -194,32 +218,43 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work
       }
       __syncthreads();
       const int nb = min(NT, gn - b0);
-#pragma unroll
-      for (int k = 0; k < PPT; k++) {
-        if (done[k]) continue;
-        for (int j = 0; j < nb; j++) {
+      for (int c0 = 0; c0 < nb; c0 += 32) {
+        if (__all_sync(0xffffffffu, alldone)) break;
+        const int jl = c0 + lane;
+        const bool hit = jl < nb && covers(sA[jl], sB[jl], sC[jl], wx0, wx1, wy0, wy1);
+        unsigned mask = __ballot_sync(0xffffffffu, hit);
+        while (mask) {
+          const int j = c0 + __ffs(mask) - 1;
+          mask &= mask - 1;
           const float4 A = sA[j], B = sB[j];
-          const PairGeo pg = pair_geo(px[k], py[k], A, B);
-          const float G = __expf(pg.power);
-          const float og = __fmul_rn(B.y, G);
-          if (og < p.alpha_min) continue;  // w <= 1: alpha < alpha_min
-          const int g = __float_as_int(B.w);
-          const WRes wr = w_cached(cache[k], g, px[k], py[k], idq[k], bprim, brec, bn, p.use_boundary);
-          const float alpha = fminf(p.alpha_max, __fmul_rn(og, wr.w));
-          if (alpha < p.alpha_min) continue;
-          const float testT = __fmul_rn(Tr[k], __fsub_rn(1.0f, alpha));
-          if (testT < p.t_stop) {
-            done[k] = true;
-            break;
+#pragma unroll
+          for (int k = 0; k < PPT; k++) {
+            if (done[k]) continue;
+            const PairGeo pg = pair_geo(px[k], py[k], A, B);
+            const float G = __expf(pg.power);
+            const float og = __fmul_rn(B.y, G);
+            if (og < p.alpha_min) continue;  // w <= 1: alpha < alpha_min
+            const int g = __float_as_int(B.w);
+            const WRes wr = cache[k].get(g, px[k], py[k], idq[k], bprim, brec, bn, p.use_boundary);
+            const float alpha = fminf(p.alpha_max, __fmul_rn(og, wr.w));
+            if (alpha < p.alpha_min) continue;
+            const float testT = __fmul_rn(Tr[k], __fsub_rn(1.0f, alpha));
+            if (testT < p.t_stop) {
+              done[k] = true;
+              continue;
+            }
+            const float4 Cc = sC[j];
+            const float ta = __fmul_rn(Tr[k], alpha);
+            C[k][0] = __fmaf_rn(ta, Cc.x, C[k][0]);
+            C[k][1] = __fmaf_rn(ta, Cc.y, C[k][1]);
+            C[k][2] = __fmaf_rn(ta, Cc.z, C[k][2]);
+            Tr[k] = testT;
+            last[k] = b0 + j + 1;
           }
-          const float4 Cc = sC[j];
-          const float ta = __fmul_rn(Tr[k], alpha);
-          C[k][0] = __fmaf_rn(ta, Cc.x, C[k][0]);
-          C[k][1] = __fmaf_rn(ta, Cc.y, C[k][1]);
-          C[k][2] = __fmaf_rn(ta, Cc.z, C[k][2]);
-          Tr[k] = testT;
-          last[k] = b0 + j + 1;
         }
+        alldone = 1;
+#pragma unroll
+        for (int k = 0; k < PPT; k++) alldone &= done[k] ? 1 : 0;
       }
     }
 #pragma unroll
@@ -244,13 +279,15 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 template <int T>
 __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work w, const float *dimage) {
-  constexpr int NT = TileCfg<T>::NT, PPT = TileCfg<T>::PPT;
+  using Cfg = TileCfg<T>;
+  constexpr int NT = Cfg::NT, PPT = Cfg::PPT;
   __shared__ float4 sA[NT], sB[NT], sC[NT];
   __shared__ int sG[NT];
   __shared__ int s_bprim[kBCap];
   __shared__ float4 s_brec[kBCap];
   __shared__ int s_tile, s_maxlast;
   const float LN2 = 0.69314718055994531f;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -272,21 +309,25 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
     const float4 *brec = bsm ? s_brec : w.bl_rec + ti.bs;
     const unsigned long long *bkeys = w.bkeys + ti.bs;
     const int bn = (int)ti.bn;
+    const int wx0 = ti.x0 + (warp % Cfg::WPR) * Cfg::WX, wy0 = ti.y0 + (warp / Cfg::WPR) * Cfg::WY;
+    const int wx1 = wx0 + Cfg::WX - 1, wy1 = wy0 + Cfg::WY - 1;
 
-    float Tr[PPT], S[PPT][3], dC[PPT][3];  // S: colour behind, normalised by T (3DGS-style)
+    // R: colour behind the current pair seen through the pairs behind it
+    float Tr[PPT], R[PPT][3], dC[PPT][3];
     int last[PPT], idq[PPT], px[PPT], py[PPT];
     WCache cache[PPT];
     int mylast = 0;
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
-      const int li = threadIdx.x + k * NT;
-      px[k] = ti.x0 + li % T;
-      py[k] = ti.y0 + li / T;
+      int lx, ly;
+      lane_pixel<T>(warp, lane, k, lx, ly);
+      px[k] = ti.x0 + lx;
+      py[k] = ti.y0 + ly;
       last[k] = 0;
       idq[k] = -1;
       Tr[k] = 1.f;
       cache[k].reset();
-      S[k][0] = S[k][1] = S[k][2] = 0.f;
+      R[k][0] = R[k][1] = R[k][2] = 0.f;
       dC[k][0] = dC[k][1] = dC[k][2] = 0.f;
       if (px[k] < ti.W && py[k] < ti.H) {
         const int pix = ti.pix_off + py[k] * ti.W + px[k];
@@ -296,12 +337,15 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
 #pragma unroll
         for (int c = 0; c < 3; c++) {
           dC[k][c] = dimage[3 * (size_t)pix + c];
-          S[k][c] = p.bg[c];
+          R[k][c] = p.bg[c];
         }
       }
       mylast = max(mylast, last[k]);
     }
-    atomicMax(&s_maxlast, mylast);
+    int wlast = mylast;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wlast = max(wlast, __shfl_xor_sync(0xffffffffu, wlast, o));
+    if (lane == 0) atomicMax(&s_maxlast, wlast);
     __syncthreads();
     const int maxlast = s_maxlast;
     for (int b1 = maxlast; b1 > 0; b1 -= NT) {
@@ -316,79 +360,87 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
         sC[threadIdx.x] = w.gC[gi];
       }
       __syncthreads();
-      for (int j = b1 - 1; j >= b0; j--) {
-        const int sj = j - b0;
-        const float4 A = sA[sj], B = sB[sj], Cc = sC[sj];
-        const int g = __float_as_int(B.w);
-        float acc[9];
+      const int cend = min(b1, wlast);  // this warp's pixels composited nothing at or beyond wlast
+      for (int c1 = cend; c1 > b0; c1 -= 32) {
+        const int c0 = max(b0, c1 - 32);
+        const int jl = c0 + lane;
+        const bool hit = jl < c1 && covers(sA[jl - b0], sB[jl - b0], sC[jl - b0], wx0, wx1, wy0, wy1);
+        unsigned mask = __ballot_sync(0xffffffffu, hit);
+        while (mask) {
+          const int bit = 31 - __clz(mask);
+          mask &= ~(1u << bit);
+          const int j = c0 + bit;
+          const int sj = j - b0;
+          const float4 A = sA[sj], B = sB[sj], Cc = sC[sj];
+          const int g = __float_as_int(B.w);
+          float acc[9];
 #pragma unroll
-        for (int q = 0; q < 9; q++) acc[q] = 0.f;
-        bool any = false;
+          for (int q = 0; q < 9; q++) acc[q] = 0.f;
+          bool any = false;
 #pragma unroll
-        for (int k = 0; k < PPT; k++) {
-          if (j >= last[k]) continue;
-          const PairGeo pg = pair_geo(px[k], py[k], A, B);
-          const float G = __expf(pg.power);
-          const float og = __fmul_rn(B.y, G);
-          if (og < p.alpha_min) continue;
-          const WRes wr = w_cached(cache[k], g, px[k], py[k], idq[k], bprim, brec, bn, p.use_boundary);
-          const float raw = __fmul_rn(og, wr.w);
-          const float alpha = fminf(p.alpha_max, raw);
-          if (alpha < p.alpha_min) continue;
-          any = true;
-          const float oma = 1.0f - alpha;
-          Tr[k] = Tr[k] / oma;  // T_i
-          const float ta = Tr[k] * alpha;
-          // dl/dalpha_i = dl/dC . (T_i c_i - S_i / (1 - alpha_i)) with
-          // S_i / (1 - alpha_i) = T_i R_i, R_i = colour behind i seen through
-          // the pairs behind it: R <- alpha_i c_i + (1 - alpha_i) R. The form
-          // T_i (c_i - R_i) avoids amplifying rounding by 1 / (1 - alpha_i).
-          float dl_da = 0.f;
-          const float col[3] = {Cc.x, Cc.y, Cc.z};
+          for (int k = 0; k < PPT; k++) {
+            if (j >= last[k]) continue;
+            const PairGeo pg = pair_geo(px[k], py[k], A, B);
+            const float G = __expf(pg.power);
+            const float og = __fmul_rn(B.y, G);
+            if (og < p.alpha_min) continue;
+            const WRes wr = cache[k].get(g, px[k], py[k], idq[k], bprim, brec, bn, p.use_boundary);
+            const float raw = __fmul_rn(og, wr.w);
+            const float alpha = fminf(p.alpha_max, raw);
+            if (alpha < p.alpha_min) continue;
+            any = true;
+            const float oma = 1.0f - alpha;
+            Tr[k] = Tr[k] / oma;  // T_i
+            const float ta = Tr[k] * alpha;
+            // dl/dalpha_i = dl/dC . (T_i c_i - S_i / (1 - alpha_i)) with
+            // S_i / (1 - alpha_i) = T_i R_i, R <- alpha_i c_i + (1 - alpha_i) R:
+            // the form T_i (c_i - R_i) avoids amplifying rounding by 1 / (1 - alpha_i)
+            float dl_da = 0.f;
+            const float col[3] = {Cc.x, Cc.y, Cc.z};
 #pragma unroll
-          for (int c = 0; c < 3; c++) {
-            acc[6 + c] += ta * dC[k][c];
-            dl_da += dC[k][c] * (col[c] - S[k][c]);
-            S[k][c] = alpha * col[c] + oma * S[k][c];
-          }
-          dl_da *= Tr[k];
-          if (raw >= p.alpha_max) continue;  // clamped: alpha is constant
-          acc[5] += dl_da * wr.w * G;
-          const float dl_dw = dl_da * B.y * G;
-          const float dl_dpow = dl_da * og * wr.w;
-          const float dx = pg.dx, dy = pg.dy;  // q - mu
-          acc[2] += dl_dpow * (-0.5f * dx * dx);
-          acc[3] += dl_dpow * (-dx * dy);
-          acc[4] += dl_dpow * (-0.5f * dy * dy);
-          acc[0] += dl_dpow * (A.z * dx + A.w * dy);
-          acc[1] += dl_dpow * (A.w * dx + B.x * dy);
-          if (wr.best >= 0 && wr.rho < 1.0f) {
-            const float4 b = brec[wr.best];
-            const unsigned qxy = __float_as_uint(b.x);
-            const float bx = (float)(px[k] - (int)(qxy & 0xffffu)) - b.y;
-            const float by = (float)(py[k] - (int)(qxy >> 16)) - b.z;
-            const float d = sqrtf(bx * bx + by * by);
-            if (d > 0.f) {
-              const float sgn = (idq[k] == g) ? 1.0f : -1.0f;
-              const float dl_drho = sgn * dl_dw * LN2 * wr.gamma;
-              const float isig = b.w;
-              const unsigned bidx = (unsigned)(bkeys[wr.best] & 0xffffffffull);
-              float *gb = reinterpret_cast<float *>(w.bg_grad + bidx);
-              atomicAdd(gb + 0, dl_drho * (-bx / d) * isig);
-              atomicAdd(gb + 1, dl_drho * (-by / d) * isig);
-              atomicAdd(gb + 2, dl_drho * (-wr.rho) * isig);
+            for (int c = 0; c < 3; c++) {
+              acc[6 + c] += ta * dC[k][c];
+              dl_da += dC[k][c] * (col[c] - R[k][c]);
+              R[k][c] = alpha * col[c] + oma * R[k][c];
+            }
+            dl_da *= Tr[k];
+            if (raw >= p.alpha_max) continue;  // clamped: alpha is constant
+            acc[5] += dl_da * wr.w * G;
+            const float dl_dw = dl_da * B.y * G;
+            const float dl_dpow = dl_da * og * wr.w;
+            const float dx = pg.dx, dy = pg.dy;  // q - mu
+            acc[2] += dl_dpow * (-0.5f * dx * dx);
+            acc[3] += dl_dpow * (-dx * dy);
+            acc[4] += dl_dpow * (-0.5f * dy * dy);
+            acc[0] += dl_dpow * (A.z * dx + A.w * dy);
+            acc[1] += dl_dpow * (A.w * dx + B.x * dy);
+            if (wr.best >= 0 && wr.rho < 1.0f) {
+              const float4 b = brec[wr.best];
+              const unsigned qxy = __float_as_uint(b.x);
+              const float bx = (float)(px[k] - (int)(qxy & 0xffffu)) - b.y;
+              const float by = (float)(py[k] - (int)(qxy >> 16)) - b.z;
+              const float d = sqrtf(bx * bx + by * by);
+              if (d > 0.f) {
+                const float sgn = (idq[k] == g) ? 1.0f : -1.0f;
+                const float dl_drho = sgn * dl_dw * LN2 * wr.gamma;
+                const float isig = b.w;
+                const unsigned bidx = (unsigned)(bkeys[wr.best] & 0xffffffffull);
+                float *gb = reinterpret_cast<float *>(w.bg_grad + bidx);
+                atomicAdd(gb + 0, dl_drho * (-bx / d) * isig);
+                atomicAdd(gb + 1, dl_drho * (-by / d) * isig);
+                atomicAdd(gb + 2, dl_drho * (-wr.rho) * isig);
+              }
             }
           }
-        }
-        const unsigned ballot = __ballot_sync(0xffffffffu, any);
-        if (ballot) {
+          if (__any_sync(0xffffffffu, any)) {
 #pragma unroll
-          for (int q = 0; q < 9; q++) acc[q] = warp_sum(acc[q]);
-          if ((threadIdx.x & 31) == 0) {
-            float *gg = w.gg + 12 * (size_t)sG[sj];
+            for (int q = 0; q < 9; q++) acc[q] = warp_sum(acc[q]);
+            if (lane == 0) {
+              float *gg = w.gg + 12 * (size_t)sG[sj];
 #pragma unroll
-            for (int q = 0; q < 9; q++)
-              if (acc[q] != 0.f) atomicAdd(gg + q, acc[q]);
+              for (int q = 0; q < 9; q++)
+                if (acc[q] != 0.f) atomicAdd(gg + q, acc[q]);
+            }
           }
         }
       }

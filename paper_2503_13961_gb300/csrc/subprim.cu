@@ -251,19 +251,22 @@ __global__ void __launch_bounds__(kGenThreads) k_generate(Params p, Scene s, Wor
                         isfinite(Kc) && det > 0.f && tz > 0.f;
     if (!finite) atomicOr(w.status, kStatusNonFinite);
     uint2 rect = make_uint2(1u, 0u);
+    float rsup = -1.0f;
     if (finite && o > p.alpha_min) {
       // support {o G >= alpha_min} lies in the box |dx| <= sqrt(lvl Sigma_xx),
       // |dy| <= sqrt(lvl Sigma_yy), lvl = 2 ln(o / alpha_min); widened slightly
       const float lvl = 2.0f * (logf(o) - p.log_alpha_min);
       const float rx = sqrtf(lvl * cA) * 1.0001f + 1e-3f;
       const float ry = sqrtf(lvl * cC) * 1.0001f + 1e-3f;
+      rsup = fmaxf(rx, ry);
       rect = tile_rect((float)qx + off.x, (float)qy + off.y, rx, ry, vw, p.tile);
       if ((rect.x & 0xffff) <= (rect.y & 0xffff)) count_tiles(w.g_tcount, vw.tile_off, vw.tiles_x, rect);
     }
     const unsigned qxy = (unsigned)qx | ((unsigned)qy << 16);
     w.gA[gi] = make_float4(off.x, off.y, Ka, Kb);
     w.gB[gi] = make_float4(Kc, o, __uint_as_float(qxy), __int_as_float(prim));
-    w.gC[gi] = make_float4(col[0], col[1], col[2], tz);
+    w.gC[gi] = make_float4(col[0], col[1], col[2], rsup);
+    w.g_depth[gi] = tz;
     w.g_pix[gi] = pix;
     w.g_view[gi] = view;
     w.g_uv[gi] = uv;

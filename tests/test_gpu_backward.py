@@ -50,7 +50,12 @@ def _assert_close(got, ref, name):
     rel = grad_rel(got, ref)
     assert rel < GRAD_TOL, f"{name}: relative error {rel}"
     scale = np.abs(ref).max()
-    assert np.all(np.abs(got - ref) <= GRAD_TOL * np.abs(ref) + 1e-4 * scale), name
+    bad = np.abs(got - ref) > GRAD_TOL * np.abs(ref) + 1e-4 * scale
+    if bad.any():
+        idx = np.argsort(-(np.abs(got - ref) / (np.abs(ref) + 1e-4 * scale)).ravel())[:6]
+        worst = [(np.unravel_index(i, ref.shape), float(got.ravel()[i]), float(ref.ravel()[i])) for i in idx]
+        raise AssertionError(f"{name}: {int(bad.sum())} of {bad.size} elements off (scale {scale:.3g}); "
+                             f"worst (index, gpu, oracle): {worst}")
 
 
 CASES = [
