@@ -573,8 +573,8 @@ __global__ void k_pack_gauss(bgt::Work w, int F, float *out) {
   if (i >= F) return;
   const float4 A = w.gA[i], B = w.gB[i], C = w.gC[i];
   float *o = out + 12 * (size_t)i;
-  o[0] = A.x; o[1] = A.y; o[2] = A.z; o[3] = A.w;
-  o[4] = B.x; o[5] = B.y; o[6] = B.z; o[7] = B.w;
+  o[0] = A.x; o[1] = A.y; o[2] = B.x; o[3] = B.y;
+  o[4] = B.z; o[5] = B.w; o[6] = A.z; o[7] = C.w;
   o[8] = C.x; o[9] = C.y; o[10] = C.z; o[11] = w.g_depth[i];
 }
 
@@ -600,14 +600,14 @@ __global__ void k_load_gaussians(bgt::Params p, bgt::Work w, int count, const in
   const float Ka = conic[3 * i], Kb = conic[3 * i + 1], Kc = conic[3 * i + 2];
   const float o = opac[i];
   const unsigned q = (unsigned)qxy[i];
-  w.gA[i] = make_float4(off[2 * i], off[2 * i + 1], Ka, Kb);
-  w.gB[i] = make_float4(Kc, o, __uint_as_float(q), __int_as_float(0));
+  w.gA[i] = make_float4(off[2 * i], off[2 * i + 1], __uint_as_float(q), -1.0f);
+  w.gB[i] = make_float4(Ka, Kb, Kc, o);
+  w.gC[i] = make_float4(0.f, 0.f, 0.f, __int_as_float(0));
   w.g_depth[i] = depth[i];
   w.g_view[i] = 0;
   w.g_dsub[i] = 16;
   uint2 rect = make_uint2(1u, 0u);
   const float det = Ka * Kc - Kb * Kb;
-  w.gC[i] = make_float4(0.f, 0.f, 0.f, -1.0f);
   if (o > p.alpha_min && det > 0.f) {
     const float lvl = 2.0f * (logf(o) - p.log_alpha_min);
     const float rx = sqrtf(lvl * Kc / det) * 1.0001f + 1e-3f;
@@ -618,7 +618,7 @@ __global__ void k_load_gaussians(bgt::Params p, bgt::Work w, int count, const in
     if (x0 <= x1 && y0 <= y1) {
       x0 /= p.tile; x1 /= p.tile; y0 /= p.tile; y1 /= p.tile;
       rect = make_uint2((unsigned)x0 | ((unsigned)y0 << 16), (unsigned)x1 | ((unsigned)y1 << 16));
-      w.gC[i] = make_float4(0.f, 0.f, 0.f, fmaxf(rx, ry));
+      w.gA[i].w = fmaxf(rx, ry);
       for (int ty = y0; ty <= y1; ty++)
         for (int tx = x0; tx <= x1; tx++) atomicAdd(w.g_tcount + ty * vw.tiles_x + tx, 1);
     }

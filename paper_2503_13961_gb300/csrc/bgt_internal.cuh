@@ -61,10 +61,11 @@ struct Grads {                // device pointers, caller-owned outputs
 };
 
 // Gaussian record (one per foreground pixel), three float4 per Gaussian:
-//   A = (off_x, off_y, K_a, K_b)   mean = pixel centre + off; conic (a, b, c)
-//   B = (K_c, opacity, bits(qx | qy << 16), bits(prim))
-//   C = (r, g, b, support radius)  the support {o G >= alpha_min} lies inside
-//                                  the square of this half-width around the mean
+//   A = (off_x, off_y, bits(qx | qy << 16), support radius)
+//        mean = pixel centre (qx, qy) + off; the support {o G >= alpha_min}
+//        lies inside the square of this half-width around the mean
+//   B = (K_a, K_b, K_c, opacity)   conic of the projected Gaussian
+//   C = (r, g, b, bits(prim))
 // Boundary record (one per pixel of B):
 //   R = (bits(qx | qy << 16), off_x, off_y, 1 / sigma)
 struct Work {

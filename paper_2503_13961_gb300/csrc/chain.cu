@@ -88,15 +88,15 @@ __global__ void __launch_bounds__(256) k_chain_gauss(Params p, Scene s, Work w, 
       const float gmx = q0.x, gmy = q0.y, gKa = q0.z, gKb = q0.w, gKc = q1.x;
       gop = q1.y;
       gcol[0] = q1.z; gcol[1] = q1.w; gcol[2] = q2.x;
-      const float4 A = w.gA[i], Bq = w.gB[i];
-      g = __float_as_int(Bq.w);
+      const float4 Bq = w.gB[i];
+      g = __float_as_int(w.gC[i].w);
       const View vw = w.views[w.g_view[i]];
       const float2 uv = w.g_uv[i];
       float t[3];
       camera_point_f32(p.n, s.ctrl + (size_t)g * m * 3, uv.x, uv.y, vw, B, t);
       const bool any = gmx != 0.f || gmy != 0.f || gKa != 0.f || gKb != 0.f || gKc != 0.f;
       if (any) {
-        const float Ka = A.z, Kb = A.w, Kc = Bq.x;
+        const float Ka = Bq.x, Kb = Bq.y, Kc = Bq.z;
         const float tx = t[0], ty = t[1], tz = t[2];
         const float iz = 1.0f / tz, iz2 = iz * iz;
         // dl/dSigma2D = -K GK K, GK = [[gKa, gKb/2], [gKb/2, gKc]]

@@ -90,15 +90,6 @@ struct PairGeo {
   float dx, dy, power;
 };
 
-__device__ __forceinline__ PairGeo pair_geo(int px, int py, const float4 &A, const float4 &B) {
-  PairGeo p;
-  const unsigned qxy = __float_as_uint(B.z);
-  p.dx = __fsub_rn((float)(px - (int)(qxy & 0xffffu)), A.x);
-  p.dy = __fsub_rn((float)(py - (int)(qxy >> 16)), A.y);
-  const float q = __fmaf_rn(A.z, __fmul_rn(p.dx, p.dx), __fmul_rn(B.x, __fmul_rn(p.dy, p.dy)));
-  p.power = __fsub_rn(__fmul_rn(-0.5f, q), __fmul_rn(A.w, __fmul_rn(p.dx, p.dy)));
-  return p;
-}
 
 // two-entry cache of (primitive -> coefficient) per pixel, in registers
 struct WCache {
@@ -109,16 +100,33 @@ struct WCache {
     g0 = g1 = -2;
     flip = false;
   }
-  __device__ __forceinline__ WRes get(int g, int px, int py, int idq, const int *bprim, const float4 *brec,
-                                      int bn, int use_boundary) {
-    if (g == g0) return r0;
-    if (g == g1) return r1;
-    const WRes r = w_search(g, px, py, idq, bprim, brec, bn, use_boundary);
+  __device__ __forceinline__ bool lookup(int g, WRes &r) const {
+    if (g == g0) { r = r0; return true; }
+    if (g == g1) { r = r1; return true; }
+    return false;
+  }
+  __device__ __forceinline__ void insert(int g, const WRes &r) {
     if (flip) { g1 = g; r1 = r; } else { g0 = g; r0 = r; }
     flip = !flip;
-    return r;
   }
 };
+
+// Coefficient of the pair (pixel, Gaussian of primitive g) for the lanes
+// with `cand` set. Within a warp g is the same for every lane, so the lanes
+// that miss their cache run the same search loop together.
+__device__ __forceinline__ WRes w_coherent(WCache &c, bool cand, int g, int px, int py, int idq,
+                                           const int *bprim, const float4 *brec, int bn, int use_boundary) {
+  WRes r;
+  const bool have = c.lookup(g, r);
+  const bool need = cand && !have;
+  if (__any_sync(0xffffffffu, need)) {
+    if (need) {
+      r = w_search(g, px, py, idq, bprim, brec, bn, use_boundary);
+      c.insert(g, r);
+    }
+  }
+  return r;
+}
 
 struct TileInfo {
   int view, W, H, pix_off, x0, y0;
@@ -147,19 +155,42 @@ __device__ inline TileInfo tile_info(const Params &p, const Work &w, int tile, i
 }
 
 // does the support square of the Gaussian cover any pixel of [x0,x1] x [y0,y1]?
-__device__ __forceinline__ bool covers(const float4 &A, const float4 &B, const float4 &C, int x0, int x1,
-                                       int y0, int y1) {
-  const unsigned qxy = __float_as_uint(B.z);
+__device__ __forceinline__ bool covers(const float4 &A, int x0, int x1, int y0, int y1) {
+  const unsigned qxy = __float_as_uint(A.z);
   const float cx = (float)(int)(qxy & 0xffffu) + A.x, cy = (float)(int)(qxy >> 16) + A.y;
-  const float r = C.w;
+  const float r = A.w;
   return r >= 0.f && cx + r >= (float)x0 && cx - r <= (float)x1 && cy + r >= (float)y0 && cy - r <= (float)y1;
+}
+
+__device__ __forceinline__ PairGeo pair_geo2(int px, int py, const float4 &A, const float4 &B) {
+  PairGeo p;
+  const unsigned qxy = __float_as_uint(A.z);
+  p.dx = __fsub_rn((float)(px - (int)(qxy & 0xffffu)), A.x);
+  p.dy = __fsub_rn((float)(py - (int)(qxy >> 16)), A.y);
+  const float q = __fmaf_rn(B.x, __fmul_rn(p.dx, p.dx), __fmul_rn(B.z, __fmul_rn(p.dy, p.dy)));
+  p.power = __fsub_rn(__fmul_rn(-0.5f, q), __fmul_rn(B.y, __fmul_rn(p.dx, p.dy)));
+  return p;
+}
+
+template <int NT>
+__device__ __forceinline__ void load_boundary_cache(const TileInfo &ti, const Work &w, int *s_bprim, float4 *s_brec,
+                                                    const int *&bprim, const float4 *&brec) {
+  const bool bsm = ti.bn <= kBCap;
+  if (bsm) {
+    for (int i = threadIdx.x; i < ti.bn; i += NT) {
+      s_bprim[i] = w.bl_prim[ti.bs + i];
+      s_brec[i] = w.bl_rec[ti.bs + i];
+    }
+  }
+  bprim = bsm ? s_bprim : w.bl_prim + ti.bs;
+  brec = bsm ? s_brec : w.bl_rec + ti.bs;
 }
 
 template <int T>
 __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work w, float *image) {
   using Cfg = TileCfg<T>;
-  constexpr int NT = Cfg::NT, PPT = Cfg::PPT;
-  __shared__ float4 sA[NT], sB[NT], sC[NT];
+  constexpr int NT = Cfg::NT, NW = Cfg::NW, PPT = Cfg::PPT;
+  __shared__ float4 sA[NW][32], sB[NW][32], sC[NW][32];
   __shared__ int s_bprim[kBCap];
   __shared__ float4 s_brec[kBCap];
   __shared__ int s_tile;
@@ -171,17 +202,11 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work
     const int tile = s_tile;
     if (tile >= p.tiles) break;
     const TileInfo ti = tile_info(p, w, tile, T);
-    const bool bsm = ti.bn <= kBCap;
-    if (bsm) {
-      for (int i = threadIdx.x; i < ti.bn; i += NT) {
-        s_bprim[i] = w.bl_prim[ti.bs + i];
-        s_brec[i] = w.bl_rec[ti.bs + i];
-      }
-    }
-    const int *bprim = bsm ? s_bprim : w.bl_prim + ti.bs;
-    const float4 *brec = bsm ? s_brec : w.bl_rec + ti.bs;
+    const int *bprim;
+    const float4 *brec;
+    load_boundary_cache<NT>(ti, w, s_bprim, s_brec, bprim, brec);
+    __syncthreads();
     const int bn = (int)ti.bn;
-    // the warp's pixel block
     const int wx0 = ti.x0 + (warp % Cfg::WPR) * Cfg::WX, wy0 = ti.y0 + (warp / Cfg::WPR) * Cfg::WY;
     const int wx1 = wx0 + Cfg::WX - 1, wy1 = wy0 + Cfg::WY - 1;
 
@@ -204,58 +229,56 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work
       cache[k].reset();
     }
     const int gn = (int)ti.gn;
-    for (int b0 = 0; b0 < gn; b0 += NT) {
-      int alldone = 1;
+    for (int c0 = 0; c0 < gn; c0 += 32) {
+      bool alldone = true;
 #pragma unroll
-      for (int k = 0; k < PPT; k++) alldone &= done[k] ? 1 : 0;
-      if (__syncthreads_and(alldone)) break;
-      const int i = b0 + threadIdx.x;
-      if (i < gn) {
-        const unsigned gi = (unsigned)(w.gkeys[ti.gs + i] & kIndexMask);
-        sA[threadIdx.x] = w.gA[gi];
-        sB[threadIdx.x] = w.gB[gi];
-        sC[threadIdx.x] = w.gC[gi];
-      }
-      __syncthreads();
-      const int nb = min(NT, gn - b0);
-      for (int c0 = 0; c0 < nb; c0 += 32) {
-        if (__all_sync(0xffffffffu, alldone)) break;
-        const int jl = c0 + lane;
-        const bool hit = jl < nb && covers(sA[jl], sB[jl], sC[jl], wx0, wx1, wy0, wy1);
-        unsigned mask = __ballot_sync(0xffffffffu, hit);
-        while (mask) {
-          const int j = c0 + __ffs(mask) - 1;
-          mask &= mask - 1;
-          const float4 A = sA[j], B = sB[j];
-#pragma unroll
-          for (int k = 0; k < PPT; k++) {
-            if (done[k]) continue;
-            const PairGeo pg = pair_geo(px[k], py[k], A, B);
-            const float G = __expf(pg.power);
-            const float og = __fmul_rn(B.y, G);
-            if (og < p.alpha_min) continue;  // w <= 1: alpha < alpha_min
-            const int g = __float_as_int(B.w);
-            const WRes wr = cache[k].get(g, px[k], py[k], idq[k], bprim, brec, bn, p.use_boundary);
-            const float alpha = fminf(p.alpha_max, __fmul_rn(og, wr.w));
-            if (alpha < p.alpha_min) continue;
-            const float testT = __fmul_rn(Tr[k], __fsub_rn(1.0f, alpha));
-            if (testT < p.t_stop) {
-              done[k] = true;
-              continue;
-            }
-            const float4 Cc = sC[j];
-            const float ta = __fmul_rn(Tr[k], alpha);
-            C[k][0] = __fmaf_rn(ta, Cc.x, C[k][0]);
-            C[k][1] = __fmaf_rn(ta, Cc.y, C[k][1]);
-            C[k][2] = __fmaf_rn(ta, Cc.z, C[k][2]);
-            Tr[k] = testT;
-            last[k] = b0 + j + 1;
-          }
+      for (int k = 0; k < PPT; k++) alldone = alldone && done[k];
+      if (__all_sync(0xffffffffu, alldone)) break;
+      // stage the chunk's Gaussians that touch this warp's block
+      const int jl = c0 + lane;
+      bool hit = false;
+      if (jl < gn) {
+        const unsigned gi = (unsigned)(w.gkeys[ti.gs + jl] & kIndexMask);
+        const float4 A = w.gA[gi];
+        hit = covers(A, wx0, wx1, wy0, wy1);
+        if (hit) {
+          sA[warp][lane] = A;
+          sB[warp][lane] = w.gB[gi];
+          sC[warp][lane] = w.gC[gi];
         }
-        alldone = 1;
-#pragma unroll
-        for (int k = 0; k < PPT; k++) alldone &= done[k] ? 1 : 0;
       }
+      unsigned mask = __ballot_sync(0xffffffffu, hit);
+      __syncwarp();
+      while (mask) {
+        const int l = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const float4 A = sA[warp][l], B = sB[warp][l];
+        const int g = __float_as_int(sC[warp][l].w);
+#pragma unroll
+        for (int k = 0; k < PPT; k++) {
+          const PairGeo pg = pair_geo2(px[k], py[k], A, B);
+          const float G = __expf(pg.power);
+          const float og = __fmul_rn(B.w, G);
+          const bool cand = !done[k] && og >= p.alpha_min;  // w <= 1: else alpha < alpha_min
+          const WRes wr = w_coherent(cache[k], cand, g, px[k], py[k], idq[k], bprim, brec, bn, p.use_boundary);
+          if (!cand) continue;
+          const float alpha = fminf(p.alpha_max, __fmul_rn(og, wr.w));
+          if (alpha < p.alpha_min) continue;
+          const float testT = __fmul_rn(Tr[k], __fsub_rn(1.0f, alpha));
+          if (testT < p.t_stop) {
+            done[k] = true;
+            continue;
+          }
+          const float4 Cc = sC[warp][l];
+          const float ta = __fmul_rn(Tr[k], alpha);
+          C[k][0] = __fmaf_rn(ta, Cc.x, C[k][0]);
+          C[k][1] = __fmaf_rn(ta, Cc.y, C[k][1]);
+          C[k][2] = __fmaf_rn(ta, Cc.z, C[k][2]);
+          Tr[k] = testT;
+          last[k] = c0 + l + 1;
+        }
+      }
+      __syncwarp();
     }
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
@@ -280,39 +303,31 @@ __device__ __forceinline__ float warp_sum(float v) {
 template <int T>
 __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work w, const float *dimage) {
   using Cfg = TileCfg<T>;
-  constexpr int NT = Cfg::NT, PPT = Cfg::PPT;
-  __shared__ float4 sA[NT], sB[NT], sC[NT];
-  __shared__ int sG[NT];
+  constexpr int NT = Cfg::NT, NW = Cfg::NW, PPT = Cfg::PPT;
+  __shared__ float4 sA[NW][32], sB[NW][32], sC[NW][32];
+  __shared__ int sG[NW][32];
   __shared__ int s_bprim[kBCap];
   __shared__ float4 s_brec[kBCap];
-  __shared__ int s_tile, s_maxlast;
+  __shared__ int s_tile;
   const float LN2 = 0.69314718055994531f;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (;;) {
     __syncthreads();
-    if (threadIdx.x == 0) {
-      s_tile = atomicAdd(w.counters + kQueueBwd, 1);
-      s_maxlast = 0;
-    }
+    if (threadIdx.x == 0) s_tile = atomicAdd(w.counters + kQueueBwd, 1);
     __syncthreads();
     const int tile = s_tile;
     if (tile >= p.tiles) break;
     const TileInfo ti = tile_info(p, w, tile, T);
-    const bool bsm = ti.bn <= kBCap;
-    if (bsm) {
-      for (int i = threadIdx.x; i < ti.bn; i += NT) {
-        s_bprim[i] = w.bl_prim[ti.bs + i];
-        s_brec[i] = w.bl_rec[ti.bs + i];
-      }
-    }
-    const int *bprim = bsm ? s_bprim : w.bl_prim + ti.bs;
-    const float4 *brec = bsm ? s_brec : w.bl_rec + ti.bs;
+    const int *bprim;
+    const float4 *brec;
+    load_boundary_cache<NT>(ti, w, s_bprim, s_brec, bprim, brec);
+    __syncthreads();
     const unsigned long long *bkeys = w.bkeys + ti.bs;
     const int bn = (int)ti.bn;
     const int wx0 = ti.x0 + (warp % Cfg::WPR) * Cfg::WX, wy0 = ti.y0 + (warp / Cfg::WPR) * Cfg::WY;
     const int wx1 = wx0 + Cfg::WX - 1, wy1 = wy0 + Cfg::WY - 1;
 
-    // R: colour behind the current pair seen through the pairs behind it
+    // R: colour behind the current pair, seen through the pairs behind it
     float Tr[PPT], R[PPT][3], dC[PPT][3];
     int last[PPT], idq[PPT], px[PPT], py[PPT];
     WCache cache[PPT];
@@ -345,105 +360,100 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
     int wlast = mylast;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wlast = max(wlast, __shfl_xor_sync(0xffffffffu, wlast, o));
-    if (lane == 0) atomicMax(&s_maxlast, wlast);
-    __syncthreads();
-    const int maxlast = s_maxlast;
-    for (int b1 = maxlast; b1 > 0; b1 -= NT) {
-      const int b0 = max(0, b1 - NT);
-      const int i = b0 + threadIdx.x;
-      __syncthreads();
-      if (i < b1) {
-        const unsigned gi = (unsigned)(w.gkeys[ti.gs + i] & kIndexMask);
-        sG[threadIdx.x] = (int)gi;
-        sA[threadIdx.x] = w.gA[gi];
-        sB[threadIdx.x] = w.gB[gi];
-        sC[threadIdx.x] = w.gC[gi];
+    for (int c1 = wlast; c1 > 0; c1 -= 32) {
+      const int c0 = max(0, c1 - 32);
+      const int jl = c0 + lane;
+      bool hit = false;
+      if (jl < c1) {
+        const unsigned gi = (unsigned)(w.gkeys[ti.gs + jl] & kIndexMask);
+        const float4 A = w.gA[gi];
+        hit = covers(A, wx0, wx1, wy0, wy1);
+        if (hit) {
+          sA[warp][lane] = A;
+          sB[warp][lane] = w.gB[gi];
+          sC[warp][lane] = w.gC[gi];
+          sG[warp][lane] = (int)gi;
+        }
       }
-      __syncthreads();
-      const int cend = min(b1, wlast);  // this warp's pixels composited nothing at or beyond wlast
-      for (int c1 = cend; c1 > b0; c1 -= 32) {
-        const int c0 = max(b0, c1 - 32);
-        const int jl = c0 + lane;
-        const bool hit = jl < c1 && covers(sA[jl - b0], sB[jl - b0], sC[jl - b0], wx0, wx1, wy0, wy1);
-        unsigned mask = __ballot_sync(0xffffffffu, hit);
-        while (mask) {
-          const int bit = 31 - __clz(mask);
-          mask &= ~(1u << bit);
-          const int j = c0 + bit;
-          const int sj = j - b0;
-          const float4 A = sA[sj], B = sB[sj], Cc = sC[sj];
-          const int g = __float_as_int(B.w);
-          float acc[9];
+      unsigned mask = __ballot_sync(0xffffffffu, hit);
+      __syncwarp();
+      while (mask) {
+        const int l = 31 - __clz(mask);
+        mask &= ~(1u << l);
+        const int j = c0 + l;
+        const float4 A = sA[warp][l], B = sB[warp][l], Cc = sC[warp][l];
+        const int g = __float_as_int(Cc.w);
+        float acc[9];
 #pragma unroll
-          for (int q = 0; q < 9; q++) acc[q] = 0.f;
-          bool any = false;
+        for (int q = 0; q < 9; q++) acc[q] = 0.f;
+        bool any = false;
 #pragma unroll
-          for (int k = 0; k < PPT; k++) {
-            if (j >= last[k]) continue;
-            const PairGeo pg = pair_geo(px[k], py[k], A, B);
-            const float G = __expf(pg.power);
-            const float og = __fmul_rn(B.y, G);
-            if (og < p.alpha_min) continue;
-            const WRes wr = cache[k].get(g, px[k], py[k], idq[k], bprim, brec, bn, p.use_boundary);
-            const float raw = __fmul_rn(og, wr.w);
-            const float alpha = fminf(p.alpha_max, raw);
-            if (alpha < p.alpha_min) continue;
-            any = true;
-            const float oma = 1.0f - alpha;
-            Tr[k] = Tr[k] / oma;  // T_i
-            const float ta = Tr[k] * alpha;
-            // dl/dalpha_i = dl/dC . (T_i c_i - S_i / (1 - alpha_i)) with
-            // S_i / (1 - alpha_i) = T_i R_i, R <- alpha_i c_i + (1 - alpha_i) R:
-            // the form T_i (c_i - R_i) avoids amplifying rounding by 1 / (1 - alpha_i)
-            float dl_da = 0.f;
-            const float col[3] = {Cc.x, Cc.y, Cc.z};
+        for (int k = 0; k < PPT; k++) {
+          const PairGeo pg = pair_geo2(px[k], py[k], A, B);
+          const float G = __expf(pg.power);
+          const float og = __fmul_rn(B.w, G);
+          const bool cand = j < last[k] && og >= p.alpha_min;
+          const WRes wr = w_coherent(cache[k], cand, g, px[k], py[k], idq[k], bprim, brec, bn, p.use_boundary);
+          if (!cand) continue;
+          const float raw = __fmul_rn(og, wr.w);
+          const float alpha = fminf(p.alpha_max, raw);
+          if (alpha < p.alpha_min) continue;
+          any = true;
+          const float oma = 1.0f - alpha;
+          Tr[k] = Tr[k] / oma;  // T_i
+          const float ta = Tr[k] * alpha;
+          // dl/dalpha_i = dl/dC . (T_i c_i - S_i / (1 - alpha_i)) with
+          // S_i / (1 - alpha_i) = T_i R_i, R <- alpha_i c_i + (1 - alpha_i) R:
+          // the form T_i (c_i - R_i) avoids amplifying rounding by 1 / (1 - alpha_i)
+          float dl_da = 0.f;
+          const float col[3] = {Cc.x, Cc.y, Cc.z};
 #pragma unroll
-            for (int c = 0; c < 3; c++) {
-              acc[6 + c] += ta * dC[k][c];
-              dl_da += dC[k][c] * (col[c] - R[k][c]);
-              R[k][c] = alpha * col[c] + oma * R[k][c];
-            }
-            dl_da *= Tr[k];
-            if (raw >= p.alpha_max) continue;  // clamped: alpha is constant
-            acc[5] += dl_da * wr.w * G;
-            const float dl_dw = dl_da * B.y * G;
-            const float dl_dpow = dl_da * og * wr.w;
-            const float dx = pg.dx, dy = pg.dy;  // q - mu
-            acc[2] += dl_dpow * (-0.5f * dx * dx);
-            acc[3] += dl_dpow * (-dx * dy);
-            acc[4] += dl_dpow * (-0.5f * dy * dy);
-            acc[0] += dl_dpow * (A.z * dx + A.w * dy);
-            acc[1] += dl_dpow * (A.w * dx + B.x * dy);
-            if (wr.best >= 0 && wr.rho < 1.0f) {
-              const float4 b = brec[wr.best];
-              const unsigned qxy = __float_as_uint(b.x);
-              const float bx = (float)(px[k] - (int)(qxy & 0xffffu)) - b.y;
-              const float by = (float)(py[k] - (int)(qxy >> 16)) - b.z;
-              const float d = sqrtf(bx * bx + by * by);
-              if (d > 0.f) {
-                const float sgn = (idq[k] == g) ? 1.0f : -1.0f;
-                const float dl_drho = sgn * dl_dw * LN2 * wr.gamma;
-                const float isig = b.w;
-                const unsigned bidx = (unsigned)(bkeys[wr.best] & 0xffffffffull);
-                float *gb = reinterpret_cast<float *>(w.bg_grad + bidx);
-                atomicAdd(gb + 0, dl_drho * (-bx / d) * isig);
-                atomicAdd(gb + 1, dl_drho * (-by / d) * isig);
-                atomicAdd(gb + 2, dl_drho * (-wr.rho) * isig);
-              }
-            }
+          for (int c = 0; c < 3; c++) {
+            acc[6 + c] += ta * dC[k][c];
+            dl_da += dC[k][c] * (col[c] - R[k][c]);
+            R[k][c] = alpha * col[c] + oma * R[k][c];
           }
-          if (__any_sync(0xffffffffu, any)) {
-#pragma unroll
-            for (int q = 0; q < 9; q++) acc[q] = warp_sum(acc[q]);
-            if (lane == 0) {
-              float *gg = w.gg + 12 * (size_t)sG[sj];
-#pragma unroll
-              for (int q = 0; q < 9; q++)
-                if (acc[q] != 0.f) atomicAdd(gg + q, acc[q]);
+          dl_da *= Tr[k];
+          if (raw >= p.alpha_max) continue;  // clamped: alpha is constant
+          acc[5] += dl_da * wr.w * G;
+          const float dl_dw = dl_da * B.w * G;
+          const float dl_dpow = dl_da * og * wr.w;
+          const float dx = pg.dx, dy = pg.dy;  // q - mu
+          acc[2] += dl_dpow * (-0.5f * dx * dx);
+          acc[3] += dl_dpow * (-dx * dy);
+          acc[4] += dl_dpow * (-0.5f * dy * dy);
+          acc[0] += dl_dpow * (B.x * dx + B.y * dy);
+          acc[1] += dl_dpow * (B.y * dx + B.z * dy);
+          if (wr.best >= 0 && wr.rho < 1.0f) {
+            const float4 b = brec[wr.best];
+            const unsigned qxy = __float_as_uint(b.x);
+            const float bx = (float)(px[k] - (int)(qxy & 0xffffu)) - b.y;
+            const float by = (float)(py[k] - (int)(qxy >> 16)) - b.z;
+            const float d = sqrtf(bx * bx + by * by);
+            if (d > 0.f) {
+              const float sgn = (idq[k] == g) ? 1.0f : -1.0f;
+              const float dl_drho = sgn * dl_dw * LN2 * wr.gamma;
+              const float isig = b.w;
+              const unsigned bidx = (unsigned)(bkeys[wr.best] & 0xffffffffull);
+              float *gb = reinterpret_cast<float *>(w.bg_grad + bidx);
+              atomicAdd(gb + 0, dl_drho * (-bx / d) * isig);
+              atomicAdd(gb + 1, dl_drho * (-by / d) * isig);
+              atomicAdd(gb + 2, dl_drho * (-wr.rho) * isig);
             }
           }
         }
+        if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+          for (int q = 0; q < 9; q++) acc[q] = warp_sum(acc[q]);
+          if (lane == 0) {
+            float *gg = w.gg + 12 * (size_t)sG[warp][l];
+#pragma unroll
+            for (int q = 0; q < 9; q++)
+              if (acc[q] != 0.f) atomicAdd(gg + q, acc[q]);
+          }
+        }
       }
+      __syncwarp();
     }
   }
 }

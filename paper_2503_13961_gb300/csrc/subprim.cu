@@ -263,9 +263,9 @@ __global__ void __launch_bounds__(kGenThreads) k_generate(Params p, Scene s, Wor
       if ((rect.x & 0xffff) <= (rect.y & 0xffff)) count_tiles(w.g_tcount, vw.tile_off, vw.tiles_x, rect);
     }
     const unsigned qxy = (unsigned)qx | ((unsigned)qy << 16);
-    w.gA[gi] = make_float4(off.x, off.y, Ka, Kb);
-    w.gB[gi] = make_float4(Kc, o, __uint_as_float(qxy), __int_as_float(prim));
-    w.gC[gi] = make_float4(col[0], col[1], col[2], rsup);
+    w.gA[gi] = make_float4(off.x, off.y, __uint_as_float(qxy), rsup);
+    w.gB[gi] = make_float4(Ka, Kb, Kc, o);
+    w.gC[gi] = make_float4(col[0], col[1], col[2], __int_as_float(prim));
     w.g_depth[gi] = tz;
     w.g_pix[gi] = pix;
     w.g_view[gi] = view;

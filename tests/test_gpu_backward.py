@@ -3,8 +3,11 @@
 Upstream gradients dl/dC are seeded normals, set to zero at pixels the oracle
 flags as within rounding distance of a discrete decision (cutoffs, stop,
 depth order, gamma saturation, a near-tie of the most influential boundary
-point, or |q - b*| ~ 0 where the direction of dl/db is ill-conditioned), so
-both sides differentiate the same piecewise-smooth function. Gradients are
+point), so both sides differentiate the same piecewise-smooth function.
+Pixels whose most influential boundary point lies within D_TOL = 5e-3 px are
+excluded too: dl/db of Eq. 6 points along (q - b)/|q - b|, and the FP32
+I_uv of the GPU places b ~1e-6 px away from the oracle's, which turns that
+direction by ~1e-6 / |q - b|. Gradients are
 compared to the oracle's analytic gradient (relative 1e-3 in norm, plus an
 elementwise bound) and to central finite differences of the oracle.
 """
@@ -15,13 +18,15 @@ from tests.gpu_util import GRAD_TOL, gpu_forward, grad_rel, make_renderer, split
 
 pytestmark = pytest.mark.gpu
 
+D_TOL = 5e-3
+
 
 def _run(oracle, sc, cams, seed=0, tile=16, use_boundary=True):
     import torch
     g = gpu_forward(sc, cams, tile=tile, use_boundary=use_boundary, stages=())
     rd, dev = g["renderer"], g["dev"]
     rng = np.random.default_rng(seed)
-    opts = {"use_boundary": 1 if use_boundary else 0}
+    opts = {"use_boundary": 1 if use_boundary else 0, "tol_d": D_TOL}
     dls, refs = [], []
     for c in cams:
         ref = oracle.render(sc, c, opts=opts)
@@ -50,9 +55,10 @@ def _assert_close(got, ref, name):
     rel = grad_rel(got, ref)
     assert rel < GRAD_TOL, f"{name}: relative error {rel}"
     scale = np.abs(ref).max()
-    bad = np.abs(got - ref) > GRAD_TOL * np.abs(ref) + 1e-4 * scale
+    bound = GRAD_TOL * np.abs(ref) + 1e-4 * scale
+    bad = np.abs(got - ref) > bound
     if bad.any():
-        idx = np.argsort(-(np.abs(got - ref) / (np.abs(ref) + 1e-4 * scale)).ravel())[:6]
+        idx = np.argsort(-(np.abs(got - ref) / bound).ravel())[:6]
         worst = [(np.unravel_index(i, ref.shape), float(got.ravel()[i]), float(ref.ravel()[i])) for i in idx]
         raise AssertionError(f"{name}: {int(bad.sum())} of {bad.size} elements off (scale {scale:.3g}); "
                              f"worst (index, gpu, oracle): {worst}")
