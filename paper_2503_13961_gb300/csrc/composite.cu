@@ -36,6 +36,7 @@ struct TileCfg {
   static constexpr int WX = (T == 32) ? 16 : 8;
   static constexpr int WY = (T == 32) ? 8 : 4;
   static constexpr int WPR = T / WX;         // warp blocks per tile row
+  static constexpr int NC = (PPT == 1) ? 8 : 4;  // coefficient cache entries per pixel
 };
 
 template <int T>
@@ -91,42 +92,52 @@ struct PairGeo {
 };
 
 
-// two-entry cache of (primitive -> coefficient) per pixel, in registers
-struct WCache {
-  int g0, g1;
-  WRes r0, r1;
-  bool flip;
+// Warp-uniform cache of (primitive -> coefficient). All lanes of a warp hold
+// the same primitive ids; each lane holds its own pixel's w and most
+// influential boundary entry for them. On a miss every lane of the warp runs
+// the same search (same primitive, same candidate list), so the search never
+// diverges, and each primitive is searched about once per warp block.
+template <int NC>
+struct WarpCache {
+  int key[NC];
+  float w[NC];
+  int best[NC];
+  int next;
   __device__ __forceinline__ void reset() {
-    g0 = g1 = -2;
-    flip = false;
+#pragma unroll
+    for (int e = 0; e < NC; e++) key[e] = -2;
+    next = 0;
   }
-  __device__ __forceinline__ bool lookup(int g, WRes &r) const {
-    if (g == g0) { r = r0; return true; }
-    if (g == g1) { r = r1; return true; }
-    return false;
-  }
-  __device__ __forceinline__ void insert(int g, const WRes &r) {
-    if (flip) { g1 = g; r1 = r; } else { g0 = g; r0 = r; }
-    flip = !flip;
+  // coefficient of primitive g for this lane's pixel; must be called by all lanes
+  // with the same g
+  __device__ __forceinline__ void get(int g, int px, int py, int idq, const int *bprim, const float4 *brec, int bn,
+                                      int use_boundary, float &wv, int &bi) {
+    int hit = -1;
+#pragma unroll
+    for (int e = 0; e < NC; e++) hit = (key[e] == g) ? e : hit;
+    if (hit >= 0) {
+      wv = w[0];
+      bi = best[0];
+#pragma unroll
+      for (int e = 1; e < NC; e++) {
+        wv = (hit == e) ? w[e] : wv;
+        bi = (hit == e) ? best[e] : bi;
+      }
+      return;
+    }
+    const WRes r = w_search(g, px, py, idq, bprim, brec, bn, use_boundary);
+    wv = r.w;
+    bi = (r.best >= 0 && r.rho < 1.0f) ? r.best : -1;
+#pragma unroll
+    for (int e = 0; e < NC; e++)
+      if (e == next) {
+        key[e] = g;
+        w[e] = wv;
+        best[e] = bi;
+      }
+    next = (next + 1 == NC) ? 0 : next + 1;
   }
 };
-
-// Coefficient of the pair (pixel, Gaussian of primitive g) for the lanes
-// with `cand` set. Within a warp g is the same for every lane, so the lanes
-// that miss their cache run the same search loop together.
-__device__ __forceinline__ WRes w_coherent(WCache &c, bool cand, int g, int px, int py, int idq,
-                                           const int *bprim, const float4 *brec, int bn, int use_boundary) {
-  WRes r;
-  const bool have = c.lookup(g, r);
-  const bool need = cand && !have;
-  if (__any_sync(0xffffffffu, need)) {
-    if (need) {
-      r = w_search(g, px, py, idq, bprim, brec, bn, use_boundary);
-      c.insert(g, r);
-    }
-  }
-  return r;
-}
 
 struct TileInfo {
   int view, W, H, pix_off, x0, y0;
@@ -213,7 +224,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work
     float C[PPT][3], Tr[PPT];
     int last[PPT], idq[PPT], px[PPT], py[PPT];
     bool done[PPT];
-    WCache cache[PPT];
+    WarpCache<Cfg::NC> cache[PPT];
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
       int lx, ly;
@@ -260,9 +271,12 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work
           const float G = __expf(pg.power);
           const float og = __fmul_rn(B.w, G);
           const bool cand = !done[k] && og >= p.alpha_min;  // w <= 1: else alpha < alpha_min
-          const WRes wr = w_coherent(cache[k], cand, g, px[k], py[k], idq[k], bprim, brec, bn, p.use_boundary);
+          if (!__any_sync(0xffffffffu, cand)) continue;
+          float wv;
+          int bi;
+          cache[k].get(g, px[k], py[k], idq[k], bprim, brec, bn, p.use_boundary, wv, bi);
           if (!cand) continue;
-          const float alpha = fminf(p.alpha_max, __fmul_rn(og, wr.w));
+          const float alpha = fminf(p.alpha_max, __fmul_rn(og, wv));
           if (alpha < p.alpha_min) continue;
           const float testT = __fmul_rn(Tr[k], __fsub_rn(1.0f, alpha));
           if (testT < p.t_stop) {
@@ -330,7 +344,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
     // R: colour behind the current pair, seen through the pairs behind it
     float Tr[PPT], R[PPT][3], dC[PPT][3];
     int last[PPT], idq[PPT], px[PPT], py[PPT];
-    WCache cache[PPT];
+    WarpCache<Cfg::NC> cache[PPT];
     int mylast = 0;
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
@@ -393,9 +407,12 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
           const float G = __expf(pg.power);
           const float og = __fmul_rn(B.w, G);
           const bool cand = j < last[k] && og >= p.alpha_min;
-          const WRes wr = w_coherent(cache[k], cand, g, px[k], py[k], idq[k], bprim, brec, bn, p.use_boundary);
+          if (!__any_sync(0xffffffffu, cand)) continue;
+          float wv;
+          int bi;
+          cache[k].get(g, px[k], py[k], idq[k], bprim, brec, bn, p.use_boundary, wv, bi);
           if (!cand) continue;
-          const float raw = __fmul_rn(og, wr.w);
+          const float raw = __fmul_rn(og, wv);
           const float alpha = fminf(p.alpha_max, raw);
           if (alpha < p.alpha_min) continue;
           any = true;
@@ -415,30 +432,35 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
           }
           dl_da *= Tr[k];
           if (raw >= p.alpha_max) continue;  // clamped: alpha is constant
-          acc[5] += dl_da * wr.w * G;
+          acc[5] += dl_da * wv * G;
           const float dl_dw = dl_da * B.w * G;
-          const float dl_dpow = dl_da * og * wr.w;
+          const float dl_dpow = dl_da * og * wv;
           const float dx = pg.dx, dy = pg.dy;  // q - mu
           acc[2] += dl_dpow * (-0.5f * dx * dx);
           acc[3] += dl_dpow * (-dx * dy);
           acc[4] += dl_dpow * (-0.5f * dy * dy);
           acc[0] += dl_dpow * (B.x * dx + B.y * dy);
           acc[1] += dl_dpow * (B.y * dx + B.z * dy);
-          if (wr.best >= 0 && wr.rho < 1.0f) {
-            const float4 b = brec[wr.best];
+          if (bi >= 0) {
+            // rho and gamma of the most influential boundary point, by the
+            // same operations as the search
+            const float4 b = brec[bi];
             const unsigned qxy = __float_as_uint(b.x);
-            const float bx = (float)(px[k] - (int)(qxy & 0xffffu)) - b.y;
-            const float by = (float)(py[k] - (int)(qxy >> 16)) - b.z;
+            const float bx = __fsub_rn((float)(px[k] - (int)(qxy & 0xffffu)), b.y);
+            const float by = __fsub_rn((float)(py[k] - (int)(qxy >> 16)), b.z);
+            const float r2 = __fmul_rn(__fmaf_rn(bx, bx, __fmul_rn(by, by)), __fmul_rn(b.w, b.w));
+            const float rho = __fsqrt_rn(r2);
+            const float gam = exp2f(__fsub_rn(rho, 1.0f));
             const float d = sqrtf(bx * bx + by * by);
             if (d > 0.f) {
               const float sgn = (idq[k] == g) ? 1.0f : -1.0f;
-              const float dl_drho = sgn * dl_dw * LN2 * wr.gamma;
+              const float dl_drho = sgn * dl_dw * LN2 * gam;
               const float isig = b.w;
-              const unsigned bidx = (unsigned)(bkeys[wr.best] & 0xffffffffull);
+              const unsigned bidx = (unsigned)(bkeys[bi] & 0xffffffffull);
               float *gb = reinterpret_cast<float *>(w.bg_grad + bidx);
               atomicAdd(gb + 0, dl_drho * (-bx / d) * isig);
               atomicAdd(gb + 1, dl_drho * (-by / d) * isig);
-              atomicAdd(gb + 2, dl_drho * (-wr.rho) * isig);
+              atomicAdd(gb + 2, dl_drho * (-rho) * isig);
             }
           }
         }
