@@ -101,6 +101,7 @@ struct Work {
   int *b_tcount, *b_tfill;
   long long *g_tstart, *b_tstart;  // [tiles + 1] exclusive prefix sums (64-bit: no wrap)
   long long *scan_aux, *scan_aux2; // scratch of the two tile-count scans
+  int *big_list;              // [2 tiles] segments too long for one warp to sort
   // pairs
   unsigned long long *gkeys;  // [Kcap] depth key (FP32 bits << 5 | sub) << 27 | gaussian index
   unsigned long long *bkeys;  // [Kbcap] (prim << 32) | boundary index
@@ -119,7 +120,7 @@ struct Work {
 constexpr int kIndexBits = 27;  // Gaussian index field of a pair key (<= 134M Gaussians per call)
 constexpr unsigned long long kIndexMask = (1ull << kIndexBits) - 1ull;
 
-enum Counter { kF = 0, kNb = 1, kK = 2, kKb = 3, kQueueFwd = 4, kQueueBwd = 5, kQueueSort = 6 };
+enum Counter { kF = 0, kNb = 1, kK = 2, kKb = 3, kQueueFwd = 4, kQueueBwd = 5, kQueueSort = 6, kBigCount = 7 };
 
 // ---------------------------------------------------------------------------
 // small helpers

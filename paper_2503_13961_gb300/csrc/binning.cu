@@ -231,45 +231,117 @@ __device__ void radix_global(unsigned long long *keys, unsigned long long *tmp, 
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_tile_sort(Params p, Work w, unsigned long long *gtmp,
-                                                           unsigned long long *btmp) {
+constexpr int kWarpSortCap = 512;  // keys a single warp sorts in its own shared memory
+
+__device__ inline void segment_bounds(const Params &p, const Work &w, int item, bool &bnd, long long &s0,
+                                      long long &s1) {
+  bnd = item >= p.tiles;
+  const int tile = bnd ? item - p.tiles : item;
+  const long long *start = bnd ? w.b_tstart : w.g_tstart;
+  const long long cap = bnd ? p.max_bpairs : p.max_pairs;
+  s0 = start[tile];
+  s1 = start[tile + 1];
+  s0 = s0 < 0 ? 0 : (s0 > cap ? cap : s0);
+  s1 = s1 < s0 ? s0 : (s1 > cap ? cap : s1);
+}
+
+__device__ inline void gather_boundary(const Work &w, long long s0, long long s1, int lane, int step) {
+  for (long long i = s0 + lane; i < s1; i += step) {
+    const unsigned long long k = w.bkeys[i];
+    w.bl_prim[i] = (int)(k >> 32);
+    w.bl_rec[i] = w.bR[(unsigned)(k & 0xffffffffu)];
+  }
+}
+
+// Warps take segments from a queue. Up to 32 keys: bitonic sort across the
+// lanes' registers; up to kWarpSortCap: bitonic sort in the warp's shared
+// memory; longer segments are appended to a list for k_tile_sort_big.
+__global__ void __launch_bounds__(kSortThreads) k_tile_sort(Params p, Work w, int *big_list) {
+  __shared__ unsigned long long s_keys[kSortThreads / 32][kWarpSortCap];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const bool g_over = w.g_tstart[p.tiles] > p.max_pairs, b_over = w.b_tstart[p.tiles] > p.max_bpairs;
+  const int items = 2 * p.tiles;
+  unsigned long long *sk = s_keys[wp];
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(w.counters + kQueueSort, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= items) break;
+    bool bnd;
+    long long s0, s1;
+    segment_bounds(p, w, item, bnd, s0, s1);
+    if (bnd ? b_over : g_over) continue;  // unwritten slots: nothing to sort
+    const int n = (int)(s1 - s0);
+    unsigned long long *keys = (bnd ? w.bkeys : w.gkeys) + s0;
+    if (n > kWarpSortCap) {
+      if (lane == 0) big_list[atomicAdd(w.counters + kQueueSort + 1, 1)] = item;
+      continue;
+    }
+    if (n > 1 && n <= 32) {
+      unsigned long long key = lane < n ? keys[lane] : ~0ull;
+      for (int k = 2; k <= 32; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          const unsigned long long other = __shfl_xor_sync(0xffffffffu, key, j);
+          const bool up = (lane & k) == 0;
+          const bool lower = (lane & j) == 0;
+          key = (lower == up) ? (key < other ? key : other) : (key < other ? other : key);
+        }
+      if (lane < n) keys[lane] = key;
+    } else if (n > 32) {
+      int N = 64;
+      while (N < n) N <<= 1;
+      for (int i = lane; i < N; i += 32) sk[i] = i < n ? keys[i] : ~0ull;
+      __syncwarp();
+      for (int k = 2; k <= N; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          for (int i = lane; i < N; i += 32) {
+            const int ixj = i ^ j;
+            if (ixj > i) {
+              const unsigned long long a = sk[i], b = sk[ixj];
+              if ((a > b) == ((i & k) == 0)) {
+                sk[i] = b;
+                sk[ixj] = a;
+              }
+            }
+          }
+          __syncwarp();
+        }
+      for (int i = lane; i < n; i += 32) keys[i] = sk[i];
+      __syncwarp();
+    }
+    if (bnd) {
+      __syncwarp();
+      gather_boundary(w, s0, s1, lane, 32);
+    }
+  }
+}
+
+// Segments longer than one warp's capacity: one block each (bitonic in
+// shared memory up to kSortCap keys, stable radix sort in global memory beyond).
+__global__ void __launch_bounds__(kSortThreads) k_tile_sort_big(Params p, Work w, const int *big_list,
+                                                               unsigned long long *gtmp, unsigned long long *btmp) {
   __shared__ unsigned long long s_keys[kSortCap];
   __shared__ int s_hist[256], s_base[256];
   __shared__ int s_wcnt[(kSortThreads / 32) * 256];
   __shared__ unsigned long long s_red[2 * (kSortThreads / 32)];
-  const int items = 2 * p.tiles;
-  // an overflowed call leaves key slots unwritten: treat its lists as empty
-  const bool g_over = w.g_tstart[p.tiles] > p.max_pairs, b_over = w.b_tstart[p.tiles] > p.max_bpairs;
-  for (int item = blockIdx.x; item < items; item += gridDim.x) {
-    const bool bnd = item >= p.tiles;
-    const int tile = bnd ? item - p.tiles : item;
-    if (bnd ? b_over : g_over) continue;
-    const long long *start = bnd ? w.b_tstart : w.g_tstart;
-    const long long cap = bnd ? p.max_bpairs : p.max_pairs;
-    unsigned long long *keys = bnd ? w.bkeys : w.gkeys;
-    unsigned long long *tmp = bnd ? btmp : gtmp;
-    long long s0 = start[tile], s1 = start[tile + 1];
-    s0 = s0 < 0 ? 0 : (s0 > cap ? cap : s0);
-    s1 = s1 < s0 ? s0 : (s1 > cap ? cap : s1);
+  const int nbig = w.counters[kQueueSort + 1];
+  for (int b = blockIdx.x; b < nbig; b += gridDim.x) {
+    bool bnd;
+    long long s0, s1;
+    segment_bounds(p, w, big_list[b], bnd, s0, s1);
     const int n = (int)(s1 - s0);
-    if (n > 1) {
-      if (n <= kSortCap) {
-        for (int i = threadIdx.x; i < n; i += kSortThreads) s_keys[i] = keys[s0 + i];
-        __syncthreads();
-        bitonic_smem(s_keys, n);
-        for (int i = threadIdx.x; i < n; i += kSortThreads) keys[s0 + i] = s_keys[i];
-      } else {
-        radix_global(keys + s0, tmp + s0, n, s_hist, s_base, s_wcnt, s_red);
-      }
+    unsigned long long *keys = (bnd ? w.bkeys : w.gkeys) + s0;
+    unsigned long long *tmp = (bnd ? btmp : gtmp) + s0;
+    if (n <= kSortCap) {
+      for (int i = threadIdx.x; i < n; i += kSortThreads) s_keys[i] = keys[i];
       __syncthreads();
+      bitonic_smem(s_keys, n);
+      for (int i = threadIdx.x; i < n; i += kSortThreads) keys[i] = s_keys[i];
+    } else {
+      radix_global(keys, tmp, n, s_hist, s_base, s_wcnt, s_red);
     }
-    if (bnd) {
-      for (int i = threadIdx.x; i < n; i += kSortThreads) {
-        const unsigned long long k = keys[s0 + i];
-        w.bl_prim[s0 + i] = (int)(k >> 32);
-        w.bl_rec[s0 + i] = w.bR[(unsigned)(k & 0xffffffffu)];
-      }
-    }
+    __syncthreads();
+    if (bnd) gather_boundary(w, s0, s1, threadIdx.x, kSortThreads);
     __syncthreads();
   }
 }
@@ -291,10 +363,11 @@ int launch_exclusive_scan(const int *in, long long *out, int n, long long *aux, 
 
 int launch_bin_sort_only(const Params &p, const Work &w, cudaStream_t st) {
   k_emit<<<4 * 152, 256, 0, st>>>(p, w);
-  int grid = 2 * p.tiles;
-  if (grid > 8 * 152) grid = 8 * 152;
-  if (grid > 0) k_tile_sort<<<grid, kSortThreads, 0, st>>>(p, w, w.gkeys + p.max_pairs, w.bkeys + p.max_bpairs);
-  return grid > 0 ? 2 : 1;
+  if (p.tiles <= 0) return 1;
+  cudaMemsetAsync(w.counters + kQueueSort, 0, 2 * sizeof(int), st);
+  k_tile_sort<<<4 * 152, kSortThreads, 0, st>>>(p, w, w.big_list);
+  k_tile_sort_big<<<2 * 152, kSortThreads, 0, st>>>(p, w, w.big_list, w.gkeys + p.max_pairs, w.bkeys + p.max_bpairs);
+  return 3;
 }
 
 int launch_binning(const Params &p, const Work &w, cudaStream_t st) {

@@ -97,11 +97,11 @@ struct PairGeo {
 // influential boundary entry for them. On a miss every lane of the warp runs
 // the same search (same primitive, same candidate list), so the search never
 // diverges, and each primitive is searched about once per warp block.
-template <int NC>
+template <int NC, bool BEST>
 struct WarpCache {
   int key[NC];
   float w[NC];
-  int best[NC];
+  int best[BEST ? NC : 1];
   int next;
   __device__ __forceinline__ void reset() {
 #pragma unroll
@@ -117,11 +117,11 @@ struct WarpCache {
     for (int e = 0; e < NC; e++) hit = (key[e] == g) ? e : hit;
     if (hit >= 0) {
       wv = w[0];
-      bi = best[0];
+      bi = BEST ? best[0] : -1;
 #pragma unroll
       for (int e = 1; e < NC; e++) {
         wv = (hit == e) ? w[e] : wv;
-        bi = (hit == e) ? best[e] : bi;
+        if (BEST) bi = (hit == e) ? best[e] : bi;
       }
       return;
     }
@@ -133,7 +133,7 @@ struct WarpCache {
       if (e == next) {
         key[e] = g;
         w[e] = wv;
-        best[e] = bi;
+        if (BEST) best[e] = bi;
       }
     next = (next + 1 == NC) ? 0 : next + 1;
   }
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work
     float C[PPT][3], Tr[PPT];
     int last[PPT], idq[PPT], px[PPT], py[PPT];
     bool done[PPT];
-    WarpCache<Cfg::NC> cache[PPT];
+    WarpCache<Cfg::NC, false> cache[PPT];
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
       int lx, ly;
@@ -314,6 +314,28 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// Reduce-scatter of 8 values over a warp in 9 shuffles: on return lane l holds
+// the warp total of value ((l >> 4) & 1) * 4 + ((l >> 3) & 1) * 2 + ((l >> 2) & 1).
+__device__ __forceinline__ float warp_reduce_scatter8(const float *v) {
+  const int lane = threadIdx.x & 31;
+  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+  float a[4], b[2];
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const float send = h4 ? v[i] : v[i + 4];
+    a[i] = (h4 ? v[i + 4] : v[i]) + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; i++) {
+    const float send = h3 ? a[i] : a[i + 2];
+    b[i] = (h3 ? a[i + 2] : a[i]) + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  float c = (h2 ? b[1] : b[0]) + __shfl_xor_sync(0xffffffffu, h2 ? b[0] : b[1], 4);
+  c += __shfl_xor_sync(0xffffffffu, c, 2);
+  c += __shfl_xor_sync(0xffffffffu, c, 1);
+  return c;
+}
+
 template <int T>
 __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work w, const float *dimage) {
   using Cfg = TileCfg<T>;
@@ -344,7 +366,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
     // R: colour behind the current pair, seen through the pairs behind it
     float Tr[PPT], R[PPT][3], dC[PPT][3];
     int last[PPT], idq[PPT], px[PPT], py[PPT];
-    WarpCache<Cfg::NC> cache[PPT];
+    WarpCache<Cfg::NC, true> cache[PPT];
     int mylast = 0;
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
@@ -417,7 +439,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
           if (alpha < p.alpha_min) continue;
           any = true;
           const float oma = 1.0f - alpha;
-          Tr[k] = Tr[k] / oma;  // T_i
+          Tr[k] = __fdividef(Tr[k], oma);  // T_i
           const float ta = Tr[k] * alpha;
           // dl/dalpha_i = dl/dC . (T_i c_i - S_i / (1 - alpha_i)) with
           // S_i / (1 - alpha_i) = T_i R_i, R <- alpha_i c_i + (1 - alpha_i) R:
@@ -465,14 +487,14 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
           }
         }
         if (__any_sync(0xffffffffu, any)) {
-#pragma unroll
-          for (int q = 0; q < 9; q++) acc[q] = warp_sum(acc[q]);
-          if (lane == 0) {
-            float *gg = w.gg + 12 * (size_t)sG[warp][l];
-#pragma unroll
-            for (int q = 0; q < 9; q++)
-              if (acc[q] != 0.f) atomicAdd(gg + q, acc[q]);
-          }
+          // gradient slots: 0 dmu x, 1 dmu y, 2-4 dK, 5 do, 6-8 dcol; slots 0-7
+          // by reduce-scatter (lanes 4m hold slot m), slot 8 by a butterfly
+          const float part = warp_reduce_scatter8(acc);
+          const float s8 = warp_sum(acc[8]);
+          float *gg = w.gg + 12 * (size_t)sG[warp][l];
+          const int slot = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+          if ((lane & 3) == 0 && part != 0.f) atomicAdd(gg + slot, part);
+          if (lane == 1 && s8 != 0.f) atomicAdd(gg + 8, s8);
         }
       }
       __syncwarp();
