@@ -63,9 +63,30 @@ def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+        return float(d["hbm_gbs"]), "measured", float(d.get("sm_max_mhz", 2070.0))
     except Exception:
-        return 6800.0, "fallback"
+        return 6800.0, "fallback", 2070.0
+
+
+# FP32 peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop per FMA x SM clock
+SMS, FP32_LANES = 152, 128
+
+# Algorithmic FP32 operations per work unit of the blending kernels (FMA = 2,
+# exp / sqrt / divide = 1): a pair inside a Gaussian's support needs the offset,
+# the quadratic form, the exponential, o G and the cutoff test (13); a composited
+# pair needs alpha, the transmittance update and three colour FMAs forward (12),
+# and the Eq. 6-8 / supplementary chain rule backward (60); one boundary candidate
+# of the Eq. 6 search costs a squared distance scaled by 1/sigma^2 and a compare (8).
+FLOPS_PER_UNIT = {"support": 13, "fwd_composited": 12, "bwd_composited": 60, "candidate": 8}
+
+
+def blend_flops(units, which):
+    u = units
+    if which == "composite_fwd":
+        return (FLOPS_PER_UNIT["support"] * u["fwd_support"] + FLOPS_PER_UNIT["fwd_composited"] * u["fwd_composited"]
+                + FLOPS_PER_UNIT["candidate"] * u["fwd_candidates"])
+    return (FLOPS_PER_UNIT["support"] * u["bwd_support"] + FLOPS_PER_UNIT["bwd_composited"] * u["bwd_composited"]
+            + FLOPS_PER_UNIT["candidate"] * u["bwd_candidates"])
 
 
 class Clocks:
@@ -138,6 +159,24 @@ def stage_bytes(stage, c, M, ncp, V):
         "chain": 48 * F + 16 * Nb + 8 * F + 4 * (2 * 3 * ncp + 2) * M,
         "prep": 8 * P,
     }[stage]
+
+
+def roofline_entry(dom, stage_ms, units, achieved_gbs, dom_bytes, peak, peak_kind, fp32_peak):
+    """Roofline of the dominant kernel: the blending kernels are bound by FP32
+    issue (no dense contraction, DRAM far from busy), the others by HBM."""
+    ms = stage_ms[dom]
+    if dom in ("composite_fwd", "composite_bwd") and units:
+        fl = blend_flops(units, dom)
+        ach = fl / (ms * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": dom, "achieved": round(ach, 3), "peak": round(fp32_peak, 1),
+                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock", "unit": "TFLOP/s",
+                "frac": round(ach / fp32_peak, 4), "traffic": None, "alg_flops_per_launch": int(fl),
+                "ms_per_launch": round(ms, 4),
+                "hbm_view": {"achieved": round(achieved_gbs, 1), "peak": peak, "unit": "GB/s",
+                             "frac": round(achieved_gbs / peak, 4), "alg_bytes_per_launch": int(dom_bytes)}}
+    return {"bound": "hbm", "kernel": dom, "achieved": round(achieved_gbs, 1), "peak": peak, "peak_kind": peak_kind,
+            "unit": "GB/s", "frac": round(achieved_gbs / peak, 4), "traffic": None,
+            "alg_bytes_per_launch": int(dom_bytes), "ms_per_launch": round(ms, 4)}
 
 
 def build_workload(seed_views, rb, workload="config4"):
@@ -223,17 +262,19 @@ def run_ours(args):
                          max_boundary_pairs=6 * P, tile_size=rd.tile_size, graph=False)
     prof_rd.set_profiling(True)
     stage_ms = {}
+    units = {}
     nprof = max(3, min(args.steps, 8))
     for i in range(nprof + 1):
         prof_rd.forward(dev, cams, images, stream=stream)
         prof_rd.l1_loss_grad(images, target, scale, dimg, loss, stream=stream)
         prof_rd.backward(dev, cams, dimg, grads, stream=stream)
         stream.synchronize()
-        prof, kf, kb = prof_rd.profile()
+        prof, kf, kb, u = prof_rd.profile()
         if i == 0:
             continue  # warm-up
         for k, v in prof.items():
             stage_ms[k] = stage_ms.get(k, 0.0) + v / nprof
+        units = u
     prof_rd.sync_status(stream)
     prof_rd.close()
     del prof_rd
@@ -277,12 +318,19 @@ def run_ours(args):
     if rank == 0:
         dom = max(("composite_fwd", "composite_bwd", "raster", "generate", "binning", "chain", "resolve"),
                   key=lambda s: stage_ms.get(s, 0.0))
-        peak, peak_kind = peaks()
+        peak, peak_kind, sm_mhz = peaks()
+        fp32_peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
         per_stage = {}
         for s_name, s_ms in stage_ms.items():
             b = stage_bytes(s_name, counts, M, ncp, V)
             per_stage[s_name] = {"ms": round(s_ms, 4), "alg_bytes": int(b),
-                                 "GBps": round(b / (s_ms * 1e-3) / 1e9, 1) if s_ms > 0 else None}
+                                 "GBps": round(b / (s_ms * 1e-3) / 1e9, 1) if s_ms > 0 else None,
+                                 "hbm_frac": round(b / (s_ms * 1e-3) / 1e9 / peak, 4) if s_ms > 0 else None}
+            if s_name in ("composite_fwd", "composite_bwd") and units:
+                fl = blend_flops(units, s_name)
+                per_stage[s_name]["alg_flops"] = int(fl)
+                per_stage[s_name]["TFLOPs"] = round(fl / (s_ms * 1e-3) / 1e12, 3)
+                per_stage[s_name]["alu_frac"] = round(fl / (s_ms * 1e-3) / 1e12 / fp32_peak, 4)
         dom_bytes = stage_bytes(dom, counts, M, ncp, V)
         achieved = dom_bytes / (stage_ms[dom] * 1e-3) / 1e9
         out = {
@@ -299,10 +347,8 @@ def run_ours(args):
             "e2e": {"value": round(e2e_value, 2), "unit": "renders/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches_per_step * args.steps),
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
-                         "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                         "traffic": None, "alg_bytes_per_launch": int(dom_bytes),
-                         "ms_per_launch": round(stage_ms[dom], 4)},
+            "roofline": roofline_entry(dom, stage_ms, units, achieved, dom_bytes, peak, peak_kind, fp32_peak),
+            "work_units": units,
             "stages": per_stage,
         }
     return out, (rd, dev, cams, sc, stream)

@@ -153,9 +153,14 @@ int bgt_get_tile_size(const bgt_handle *h);
  * raster, [2] resolve, [3] sub-primitive generation, [4] binning + sort,
  * [5] forward blending, [6] backward blending, [7] chain to parameters;
  * *kernels_fwd / *kernels_bwd receive the kernels each pass enqueues.
+ * units (nullable) receives the work units the blending kernels counted:
+ * [0] pairs inside a Gaussian's support (o G >= alpha_min), [1] pairs
+ * composited, [2] boundary candidates scanned by the Eq. 6 search, for the
+ * forward; [4], [5], [6] the same for the backward; [3], [7] zero.
  * BGT_ERR_STATE if profiling is off or no profiled pair has run. */
 bgt_status bgt_set_profiling(bgt_handle *h, int on);
-bgt_status bgt_get_profile(bgt_handle *h, float ms[8], int *kernels_fwd, int *kernels_bwd);
+bgt_status bgt_get_profile(bgt_handle *h, float ms[8], int *kernels_fwd, int *kernels_bwd,
+                           unsigned long long units[8]);
 
 /* Autotuner: time `iters` forward + backward passes of this workload at each
  * tile size in {8, 16, 32} with CUDA events on `stream`, keep the fastest and

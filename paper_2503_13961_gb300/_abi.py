@@ -72,7 +72,8 @@ def _declare(L):
     L.bgt_get_stage.argtypes = [P, c_int, P, c_ll, ctypes.POINTER(c_ll), P]
     L.bgt_bin_sort.argtypes = [P, c_int, c_int, c_int, P, P, P, P, P, P]
     L.bgt_set_profiling.argtypes = [P, c_int]
-    L.bgt_get_profile.argtypes = [P, ctypes.POINTER(c_float), ctypes.POINTER(c_int), ctypes.POINTER(c_int)]
+    L.bgt_get_profile.argtypes = [P, ctypes.POINTER(c_float), ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                                  ctypes.POINTER(ctypes.c_ulonglong)]
     return L
 
 

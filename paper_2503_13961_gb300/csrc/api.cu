@@ -82,6 +82,7 @@ void carve(bgt_handle *h, char *base, size_t *total) {
   w.n_contrib = c.take<int>(P);
   w.blk_cnt = c.take<int>(2 * (long long)h->nblk_cap);
   w.counters = c.take<int>(16);
+  w.stats = c.take<unsigned long long>(8);
   w.status = c.take<int>(1);
   w.sig3 = c.take<float>(6 * (long long)h->Mcap);
   w.gA = c.take<float4>(F);
@@ -205,6 +206,7 @@ bgt_status setup_call(bgt_handle *h, const bgt_scene *sc, const bgt_camera *cams
   p.bg[0] = sc->bg[0]; p.bg[1] = sc->bg[1]; p.bg[2] = sc->bg[2];
   p.max_pairs = h->Kcap;
   p.max_bpairs = h->Kbcap;
+  p.stats = h->profiling ? 1 : 0;
   return BGT_OK;
 }
 
@@ -227,6 +229,7 @@ cudaError_t enqueue_fwd(bgt_handle *h, const bgt::Params &p, const bgt::Scene &s
   const bgt::Work &w = h->w;
   const size_t tb = sizeof(int) * (size_t)(p.tiles + 1);
   mark(h, 0, st);
+  if (p.stats) cudaMemsetAsync(w.stats, 0, 8 * sizeof(unsigned long long), st);
   cudaMemsetAsync(w.zbuf, 0xff, sizeof(unsigned long long) * (size_t)p.P, st);
   cudaMemsetAsync(w.g_tcount, 0, tb, st);
   cudaMemsetAsync(w.g_tfill, 0, tb, st);
@@ -497,7 +500,8 @@ bgt_status bgt_set_profiling(bgt_handle *h, int on) {
   return BGT_OK;
 }
 
-bgt_status bgt_get_profile(bgt_handle *h, float ms[8], int *kernels_fwd, int *kernels_bwd) {
+bgt_status bgt_get_profile(bgt_handle *h, float ms[8], int *kernels_fwd, int *kernels_bwd,
+                           unsigned long long units[8]) {
   if (!h || !ms) return BGT_ERR_INVALID_ARG;
   if (!h->profiling) return fail(h, BGT_ERR_STATE, "profiling is off");
   cudaError_t e = cudaEventSynchronize(h->prof[9]);
@@ -512,6 +516,10 @@ bgt_status bgt_get_profile(bgt_handle *h, float ms[8], int *kernels_fwd, int *ke
   }
   if (kernels_fwd) *kernels_fwd = h->kernels_fwd;
   if (kernels_bwd) *kernels_bwd = h->kernels_bwd;
+  if (units) {
+    e = cudaMemcpy(units, h->w.stats, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "profile units");
+  }
   return BGT_OK;
 }
 

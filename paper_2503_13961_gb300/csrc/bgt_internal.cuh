@@ -50,6 +50,7 @@ struct Params {
   int V, P, tiles;            // views, total pixels, total tiles of this call
   float bg[3];
   long long max_pairs, max_bpairs;
+  int stats;                  // 1: blending kernels count their work units into Work::stats
 };
 
 struct Scene {                // device pointers, caller-owned
@@ -113,9 +114,16 @@ struct Work {
   // intermediate gradients
   float *gg;                  // [Fcap][12]: dmu x,y; dK a,b,c; do; dcol r,g,b; pad
   float4 *bg_grad;            // [Fcap] (db x, db y, dsigma, 0)
+  unsigned long long *stats;  // [8] work units of the last profiled call (see Stat)
   long long Fcap;
   int nblk;
 };
+
+// Work units counted by the blending kernels when Params::stats is set:
+// pairs inside a Gaussian's support (o G >= alpha_min), pairs composited,
+// boundary candidates scanned by the coefficient search; forward then backward.
+enum Stat { kFwdSupport = 0, kFwdComposited = 1, kFwdCandidates = 2, kBwdSupport = 4, kBwdComposited = 5,
+            kBwdCandidates = 6 };
 
 constexpr int kIndexBits = 27;  // Gaussian index field of a pair key (<= 134M Gaussians per call)
 constexpr unsigned long long kIndexMask = (1ull << kIndexBits) - 1ull;

@@ -48,7 +48,8 @@ __device__ __forceinline__ void lane_pixel(int warp, int lane, int k, int &lx, i
 
 struct WRes {
   float w, gamma, rho;
-  int best;  // position in the tile's boundary list, -1 if none within range
+  int best;   // position in the tile's boundary list, -1 if none within range
+  int cands;  // boundary candidates scanned
 };
 
 // Eq. 6-7 for pixel (px, py) and primitive g over the tile's boundary list.
@@ -58,6 +59,7 @@ __device__ __forceinline__ WRes w_search(int g, int px, int py, int idq, const i
   r.best = -1;
   r.rho = 3.0e38f;
   r.gamma = 1.0f;
+  r.cands = 0;
   if (!use_boundary) {  // the paper's "w/o B" ablation: no blending coefficient
     r.w = 1.0f;
     return r;
@@ -78,6 +80,7 @@ __device__ __forceinline__ WRes w_search(int g, int px, int py, int idq, const i
       best = r2;
       r.best = i;
     }
+    r.cands++;
   }
   if (r.best >= 0) {
     r.rho = __fsqrt_rn(best);
@@ -111,7 +114,7 @@ struct WarpCache {
   // coefficient of primitive g for this lane's pixel; must be called by all lanes
   // with the same g
   __device__ __forceinline__ void get(int g, int px, int py, int idq, const int *bprim, const float4 *brec, int bn,
-                                      int use_boundary, float &wv, int &bi) {
+                                      int use_boundary, float &wv, int &bi, unsigned &cands) {
     int hit = -1;
 #pragma unroll
     for (int e = 0; e < NC; e++) hit = (key[e] == g) ? e : hit;
@@ -126,6 +129,7 @@ struct WarpCache {
       return;
     }
     const WRes r = w_search(g, px, py, idq, bprim, brec, bn, use_boundary);
+    cands += (unsigned)r.cands;
     wv = r.w;
     bi = (r.best >= 0 && r.rho < 1.0f) ? r.best : -1;
 #pragma unroll
@@ -183,6 +187,18 @@ __device__ __forceinline__ PairGeo pair_geo2(int px, int py, const float4 &A, co
   return p;
 }
 
+__device__ __forceinline__ void flush_stats(unsigned long long *stats, int base, unsigned a, unsigned b, unsigned c) {
+  unsigned long long v[3] = {a, b, c};
+#pragma unroll
+  for (int q = 0; q < 3; q++) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  }
+  if ((threadIdx.x & 31) == 0)
+    for (int q = 0; q < 3; q++)
+      if (v[q]) atomicAdd(stats + base + q, v[q]);
+}
+
 template <int NT>
 __device__ __forceinline__ void load_boundary_cache(const TileInfo &ti, const Work &w, int *s_bprim, float4 *s_brec,
                                                     const int *&bprim, const float4 *&brec) {
@@ -225,6 +241,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work
     int last[PPT], idq[PPT], px[PPT], py[PPT];
     bool done[PPT];
     WarpCache<Cfg::NC, false> cache[PPT];
+    unsigned n_sup = 0, n_comp = 0, n_cand = 0;
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
       int lx, ly;
@@ -274,8 +291,9 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work
           if (!__any_sync(0xffffffffu, cand)) continue;
           float wv;
           int bi;
-          cache[k].get(g, px[k], py[k], idq[k], bprim, brec, bn, p.use_boundary, wv, bi);
+          cache[k].get(g, px[k], py[k], idq[k], bprim, brec, bn, p.use_boundary, wv, bi, n_cand);
           if (!cand) continue;
+          n_sup++;
           const float alpha = fminf(p.alpha_max, __fmul_rn(og, wv));
           if (alpha < p.alpha_min) continue;
           const float testT = __fmul_rn(Tr[k], __fsub_rn(1.0f, alpha));
@@ -290,6 +308,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work
           C[k][2] = __fmaf_rn(ta, Cc.z, C[k][2]);
           Tr[k] = testT;
           last[k] = c0 + l + 1;
+          n_comp++;
         }
       }
       __syncwarp();
@@ -305,6 +324,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work
         w.n_contrib[pix] = last[k];
       }
     }
+    if (p.stats) flush_stats(w.stats, kFwdSupport, n_sup, n_comp, n_cand);
   }
 }
 
@@ -367,6 +387,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
     float Tr[PPT], R[PPT][3], dC[PPT][3];
     int last[PPT], idq[PPT], px[PPT], py[PPT];
     WarpCache<Cfg::NC, true> cache[PPT];
+    unsigned n_sup = 0, n_comp = 0, n_cand = 0;
     int mylast = 0;
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
@@ -432,12 +453,14 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
           if (!__any_sync(0xffffffffu, cand)) continue;
           float wv;
           int bi;
-          cache[k].get(g, px[k], py[k], idq[k], bprim, brec, bn, p.use_boundary, wv, bi);
+          cache[k].get(g, px[k], py[k], idq[k], bprim, brec, bn, p.use_boundary, wv, bi, n_cand);
           if (!cand) continue;
+          n_sup++;
           const float raw = __fmul_rn(og, wv);
           const float alpha = fminf(p.alpha_max, raw);
           if (alpha < p.alpha_min) continue;
           any = true;
+          n_comp++;
           const float oma = 1.0f - alpha;
           Tr[k] = __fdividef(Tr[k], oma);  // T_i
           const float ta = Tr[k] * alpha;
@@ -499,6 +522,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
       }
       __syncwarp();
     }
+    if (p.stats) flush_stats(w.stats, kBwdSupport, n_sup, n_comp, n_cand);
   }
 }
 

@@ -156,12 +156,18 @@ class Renderer:
     def set_profiling(self, on=True):
         self._check(self.lib.bgt_set_profiling(self.h, 1 if on else 0))
 
+    UNITS = ("fwd_support", "fwd_composited", "fwd_candidates", None, "bwd_support", "bwd_composited",
+             "bwd_candidates", None)
+
     def profile(self):
-        """Device ms per stage of the last profiled forward + backward, and kernel counts."""
+        """Device ms per stage of the last profiled forward + backward, kernel counts
+        per pass, and the blending kernels' work units."""
         ms = (ctypes.c_float * 8)()
         kf, kb = ctypes.c_int(0), ctypes.c_int(0)
-        self._check(self.lib.bgt_get_profile(self.h, ms, ctypes.byref(kf), ctypes.byref(kb)))
-        return dict(zip(self.STAGES, list(ms))), kf.value, kb.value
+        units = (ctypes.c_ulonglong * 8)()
+        self._check(self.lib.bgt_get_profile(self.h, ms, ctypes.byref(kf), ctypes.byref(kb), units))
+        u = {k: int(v) for k, v in zip(self.UNITS, units) if k}
+        return dict(zip(self.STAGES, list(ms))), kf.value, kb.value, u
 
     def l1_loss_grad(self, images, target, scale, d_images=None, loss=None, stream=None):
         if d_images is None:
