@@ -202,6 +202,34 @@ bgt_status bgt_get_stage(bgt_handle *h, int which, void *dst, long long bytes, l
 bgt_status bgt_bin_sort(bgt_handle *h, int width, int height, int count, const int *qxy, const float *off,
                         const float *conic, const float *opacity, const float *depth, void *stream);
 
+/* Binning + per-tile sort without any device allocation. The paper has no
+ * counterpart: this entry exists for callers that cannot call cudaMalloc --
+ * code running inside another framework's memory pool, plugins whose device
+ * memory is fixed when they are loaded, or loops that must not synchronize
+ * the device at run time (an allocation can) -- and so cannot create a handle.
+ *
+ * It computes what bgt_bin_sort computes (same Gaussians in, same tile
+ * ranges and sorted keys out), for one width x height view with tiles of
+ * tile_size (8, 16, 32) and the given alpha_min. Inputs as for bgt_bin_sort
+ * (device). Outputs (device, caller-owned): out_ranges int64[tiles + 1], the
+ * start of each tile's keys plus the total; out_keys uint64[key_capacity],
+ * the keys of each tile sorted ascending (FP32 depth bits << 32 | 5 finer
+ * depth bits << 27 | Gaussian index).
+ *
+ * Scratch: one static device array of about 5.4 MB, held by every GPU that
+ * loads the library until the process exits. Limits: count <= 65,536
+ * Gaussians, tiles <= 16,384, total keys <= 262,144; larger inputs return
+ * BGT_ERR_CAPACITY (count and tiles before any work, the key total after the
+ * counting pass). The call waits for `stream` once (to read the key total)
+ * and returns after the sort is enqueued. The first call on a device looks
+ * up the array's device address; make that first call before any stream
+ * capture. Calls share the array: two calls that overlap on the GPU (other
+ * streams, other threads) race and corrupt each other's results. */
+bgt_status bgt_bin_sort_static(int width, int height, int tile_size, int count, const int *qxy,
+                               const float *off, const float *conic, const float *opacity,
+                               const float *depth, float alpha_min, long long *out_ranges,
+                               unsigned long long *out_keys, long long key_capacity, void *stream);
+
 #ifdef __cplusplus
 }
 #endif
