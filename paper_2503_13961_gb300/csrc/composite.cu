@@ -23,10 +23,11 @@ namespace bgt {
 
 namespace {
 
-constexpr int kBCap = 1536;  // boundary entries staged in shared memory
+constexpr int kBCap = 1024;        // boundary candidates staged in shared memory per tile
+constexpr float kLog2e = 1.4426950408889634f;
 
 // Block layout: NT threads; every warp owns a WX x WY block of the tile's
-// pixels (PPT pixels per lane), so that a chunk of 32 staged Gaussians can be
+// pixels (PPT pixels per lane), so that a chunk of 32 listed Gaussians can be
 // culled against the warp's block with one ballot.
 template <int T>
 struct TileCfg {
@@ -36,7 +37,7 @@ struct TileCfg {
   static constexpr int WX = (T == 32) ? 16 : 8;
   static constexpr int WY = (T == 32) ? 8 : 4;
   static constexpr int WPR = T / WX;         // warp blocks per tile row
-  static constexpr int NC = (PPT == 1) ? 8 : 4;  // coefficient cache entries per pixel
+  static constexpr int SLOTS = (PPT == 1) ? 16 : 4;  // direct-mapped primitive cache per warp
 };
 
 template <int T>
@@ -46,102 +47,63 @@ __device__ __forceinline__ void lane_pixel(int warp, int lane, int k, int &lx, i
   ly = (warp / C::WPR) * C::WY + (lane >> 3) + 4 * (k >> 1);
 }
 
-struct WRes {
-  float w, gamma, rho;
-  int best;   // position in the tile's boundary list, -1 if none within range
-  int cands;  // boundary candidates scanned
-};
-
-// Eq. 6-7 for pixel (px, py) and primitive g over the tile's boundary list.
-__device__ __forceinline__ WRes w_search(int g, int px, int py, int idq, const int *bprim,
-                                         const float4 *brec, int bn, int use_boundary) {
-  WRes r;
-  r.best = -1;
-  r.rho = 3.0e38f;
-  r.gamma = 1.0f;
-  r.cands = 0;
-  if (!use_boundary) {  // the paper's "w/o B" ablation: no blending coefficient
-    r.w = 1.0f;
-    return r;
-  }
-  int lo = 0, hi = bn;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (bprim[mid] < g) lo = mid + 1; else hi = mid;
-  }
-  float best = 3.0e38f;
-  for (int i = lo; i < bn && bprim[i] == g; i++) {
-    const float4 b = brec[i];
-    const unsigned qxy = __float_as_uint(b.x);
-    const float dx = __fsub_rn((float)(px - (int)(qxy & 0xffffu)), b.y);
-    const float dy = __fsub_rn((float)(py - (int)(qxy >> 16)), b.z);
-    const float r2 = __fmul_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)), __fmul_rn(b.w, b.w));
-    if (r2 < best) {
-      best = r2;
-      r.best = i;
-    }
-    r.cands++;
-  }
-  if (r.best >= 0) {
-    r.rho = __fsqrt_rn(best);
-    if (best < 1.0f) r.gamma = exp2f(__fsub_rn(r.rho, 1.0f));
-  }
-  r.w = (idq == g) ? r.gamma : __fsub_rn(1.0f, r.gamma);
-  return r;
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
-struct PairGeo {
-  float dx, dy, power;
+// G = exp(-1/2 (a dx^2 + 2 b dx dy + c dy^2)) evaluated as a power of two
+__device__ __forceinline__ float gauss(float dx, float dy, const float4 &Q) {
+  const float e = __fmaf_rn(Q.x, __fmul_rn(dx, dx), __fmul_rn(Q.z, __fmul_rn(dy, dy)));
+  const float f = __fmul_rn(Q.y, __fmul_rn(dx, dy));
+  return ex2(__fmaf_rn(e, -0.5f * kLog2e, __fmul_rn(-kLog2e, f)));
+}
+
+// a boundary record relative to the tile origin: (x, y, 1/sigma^2, 1/sigma)
+__device__ __forceinline__ float4 to_local(const float4 rec, int x0, int y0) {
+  const unsigned qxy = __float_as_uint(rec.x);
+  return make_float4(__fadd_rn((float)((int)(qxy & 0xffffu) - x0), rec.y),
+                     __fadd_rn((float)((int)(qxy >> 16) - y0), rec.z), __fmul_rn(rec.w, rec.w), rec.w);
+}
+
+// the tile's boundary candidates, sorted by (primitive, index)
+struct BList {
+  const int *prim;
+  const float4 *loc;   // tile-local records in shared memory (if cached)
+  const float4 *glob;  // pixel-relative records in global memory
+  int n, x0, y0;
+  bool cached;
+  __device__ __forceinline__ float4 get(int i) const { return cached ? loc[i] : to_local(glob[i], x0, y0); }
 };
 
-
-// Warp-uniform cache of (primitive -> coefficient). All lanes of a warp hold
-// the same primitive ids; each lane holds its own pixel's w and most
-// influential boundary entry for them. On a miss every lane of the warp runs
-// the same search (same primitive, same candidate list), so the search never
-// diverges, and each primitive is searched about once per warp block.
-template <int NC, bool BEST>
-struct WarpCache {
-  int key[NC];
-  float w[NC];
-  int best[BEST ? NC : 1];
-  int next;
-  __device__ __forceinline__ void reset() {
-#pragma unroll
-    for (int e = 0; e < NC; e++) key[e] = -2;
-    next = 0;
+// Eq. 6-7 at tile-local pixel (lx, ly) for primitive g: gamma* = min over
+// g's boundary points of min(2^(rho - 1), 1), rho = |q - b| / sigma_b;
+// w = gamma* inside g, 1 - gamma* outside. best: candidate with rho < 1, else -1.
+__device__ __forceinline__ float w_search(const BList &bl, int g, float lx, float ly, bool inside, int &best,
+                                          unsigned &cands) {
+  int lo = 0, hi = bl.n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (bl.prim[mid] < g) lo = mid + 1; else hi = mid;
   }
-  // coefficient of primitive g for this lane's pixel; must be called by all lanes
-  // with the same g
-  __device__ __forceinline__ void get(int g, int px, int py, int idq, const int *bprim, const float4 *brec, int bn,
-                                      int use_boundary, float &wv, int &bi, unsigned &cands) {
-    int hit = -1;
-#pragma unroll
-    for (int e = 0; e < NC; e++) hit = (key[e] == g) ? e : hit;
-    if (hit >= 0) {
-      wv = w[0];
-      bi = BEST ? best[0] : -1;
-#pragma unroll
-      for (int e = 1; e < NC; e++) {
-        wv = (hit == e) ? w[e] : wv;
-        if (BEST) bi = (hit == e) ? best[e] : bi;
-      }
-      return;
+  float r2min = 3.0e38f;
+  best = -1;
+  for (int i = lo; i < bl.n && bl.prim[i] == g; i++) {
+    const float4 b = bl.get(i);
+    const float dx = __fsub_rn(lx, b.x), dy = __fsub_rn(ly, b.y);
+    const float r2 = __fmul_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)), b.z);
+    if (r2 < r2min) {
+      r2min = r2;
+      best = i;
     }
-    const WRes r = w_search(g, px, py, idq, bprim, brec, bn, use_boundary);
-    cands += (unsigned)r.cands;
-    wv = r.w;
-    bi = (r.best >= 0 && r.rho < 1.0f) ? r.best : -1;
-#pragma unroll
-    for (int e = 0; e < NC; e++)
-      if (e == next) {
-        key[e] = g;
-        w[e] = wv;
-        if (BEST) best[e] = bi;
-      }
-    next = (next + 1 == NC) ? 0 : next + 1;
+    cands++;
   }
-};
+  float gamma = 1.0f;
+  if (best >= 0 && r2min < 1.0f) gamma = exp2f(__fsub_rn(__fsqrt_rn(r2min), 1.0f));
+  else best = -1;
+  return inside ? gamma : __fsub_rn(1.0f, gamma);
+}
 
 struct TileInfo {
   int view, W, H, pix_off, x0, y0;
@@ -169,22 +131,51 @@ __device__ inline TileInfo tile_info(const Params &p, const Work &w, int tile, i
   return t;
 }
 
-// does the support square of the Gaussian cover any pixel of [x0,x1] x [y0,y1]?
-__device__ __forceinline__ bool covers(const float4 &A, int x0, int x1, int y0, int y1) {
-  const unsigned qxy = __float_as_uint(A.z);
-  const float cx = (float)(int)(qxy & 0xffffu) + A.x, cy = (float)(int)(qxy >> 16) + A.y;
-  const float r = A.w;
-  return r >= 0.f && cx + r >= (float)x0 && cx - r <= (float)x1 && cy + r >= (float)y0 && cy - r <= (float)y1;
+template <int NT>
+__device__ __forceinline__ BList load_boundary(const TileInfo &ti, const Work &w, int *s_bprim, float4 *s_bloc) {
+  BList bl;
+  bl.n = (int)ti.bn;
+  bl.x0 = ti.x0;
+  bl.y0 = ti.y0;
+  bl.glob = w.bl_rec + ti.bs;
+  bl.cached = ti.bn <= kBCap;
+  if (bl.cached) {
+    for (int i = threadIdx.x; i < ti.bn; i += NT) {
+      s_bprim[i] = w.bl_prim[ti.bs + i];
+      s_bloc[i] = to_local(w.bl_rec[ti.bs + i], ti.x0, ti.y0);
+    }
+  }
+  bl.prim = bl.cached ? s_bprim : w.bl_prim + ti.bs;
+  bl.loc = s_bloc;
+  return bl;
 }
 
-__device__ __forceinline__ PairGeo pair_geo2(int px, int py, const float4 &A, const float4 &B) {
-  PairGeo p;
-  const unsigned qxy = __float_as_uint(A.z);
-  p.dx = __fsub_rn((float)(px - (int)(qxy & 0xffffu)), A.x);
-  p.dy = __fsub_rn((float)(py - (int)(qxy >> 16)), A.y);
-  const float q = __fmaf_rn(B.x, __fmul_rn(p.dx, p.dx), __fmul_rn(B.z, __fmul_rn(p.dy, p.dy)));
-  p.power = __fsub_rn(__fmul_rn(-0.5f, q), __fmul_rn(B.y, __fmul_rn(p.dx, p.dy)));
-  return p;
+// Stage this warp's hits of the chunk [c0, c0 + 32) of the tile's list:
+// P = (centre x, y relative to the tile origin, opacity, bits(prim)),
+// Q = conic (a, b, c), C = colour. Returns the ballot of hits.
+__device__ __forceinline__ unsigned stage_chunk(const Work &w, const TileInfo &ti, int jl, int jend, float bx0, float bx1,
+                                                float by0, float by1, float4 *sP, float4 *sQ, float4 *sC, int *sG) {
+  const int lane = threadIdx.x & 31;
+  bool hit = false;
+  if (jl < jend) {
+    const unsigned gi = (unsigned)(w.gkeys[ti.gs + jl] & kIndexMask);
+    const float4 A = w.gA[gi];
+    const unsigned qxy = __float_as_uint(A.z);
+    const float cx = __fadd_rn((float)((int)(qxy & 0xffffu) - ti.x0), A.x);
+    const float cy = __fadd_rn((float)((int)(qxy >> 16) - ti.y0), A.y);
+    const float r = A.w;
+    hit = r >= 0.f && cx + r >= bx0 && cx - r <= bx1 && cy + r >= by0 && cy - r <= by1;
+    if (hit) {
+      const float4 B = w.gB[gi], C = w.gC[gi];
+      sP[lane] = make_float4(cx, cy, B.w, C.w);
+      sQ[lane] = make_float4(B.x, B.y, B.z, 0.f);
+      sC[lane] = make_float4(C.x, C.y, C.z, 0.f);
+      if (sG) sG[lane] = (int)gi;
+    }
+  }
+  const unsigned mask = __ballot_sync(0xffffffffu, hit);
+  __syncwarp();
+  return mask;
 }
 
 __device__ __forceinline__ void flush_stats(unsigned long long *stats, int base, unsigned a, unsigned b, unsigned c) {
@@ -199,28 +190,34 @@ __device__ __forceinline__ void flush_stats(unsigned long long *stats, int base,
       if (v[q]) atomicAdd(stats + base + q, v[q]);
 }
 
-template <int NT>
-__device__ __forceinline__ void load_boundary_cache(const TileInfo &ti, const Work &w, int *s_bprim, float4 *s_brec,
-                                                    const int *&bprim, const float4 *&brec) {
-  const bool bsm = ti.bn <= kBCap;
-  if (bsm) {
-    for (int i = threadIdx.x; i < ti.bn; i += NT) {
-      s_bprim[i] = w.bl_prim[ti.bs + i];
-      s_brec[i] = w.bl_rec[ti.bs + i];
-    }
-  }
-  bprim = bsm ? s_bprim : w.bl_prim + ti.bs;
-  brec = bsm ? s_brec : w.bl_rec + ti.bs;
-}
+// shared memory of the blending kernels (dynamic: above the 48 KB static limit)
+template <int T, bool BWD>
+struct BlendShared {
+  using Cfg = TileCfg<T>;
+  float4 sP[Cfg::NW][32], sQ[Cfg::NW][32], sC[Cfg::NW][32];
+  float4 s_bloc[kBCap];
+  float s_cw[Cfg::NW][Cfg::SLOTS][Cfg::PPT][32];
+  int s_cb[BWD ? Cfg::NW : 1][Cfg::SLOTS][Cfg::PPT][32];
+  int sG[Cfg::NW][32];
+  int s_ckey[Cfg::NW][Cfg::SLOTS];
+  int s_bprim[kBCap];
+  int s_tile;
+};
 
 template <int T>
 __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work w, float *image) {
   using Cfg = TileCfg<T>;
-  constexpr int NT = Cfg::NT, NW = Cfg::NW, PPT = Cfg::PPT;
-  __shared__ float4 sA[NW][32], sB[NW][32], sC[NW][32];
-  __shared__ int s_bprim[kBCap];
-  __shared__ float4 s_brec[kBCap];
-  __shared__ int s_tile;
+  constexpr int NT = Cfg::NT, PPT = Cfg::PPT, S = Cfg::SLOTS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto &sh = *reinterpret_cast<BlendShared<T, false> *>(smem_raw);
+  auto &sP = sh.sP;
+  auto &sQ = sh.sQ;
+  auto &sC = sh.sC;
+  auto &s_ckey = sh.s_ckey;
+  auto &s_cw = sh.s_cw;
+  auto &s_bprim = sh.s_bprim;
+  auto &s_bloc = sh.s_bloc;
+  auto &s_tile = sh.s_tile;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (;;) {
     __syncthreads();
@@ -229,32 +226,32 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work
     const int tile = s_tile;
     if (tile >= p.tiles) break;
     const TileInfo ti = tile_info(p, w, tile, T);
-    const int *bprim;
-    const float4 *brec;
-    load_boundary_cache<NT>(ti, w, s_bprim, s_brec, bprim, brec);
+    const BList bl = load_boundary<NT>(ti, w, s_bprim, s_bloc);
+    if (lane < S) s_ckey[warp][lane] = -2;
     __syncthreads();
-    const int bn = (int)ti.bn;
-    const int wx0 = ti.x0 + (warp % Cfg::WPR) * Cfg::WX, wy0 = ti.y0 + (warp / Cfg::WPR) * Cfg::WY;
-    const int wx1 = wx0 + Cfg::WX - 1, wy1 = wy0 + Cfg::WY - 1;
+    // the warp's pixel block, relative to the tile origin
+    const int wxl = (warp % Cfg::WPR) * Cfg::WX, wyl = (warp / Cfg::WPR) * Cfg::WY;
+    const float bx0 = (float)wxl, bx1 = (float)(wxl + Cfg::WX - 1);
+    const float by0 = (float)wyl, by1 = (float)(wyl + Cfg::WY - 1);
 
-    float C[PPT][3], Tr[PPT];
-    int last[PPT], idq[PPT], px[PPT], py[PPT];
+    float C[PPT][3], Tr[PPT], lxf[PPT], lyf[PPT];
+    int last[PPT], idq[PPT], pix[PPT];
     bool done[PPT];
-    WarpCache<Cfg::NC, false> cache[PPT];
     unsigned n_sup = 0, n_comp = 0, n_cand = 0;
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
       int lx, ly;
       lane_pixel<T>(warp, lane, k, lx, ly);
-      px[k] = ti.x0 + lx;
-      py[k] = ti.y0 + ly;
-      const bool inside = px[k] < ti.W && py[k] < ti.H;
+      lxf[k] = (float)lx;
+      lyf[k] = (float)ly;
+      const int px = ti.x0 + lx, py = ti.y0 + ly;
+      const bool inside = px < ti.W && py < ti.H;
+      pix[k] = inside ? ti.pix_off + py * ti.W + px : -1;
       done[k] = !inside;
-      idq[k] = inside ? w.pid[ti.pix_off + py[k] * ti.W + px[k]] : -1;
+      idq[k] = inside ? w.pid[pix[k]] : -1;
       C[k][0] = C[k][1] = C[k][2] = 0.f;
       Tr[k] = 1.0f;
       last[k] = 0;
-      cache[k].reset();
     }
     const int gn = (int)ti.gn;
     for (int c0 = 0; c0 < gn; c0 += 32) {
@@ -262,39 +259,39 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work
 #pragma unroll
       for (int k = 0; k < PPT; k++) alldone = alldone && done[k];
       if (__all_sync(0xffffffffu, alldone)) break;
-      // stage the chunk's Gaussians that touch this warp's block
-      const int jl = c0 + lane;
-      bool hit = false;
-      if (jl < gn) {
-        const unsigned gi = (unsigned)(w.gkeys[ti.gs + jl] & kIndexMask);
-        const float4 A = w.gA[gi];
-        hit = covers(A, wx0, wx1, wy0, wy1);
-        if (hit) {
-          sA[warp][lane] = A;
-          sB[warp][lane] = w.gB[gi];
-          sC[warp][lane] = w.gC[gi];
-        }
-      }
-      unsigned mask = __ballot_sync(0xffffffffu, hit);
-      __syncwarp();
+      unsigned mask = stage_chunk(w, ti, c0 + lane, gn, bx0, bx1, by0, by1, sP[warp], sQ[warp], sC[warp], nullptr);
       while (mask) {
         const int l = __ffs(mask) - 1;
         mask &= mask - 1;
-        const float4 A = sA[warp][l], B = sB[warp][l];
-        const int g = __float_as_int(sC[warp][l].w);
+        const float4 P = sP[warp][l], Q = sQ[warp][l];
+        const int g = __float_as_int(P.w);
+        float og[PPT];
+        bool cand[PPT];
+        bool anyc = false;
 #pragma unroll
         for (int k = 0; k < PPT; k++) {
-          const PairGeo pg = pair_geo2(px[k], py[k], A, B);
-          const float G = __expf(pg.power);
-          const float og = __fmul_rn(B.w, G);
-          const bool cand = !done[k] && og >= p.alpha_min;  // w <= 1: else alpha < alpha_min
-          if (!__any_sync(0xffffffffu, cand)) continue;
-          float wv;
-          int bi;
-          cache[k].get(g, px[k], py[k], idq[k], bprim, brec, bn, p.use_boundary, wv, bi, n_cand);
-          if (!cand) continue;
+          og[k] = __fmul_rn(P.z, gauss(__fsub_rn(lxf[k], P.x), __fsub_rn(lyf[k], P.y), Q));
+          cand[k] = !done[k] && og[k] >= p.alpha_min;  // w <= 1: else alpha < alpha_min
+          anyc = anyc || cand[k];
+        }
+        if (!__any_sync(0xffffffffu, anyc)) continue;
+        const int slot = g & (S - 1);
+        if (s_ckey[warp][slot] != g) {  // warp-uniform miss: every lane searches, coherently
+#pragma unroll
+          for (int k = 0; k < PPT; k++) {
+            int best;
+            s_cw[warp][slot][k][lane] = p.use_boundary
+                ? w_search(bl, g, lxf[k], lyf[k], idq[k] == g, best, n_cand) : 1.0f;
+          }
+          __syncwarp();
+          if (lane == 0) s_ckey[warp][slot] = g;
+          __syncwarp();
+        }
+#pragma unroll
+        for (int k = 0; k < PPT; k++) {
+          if (!cand[k]) continue;
           n_sup++;
-          const float alpha = fminf(p.alpha_max, __fmul_rn(og, wv));
+          const float alpha = fminf(p.alpha_max, __fmul_rn(og[k], s_cw[warp][slot][k][lane]));
           if (alpha < p.alpha_min) continue;
           const float testT = __fmul_rn(Tr[k], __fsub_rn(1.0f, alpha));
           if (testT < p.t_stop) {
@@ -315,13 +312,12 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work
     }
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
-      if (px[k] < ti.W && py[k] < ti.H) {
-        const int pix = ti.pix_off + py[k] * ti.W + px[k];
-        image[3 * (size_t)pix + 0] = __fmaf_rn(Tr[k], p.bg[0], C[k][0]);
-        image[3 * (size_t)pix + 1] = __fmaf_rn(Tr[k], p.bg[1], C[k][1]);
-        image[3 * (size_t)pix + 2] = __fmaf_rn(Tr[k], p.bg[2], C[k][2]);
-        w.T_final[pix] = Tr[k];
-        w.n_contrib[pix] = last[k];
+      if (pix[k] >= 0) {
+        image[3 * (size_t)pix[k] + 0] = __fmaf_rn(Tr[k], p.bg[0], C[k][0]);
+        image[3 * (size_t)pix[k] + 1] = __fmaf_rn(Tr[k], p.bg[1], C[k][1]);
+        image[3 * (size_t)pix[k] + 2] = __fmaf_rn(Tr[k], p.bg[2], C[k][2]);
+        w.T_final[pix[k]] = Tr[k];
+        w.n_contrib[pix[k]] = last[k];
       }
     }
     if (p.stats) flush_stats(w.stats, kFwdSupport, n_sup, n_comp, n_cand);
@@ -359,12 +355,19 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float *v) {
 template <int T>
 __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work w, const float *dimage) {
   using Cfg = TileCfg<T>;
-  constexpr int NT = Cfg::NT, NW = Cfg::NW, PPT = Cfg::PPT;
-  __shared__ float4 sA[NW][32], sB[NW][32], sC[NW][32];
-  __shared__ int sG[NW][32];
-  __shared__ int s_bprim[kBCap];
-  __shared__ float4 s_brec[kBCap];
-  __shared__ int s_tile;
+  constexpr int NT = Cfg::NT, PPT = Cfg::PPT, S = Cfg::SLOTS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto &sh = *reinterpret_cast<BlendShared<T, true> *>(smem_raw);
+  auto &sP = sh.sP;
+  auto &sQ = sh.sQ;
+  auto &sC = sh.sC;
+  auto &sG = sh.sG;
+  auto &s_ckey = sh.s_ckey;
+  auto &s_cw = sh.s_cw;
+  auto &s_cb = sh.s_cb;
+  auto &s_bprim = sh.s_bprim;
+  auto &s_bloc = sh.s_bloc;
+  auto &s_tile = sh.s_tile;
   const float LN2 = 0.69314718055994531f;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (;;) {
@@ -374,35 +377,33 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
     const int tile = s_tile;
     if (tile >= p.tiles) break;
     const TileInfo ti = tile_info(p, w, tile, T);
-    const int *bprim;
-    const float4 *brec;
-    load_boundary_cache<NT>(ti, w, s_bprim, s_brec, bprim, brec);
+    const BList bl = load_boundary<NT>(ti, w, s_bprim, s_bloc);
+    if (lane < S) s_ckey[warp][lane] = -2;
     __syncthreads();
     const unsigned long long *bkeys = w.bkeys + ti.bs;
-    const int bn = (int)ti.bn;
-    const int wx0 = ti.x0 + (warp % Cfg::WPR) * Cfg::WX, wy0 = ti.y0 + (warp / Cfg::WPR) * Cfg::WY;
-    const int wx1 = wx0 + Cfg::WX - 1, wy1 = wy0 + Cfg::WY - 1;
+    const int wxl = (warp % Cfg::WPR) * Cfg::WX, wyl = (warp / Cfg::WPR) * Cfg::WY;
+    const float bx0 = (float)wxl, bx1 = (float)(wxl + Cfg::WX - 1);
+    const float by0 = (float)wyl, by1 = (float)(wyl + Cfg::WY - 1);
 
     // R: colour behind the current pair, seen through the pairs behind it
-    float Tr[PPT], R[PPT][3], dC[PPT][3];
-    int last[PPT], idq[PPT], px[PPT], py[PPT];
-    WarpCache<Cfg::NC, true> cache[PPT];
+    float Tr[PPT], R[PPT][3], dC[PPT][3], lxf[PPT], lyf[PPT];
+    int last[PPT], idq[PPT];
     unsigned n_sup = 0, n_comp = 0, n_cand = 0;
     int mylast = 0;
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
       int lx, ly;
       lane_pixel<T>(warp, lane, k, lx, ly);
-      px[k] = ti.x0 + lx;
-      py[k] = ti.y0 + ly;
+      lxf[k] = (float)lx;
+      lyf[k] = (float)ly;
+      const int px = ti.x0 + lx, py = ti.y0 + ly;
       last[k] = 0;
       idq[k] = -1;
       Tr[k] = 1.f;
-      cache[k].reset();
       R[k][0] = R[k][1] = R[k][2] = 0.f;
       dC[k][0] = dC[k][1] = dC[k][2] = 0.f;
-      if (px[k] < ti.W && py[k] < ti.H) {
-        const int pix = ti.pix_off + py[k] * ti.W + px[k];
+      if (px < ti.W && py < ti.H) {
+        const int pix = ti.pix_off + py * ti.W + px;
         idq[k] = w.pid[pix];
         last[k] = w.n_contrib[pix];
         Tr[k] = w.T_final[pix];
@@ -419,44 +420,50 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
     for (int o = 16; o > 0; o >>= 1) wlast = max(wlast, __shfl_xor_sync(0xffffffffu, wlast, o));
     for (int c1 = wlast; c1 > 0; c1 -= 32) {
       const int c0 = max(0, c1 - 32);
-      const int jl = c0 + lane;
-      bool hit = false;
-      if (jl < c1) {
-        const unsigned gi = (unsigned)(w.gkeys[ti.gs + jl] & kIndexMask);
-        const float4 A = w.gA[gi];
-        hit = covers(A, wx0, wx1, wy0, wy1);
-        if (hit) {
-          sA[warp][lane] = A;
-          sB[warp][lane] = w.gB[gi];
-          sC[warp][lane] = w.gC[gi];
-          sG[warp][lane] = (int)gi;
-        }
-      }
-      unsigned mask = __ballot_sync(0xffffffffu, hit);
-      __syncwarp();
+      unsigned mask = stage_chunk(w, ti, c0 + lane, c1, bx0, bx1, by0, by1, sP[warp], sQ[warp], sC[warp], sG[warp]);
       while (mask) {
         const int l = 31 - __clz(mask);
         mask &= ~(1u << l);
         const int j = c0 + l;
-        const float4 A = sA[warp][l], B = sB[warp][l], Cc = sC[warp][l];
-        const int g = __float_as_int(Cc.w);
+        const float4 P = sP[warp][l], Q = sQ[warp][l];
+        const int g = __float_as_int(P.w);
+        float G[PPT], og[PPT], dxs[PPT], dys[PPT];
+        bool cand[PPT];
+        bool anyc = false;
+#pragma unroll
+        for (int k = 0; k < PPT; k++) {
+          dxs[k] = __fsub_rn(lxf[k], P.x);
+          dys[k] = __fsub_rn(lyf[k], P.y);
+          G[k] = gauss(dxs[k], dys[k], Q);
+          og[k] = __fmul_rn(P.z, G[k]);
+          cand[k] = j < last[k] && og[k] >= p.alpha_min;
+          anyc = anyc || cand[k];
+        }
+        if (!__any_sync(0xffffffffu, anyc)) continue;
+        const int slot = g & (S - 1);
+        if (s_ckey[warp][slot] != g) {  // warp-uniform miss: every lane searches, coherently
+#pragma unroll
+          for (int k = 0; k < PPT; k++) {
+            int best = -1;
+            s_cw[warp][slot][k][lane] = p.use_boundary
+                ? w_search(bl, g, lxf[k], lyf[k], idq[k] == g, best, n_cand) : 1.0f;
+            s_cb[warp][slot][k][lane] = best;
+          }
+          __syncwarp();
+          if (lane == 0) s_ckey[warp][slot] = g;
+          __syncwarp();
+        }
         float acc[9];
 #pragma unroll
         for (int q = 0; q < 9; q++) acc[q] = 0.f;
         bool any = false;
+        const float4 Cc = sC[warp][l];
 #pragma unroll
         for (int k = 0; k < PPT; k++) {
-          const PairGeo pg = pair_geo2(px[k], py[k], A, B);
-          const float G = __expf(pg.power);
-          const float og = __fmul_rn(B.w, G);
-          const bool cand = j < last[k] && og >= p.alpha_min;
-          if (!__any_sync(0xffffffffu, cand)) continue;
-          float wv;
-          int bi;
-          cache[k].get(g, px[k], py[k], idq[k], bprim, brec, bn, p.use_boundary, wv, bi, n_cand);
-          if (!cand) continue;
+          if (!cand[k]) continue;
           n_sup++;
-          const float raw = __fmul_rn(og, wv);
+          const float wv = s_cw[warp][slot][k][lane];
+          const float raw = __fmul_rn(og[k], wv);
           const float alpha = fminf(p.alpha_max, raw);
           if (alpha < p.alpha_min) continue;
           any = true;
@@ -477,25 +484,28 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
           }
           dl_da *= Tr[k];
           if (raw >= p.alpha_max) continue;  // clamped: alpha is constant
-          acc[5] += dl_da * wv * G;
-          const float dl_dw = dl_da * B.w * G;
-          const float dl_dpow = dl_da * og * wv;
-          const float dx = pg.dx, dy = pg.dy;  // q - mu
+          acc[5] += dl_da * wv * G[k];
+          const float dl_dw = dl_da * P.z * G[k];
+          const float dl_dpow = dl_da * og[k] * wv;
+          const float dx = dxs[k], dy = dys[k];  // q - mu
           acc[2] += dl_dpow * (-0.5f * dx * dx);
           acc[3] += dl_dpow * (-dx * dy);
           acc[4] += dl_dpow * (-0.5f * dy * dy);
-          acc[0] += dl_dpow * (B.x * dx + B.y * dy);
-          acc[1] += dl_dpow * (B.y * dx + B.z * dy);
+          acc[0] += dl_dpow * (Q.x * dx + Q.y * dy);
+          acc[1] += dl_dpow * (Q.y * dx + Q.z * dy);
+          const int bi = s_cb[warp][slot][k][lane];
           if (bi >= 0) {
-            // rho and gamma of the most influential boundary point, by the
-            // same operations as the search
-            const float4 b = brec[bi];
-            const unsigned qxy = __float_as_uint(b.x);
-            const float bx = __fsub_rn((float)(px[k] - (int)(qxy & 0xffffu)), b.y);
-            const float by = __fsub_rn((float)(py[k] - (int)(qxy >> 16)), b.z);
-            const float r2 = __fmul_rn(__fmaf_rn(bx, bx, __fmul_rn(by, by)), __fmul_rn(b.w, b.w));
+            // rho, gamma of the most influential boundary point from the search's
+            // tile-local record; the direction of dl/db from the pixel-relative one
+            const float4 b = bl.get(bi);
+            const float ex = __fsub_rn(lxf[k], b.x), ey = __fsub_rn(lyf[k], b.y);
+            const float r2 = __fmul_rn(__fmaf_rn(ex, ex, __fmul_rn(ey, ey)), b.z);
             const float rho = __fsqrt_rn(r2);
             const float gam = exp2f(__fsub_rn(rho, 1.0f));
+            const float4 bg = bl.glob[bi];
+            const unsigned qxy = __float_as_uint(bg.x);
+            const float bx = (float)(ti.x0 + (int)lxf[k] - (int)(qxy & 0xffffu)) - bg.y;
+            const float by = (float)(ti.y0 + (int)lyf[k] - (int)(qxy >> 16)) - bg.z;
             const float d = sqrtf(bx * bx + by * by);
             if (d > 0.f) {
               const float sgn = (idq[k] == g) ? 1.0f : -1.0f;
@@ -515,8 +525,8 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
           const float part = warp_reduce_scatter8(acc);
           const float s8 = warp_sum(acc[8]);
           float *gg = w.gg + 12 * (size_t)sG[warp][l];
-          const int slot = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-          if ((lane & 3) == 0 && part != 0.f) atomicAdd(gg + slot, part);
+          const int gslot = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+          if ((lane & 3) == 0 && part != 0.f) atomicAdd(gg + gslot, part);
           if (lane == 1 && s8 != 0.f) atomicAdd(gg + 8, s8);
         }
       }
@@ -529,15 +539,27 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
 template <int T>
 int launch_fwd_t(const Params &p, const Work &w, float *image, cudaStream_t st, int sms) {
   int grid = p.tiles < sms * 8 ? p.tiles : sms * 8;
-  if (grid > 0) k_composite_fwd<T><<<grid, TileCfg<T>::NT, 0, st>>>(p, w, image);
+  if (grid > 0)
+    k_composite_fwd<T><<<grid, TileCfg<T>::NT, sizeof(BlendShared<T, false>), st>>>(p, w, image);
   return grid > 0 ? 1 : 0;
 }
 
 template <int T>
 int launch_bwd_t(const Params &p, const Work &w, const float *dimage, cudaStream_t st, int sms) {
   int grid = p.tiles < sms * 8 ? p.tiles : sms * 8;
-  if (grid > 0) k_composite_bwd<T><<<grid, TileCfg<T>::NT, 0, st>>>(p, w, dimage);
+  if (grid > 0)
+    k_composite_bwd<T><<<grid, TileCfg<T>::NT, sizeof(BlendShared<T, true>), st>>>(p, w, dimage);
   return grid > 0 ? 1 : 0;
+}
+
+template <int T>
+cudaError_t configure_t() {
+  cudaError_t e = cudaFuncSetAttribute(k_composite_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(BlendShared<T, false>));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_composite_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(BlendShared<T, true>));
+  return e;
 }
 
 int num_sms() {
@@ -552,6 +574,13 @@ int num_sms() {
 }
 
 }  // namespace
+
+cudaError_t configure_composite() {
+  cudaError_t e = configure_t<8>();
+  if (e == cudaSuccess) e = configure_t<16>();
+  if (e == cudaSuccess) e = configure_t<32>();
+  return e;
+}
 
 int launch_composite_fwd(const Params &p, const Work &w, float *image, cudaStream_t st) {
   cudaMemsetAsync(w.counters + kQueueFwd, 0, sizeof(int), st);
