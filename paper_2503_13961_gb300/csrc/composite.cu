@@ -37,7 +37,11 @@ struct TileCfg {
   static constexpr int WX = (T == 32) ? 16 : 8;
   static constexpr int WY = (T == 32) ? 8 : 4;
   static constexpr int WPR = T / WX;         // warp blocks per tile row
-  static constexpr int SLOTS = (PPT == 1) ? 16 : 4;  // direct-mapped primitive cache per warp
+  // primitive cache per warp (fully associative, FIFO): slot keys one per lane
+  static constexpr int SLOTS = (PPT == 1) ? 16 : 8;
+  // resident blocks per SM the backward kernel is compiled for (its shared
+  // memory allows this many; the register budget follows)
+  static constexpr int MINB_BWD = (T == 8) ? 6 : (T == 16) ? 3 : 2;
 };
 
 template <int T>
@@ -60,27 +64,38 @@ __device__ __forceinline__ float gauss(float dx, float dy, const float4 &Q) {
   return ex2(__fmaf_rn(e, -0.5f * kLog2e, __fmul_rn(-kLog2e, f)));
 }
 
-// a boundary record relative to the tile origin: (x, y, 1/sigma^2, 1/sigma)
-__device__ __forceinline__ float4 to_local(const float4 rec, int x0, int y0) {
+// A boundary record in the form the search uses: pixel coordinates of the
+// boundary pixel as exact floats and the offset of b from its centre, so that
+// q - b = (q - qb) - off takes one exact and one rounded subtraction whatever
+// the tile (images do not depend on the tile size).
+__device__ __forceinline__ float4 to_search(const float4 rec) {
   const unsigned qxy = __float_as_uint(rec.x);
-  return make_float4(__fadd_rn((float)((int)(qxy & 0xffffu) - x0), rec.y),
-                     __fadd_rn((float)((int)(qxy >> 16) - y0), rec.z), __fmul_rn(rec.w, rec.w), rec.w);
+  return make_float4((float)(int)(qxy & 0xffffu), (float)(int)(qxy >> 16), rec.y, rec.z);
 }
 
 // the tile's boundary candidates, sorted by (primitive, index)
 struct BList {
   const int *prim;
-  const float4 *loc;   // tile-local records in shared memory (if cached)
+  const float4 *loc;   // search-form records in shared memory (if cached)
+  const float *isig;   // 1 / sigma in shared memory (if cached)
   const float4 *glob;  // pixel-relative records in global memory
-  int n, x0, y0;
+  int n;
   bool cached;
-  __device__ __forceinline__ float4 get(int i) const { return cached ? loc[i] : to_local(glob[i], x0, y0); }
+  __device__ __forceinline__ float4 get(int i, float &is) const {
+    if (cached) {
+      is = isig[i];
+      return loc[i];
+    }
+    const float4 r = glob[i];
+    is = r.w;
+    return to_search(r);
+  }
 };
 
-// Eq. 6-7 at tile-local pixel (lx, ly) for primitive g: gamma* = min over
-// g's boundary points of min(2^(rho - 1), 1), rho = |q - b| / sigma_b;
-// w = gamma* inside g, 1 - gamma* outside. best: candidate with rho < 1, else -1.
-__device__ __forceinline__ float w_search(const BList &bl, int g, float lx, float ly, bool inside, int &best,
+// Eq. 6-7 at pixel (px, py) for primitive g: gamma* = min over g's boundary
+// points of min(2^(rho - 1), 1), rho = |q - b| / sigma_b; w = gamma* inside
+// g, 1 - gamma* outside. best: candidate with rho < 1, else -1.
+__device__ __forceinline__ float w_search(const BList &bl, int g, float pxf, float pyf, bool inside, int &best,
                                           unsigned &cands) {
   int lo = 0, hi = bl.n;
   while (lo < hi) {
@@ -90,9 +105,10 @@ __device__ __forceinline__ float w_search(const BList &bl, int g, float lx, floa
   float r2min = 3.0e38f;
   best = -1;
   for (int i = lo; i < bl.n && bl.prim[i] == g; i++) {
-    const float4 b = bl.get(i);
-    const float dx = __fsub_rn(lx, b.x), dy = __fsub_rn(ly, b.y);
-    const float r2 = __fmul_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)), b.z);
+    float is;
+    const float4 b = bl.get(i, is);
+    const float dx = __fsub_rn(__fsub_rn(pxf, b.x), b.z), dy = __fsub_rn(__fsub_rn(pyf, b.y), b.w);
+    const float r2 = __fmul_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)), __fmul_rn(is, is));
     if (r2 < r2min) {
       r2min = r2;
       best = i;
@@ -132,27 +148,30 @@ __device__ inline TileInfo tile_info(const Params &p, const Work &w, int tile, i
 }
 
 template <int NT>
-__device__ __forceinline__ BList load_boundary(const TileInfo &ti, const Work &w, int *s_bprim, float4 *s_bloc) {
+__device__ __forceinline__ BList load_boundary(const TileInfo &ti, const Work &w, int *s_bprim, float4 *s_bloc,
+                                               float *s_bisig) {
   BList bl;
   bl.n = (int)ti.bn;
-  bl.x0 = ti.x0;
-  bl.y0 = ti.y0;
   bl.glob = w.bl_rec + ti.bs;
   bl.cached = ti.bn <= kBCap;
   if (bl.cached) {
     for (int i = threadIdx.x; i < ti.bn; i += NT) {
+      const float4 r = w.bl_rec[ti.bs + i];
       s_bprim[i] = w.bl_prim[ti.bs + i];
-      s_bloc[i] = to_local(w.bl_rec[ti.bs + i], ti.x0, ti.y0);
+      s_bloc[i] = to_search(r);
+      s_bisig[i] = r.w;
     }
   }
   bl.prim = bl.cached ? s_bprim : w.bl_prim + ti.bs;
   bl.loc = s_bloc;
+  bl.isig = s_bisig;
   return bl;
 }
 
 // Stage this warp's hits of the chunk [c0, c0 + 32) of the tile's list:
-// P = (centre x, y relative to the tile origin, opacity, bits(prim)),
-// Q = conic (a, b, c), C = colour. Returns the ballot of hits.
+// P = (pixel x, y of the Gaussian as exact floats, offset x, y of its mean),
+// Q = (conic a, b, c, opacity), C = (colour, bits(prim)). The warp block is
+// [bx0, bx1] x [by0, by1] in pixel coordinates. Returns the ballot of hits.
 __device__ __forceinline__ unsigned stage_chunk(const Work &w, const TileInfo &ti, int jl, int jend, float bx0, float bx1,
                                                 float by0, float by1, float4 *sP, float4 *sQ, float4 *sC, int *sG) {
   const int lane = threadIdx.x & 31;
@@ -161,15 +180,13 @@ __device__ __forceinline__ unsigned stage_chunk(const Work &w, const TileInfo &t
     const unsigned gi = (unsigned)(w.gkeys[ti.gs + jl] & kIndexMask);
     const float4 A = w.gA[gi];
     const unsigned qxy = __float_as_uint(A.z);
-    const float cx = __fadd_rn((float)((int)(qxy & 0xffffu) - ti.x0), A.x);
-    const float cy = __fadd_rn((float)((int)(qxy >> 16) - ti.y0), A.y);
-    const float r = A.w;
+    const float gx = (float)(int)(qxy & 0xffffu), gy = (float)(int)(qxy >> 16);
+    const float cx = gx + A.x, cy = gy + A.y, r = A.w;
     hit = r >= 0.f && cx + r >= bx0 && cx - r <= bx1 && cy + r >= by0 && cy - r <= by1;
     if (hit) {
-      const float4 B = w.gB[gi], C = w.gC[gi];
-      sP[lane] = make_float4(cx, cy, B.w, C.w);
-      sQ[lane] = make_float4(B.x, B.y, B.z, 0.f);
-      sC[lane] = make_float4(C.x, C.y, C.z, 0.f);
+      sP[lane] = make_float4(gx, gy, A.x, A.y);
+      sQ[lane] = w.gB[gi];
+      sC[lane] = w.gC[gi];
       if (sG) sG[lane] = (int)gi;
     }
   }
@@ -196,13 +213,20 @@ struct BlendShared {
   using Cfg = TileCfg<T>;
   float4 sP[Cfg::NW][32], sQ[Cfg::NW][32], sC[Cfg::NW][32];
   float4 s_bloc[kBCap];
-  float s_cw[Cfg::NW][Cfg::SLOTS][Cfg::PPT][32];
-  int s_cb[BWD ? Cfg::NW : 1][Cfg::SLOTS][Cfg::PPT][32];
+  float s_cw[Cfg::NW][Cfg::SLOTS][Cfg::PPT][32];     // cached w per slot and pixel
+  int s_cb[BWD ? Cfg::NW : 1][Cfg::SLOTS][Cfg::PPT][32];  // cached boundary candidate
   int sG[Cfg::NW][32];
-  int s_ckey[Cfg::NW][Cfg::SLOTS];
   int s_bprim[kBCap];
+  float s_bisig[kBCap];
   int s_tile;
 };
+
+// Warp-wide lookup of primitive g in the warp's cache: lane s < SLOTS holds
+// the key of slot s. Returns the slot, or -1 (warp-uniform) on a miss.
+__device__ __forceinline__ int cache_find(int ckey, int g) {
+  const unsigned m = __ballot_sync(0xffffffffu, ckey == g);
+  return m ? __ffs(m) - 1 : -1;
+}
 
 template <int T>
 __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work w, float *image) {
@@ -213,10 +237,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work
   auto &sP = sh.sP;
   auto &sQ = sh.sQ;
   auto &sC = sh.sC;
-  auto &s_ckey = sh.s_ckey;
   auto &s_cw = sh.s_cw;
-  auto &s_bprim = sh.s_bprim;
-  auto &s_bloc = sh.s_bloc;
   auto &s_tile = sh.s_tile;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (;;) {
@@ -226,25 +247,25 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work
     const int tile = s_tile;
     if (tile >= p.tiles) break;
     const TileInfo ti = tile_info(p, w, tile, T);
-    const BList bl = load_boundary<NT>(ti, w, s_bprim, s_bloc);
-    if (lane < S) s_ckey[warp][lane] = -2;
+    const BList bl = load_boundary<NT>(ti, w, sh.s_bprim, sh.s_bloc, sh.s_bisig);
     __syncthreads();
-    // the warp's pixel block, relative to the tile origin
-    const int wxl = (warp % Cfg::WPR) * Cfg::WX, wyl = (warp / Cfg::WPR) * Cfg::WY;
-    const float bx0 = (float)wxl, bx1 = (float)(wxl + Cfg::WX - 1);
-    const float by0 = (float)wyl, by1 = (float)(wyl + Cfg::WY - 1);
+    // the warp's pixel block
+    const int wx = ti.x0 + (warp % Cfg::WPR) * Cfg::WX, wy = ti.y0 + (warp / Cfg::WPR) * Cfg::WY;
+    const float bx0 = (float)wx, bx1 = (float)(wx + Cfg::WX - 1);
+    const float by0 = (float)wy, by1 = (float)(wy + Cfg::WY - 1);
 
-    float C[PPT][3], Tr[PPT], lxf[PPT], lyf[PPT];
+    float C[PPT][3], Tr[PPT], pxf[PPT], pyf[PPT];
     int last[PPT], idq[PPT], pix[PPT];
     bool done[PPT];
     unsigned n_sup = 0, n_comp = 0, n_cand = 0;
+    int ckey = -2, cnext = 0;
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
       int lx, ly;
       lane_pixel<T>(warp, lane, k, lx, ly);
-      lxf[k] = (float)lx;
-      lyf[k] = (float)ly;
       const int px = ti.x0 + lx, py = ti.y0 + ly;
+      pxf[k] = (float)px;
+      pyf[k] = (float)py;
       const bool inside = px < ti.W && py < ti.H;
       pix[k] = inside ? ti.pix_off + py * ti.W + px : -1;
       done[k] = !inside;
@@ -264,28 +285,31 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work
         const int l = __ffs(mask) - 1;
         mask &= mask - 1;
         const float4 P = sP[warp][l], Q = sQ[warp][l];
-        const int g = __float_as_int(P.w);
         float og[PPT];
         bool cand[PPT];
         bool anyc = false;
 #pragma unroll
         for (int k = 0; k < PPT; k++) {
-          og[k] = __fmul_rn(P.z, gauss(__fsub_rn(lxf[k], P.x), __fsub_rn(lyf[k], P.y), Q));
+          // q - mu: the first difference is exact
+          const float dx = __fsub_rn(__fsub_rn(pxf[k], P.x), P.z), dy = __fsub_rn(__fsub_rn(pyf[k], P.y), P.w);
+          og[k] = __fmul_rn(Q.w, gauss(dx, dy, Q));
           cand[k] = !done[k] && og[k] >= p.alpha_min;  // w <= 1: else alpha < alpha_min
           anyc = anyc || cand[k];
         }
         if (!__any_sync(0xffffffffu, anyc)) continue;
-        const int slot = g & (S - 1);
-        if (s_ckey[warp][slot] != g) {  // warp-uniform miss: every lane searches, coherently
+        const float4 Cc = sC[warp][l];
+        const int g = __float_as_int(Cc.w);
+        int slot = cache_find(ckey, g);
+        if (slot < 0) {  // warp-uniform miss: every lane searches, coherently
+          slot = cnext;
+          cnext = (cnext + 1) & (S - 1);
 #pragma unroll
           for (int k = 0; k < PPT; k++) {
             int best;
             s_cw[warp][slot][k][lane] = p.use_boundary
-                ? w_search(bl, g, lxf[k], lyf[k], idq[k] == g, best, n_cand) : 1.0f;
+                ? w_search(bl, g, pxf[k], pyf[k], idq[k] == g, best, n_cand) : 1.0f;
           }
-          __syncwarp();
-          if (lane == 0) s_ckey[warp][slot] = g;
-          __syncwarp();
+          if (lane == slot) ckey = g;
         }
 #pragma unroll
         for (int k = 0; k < PPT; k++) {
@@ -298,7 +322,6 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work
             done[k] = true;
             continue;
           }
-          const float4 Cc = sC[warp][l];
           const float ta = __fmul_rn(Tr[k], alpha);
           C[k][0] = __fmaf_rn(ta, Cc.x, C[k][0]);
           C[k][1] = __fmaf_rn(ta, Cc.y, C[k][1]);
@@ -353,7 +376,7 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float *v) {
 }
 
 template <int T>
-__global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work w, const float *dimage) {
+__global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_composite_bwd(Params p, Work w, const float *dimage) {
   using Cfg = TileCfg<T>;
   constexpr int NT = Cfg::NT, PPT = Cfg::PPT, S = Cfg::SLOTS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -362,11 +385,8 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
   auto &sQ = sh.sQ;
   auto &sC = sh.sC;
   auto &sG = sh.sG;
-  auto &s_ckey = sh.s_ckey;
   auto &s_cw = sh.s_cw;
   auto &s_cb = sh.s_cb;
-  auto &s_bprim = sh.s_bprim;
-  auto &s_bloc = sh.s_bloc;
   auto &s_tile = sh.s_tile;
   const float LN2 = 0.69314718055994531f;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -377,26 +397,26 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
     const int tile = s_tile;
     if (tile >= p.tiles) break;
     const TileInfo ti = tile_info(p, w, tile, T);
-    const BList bl = load_boundary<NT>(ti, w, s_bprim, s_bloc);
-    if (lane < S) s_ckey[warp][lane] = -2;
+    const BList bl = load_boundary<NT>(ti, w, sh.s_bprim, sh.s_bloc, sh.s_bisig);
     __syncthreads();
     const unsigned long long *bkeys = w.bkeys + ti.bs;
-    const int wxl = (warp % Cfg::WPR) * Cfg::WX, wyl = (warp / Cfg::WPR) * Cfg::WY;
-    const float bx0 = (float)wxl, bx1 = (float)(wxl + Cfg::WX - 1);
-    const float by0 = (float)wyl, by1 = (float)(wyl + Cfg::WY - 1);
+    const int wx = ti.x0 + (warp % Cfg::WPR) * Cfg::WX, wy = ti.y0 + (warp / Cfg::WPR) * Cfg::WY;
+    const float bx0 = (float)wx, bx1 = (float)(wx + Cfg::WX - 1);
+    const float by0 = (float)wy, by1 = (float)(wy + Cfg::WY - 1);
 
     // R: colour behind the current pair, seen through the pairs behind it
-    float Tr[PPT], R[PPT][3], dC[PPT][3], lxf[PPT], lyf[PPT];
+    float Tr[PPT], R[PPT][3], dC[PPT][3], pxf[PPT], pyf[PPT];
     int last[PPT], idq[PPT];
     unsigned n_sup = 0, n_comp = 0, n_cand = 0;
+    int ckey = -2, cnext = 0;
     int mylast = 0;
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
       int lx, ly;
       lane_pixel<T>(warp, lane, k, lx, ly);
-      lxf[k] = (float)lx;
-      lyf[k] = (float)ly;
       const int px = ti.x0 + lx, py = ti.y0 + ly;
+      pxf[k] = (float)px;
+      pyf[k] = (float)py;
       last[k] = 0;
       idq[k] = -1;
       Tr[k] = 1.f;
@@ -426,38 +446,38 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
         mask &= ~(1u << l);
         const int j = c0 + l;
         const float4 P = sP[warp][l], Q = sQ[warp][l];
-        const int g = __float_as_int(P.w);
         float G[PPT], og[PPT], dxs[PPT], dys[PPT];
         bool cand[PPT];
         bool anyc = false;
 #pragma unroll
         for (int k = 0; k < PPT; k++) {
-          dxs[k] = __fsub_rn(lxf[k], P.x);
-          dys[k] = __fsub_rn(lyf[k], P.y);
+          dxs[k] = __fsub_rn(__fsub_rn(pxf[k], P.x), P.z);
+          dys[k] = __fsub_rn(__fsub_rn(pyf[k], P.y), P.w);
           G[k] = gauss(dxs[k], dys[k], Q);
-          og[k] = __fmul_rn(P.z, G[k]);
+          og[k] = __fmul_rn(Q.w, G[k]);
           cand[k] = j < last[k] && og[k] >= p.alpha_min;
           anyc = anyc || cand[k];
         }
         if (!__any_sync(0xffffffffu, anyc)) continue;
-        const int slot = g & (S - 1);
-        if (s_ckey[warp][slot] != g) {  // warp-uniform miss: every lane searches, coherently
+        const float4 Cc = sC[warp][l];
+        const int g = __float_as_int(Cc.w);
+        int slot = cache_find(ckey, g);
+        if (slot < 0) {  // warp-uniform miss: every lane searches, coherently
+          slot = cnext;
+          cnext = (cnext + 1) & (S - 1);
 #pragma unroll
           for (int k = 0; k < PPT; k++) {
             int best = -1;
             s_cw[warp][slot][k][lane] = p.use_boundary
-                ? w_search(bl, g, lxf[k], lyf[k], idq[k] == g, best, n_cand) : 1.0f;
+                ? w_search(bl, g, pxf[k], pyf[k], idq[k] == g, best, n_cand) : 1.0f;
             s_cb[warp][slot][k][lane] = best;
           }
-          __syncwarp();
-          if (lane == 0) s_ckey[warp][slot] = g;
-          __syncwarp();
+          if (lane == slot) ckey = g;
         }
         float acc[9];
 #pragma unroll
         for (int q = 0; q < 9; q++) acc[q] = 0.f;
         bool any = false;
-        const float4 Cc = sC[warp][l];
 #pragma unroll
         for (int k = 0; k < PPT; k++) {
           if (!cand[k]) continue;
@@ -485,7 +505,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
           dl_da *= Tr[k];
           if (raw >= p.alpha_max) continue;  // clamped: alpha is constant
           acc[5] += dl_da * wv * G[k];
-          const float dl_dw = dl_da * P.z * G[k];
+          const float dl_dw = dl_da * Q.w * G[k];
           const float dl_dpow = dl_da * og[k] * wv;
           const float dx = dxs[k], dy = dys[k];  // q - mu
           acc[2] += dl_dpow * (-0.5f * dx * dx);
@@ -495,26 +515,22 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd(Params p, Work
           acc[1] += dl_dpow * (Q.y * dx + Q.z * dy);
           const int bi = s_cb[warp][slot][k][lane];
           if (bi >= 0) {
-            // rho, gamma of the most influential boundary point from the search's
-            // tile-local record; the direction of dl/db from the pixel-relative one
-            const float4 b = bl.get(bi);
-            const float ex = __fsub_rn(lxf[k], b.x), ey = __fsub_rn(lyf[k], b.y);
-            const float r2 = __fmul_rn(__fmaf_rn(ex, ex, __fmul_rn(ey, ey)), b.z);
+            // rho and gamma of the most influential boundary point, with the
+            // operations of the search: q - b = (q - qb) - off
+            float isig;
+            const float4 b = bl.get(bi, isig);
+            const float ex = __fsub_rn(__fsub_rn(pxf[k], b.x), b.z), ey = __fsub_rn(__fsub_rn(pyf[k], b.y), b.w);
+            const float r2 = __fmul_rn(__fmaf_rn(ex, ex, __fmul_rn(ey, ey)), __fmul_rn(isig, isig));
             const float rho = __fsqrt_rn(r2);
             const float gam = exp2f(__fsub_rn(rho, 1.0f));
-            const float4 bg = bl.glob[bi];
-            const unsigned qxy = __float_as_uint(bg.x);
-            const float bx = (float)(ti.x0 + (int)lxf[k] - (int)(qxy & 0xffffu)) - bg.y;
-            const float by = (float)(ti.y0 + (int)lyf[k] - (int)(qxy >> 16)) - bg.z;
-            const float d = sqrtf(bx * bx + by * by);
+            const float d = sqrtf(ex * ex + ey * ey);
             if (d > 0.f) {
               const float sgn = (idq[k] == g) ? 1.0f : -1.0f;
               const float dl_drho = sgn * dl_dw * LN2 * gam;
-              const float isig = b.w;
               const unsigned bidx = (unsigned)(bkeys[bi] & 0xffffffffull);
               float *gb = reinterpret_cast<float *>(w.bg_grad + bidx);
-              atomicAdd(gb + 0, dl_drho * (-bx / d) * isig);
-              atomicAdd(gb + 1, dl_drho * (-by / d) * isig);
+              atomicAdd(gb + 0, dl_drho * (-ex / d) * isig);
+              atomicAdd(gb + 1, dl_drho * (-ey / d) * isig);
               atomicAdd(gb + 2, dl_drho * (-rho) * isig);
             }
           }
