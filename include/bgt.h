@@ -155,8 +155,10 @@ int bgt_get_tile_size(const bgt_handle *h);
  * *kernels_fwd / *kernels_bwd receive the kernels each pass enqueues.
  * units (nullable) receives the work units the blending kernels counted:
  * [0] pairs inside a Gaussian's support (o G >= alpha_min), [1] pairs
- * composited, [2] boundary candidates scanned by the Eq. 6 search, for the
- * forward; [4], [5], [6] the same for the backward; [3], [7] zero.
+ * composited, [2] boundary candidates scanned by the Eq. 6 search, [3]
+ * warp visits (a warp of 32 pixels evaluating one listed Gaussian with at
+ * least one pixel in its support), for the forward; [4]-[7] the same for
+ * the backward.
  * BGT_ERR_STATE if profiling is off or no profiled pair has run. */
 bgt_status bgt_set_profiling(bgt_handle *h, int on);
 bgt_status bgt_get_profile(bgt_handle *h, float ms[8], int *kernels_fwd, int *kernels_bwd,

@@ -122,8 +122,8 @@ struct Work {
 // Work units counted by the blending kernels when Params::stats is set:
 // pairs inside a Gaussian's support (o G >= alpha_min), pairs composited,
 // boundary candidates scanned by the coefficient search; forward then backward.
-enum Stat { kFwdSupport = 0, kFwdComposited = 1, kFwdCandidates = 2, kBwdSupport = 4, kBwdComposited = 5,
-            kBwdCandidates = 6 };
+enum Stat { kFwdSupport = 0, kFwdComposited = 1, kFwdCandidates = 2, kFwdVisits = 3, kBwdSupport = 4,
+            kBwdComposited = 5, kBwdCandidates = 6, kBwdVisits = 7 };
 
 constexpr int kIndexBits = 27;  // Gaussian index field of a pair key (<= 134M Gaussians per call)
 constexpr unsigned long long kIndexMask = (1ull << kIndexBits) - 1ull;

@@ -38,7 +38,8 @@ struct TileCfg {
   static constexpr int WY = (T == 32) ? 8 : 4;
   static constexpr int WPR = T / WX;         // warp blocks per tile row
   // primitive cache per warp (fully associative, FIFO): slot keys one per lane
-  static constexpr int SLOTS = (PPT == 1) ? 16 : 8;
+  static constexpr int SLOTS_FWD = (PPT == 1) ? 16 : 8;
+  static constexpr int SLOTS_BWD = (PPT == 1) ? 12 : 4;
   // resident blocks per SM the backward kernel is compiled for (its shared
   // memory allows this many; the register budget follows)
   static constexpr int MINB_BWD = (T == 8) ? 6 : (T == 16) ? 3 : 2;
@@ -92,16 +93,30 @@ struct BList {
   }
 };
 
-// Eq. 6-7 at pixel (px, py) for primitive g: gamma* = min over g's boundary
-// points of min(2^(rho - 1), 1), rho = |q - b| / sigma_b; w = gamma* inside
-// g, 1 - gamma* outside. best: candidate with rho < 1, else -1.
-__device__ __forceinline__ float w_search(const BList &bl, int g, float pxf, float pyf, bool inside, int &best,
-                                          unsigned &cands) {
-  int lo = 0, hi = bl.n;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (bl.prim[mid] < g) lo = mid + 1; else hi = mid;
+// First index i in the sorted prim[0, n) with prim[i] >= g, found by the
+// whole warp (g warp-uniform): each round probes 32 evenly spaced entries and
+// narrows the range 32-fold, so n <= 1024 takes two rounds.
+__device__ __forceinline__ int warp_lower_bound(const int *prim, int n, int g) {
+  const int lane = threadIdx.x & 31;
+  int lo = 0, len = n;
+  while (len > 32) {
+    const int step = (len + 31) >> 5;
+    const int idx = lo + (lane + 1) * step - 1;
+    const int v = idx < lo + len ? prim[idx] : 0x7fffffff;
+    const int c = __popc(__ballot_sync(0xffffffffu, v < g));
+    lo += c * step;
+    len = min(step, n - lo);
   }
+  const int v = lane < len ? prim[lo + lane] : 0x7fffffff;
+  return lo + __popc(__ballot_sync(0xffffffffu, v < g));
+}
+
+// Eq. 6-7 at pixel (px, py) for primitive g, whose boundary candidates start
+// at index lo: gamma* = min over g's boundary points of min(2^(rho - 1), 1),
+// rho = |q - b| / sigma_b; w = gamma* inside g, 1 - gamma* outside.
+// best: candidate with rho < 1, else -1.
+__device__ __forceinline__ float w_search(const BList &bl, int lo, int g, float pxf, float pyf, bool inside,
+                                          int &best, unsigned &cands) {
   float r2min = 3.0e38f;
   best = -1;
   for (int i = lo; i < bl.n && bl.prim[i] == g; i++) {
@@ -195,26 +210,33 @@ __device__ __forceinline__ unsigned stage_chunk(const Work &w, const TileInfo &t
   return mask;
 }
 
-__device__ __forceinline__ void flush_stats(unsigned long long *stats, int base, unsigned a, unsigned b, unsigned c) {
+// per-lane counts a, b, c summed over the warp; d is warp-uniform
+__device__ __forceinline__ void flush_stats(unsigned long long *stats, int base, unsigned a, unsigned b, unsigned c,
+                                            unsigned d) {
   unsigned long long v[3] = {a, b, c};
 #pragma unroll
   for (int q = 0; q < 3; q++) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
   }
-  if ((threadIdx.x & 31) == 0)
+  if ((threadIdx.x & 31) == 0) {
     for (int q = 0; q < 3; q++)
       if (v[q]) atomicAdd(stats + base + q, v[q]);
+    if (d) atomicAdd(stats + base + 3, (unsigned long long)d);
+  }
 }
 
 // shared memory of the blending kernels (dynamic: above the 48 KB static limit)
 template <int T, bool BWD>
 struct BlendShared {
   using Cfg = TileCfg<T>;
+  static constexpr int S = BWD ? Cfg::SLOTS_BWD : Cfg::SLOTS_FWD;
   float4 sP[Cfg::NW][32], sQ[Cfg::NW][32], sC[Cfg::NW][32];
   float4 s_bloc[kBCap];
-  float s_cw[Cfg::NW][Cfg::SLOTS][Cfg::PPT][32];     // cached w per slot and pixel
-  int s_cb[BWD ? Cfg::NW : 1][Cfg::SLOTS][Cfg::PPT][32];  // cached boundary candidate
+  float s_cw[Cfg::NW][S][Cfg::PPT][32];                // cached w per slot and pixel
+  // backward only: the slot's boundary candidate (or -1), sum of dl/dw over its Gaussians
+  int s_cb[BWD ? Cfg::NW : 1][BWD ? S : 1][BWD ? Cfg::PPT : 1][32];
+  float s_cacc[BWD ? Cfg::NW : 1][BWD ? S : 1][BWD ? Cfg::PPT : 1][32];
   int sG[Cfg::NW][32];
   int s_bprim[kBCap];
   float s_bisig[kBCap];
@@ -231,7 +253,7 @@ __device__ __forceinline__ int cache_find(int ckey, int g) {
 template <int T>
 __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work w, float *image) {
   using Cfg = TileCfg<T>;
-  constexpr int NT = Cfg::NT, PPT = Cfg::PPT, S = Cfg::SLOTS;
+  constexpr int NT = Cfg::NT, PPT = Cfg::PPT, S = Cfg::SLOTS_FWD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto &sh = *reinterpret_cast<BlendShared<T, false> *>(smem_raw);
   auto &sP = sh.sP;
@@ -257,7 +279,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work
     float C[PPT][3], Tr[PPT], pxf[PPT], pyf[PPT];
     int last[PPT], idq[PPT], pix[PPT];
     bool done[PPT];
-    unsigned n_sup = 0, n_comp = 0, n_cand = 0;
+    unsigned n_sup = 0, n_comp = 0, n_cand = 0, n_visit = 0;
     int ckey = -2, cnext = 0;
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
@@ -297,17 +319,19 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work
           anyc = anyc || cand[k];
         }
         if (!__any_sync(0xffffffffu, anyc)) continue;
+        n_visit++;
         const float4 Cc = sC[warp][l];
         const int g = __float_as_int(Cc.w);
         int slot = cache_find(ckey, g);
         if (slot < 0) {  // warp-uniform miss: every lane searches, coherently
           slot = cnext;
-          cnext = (cnext + 1) & (S - 1);
+          cnext = (cnext + 1 == S) ? 0 : cnext + 1;
+          const int lo = p.use_boundary ? warp_lower_bound(bl.prim, bl.n, g) : 0;
 #pragma unroll
           for (int k = 0; k < PPT; k++) {
             int best;
             s_cw[warp][slot][k][lane] = p.use_boundary
-                ? w_search(bl, g, pxf[k], pyf[k], idq[k] == g, best, n_cand) : 1.0f;
+                ? w_search(bl, lo, g, pxf[k], pyf[k], idq[k] == g, best, n_cand) : 1.0f;
           }
           if (lane == slot) ckey = g;
         }
@@ -343,7 +367,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work
         w.n_contrib[pix[k]] = last[k];
       }
     }
-    if (p.stats) flush_stats(w.stats, kFwdSupport, n_sup, n_comp, n_cand);
+    if (p.stats) flush_stats(w.stats, kFwdSupport, n_sup, n_comp, n_cand, n_visit);
   }
 }
 
@@ -375,10 +399,44 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float *v) {
   return c;
 }
 
+// Boundary-point gradients of one cache slot (primitive g). For every pixel
+// the slot's w = gamma (inside g) or 1 - gamma with gamma = 2^(rho - 1) of the
+// same boundary point b for all of g's Gaussians, so their dl/dw add up
+// (sum) before dl/drho = +-ln2 gamma sum is taken through rho = |q - b| / sigma:
+// drho/db = -(q - b) / (|q - b| sigma), drho/dsigma = -rho / sigma.
+template <int PPT>
+__device__ __forceinline__ void flush_boundary(const BList &bl, const unsigned long long *bkeys, float4 *bg_grad,
+                                               const int *cb, const float *cacc, int g, const int *idq,
+                                               const float *pxf, const float *pyf) {
+  const float LN2 = 0.69314718055994531f;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < PPT; k++) {
+    const int bi = cb[k * 32 + lane];
+    const float sum = cacc[k * 32 + lane];
+    if (bi < 0 || sum == 0.f) continue;
+    // rho and gamma with the operations of the search
+    float isig;
+    const float4 b = bl.get(bi, isig);
+    const float ex = __fsub_rn(__fsub_rn(pxf[k], b.x), b.z), ey = __fsub_rn(__fsub_rn(pyf[k], b.y), b.w);
+    const float r2 = __fmul_rn(__fmaf_rn(ex, ex, __fmul_rn(ey, ey)), __fmul_rn(isig, isig));
+    const float rho = __fsqrt_rn(r2);
+    if (!(rho > 0.f)) continue;
+    const float gam = exp2f(__fsub_rn(rho, 1.0f));
+    const float dl_drho = ((idq[k] == g) ? LN2 : -LN2) * gam * sum;
+    const float s = dl_drho * isig * __frcp_rn(rho);  // (q - b) isig / rho is the unit direction
+    const unsigned bidx = (unsigned)(bkeys[bi] & 0xffffffffull);
+    float *gb = reinterpret_cast<float *>(bg_grad + bidx);
+    atomicAdd(gb + 0, -(ex * isig) * s);
+    atomicAdd(gb + 1, -(ey * isig) * s);
+    atomicAdd(gb + 2, -dl_drho * rho * isig);
+  }
+}
+
 template <int T>
 __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_composite_bwd(Params p, Work w, const float *dimage) {
   using Cfg = TileCfg<T>;
-  constexpr int NT = Cfg::NT, PPT = Cfg::PPT, S = Cfg::SLOTS;
+  constexpr int NT = Cfg::NT, PPT = Cfg::PPT, S = Cfg::SLOTS_BWD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto &sh = *reinterpret_cast<BlendShared<T, true> *>(smem_raw);
   auto &sP = sh.sP;
@@ -387,8 +445,8 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
   auto &sG = sh.sG;
   auto &s_cw = sh.s_cw;
   auto &s_cb = sh.s_cb;
+  auto &s_cacc = sh.s_cacc;
   auto &s_tile = sh.s_tile;
-  const float LN2 = 0.69314718055994531f;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (;;) {
     __syncthreads();
@@ -407,7 +465,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
     // R: colour behind the current pair, seen through the pairs behind it
     float Tr[PPT], R[PPT][3], dC[PPT][3], pxf[PPT], pyf[PPT];
     int last[PPT], idq[PPT];
-    unsigned n_sup = 0, n_comp = 0, n_cand = 0;
+    unsigned n_sup = 0, n_comp = 0, n_cand = 0, n_visit = 0;
     int ckey = -2, cnext = 0;
     int mylast = 0;
 #pragma unroll
@@ -459,18 +517,25 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
           anyc = anyc || cand[k];
         }
         if (!__any_sync(0xffffffffu, anyc)) continue;
+        n_visit++;
         const float4 Cc = sC[warp][l];
         const int g = __float_as_int(Cc.w);
         int slot = cache_find(ckey, g);
         if (slot < 0) {  // warp-uniform miss: every lane searches, coherently
           slot = cnext;
-          cnext = (cnext + 1) & (S - 1);
+          cnext = (cnext + 1 == S) ? 0 : cnext + 1;
+          const int old = __shfl_sync(0xffffffffu, ckey, slot);
+          if (old >= 0 && p.use_boundary)
+            flush_boundary<PPT>(bl, bkeys, w.bg_grad, &s_cb[warp][slot][0][0], &s_cacc[warp][slot][0][0], old, idq,
+                                pxf, pyf);
+          const int lo = p.use_boundary ? warp_lower_bound(bl.prim, bl.n, g) : 0;
 #pragma unroll
           for (int k = 0; k < PPT; k++) {
             int best = -1;
             s_cw[warp][slot][k][lane] = p.use_boundary
-                ? w_search(bl, g, pxf[k], pyf[k], idq[k] == g, best, n_cand) : 1.0f;
+                ? w_search(bl, lo, g, pxf[k], pyf[k], idq[k] == g, best, n_cand) : 1.0f;
             s_cb[warp][slot][k][lane] = best;
+            s_cacc[warp][slot][k][lane] = 0.f;
           }
           if (lane == slot) ckey = g;
         }
@@ -513,27 +578,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
           acc[4] += dl_dpow * (-0.5f * dy * dy);
           acc[0] += dl_dpow * (Q.x * dx + Q.y * dy);
           acc[1] += dl_dpow * (Q.y * dx + Q.z * dy);
-          const int bi = s_cb[warp][slot][k][lane];
-          if (bi >= 0) {
-            // rho and gamma of the most influential boundary point, with the
-            // operations of the search: q - b = (q - qb) - off
-            float isig;
-            const float4 b = bl.get(bi, isig);
-            const float ex = __fsub_rn(__fsub_rn(pxf[k], b.x), b.z), ey = __fsub_rn(__fsub_rn(pyf[k], b.y), b.w);
-            const float r2 = __fmul_rn(__fmaf_rn(ex, ex, __fmul_rn(ey, ey)), __fmul_rn(isig, isig));
-            const float rho = __fsqrt_rn(r2);
-            const float gam = exp2f(__fsub_rn(rho, 1.0f));
-            const float d = sqrtf(ex * ex + ey * ey);
-            if (d > 0.f) {
-              const float sgn = (idq[k] == g) ? 1.0f : -1.0f;
-              const float dl_drho = sgn * dl_dw * LN2 * gam;
-              const unsigned bidx = (unsigned)(bkeys[bi] & 0xffffffffull);
-              float *gb = reinterpret_cast<float *>(w.bg_grad + bidx);
-              atomicAdd(gb + 0, dl_drho * (-ex / d) * isig);
-              atomicAdd(gb + 1, dl_drho * (-ey / d) * isig);
-              atomicAdd(gb + 2, dl_drho * (-rho) * isig);
-            }
-          }
+          s_cacc[warp][slot][k][lane] += dl_dw;  // boundary-point gradient, taken per slot
         }
         if (__any_sync(0xffffffffu, any)) {
           // gradient slots: 0 dmu x, 1 dmu y, 2-4 dK, 5 do, 6-8 dcol; slots 0-7
@@ -548,7 +593,15 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
       }
       __syncwarp();
     }
-    if (p.stats) flush_stats(w.stats, kBwdSupport, n_sup, n_comp, n_cand);
+    if (p.use_boundary) {
+      for (int sl = 0; sl < S; sl++) {
+        const int old = __shfl_sync(0xffffffffu, ckey, sl);
+        if (old >= 0)
+          flush_boundary<PPT>(bl, bkeys, w.bg_grad, &s_cb[warp][sl][0][0], &s_cacc[warp][sl][0][0], old, idq, pxf,
+                              pyf);
+      }
+    }
+    if (p.stats) flush_stats(w.stats, kBwdSupport, n_sup, n_comp, n_cand, n_visit);
   }
 }
 

@@ -156,8 +156,8 @@ class Renderer:
     def set_profiling(self, on=True):
         self._check(self.lib.bgt_set_profiling(self.h, 1 if on else 0))
 
-    UNITS = ("fwd_support", "fwd_composited", "fwd_candidates", None, "bwd_support", "bwd_composited",
-             "bwd_candidates", None)
+    UNITS = ("fwd_support", "fwd_composited", "fwd_candidates", "fwd_warp_visits", "bwd_support",
+             "bwd_composited", "bwd_candidates", "bwd_warp_visits")
 
     def profile(self):
         """Device ms per stage of the last profiled forward + backward, kernel counts
