@@ -40,8 +40,9 @@ struct TileCfg {
   // primitive cache per warp (fully associative, FIFO): slot keys one per lane
   static constexpr int SLOTS_FWD = (PPT == 1) ? 16 : 8;
   static constexpr int SLOTS_BWD = (PPT == 1) ? 12 : 4;
-  // resident blocks per SM the backward kernel is compiled for (its shared
-  // memory allows this many; the register budget follows)
+  // resident blocks per SM the kernels are compiled for (their shared memory
+  // allows this many; the register budget follows)
+  static constexpr int MINB_FWD = (T == 8) ? 6 : (T == 16) ? 4 : 2;
   static constexpr int MINB_BWD = (T == 8) ? 6 : (T == 16) ? 3 : 2;
 };
 
@@ -93,45 +94,76 @@ struct BList {
   }
 };
 
-// First index i in the sorted prim[0, n) with prim[i] >= g, found by the
-// whole warp (g warp-uniform): each round probes 32 evenly spaced entries and
-// narrows the range 32-fold, so n <= 1024 takes two rounds.
-__device__ __forceinline__ int warp_lower_bound(const int *prim, int n, int g) {
-  const int lane = threadIdx.x & 31;
-  int lo = 0, len = n;
-  while (len > 32) {
-    const int step = (len + 31) >> 5;
-    const int idx = lo + (lane + 1) * step - 1;
-    const int v = idx < lo + len ? prim[idx] : 0x7fffffff;
-    const int c = __popc(__ballot_sync(0xffffffffu, v < g));
-    lo += c * step;
-    len = min(step, n - lo);
-  }
-  const int v = lane < len ? prim[lo + lane] : 0x7fffffff;
-  return lo + __popc(__ballot_sync(0xffffffffu, v < g));
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
-// Eq. 6-7 at pixel (px, py) for primitive g, whose boundary candidates start
-// at index lo: gamma* = min over g's boundary points of min(2^(rho - 1), 1),
+// One round of a warp-wide search in the sorted prim[a, a + len): 32 evenly
+// spaced probes narrow the range holding the first index whose entry fails
+// pred (entry < g, or entry <= g) 32-fold.
+template <bool LE>
+__device__ __forceinline__ void search_round(const int *prim, int g, int &a, int &len) {
+  const int lane = threadIdx.x & 31;
+  const int step = (len + 31) >> 5, end = a + len;
+  const int idx = a + (lane + 1) * step - 1;
+  const int v = idx < end ? prim[idx] : 0x7fffffff;
+  a += __popc(__ballot_sync(0xffffffffu, LE ? v <= g : v < g)) * step;
+  len = min(step, end - a);
+}
+
+// [lo, hi): the entries equal to g in the sorted prim[0, n), found by the
+// whole warp (g warp-uniform); both bounds are narrowed in the same rounds,
+// so n <= 1024 takes two rounds.
+__device__ __forceinline__ void warp_equal_range(const int *prim, int n, int g, int &lo, int &hi) {
+  const int lane = threadIdx.x & 31;
+  int a = 0, la = n, b = 0, lb = n;
+  while (la > 32 || lb > 32) {
+    if (la > 32) search_round<false>(prim, g, a, la);
+    if (lb > 32) search_round<true>(prim, g, b, lb);
+  }
+  const int va = lane < la ? prim[a + lane] : 0x7fffffff;
+  const int vb = lane < lb ? prim[b + lane] : 0x7fffffff;
+  lo = a + __popc(__ballot_sync(0xffffffffu, va < g));
+  hi = b + __popc(__ballot_sync(0xffffffffu, vb <= g));
+}
+
+// |q - b|^2 / sigma^2 for boundary candidate i at pixel (pxf, pyf)
+__device__ __forceinline__ float cand_r2(const BList &bl, int i, float pxf, float pyf) {
+  float is;
+  const float4 b = bl.get(i, is);
+  const float dx = __fsub_rn(__fsub_rn(pxf, b.x), b.z), dy = __fsub_rn(__fsub_rn(pyf, b.y), b.w);
+  return __fmul_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)), __fmul_rn(is, is));
+}
+
+// gamma = min(2^(rho - 1), 1) (Eq. 7) for rho^2 = r2 < 1
+__device__ __forceinline__ float gamma_of(float r2) { return ex2(__fsub_rn(sqrt_approx(r2), 1.0f)); }
+
+// Eq. 6-7 at pixel (px, py) for primitive g, whose boundary candidates are
+// [lo, hi): gamma* = min over g's boundary points of min(2^(rho - 1), 1),
 // rho = |q - b| / sigma_b; w = gamma* inside g, 1 - gamma* outside.
-// best: candidate with rho < 1, else -1.
-__device__ __forceinline__ float w_search(const BList &bl, int lo, int g, float pxf, float pyf, bool inside,
+// best: the first candidate of least rho if rho < 1, else -1. U candidates
+// are evaluated per iteration (instruction-level parallelism vs registers).
+template <int U>
+__device__ __forceinline__ float w_search(const BList &bl, int lo, int hi, float pxf, float pyf, bool inside,
                                           int &best, unsigned &cands) {
   float r2min = 3.0e38f;
   best = -1;
-  for (int i = lo; i < bl.n && bl.prim[i] == g; i++) {
-    float is;
-    const float4 b = bl.get(i, is);
-    const float dx = __fsub_rn(__fsub_rn(pxf, b.x), b.z), dy = __fsub_rn(__fsub_rn(pyf, b.y), b.w);
-    const float r2 = __fmul_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)), __fmul_rn(is, is));
-    if (r2 < r2min) {
-      r2min = r2;
-      best = i;
-    }
-    cands++;
+  for (int i = lo; i < hi; i += U) {
+    float r[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) r[u] = cand_r2(bl, min(i + u, hi - 1), pxf, pyf);
+#pragma unroll
+    for (int u = 0; u < U; u++)
+      if (r[u] < r2min) {  // a repeated last candidate never replaces itself
+        r2min = r[u];
+        best = min(i + u, hi - 1);
+      }
   }
+  cands += hi - lo;
   float gamma = 1.0f;
-  if (best >= 0 && r2min < 1.0f) gamma = exp2f(__fsub_rn(__fsqrt_rn(r2min), 1.0f));
+  if (best >= 0 && r2min < 1.0f) gamma = gamma_of(r2min);
   else best = -1;
   return inside ? gamma : __fsub_rn(1.0f, gamma);
 }
@@ -251,7 +283,7 @@ __device__ __forceinline__ int cache_find(int ckey, int g) {
 }
 
 template <int T>
-__global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work w, float *image) {
+__global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_composite_fwd(Params p, Work w, float *image) {
   using Cfg = TileCfg<T>;
   constexpr int NT = Cfg::NT, PPT = Cfg::PPT, S = Cfg::SLOTS_FWD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -326,12 +358,13 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_fwd(Params p, Work
         if (slot < 0) {  // warp-uniform miss: every lane searches, coherently
           slot = cnext;
           cnext = (cnext + 1 == S) ? 0 : cnext + 1;
-          const int lo = p.use_boundary ? warp_lower_bound(bl.prim, bl.n, g) : 0;
+          int lo = 0, hi = 0;
+          if (p.use_boundary) warp_equal_range(bl.prim, bl.n, g, lo, hi);
 #pragma unroll
           for (int k = 0; k < PPT; k++) {
             int best;
             s_cw[warp][slot][k][lane] = p.use_boundary
-                ? w_search(bl, lo, g, pxf[k], pyf[k], idq[k] == g, best, n_cand) : 1.0f;
+                ? w_search<2>(bl, lo, hi, pxf[k], pyf[k], idq[k] == g, best, n_cand) : 1.0f;
           }
           if (lane == slot) ckey = g;
         }
@@ -420,9 +453,9 @@ __device__ __forceinline__ void flush_boundary(const BList &bl, const unsigned l
     const float4 b = bl.get(bi, isig);
     const float ex = __fsub_rn(__fsub_rn(pxf[k], b.x), b.z), ey = __fsub_rn(__fsub_rn(pyf[k], b.y), b.w);
     const float r2 = __fmul_rn(__fmaf_rn(ex, ex, __fmul_rn(ey, ey)), __fmul_rn(isig, isig));
-    const float rho = __fsqrt_rn(r2);
+    const float rho = sqrt_approx(r2);
     if (!(rho > 0.f)) continue;
-    const float gam = exp2f(__fsub_rn(rho, 1.0f));
+    const float gam = gamma_of(r2);
     const float dl_drho = ((idq[k] == g) ? LN2 : -LN2) * gam * sum;
     const float s = dl_drho * isig * __frcp_rn(rho);  // (q - b) isig / rho is the unit direction
     const unsigned bidx = (unsigned)(bkeys[bi] & 0xffffffffull);
@@ -528,12 +561,13 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
           if (old >= 0 && p.use_boundary)
             flush_boundary<PPT>(bl, bkeys, w.bg_grad, &s_cb[warp][slot][0][0], &s_cacc[warp][slot][0][0], old, idq,
                                 pxf, pyf);
-          const int lo = p.use_boundary ? warp_lower_bound(bl.prim, bl.n, g) : 0;
+          int lo = 0, hi = 0;
+          if (p.use_boundary) warp_equal_range(bl.prim, bl.n, g, lo, hi);
 #pragma unroll
           for (int k = 0; k < PPT; k++) {
             int best = -1;
             s_cw[warp][slot][k][lane] = p.use_boundary
-                ? w_search(bl, lo, g, pxf[k], pyf[k], idq[k] == g, best, n_cand) : 1.0f;
+                ? w_search<2>(bl, lo, hi, pxf[k], pyf[k], idq[k] == g, best, n_cand) : 1.0f;
             s_cb[warp][slot][k][lane] = best;
             s_cacc[warp][slot][k][lane] = 0.f;
           }
