@@ -368,6 +368,7 @@ bgt_status bgt_create(const bgt_config *cfg, bgt_handle **out) {
   if (e == cudaSuccess) e = cudaMemset(h->w.status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(h->w.counters, 0, 16 * sizeof(int));
   if (e == cudaSuccess) e = bgt::configure_composite();
+  if (e == cudaSuccess) e = bgt::configure_binning();
   if (e != cudaSuccess) {
     bgt_destroy(h);
     return BGT_ERR_CUDA;

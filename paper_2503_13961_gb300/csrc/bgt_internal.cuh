@@ -350,6 +350,7 @@ int launch_resolve(const Params &p, const Scene &s, const Work &w, cudaStream_t 
 int launch_generate(const Params &p, const Scene &s, const Work &w, cudaStream_t st);
 int launch_binning(const Params &p, const Work &w, cudaStream_t st);
 cudaError_t configure_composite();  // opt the blending kernels into > 48 KB shared memory
+cudaError_t configure_binning();    // the same for the per-tile sort
 int launch_composite_fwd(const Params &p, const Work &w, float *image, cudaStream_t st);
 int launch_composite_bwd(const Params &p, const Work &w, const float *dimage, cudaStream_t st);
 int launch_chain(const Params &p, const Scene &s, const Work &w, const Grads &g, cudaStream_t st);

@@ -231,7 +231,8 @@ __device__ void radix_global(unsigned long long *keys, unsigned long long *tmp, 
   __syncthreads();
 }
 
-constexpr int kWarpSortCap = 512;  // keys a single warp sorts in its own shared memory
+constexpr int kWarpSortCap = 1024;  // keys a single warp sorts in its own shared memory
+constexpr int kTileSortSmem = (kSortThreads / 32) * kWarpSortCap * (int)sizeof(unsigned long long);
 
 __device__ inline void segment_bounds(const Params &p, const Work &w, int item, bool &bnd, long long &s0,
                                       long long &s1) {
@@ -253,15 +254,32 @@ __device__ inline void gather_boundary(const Work &w, long long s0, long long s1
   }
 }
 
+// Bitonic sort of sk[0, N) (N a power of two, 64..kWarpSortCap) by one warp:
+// every stage is N / 2 independent compare-exchanges, 1 / 32 of them per lane.
+__device__ __forceinline__ void warp_bitonic_smem(unsigned long long *sk, int N, int lane) {
+  for (int k = 2; k <= N; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = lane; t < (N >> 1); t += 32) {
+        const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));  // i has bit j clear; its partner is i + j
+        const unsigned long long a = sk[i], b = sk[i + j];
+        if ((a > b) == ((i & k) == 0)) {
+          sk[i] = b;
+          sk[i + j] = a;
+        }
+      }
+      __syncwarp();
+    }
+}
+
 // Warps take segments from a queue. Up to 32 keys: bitonic sort across the
 // lanes' registers; up to kWarpSortCap: bitonic sort in the warp's shared
 // memory; longer segments are appended to a list for k_tile_sort_big.
 __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Params p, Work w, int *big_list) {
-  __shared__ unsigned long long s_keys[kSortThreads / 32][kWarpSortCap];
+  extern __shared__ __align__(16) unsigned long long s_sort[];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const bool g_over = w.g_tstart[p.tiles] > p.max_pairs, b_over = w.b_tstart[p.tiles] > p.max_bpairs;
   const int items = 2 * p.tiles;
-  unsigned long long *sk = s_keys[wp];
+  unsigned long long *sk = s_sort + wp * kWarpSortCap;
   for (;;) {
     int item = 0;
     if (lane == 0) item = atomicAdd(w.counters + kQueueSort, 1);
@@ -292,20 +310,7 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Params p, Work w, in
       while (N < n) N <<= 1;
       for (int i = lane; i < N; i += 32) sk[i] = i < n ? keys[i] : ~0ull;
       __syncwarp();
-      for (int k = 2; k <= N; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
-          for (int i = lane; i < N; i += 32) {
-            const int ixj = i ^ j;
-            if (ixj > i) {
-              const unsigned long long a = sk[i], b = sk[ixj];
-              if ((a > b) == ((i & k) == 0)) {
-                sk[i] = b;
-                sk[ixj] = a;
-              }
-            }
-          }
-          __syncwarp();
-        }
+      warp_bitonic_smem(sk, N, lane);
       for (int i = lane; i < n; i += 32) keys[i] = sk[i];
       __syncwarp();
     }
@@ -361,12 +366,16 @@ int launch_exclusive_scan(const int *in, long long *out, int n, long long *aux, 
   return 3;
 }
 
+cudaError_t configure_binning() {
+  return cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSortSmem);
+}
+
 int launch_bin_sort_only(const Params &p, const Work &w, cudaStream_t st) {
   k_emit<<<4 * 152, 256, 0, st>>>(p, w);
   if (p.tiles <= 0) return 1;
   cudaMemsetAsync(w.counters + kQueueSort, 0, 2 * sizeof(int), st);
-  k_tile_sort<<<4 * 152, kSortThreads, 0, st>>>(p, w, w.big_list);
-  k_tile_sort_big<<<2 * 152, kSortThreads, 0, st>>>(p, w, w.big_list, w.gkeys + p.max_pairs, w.bkeys + p.max_bpairs);
+  k_tile_sort<<<3 * 152, kSortThreads, kTileSortSmem, st>>>(p, w, w.big_list);
+  k_tile_sort_big<<<4 * 152, kSortThreads, 0, st>>>(p, w, w.big_list, w.gkeys + p.max_pairs, w.bkeys + p.max_bpairs);
   return 3;
 }
 

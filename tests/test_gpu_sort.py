@@ -56,7 +56,7 @@ def _check_lists(g, W, H, tile, ranges, keys, ptr, idx, alpha_min):
             lst = lists[(y // tile) * tx + x // tile]
             keep = np.isin(lst, want)
             assert np.array_equal(lst[keep], want), f"pixel ({x},{y})"
-    return max(len(x) for x in lists)
+    return sorted(len(x) for x in lists)
 
 
 @pytest.mark.parametrize("tile", [8, 16, 32])
@@ -78,8 +78,22 @@ def test_bin_sort_large_tiles_use_global_radix_path(oracle, scenes):
     res = rd.bin_sort(g, W, H)
     rd.sync_status()
     ptr, idx = oracle.pixel_lists(g, W, H)
-    longest = _check_lists(g, W, H, 32, res["ranges"], res["keys"], ptr, idx, oracle.DEFAULTS["alpha_min"])
-    assert longest > 4096
+    lengths = _check_lists(g, W, H, 32, res["ranges"], res["keys"], ptr, idx, oracle.DEFAULTS["alpha_min"])
+    assert lengths[-1] > 4096
+
+
+def test_bin_sort_mid_size_tiles(oracle, scenes):
+    # tiles of 513..1024 keys (one warp, shared memory) and 1025..4096 keys
+    # (one block, shared memory) in the same call
+    W, H, n = 40, 36, 2000
+    g = scenes.random_gaussians(7, W, H, n, radius_px=(2.0, 5.0))
+    rd = _renderer(W, H, n, 32)
+    res = rd.bin_sort(g, W, H)
+    rd.sync_status()
+    ptr, idx = oracle.pixel_lists(g, W, H)
+    lengths = _check_lists(g, W, H, 32, res["ranges"], res["keys"], ptr, idx, oracle.DEFAULTS["alpha_min"])
+    assert any(512 < m <= 1024 for m in lengths)
+    assert any(1024 < m <= 4096 for m in lengths)
 
 
 def test_bin_sort_empty_and_single(oracle, scenes):
