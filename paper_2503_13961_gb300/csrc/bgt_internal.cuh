@@ -145,10 +145,23 @@ __device__ inline int find_view(const int *off, int V, int idx) {
   return lo;
 }
 
-__device__ inline float multinom(int n, int i, int j, int k) {
-  // n! / (i! j! k!) for n <= 4, exact in FP32
-  const float f[5] = {1.f, 1.f, 2.f, 6.f, 24.f};
-  return f[n] / (f[i] * f[j] * f[k]);
+// n! / (i! j! k!) for n <= 4 (exact in FP32)
+__host__ __device__ constexpr int factorial(int k) { return k <= 1 ? 1 : k * factorial(k - 1); }
+__host__ __device__ constexpr float multinom(int n, int i, int j, int k) {
+  return (float)(factorial(n) / (factorial(i) * factorial(j) * factorial(k)));
+}
+
+// Calls f(Degree<N>()) for the degree n (1..kMaxDegree), so that every loop
+// over Bernstein terms is unrolled at compile time.
+template <int N> struct Degree { static constexpr int value = N; };
+template <class F>
+inline void dispatch_degree(int n, F &&f) {
+  switch (n) {
+    case 1: f(Degree<1>()); break;
+    case 2: f(Degree<2>()); break;
+    case 3: f(Degree<3>()); break;
+    default: f(Degree<4>()); break;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -166,30 +179,32 @@ struct RVert {
   bool valid;
 };
 
-__device__ inline RVert raster_vertex(int n, const float *cp, int a, int b, int L, const View &v,
-                                      float near_z) {
+template <int N>
+__device__ inline RVert raster_vertex(const float *cp, int a, int b, int L, const View &v, float near_z) {
   RVert o;
   const float fL = (float)L;
   const float u = __fdiv_rn((float)a, fL);
   const float vv = __fdiv_rn((float)b, fL);
   const float w = __fdiv_rn((float)(L - a - b), fL);
-  float pu[kMaxDegree + 1], pv[kMaxDegree + 1], pw[kMaxDegree + 1];
+  float pu[N + 1], pv[N + 1], pw[N + 1];
   pu[0] = pv[0] = pw[0] = 1.0f;
 #pragma unroll
-  for (int m = 1; m <= kMaxDegree; m++) {
+  for (int m = 1; m <= N; m++) {
     pu[m] = __fmul_rn(pu[m - 1], u);
     pv[m] = __fmul_rn(pv[m - 1], vv);
     pw[m] = __fmul_rn(pw[m - 1], w);
   }
   float Sx = 0.f, Sy = 0.f, Sz = 0.f;
   int idx = 0;
-  for (int i = n; i >= 0; i--)
-    for (int j = n - i; j >= 0; j--) {
-      const int k = n - i - j;
-      const float B = __fmul_rn(__fmul_rn(__fmul_rn(multinom(n, i, j, k), pu[i]), pv[j]), pw[k]);
-      Sx = __fmaf_rn(B, cp[3 * idx + 0], Sx);
-      Sy = __fmaf_rn(B, cp[3 * idx + 1], Sy);
-      Sz = __fmaf_rn(B, cp[3 * idx + 2], Sz);
+#pragma unroll
+  for (int i = N; i >= 0; i--)
+#pragma unroll
+    for (int j = N - i; j >= 0; j--) {
+      const int k = N - i - j;
+      const float B = __fmul_rn(__fmul_rn(__fmul_rn(multinom(N, i, j, k), pu[i]), pv[j]), pw[k]);
+      Sx = __fmaf_rn(B, __ldg(cp + 3 * idx + 0), Sx);
+      Sy = __fmaf_rn(B, __ldg(cp + 3 * idx + 1), Sy);
+      Sz = __fmaf_rn(B, __ldg(cp + 3 * idx + 2), Sz);
       idx++;
     }
   float Xc = __fmul_rn(v.R[0], Sx); Xc = __fmaf_rn(v.R[1], Sy, Xc); Xc = __fmaf_rn(v.R[2], Sz, Xc); Xc = __fadd_rn(Xc, v.t[0]);
@@ -280,36 +295,43 @@ __device__ inline df df_div(df a, df b) {
 // a few 1e-9 world units: S = p_ref + sum_ijk B_ijk (p_ijk - p_ref) (the
 // weights sum to one), p_ref = first control point; the camera transform of
 // p_ref is taken in double-float.
+template <int N>
 struct SurfPoint {
+  static constexpr int M = (N + 1) * (N + 2) / 2;
   df t[3];        // camera-space position
   float S[3];     // world position (FP32, for derivatives)
-  float B[kMaxCp];
+  float B[M];
 };
 
-__device__ inline void bernstein_f32(int n, float u, float v, float *B) {
+template <int N>
+__device__ inline void bernstein_f32(float u, float v, float *B) {
   const float w = 1.0f - u - v;
-  float pu[kMaxDegree + 1], pv[kMaxDegree + 1], pw[kMaxDegree + 1];
+  float pu[N + 1], pv[N + 1], pw[N + 1];
   pu[0] = pv[0] = pw[0] = 1.0f;
 #pragma unroll
-  for (int m = 1; m <= kMaxDegree; m++) {
+  for (int m = 1; m <= N; m++) {
     pu[m] = pu[m - 1] * u;
     pv[m] = pv[m - 1] * v;
     pw[m] = pw[m - 1] * w;
   }
   int idx = 0;
-  for (int i = n; i >= 0; i--)
-    for (int j = n - i; j >= 0; j--) {
-      const int k = n - i - j;
-      B[idx++] = multinom(n, i, j, k) * pu[i] * pv[j] * pw[k];
+#pragma unroll
+  for (int i = N; i >= 0; i--)
+#pragma unroll
+    for (int j = N - i; j >= 0; j--) {
+      const int k = N - i - j;
+      B[idx++] = multinom(N, i, j, k) * pu[i] * pv[j] * pw[k];
     }
 }
 
-__device__ inline void surface_point(int n, const float *__restrict__ cp, float u, float v,
-                                     const View &vw, SurfPoint &sp) {
-  const int m = ncp_of(n);
-  bernstein_f32(n, u, v, sp.B);
+template <int N>
+__device__ inline void surface_point(const float *__restrict__ cp, float u, float v, const View &vw,
+                                     SurfPoint<N> &sp) {
+  constexpr int m = SurfPoint<N>::M;
+  bernstein_f32<N>(u, v, sp.B);
   const float r0 = __ldg(cp + 0), r1 = __ldg(cp + 1), r2 = __ldg(cp + 2);
   float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+#pragma unroll
   for (int a = 1; a < m; a++) {
     d0 = fmaf(sp.B[a], __ldg(cp + 3 * a + 0) - r0, d0);
     d1 = fmaf(sp.B[a], __ldg(cp + 3 * a + 1) - r1, d1);

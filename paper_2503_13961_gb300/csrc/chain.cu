@@ -46,11 +46,12 @@ __device__ inline float seg_sum(float v, const Seg &s) {
   return v;
 }
 
-__device__ inline void camera_point_f32(int n, const float *cp, float u, float v, const View &vw,
-                                        float *B, float *t) {
-  bernstein_f32(n, u, v, B);
+template <int N>
+__device__ inline void camera_point_f32(const float *cp, float u, float v, const View &vw, float *B, float *t) {
+  bernstein_f32<N>(u, v, B);
   float S[3] = {0.f, 0.f, 0.f};
-  const int m = ncp_of(n);
+  constexpr int m = SurfPoint<N>::M;
+#pragma unroll
   for (int a = 0; a < m; a++)
 #pragma unroll
     for (int c = 0; c < 3; c++) S[c] = fmaf(B[a], __ldg(cp + 3 * a + c), S[c]);
@@ -59,8 +60,9 @@ __device__ inline void camera_point_f32(int n, const float *cp, float u, float v
 }
 
 // scatter sum_run B[a] * v[c] into dst[(g * m + a) * 3 + c] (runs of equal g)
-__device__ inline void scatter_cp(float *dst, int g, int m, const float *B, const float *v, const Seg &sg,
-                                  bool active) {
+template <int m>
+__device__ inline void scatter_cp(float *dst, int g, const float *B, const float *v, const Seg &sg, bool active) {
+#pragma unroll
   for (int a = 0; a < m; a++)
 #pragma unroll
     for (int c = 0; c < 3; c++) {
@@ -69,17 +71,18 @@ __device__ inline void scatter_cp(float *dst, int g, int m, const float *B, cons
     }
 }
 
+template <int N>
 __global__ void __launch_bounds__(256) k_chain_gauss(Params p, Scene s, Work w, Grads out) {
   const int F = w.counters[kF];
   const int lane = threadIdx.x & 31;
   const int warps_total = gridDim.x * (blockDim.x >> 5);
-  const int m = p.ncp;
+  constexpr int m = SurfPoint<N>::M;
   for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < F; base += warps_total * 32) {
     const int i = base + lane;
     bool active = i < F;
     int g = -1;
     float gS[3] = {0.f, 0.f, 0.f}, gcol[3] = {0.f, 0.f, 0.f}, gop = 0.f;
-    float B[kMaxCp];
+    float B[m];
     if (active) {
       const float *gg = w.gg + 12 * (size_t)i;
       const float4 q0 = reinterpret_cast<const float4 *>(gg)[0];
@@ -93,7 +96,7 @@ __global__ void __launch_bounds__(256) k_chain_gauss(Params p, Scene s, Work w, 
       const View vw = w.views[w.g_view[i]];
       const float2 uv = w.g_uv[i];
       float t[3];
-      camera_point_f32(p.n, s.ctrl + (size_t)g * m * 3, uv.x, uv.y, vw, B, t);
+      camera_point_f32<N>(s.ctrl + (size_t)g * m * 3, uv.x, uv.y, vw, B, t);
       const bool any = gmx != 0.f || gmy != 0.f || gKa != 0.f || gKb != 0.f || gKc != 0.f;
       if (any) {
         const float Ka = Bq.x, Kb = Bq.y, Kc = Bq.z;
@@ -148,24 +151,25 @@ __global__ void __launch_bounds__(256) k_chain_gauss(Params p, Scene s, Work w, 
                                gcol[1] != 0.f || gcol[2] != 0.f || gop != 0.f);
     if (!__any_sync(0xffffffffu, nz)) continue;
     const Seg sg = seg_info(nz ? g : -1 - lane);
-    scatter_cp(out.ctrl, g, m, B, gS, sg, nz);
-    scatter_cp(out.color, g, m, B, gcol, sg, nz);
+    scatter_cp<m>(out.ctrl, g, B, gS, sg, nz);
+    scatter_cp<m>(out.color, g, B, gcol, sg, nz);
     const float so = seg_sum(nz ? gop : 0.f, sg);
     if (sg.tail && nz && so != 0.f) atomicAdd(out.opacity + g, so);
   }
 }
 
+template <int N>
 __global__ void __launch_bounds__(256) k_chain_bnd(Params p, Scene s, Work w, Grads out) {
   const int Nb = w.counters[kNb];
   const int lane = threadIdx.x & 31;
   const int warps_total = gridDim.x * (blockDim.x >> 5);
-  const int m = p.ncp;
+  constexpr int m = SurfPoint<N>::M;
   for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < Nb; base += warps_total * 32) {
     const int i = base + lane;
     bool nz = false;
     int g = -1;
     float gS[3] = {0.f, 0.f, 0.f}, grb = 0.f;
-    float B[kMaxCp];
+    float B[m];
     if (i < Nb) {
       const float4 gb = w.bg_grad[i];
       nz = gb.x != 0.f || gb.y != 0.f || gb.z != 0.f;
@@ -174,7 +178,7 @@ __global__ void __launch_bounds__(256) k_chain_bnd(Params p, Scene s, Work w, Gr
         const View vw = w.views[w.b_view[i]];
         const float2 uv = w.b_uv[i];
         float t[3];
-        camera_point_f32(p.n, s.ctrl + (size_t)g * m * 3, uv.x, uv.y, vw, B, t);
+        camera_point_f32<N>(s.ctrl + (size_t)g * m * 3, uv.x, uv.y, vw, B, t);
         const float tz = w.b_z[i], sigma = w.b_sigma[i];
         const float iz = 1.0f / tz, iz2 = iz * iz;
         const float gt0 = gb.x * vw.fx * iz;
@@ -187,7 +191,7 @@ __global__ void __launch_bounds__(256) k_chain_bnd(Params p, Scene s, Work w, Gr
     }
     if (!__any_sync(0xffffffffu, nz)) continue;
     const Seg sg = seg_info(nz ? g : -1 - lane);
-    scatter_cp(out.ctrl, g, m, B, gS, sg, nz);
+    scatter_cp<m>(out.ctrl, g, B, gS, sg, nz);
     const float sr = seg_sum(nz ? grb : 0.f, sg);
     if (sg.tail && nz && sr != 0.f) atomicAdd(out.r_b + g, sr);
   }
@@ -208,8 +212,10 @@ __global__ void k_l1_grad(const float *img, const float *tgt, long long n, float
 
 int launch_chain(const Params &p, const Scene &s, const Work &w, const Grads &g, cudaStream_t st) {
   const int grid = 152 * 8;
-  k_chain_gauss<<<grid, 256, 0, st>>>(p, s, w, g);
-  k_chain_bnd<<<grid, 256, 0, st>>>(p, s, w, g);
+  dispatch_degree(p.n, [&](auto d) {
+    k_chain_gauss<decltype(d)::value><<<grid, 256, 0, st>>>(p, s, w, g);
+    k_chain_bnd<decltype(d)::value><<<grid, 256, 0, st>>>(p, s, w, g);
+  });
   return 2;
 }
 

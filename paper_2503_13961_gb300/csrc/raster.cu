@@ -33,6 +33,7 @@ __device__ inline void slot_to_ab(int vi, int L, int &a, int &b) {
   b = rem;
 }
 
+template <int N>
 __global__ void __launch_bounds__(kRasterWarps * 32) k_raster(Params p, Scene s, Work w) {
   __shared__ int sX[kRasterWarps][kMaxVerts];
   __shared__ int sY[kRasterWarps][kMaxVerts];
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(kRasterWarps * 32) k_raster(Params p, Scene s,
     for (int vi = lane; vi < NV; vi += 32) {
       int a, b;
       slot_to_ab(vi, L, a, b);
-      const RVert r = raster_vertex(p.n, cp, a, b, L, vw, p.near_z);
+      const RVert r = raster_vertex<N>(cp, a, b, L, vw, p.near_z);
       sX[warp][vi] = r.valid ? r.X : INT_MIN;
       sY[warp][vi] = r.Y;
       sIZ[warp][vi] = r.iz;
@@ -137,6 +138,7 @@ __global__ void __launch_bounds__(kRasterWarps * 32) k_raster(Params p, Scene s,
   }
 }
 
+template <int N>
 __global__ void k_resolve(Params p, Scene s, Work w) {
   const int pix = blockIdx.x * blockDim.x + threadIdx.x;
   if (pix >= p.P) return;
@@ -162,7 +164,7 @@ __global__ void k_resolve(Params p, Scene s, Work w) {
   subtri_verts(L, sid, va, vb);
   RVert r[3];
 #pragma unroll
-  for (int c = 0; c < 3; c++) r[c] = raster_vertex(p.n, cp, va[c], vb[c], L, vw, p.near_z);
+  for (int c = 0; c < 3; c++) r[c] = raster_vertex<N>(cp, va[c], vb[c], L, vw, p.near_z);
   long long area2 = edge_fn(r[0].X, r[0].Y, r[1].X, r[1].Y, r[2].X, r[2].Y);
   if (area2 < 0) {
     RVert t = r[1]; r[1] = r[2]; r[2] = t;
@@ -194,13 +196,13 @@ int launch_raster(const Params &p, const Scene &s, const Work &w, cudaStream_t s
   if (items == 0) return 0;
   long long blocks = (items + kRasterWarps - 1) / kRasterWarps;
   if (blocks > (1ll << 30)) blocks = 1ll << 30;
-  k_raster<<<(unsigned)blocks, kRasterWarps * 32, 0, st>>>(p, s, w);
+  dispatch_degree(p.n, [&](auto d) { k_raster<decltype(d)::value><<<(unsigned)blocks, kRasterWarps * 32, 0, st>>>(p, s, w); });
   return 1;
 }
 
 int launch_resolve(const Params &p, const Scene &s, const Work &w, cudaStream_t st) {
   if (p.P == 0) return 0;
-  k_resolve<<<(p.P + 255) / 256, 256, 0, st>>>(p, s, w);
+  dispatch_degree(p.n, [&](auto d) { k_resolve<decltype(d)::value><<<(p.P + 255) / 256, 256, 0, st>>>(p, s, w); });
   return 1;
 }
 

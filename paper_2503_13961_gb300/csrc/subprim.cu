@@ -164,6 +164,7 @@ __device__ inline uint2 tile_rect(float cx, float cy, float rx, float ry, const 
   return make_uint2((unsigned)x0 | ((unsigned)y0 << 16), (unsigned)x1 | ((unsigned)y1 << 16));
 }
 
+template <int N>
 __global__ void __launch_bounds__(kGenThreads) k_generate(Params p, Scene s, Work w) {
   __shared__ int s_wf[kGenThreads / 32], s_wb[kGenThreads / 32];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
@@ -198,8 +199,8 @@ __global__ void __launch_bounds__(kGenThreads) k_generate(Params p, Scene s, Wor
     const int local = pix - vw.pix_off;
     const int qy = local / vw.W, qx = local - qy * vw.W;
     const float *cp = s.ctrl + (size_t)prim * p.ncp * 3;
-    SurfPoint sp;
-    surface_point(p.n, cp, uv.x, uv.y, vw, sp);
+    SurfPoint<N> sp;
+    surface_point<N>(cp, uv.x, uv.y, vw, sp);
     const float2 off = project_offset(sp.t, vw, qx, qy);
     const float tx = sp.t[0].hi + sp.t[0].lo, ty = sp.t[1].hi + sp.t[1].lo, tz = sp.t[2].hi + sp.t[2].lo;
     // depth sort key refinement: the exact depth hi + lo lies in the rounding
@@ -241,7 +242,8 @@ __global__ void __launch_bounds__(kGenThreads) k_generate(Params p, Scene s, Wor
     const float Ka = cC * idet, Kb = -cB * idet, Kc = cA * idet;
     float col[3] = {0.f, 0.f, 0.f};
     const float *cc = s.color + (size_t)prim * p.ncp * 3;
-    for (int a = 0; a < p.ncp; a++) {
+#pragma unroll
+    for (int a = 0; a < SurfPoint<N>::M; a++) {
       col[0] = fmaf(sp.B[a], __ldg(cc + 3 * a + 0), col[0]);
       col[1] = fmaf(sp.B[a], __ldg(cc + 3 * a + 1), col[1]);
       col[2] = fmaf(sp.B[a], __ldg(cc + 3 * a + 2), col[2]);
@@ -311,7 +313,7 @@ int launch_generate(const Params &p, const Scene &s, const Work &w, cudaStream_t
   }
   k_count<<<nblk, kGenThreads, 0, st>>>(p, w);
   k_scan_blocks<<<1, 1024, 0, st>>>(w, nblk);
-  k_generate<<<nblk, kGenThreads, 0, st>>>(p, s, w);
+  dispatch_degree(p.n, [&](auto d) { k_generate<decltype(d)::value><<<nblk, kGenThreads, 0, st>>>(p, s, w); });
   return 3;
 }
 

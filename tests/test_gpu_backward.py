@@ -69,6 +69,8 @@ CASES = [
     ("two_wide_boundary", lambda S: S.tiny_scene("two", size=(72, 64), r_b=0.08)),
     ("ico1_ragged", lambda S: S.tiny_scene("ico1", noise=0.04, size=(90, 70), r_b=0.04)),
     ("degree3", lambda S: S.tiny_scene("ico1", n=3, noise=0.03, size=(70, 66), r_b=0.04)),
+    ("degree1", lambda S: S.tiny_scene("octa", n=1, size=(48, 40), r_b=0.04)),
+    ("degree4", lambda S: S.tiny_scene("octa", n=4, noise=0.02, size=(56, 48), r_b=0.04)),
 ]
 
 

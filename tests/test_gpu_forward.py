@@ -27,6 +27,8 @@ def _cases():
     out.append(("degree3", sc, cams))
     sc, cams = S.tiny_scene("octa", n=1, size=(48, 40), r_b=0.03)
     out.append(("degree1", sc, cams))
+    sc, cams = S.tiny_scene("octa", n=4, noise=0.02, size=(56, 48), r_b=0.03)
+    out.append(("degree4", sc, cams))
     sc, cams, _ = S.config_scene(2)
     out.append(("config2_crop", sc, [S.crop_camera(cams[0], 300, 330, 160, 121)]))
     sc, cams = S.config_scene(4)
@@ -46,7 +48,8 @@ def cases():
     return CASES
 
 
-CASE_NAMES = ["config1_64", "two_ragged", "ico1_100x75", "degree3", "degree1", "config2_crop", "config4_multiview"]
+CASE_NAMES = ["config1_64", "two_ragged", "ico1_100x75", "degree3", "degree1", "degree4", "config2_crop",
+              "config4_multiview"]
 
 
 @pytest.fixture(scope="module")
