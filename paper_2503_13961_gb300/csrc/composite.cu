@@ -215,16 +215,18 @@ __device__ __forceinline__ BList load_boundary(const TileInfo &ti, const Work &w
   return bl;
 }
 
-// Stage this warp's hits of the chunk [c0, c0 + 32) of the tile's list:
+// Stage this warp's hits of a chunk of 32 entries of the tile's list (this
+// lane's sort key, prefetched, if valid):
 // P = (pixel x, y of the Gaussian as exact floats, offset x, y of its mean),
 // Q = (conic a, b, c, opacity), C = (colour, bits(prim)). The warp block is
 // [bx0, bx1] x [by0, by1] in pixel coordinates. Returns the ballot of hits.
-__device__ __forceinline__ unsigned stage_chunk(const Work &w, const TileInfo &ti, int jl, int jend, float bx0, float bx1,
-                                                float by0, float by1, float4 *sP, float4 *sQ, float4 *sC, int *sG) {
+__device__ __forceinline__ unsigned stage_chunk(const Work &w, unsigned long long key, bool valid, float bx0,
+                                                float bx1, float by0, float by1, float4 *sP, float4 *sQ, float4 *sC,
+                                                int *sG) {
   const int lane = threadIdx.x & 31;
   bool hit = false;
-  if (jl < jend) {
-    const unsigned gi = (unsigned)(w.gkeys[ti.gs + jl] & kIndexMask);
+  if (valid) {
+    const unsigned gi = (unsigned)(key & kIndexMask);
     const float4 A = w.gA[gi];
     const unsigned qxy = __float_as_uint(A.z);
     const float gx = (float)(int)(qxy & 0xffffu), gy = (float)(int)(qxy >> 16);
@@ -294,15 +296,16 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_compos
   auto &s_cw = sh.s_cw;
   auto &s_tile = sh.s_tile;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) s_tile = atomicAdd(w.counters + kQueueFwd, 1);
+  __syncthreads();
   for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_tile = atomicAdd(w.counters + kQueueFwd, 1);
-    __syncthreads();
     const int tile = s_tile;
     if (tile >= p.tiles) break;
     const TileInfo ti = tile_info(p, w, tile, T);
     const BList bl = load_boundary<NT>(ti, w, sh.s_bprim, sh.s_bloc, sh.s_bisig);
-    __syncthreads();
+    __syncthreads();  // boundary list staged, s_tile read by every thread
+    // the next tile, fetched while this one is blended
+    if (threadIdx.x == 0) s_tile = atomicAdd(w.counters + kQueueFwd, 1);
     // the warp's pixel block
     const int wx = ti.x0 + (warp % Cfg::WPR) * Cfg::WX, wy = ti.y0 + (warp / Cfg::WPR) * Cfg::WY;
     const float bx0 = (float)wx, bx1 = (float)(wx + Cfg::WX - 1);
@@ -329,12 +332,16 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_compos
       last[k] = 0;
     }
     const int gn = (int)ti.gn;
+    const unsigned long long *gkeys = w.gkeys + ti.gs;
+    unsigned long long knext = lane < gn ? gkeys[lane] : 0ull;
     for (int c0 = 0; c0 < gn; c0 += 32) {
       bool alldone = true;
 #pragma unroll
       for (int k = 0; k < PPT; k++) alldone = alldone && done[k];
       if (__all_sync(0xffffffffu, alldone)) break;
-      unsigned mask = stage_chunk(w, ti, c0 + lane, gn, bx0, bx1, by0, by1, sP[warp], sQ[warp], sC[warp], nullptr);
+      const unsigned long long key = knext;
+      if (c0 + 32 + lane < gn) knext = gkeys[c0 + 32 + lane];  // prefetch the next chunk's keys
+      unsigned mask = stage_chunk(w, key, c0 + lane < gn, bx0, bx1, by0, by1, sP[warp], sQ[warp], sC[warp], nullptr);
       while (mask) {
         const int l = __ffs(mask) - 1;
         mask &= mask - 1;
@@ -401,6 +408,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_compos
       }
     }
     if (p.stats) flush_stats(w.stats, kFwdSupport, n_sup, n_comp, n_cand, n_visit);
+    __syncthreads();  // the staged boundary list is free again
   }
 }
 
@@ -481,15 +489,16 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
   auto &s_cacc = sh.s_cacc;
   auto &s_tile = sh.s_tile;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) s_tile = atomicAdd(w.counters + kQueueBwd, 1);
+  __syncthreads();
   for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_tile = atomicAdd(w.counters + kQueueBwd, 1);
-    __syncthreads();
     const int tile = s_tile;
     if (tile >= p.tiles) break;
     const TileInfo ti = tile_info(p, w, tile, T);
     const BList bl = load_boundary<NT>(ti, w, sh.s_bprim, sh.s_bloc, sh.s_bisig);
-    __syncthreads();
+    __syncthreads();  // boundary list staged, s_tile read by every thread
+    // the next tile, fetched while this one is blended
+    if (threadIdx.x == 0) s_tile = atomicAdd(w.counters + kQueueBwd, 1);
     const unsigned long long *bkeys = w.bkeys + ti.bs;
     const int wx = ti.x0 + (warp % Cfg::WPR) * Cfg::WX, wy = ti.y0 + (warp / Cfg::WPR) * Cfg::WY;
     const float bx0 = (float)wx, bx1 = (float)(wx + Cfg::WX - 1);
@@ -529,9 +538,13 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
     int wlast = mylast;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wlast = max(wlast, __shfl_xor_sync(0xffffffffu, wlast, o));
+    const unsigned long long *gkeys = w.gkeys + ti.gs;
+    unsigned long long knext = (wlast > 0 && max(0, wlast - 32) + lane < wlast) ? gkeys[max(0, wlast - 32) + lane] : 0ull;
     for (int c1 = wlast; c1 > 0; c1 -= 32) {
       const int c0 = max(0, c1 - 32);
-      unsigned mask = stage_chunk(w, ti, c0 + lane, c1, bx0, bx1, by0, by1, sP[warp], sQ[warp], sC[warp], sG[warp]);
+      const unsigned long long key = knext;
+      if (c0 > 0) knext = gkeys[max(0, c0 - 32) + lane];  // prefetch the next (earlier) chunk's keys
+      unsigned mask = stage_chunk(w, key, c0 + lane < c1, bx0, bx1, by0, by1, sP[warp], sQ[warp], sC[warp], sG[warp]);
       while (mask) {
         const int l = 31 - __clz(mask);
         mask &= ~(1u << l);
@@ -636,6 +649,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
       }
     }
     if (p.stats) flush_stats(w.stats, kBwdSupport, n_sup, n_comp, n_cand, n_visit);
+    __syncthreads();  // the staged boundary list is free again
   }
 }
 
