@@ -111,6 +111,7 @@ void carve(bgt_handle *h, char *base, size_t *total) {
   w.scan_aux = c.take<long long>(2 * (T / 4096 + 4));
   w.scan_aux2 = w.scan_aux ? w.scan_aux + (T / 4096 + 4) : nullptr;
   w.big_list = c.take<int>(2 * (long long)T + 2);
+  w.tile_desc = c.take<int4>(T + 1);
   w.gkeys = c.take<unsigned long long>(2 * K);   // second half: sort scratch
   w.bkeys = c.take<unsigned long long>(2 * Kb);  // second half: sort scratch
   w.bl_prim = c.take<int>(Kb);

@@ -103,6 +103,7 @@ struct Work {
   long long *g_tstart, *b_tstart;  // [tiles + 1] exclusive prefix sums (64-bit: no wrap)
   long long *scan_aux, *scan_aux2; // scratch of the two tile-count scans
   int *big_list;              // [2 tiles] segments too long for one warp to sort
+  int4 *tile_desc;            // [tiles] view, x0 | y0 << 16, W | H << 16, view pixel offset
   // pairs
   unsigned long long *gkeys;  // [Kcap] depth key (FP32 bits << 5 | sub) << 27 | gaussian index
   unsigned long long *bkeys;  // [Kbcap] (prim << 32) | boundary index

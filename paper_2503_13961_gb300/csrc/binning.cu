@@ -131,6 +131,19 @@ __global__ void k_emit(Params p, Work w) {
   }
 }
 
+// per-tile descriptor, so that the blending kernels read one record instead
+// of searching the view offsets
+__global__ void k_tile_desc(Params p, Work w) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.tiles) return;
+  const int view = find_view(w.view_tile_off, p.V, t);
+  const View &vw = w.views[view];
+  const int lt = t - vw.tile_off;
+  const int ty = lt / vw.tiles_x, tx = lt - ty * vw.tiles_x;
+  w.tile_desc[t] = make_int4(view, (int)((unsigned)(tx * p.tile) | ((unsigned)(ty * p.tile) << 16)),
+                             (int)((unsigned)vw.W | ((unsigned)vw.H << 16)), vw.pix_off);
+}
+
 __global__ void k_check_capacity(Params p, Work w) {
   const long long K = w.g_tstart[p.tiles], Kb = w.b_tstart[p.tiles];
   w.counters[kK] = (int)(K < 0x7fffffffll ? K : 0x7fffffffll);
@@ -383,7 +396,12 @@ int launch_binning(const Params &p, const Work &w, cudaStream_t st) {
   int k = launch_exclusive_scan(w.g_tcount, w.g_tstart, p.tiles, w.scan_aux, st);
   k += launch_exclusive_scan(w.b_tcount, w.b_tstart, p.tiles, w.scan_aux2, st);
   k_check_capacity<<<1, 1, 0, st>>>(p, w);
-  return k + 1 + launch_bin_sort_only(p, w, st);
+  k += 2;
+  if (p.tiles > 0) {
+    k_tile_desc<<<(p.tiles + 255) / 256, 256, 0, st>>>(p, w);
+    k++;
+  }
+  return k + launch_bin_sort_only(p, w, st);
 }
 
 }  // namespace bgt

@@ -173,17 +173,15 @@ struct TileInfo {
   long long gs, gn, bs, bn;
 };
 
-__device__ inline TileInfo tile_info(const Params &p, const Work &w, int tile, int T) {
+__device__ inline TileInfo tile_info(const Params &p, const Work &w, int tile) {
   TileInfo t;
-  t.view = find_view(w.view_tile_off, p.V, tile);
-  const View *vw = w.views + t.view;
-  t.W = __ldg(&vw->W);
-  t.H = __ldg(&vw->H);
-  t.pix_off = __ldg(&vw->pix_off);
-  const int lt = tile - __ldg(&vw->tile_off);
-  const int tx = __ldg(&vw->tiles_x);
-  t.y0 = (lt / tx) * T;
-  t.x0 = (lt - (lt / tx) * tx) * T;
+  const int4 d = w.tile_desc[tile];
+  t.view = d.x;
+  t.x0 = d.y & 0xffff;
+  t.y0 = (int)((unsigned)d.y >> 16);
+  t.W = d.z & 0xffff;
+  t.H = (int)((unsigned)d.z >> 16);
+  t.pix_off = d.w;
   // an overflowed call (reported through the status word) leaves key slots
   // unwritten: its lists are treated as empty so that no slot is read
   const bool g_over = w.g_tstart[p.tiles] > p.max_pairs, b_over = w.b_tstart[p.tiles] > p.max_bpairs;
@@ -301,7 +299,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_compos
   for (;;) {
     const int tile = s_tile;
     if (tile >= p.tiles) break;
-    const TileInfo ti = tile_info(p, w, tile, T);
+    const TileInfo ti = tile_info(p, w, tile);
     const BList bl = load_boundary<NT>(ti, w, sh.s_bprim, sh.s_bloc, sh.s_bisig);
     __syncthreads();  // boundary list staged, s_tile read by every thread
     // the next tile, fetched while this one is blended
@@ -494,7 +492,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
   for (;;) {
     const int tile = s_tile;
     if (tile >= p.tiles) break;
-    const TileInfo ti = tile_info(p, w, tile, T);
+    const TileInfo ti = tile_info(p, w, tile);
     const BList bl = load_boundary<NT>(ti, w, sh.s_bprim, sh.s_bloc, sh.s_bisig);
     __syncthreads();  // boundary list staged, s_tile read by every thread
     // the next tile, fetched while this one is blended
