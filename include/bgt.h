@@ -60,6 +60,9 @@ typedef struct {
   long long max_pixels;         /* capacity: sum of W*H over the views of one call (<= 2^27) */
   long long max_pairs;          /* capacity: (Gaussian, tile) pairs per call */
   long long max_boundary_pairs; /* capacity: (boundary point, tile) pairs per call */
+  long long max_blend_pairs;    /* capacity: (pixel, Gaussian) pairs the forward pass composites
+                                   per call, recorded for the backward pass; 0 = 24 per pixel,
+                                   at least 2^22 */
   int tess_level;               /* L: each primitive becomes L^2 flat triangles (1..16) */
   int tile_size;                /* screen tile edge: 8, 16 or 32 pixels */
   float k_b;                    /* boundary radius sigma = k_b fx r_b / z (Sec. 3.2) */

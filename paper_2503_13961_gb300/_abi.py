@@ -27,7 +27,8 @@ HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))
 
 class Config(ctypes.Structure):
     _fields_ = [("degree", c_int), ("max_prims", c_int), ("max_views", c_int), ("max_pixels", c_ll),
-                ("max_pairs", c_ll), ("max_boundary_pairs", c_ll), ("tess_level", c_int), ("tile_size", c_int),
+                ("max_pairs", c_ll), ("max_boundary_pairs", c_ll), ("max_blend_pairs", c_ll),
+                ("tess_level", c_int), ("tile_size", c_int),
                 ("k_b", c_float), ("alpha_min", c_float), ("alpha_max", c_float), ("t_stop", c_float),
                 ("dilation", c_float), ("near_z", c_float), ("flags", c_int)]
 

@@ -2,6 +2,7 @@
 // CUDA-graph capture, autotuner and stage access. See include/bgt.h.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -14,7 +15,7 @@ using bgt::View;
 struct bgt_handle {
   bgt_config cfg;
   int device = 0;
-  long long Pcap = 0, Fcap = 0, Kcap = 0, Kbcap = 0;
+  long long Pcap = 0, Fcap = 0, Kcap = 0, Kbcap = 0, Bcap = 0;
   int Tcap = 0, Vcap = 0, Mcap = 0, nblk_cap = 0;
   void *arena = nullptr;
   size_t arena_bytes = 0;
@@ -112,6 +113,12 @@ void carve(bgt_handle *h, char *base, size_t *total) {
   w.scan_aux2 = w.scan_aux ? w.scan_aux + (T / 4096 + 4) : nullptr;
   w.big_list = c.take<int>(2 * (long long)T + 2);
   w.tile_desc = c.take<int4>(T + 1);
+  w.rec_chunk_cap = (int)(h->Bcap / 4 / bgt::kRecChunk + 1);
+  w.pay_chunk_cap = (int)(h->Bcap / bgt::kPayChunk + 1);
+  w.rec_hdr = c.take<uint4>((long long)w.rec_chunk_cap * bgt::kRecChunk);
+  w.rec_prev = c.take<int>(w.rec_chunk_cap);
+  w.rec_pay = c.take<uint2>((long long)w.pay_chunk_cap * bgt::kPayChunk);
+  w.blk_rec = c.take<int2>(8 * (long long)T + 8);  // warp blocks: at most 8 per tile at any tile size
   w.gkeys = c.take<unsigned long long>(2 * K);   // second half: sort scratch
   w.bkeys = c.take<unsigned long long>(2 * Kb);  // second half: sort scratch
   w.bl_prim = c.take<int>(Kb);
@@ -132,6 +139,7 @@ bool cfg_ok(const bgt_config *c, const char **why) {
   if (c->max_pixels < 1 || c->max_pixels > (1ll << bgt::kIndexBits)) return *why = "max_pixels must be 1..2^27", false;
   if (c->max_pairs < 1 || c->max_pairs > (1ll << 31) - 1) return *why = "max_pairs must be 1..2^31-1", false;
   if (c->max_boundary_pairs < 1 || c->max_boundary_pairs > (1ll << 31) - 1) return *why = "max_boundary_pairs must be 1..2^31-1", false;
+  if (c->max_blend_pairs < 0 || c->max_blend_pairs > (1ll << 31) - 1) return *why = "max_blend_pairs must be 0..2^31-1", false;
   if (c->tess_level < 1 || c->tess_level > bgt::kMaxTess) return *why = "tess_level must be 1..16", false;
   if (c->tile_size != 8 && c->tile_size != 16 && c->tile_size != 32) return *why = "tile_size must be 8, 16 or 32", false;
   if ((long long)c->max_prims * 2 * c->tess_level * c->tess_level > 0xffffffffll) return *why = "max_prims * 2 L^2 must fit 32 bits", false;
@@ -347,6 +355,9 @@ bgt_status bgt_create(const bgt_config *cfg, bgt_handle **out) {
   h->Fcap = cfg->max_pixels;
   h->Kcap = cfg->max_pairs;
   h->Kbcap = cfg->max_boundary_pairs;
+  // default 24 records per pixel, at least 4M (every resident warp holds a partly used payload chunk)
+  h->Bcap = cfg->max_blend_pairs > 0 ? cfg->max_blend_pairs : std::max(24 * cfg->max_pixels, 1ll << 22);
+  if (h->Bcap > (1ll << 31) - 2 * bgt::kPayChunk) h->Bcap = (1ll << 31) - 2 * bgt::kPayChunk;
   h->Vcap = cfg->max_views;
   h->Mcap = cfg->max_prims;
   // tiles of all views at the smallest tile size: sum (W/8+1)(H/8+1) <= P (1/64 + 1/8) + 2 V
@@ -464,6 +475,7 @@ bgt_status bgt_sync_status(bgt_handle *h, void *stream) {
   cudaMemsetAsync(h->w.status, 0, sizeof(int), st);
   if (s & (bgt::kStatusPairOverflow | bgt::kStatusBoundaryOverflow | bgt::kStatusTileOverflow))
     return fail(h, BGT_ERR_CAPACITY, "device-side pair count exceeded its capacity");
+  if (s & bgt::kStatusBlendOverflow) return fail(h, BGT_ERR_CAPACITY, "blend records exceeded max_blend_pairs");
   if (s & bgt::kStatusNonFinite) return fail(h, BGT_ERR_NONFINITE, "non-finite projected Gaussian");
   if (s & bgt::kStatusBadPrim) return fail(h, BGT_ERR_STATE, "depth buffer held an invalid primitive id");
   return BGT_OK;

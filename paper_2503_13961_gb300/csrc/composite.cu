@@ -23,7 +23,7 @@ namespace bgt {
 
 namespace {
 
-constexpr int kBCap = 1024;        // boundary candidates staged in shared memory per tile
+constexpr int kBCap = 768;         // boundary candidates staged in shared memory per tile
 constexpr float kLog2e = 1.4426950408889634f;
 
 // Block layout: NT threads; every warp owns a WX x WY block of the tile's
@@ -38,7 +38,7 @@ struct TileCfg {
   static constexpr int WY = (T == 32) ? 8 : 4;
   static constexpr int WPR = T / WX;         // warp blocks per tile row
   // primitive cache per warp (fully associative, FIFO): slot keys one per lane
-  static constexpr int SLOTS_FWD = (PPT == 1) ? 16 : 8;
+  static constexpr int SLOTS_FWD = (PPT == 1) ? 12 : 4;
   static constexpr int SLOTS_BWD = (PPT == 1) ? 12 : 4;
   // resident blocks per SM the kernels are compiled for (their shared memory
   // allows this many; the register budget follows)
@@ -259,20 +259,28 @@ __device__ __forceinline__ void flush_stats(unsigned long long *stats, int base,
 }
 
 // shared memory of the blending kernels (dynamic: above the 48 KB static limit)
-template <int T, bool BWD>
-struct BlendShared {
+template <int T>
+struct FwdShared {
   using Cfg = TileCfg<T>;
-  static constexpr int S = BWD ? Cfg::SLOTS_BWD : Cfg::SLOTS_FWD;
+  static constexpr int S = Cfg::SLOTS_FWD;
   float4 sP[Cfg::NW][32], sQ[Cfg::NW][32], sC[Cfg::NW][32];
   float4 s_bloc[kBCap];
-  float s_cw[Cfg::NW][S][Cfg::PPT][32];                // cached w per slot and pixel
-  // backward only: the slot's boundary candidate (or -1), sum of dl/dw over its Gaussians
-  int s_cb[BWD ? Cfg::NW : 1][BWD ? S : 1][BWD ? Cfg::PPT : 1][32];
-  float s_cacc[BWD ? Cfg::NW : 1][BWD ? S : 1][BWD ? Cfg::PPT : 1][32];
+  float s_cw[Cfg::NW][S][Cfg::PPT][32];  // cached w per slot and pixel
+  int s_cb[Cfg::NW][S][Cfg::PPT][32];    // its boundary candidate (tile list index) or -1
   int sG[Cfg::NW][32];
   int s_bprim[kBCap];
   float s_bisig[kBCap];
   int s_tile;
+};
+
+template <int T>
+struct BwdShared {
+  using Cfg = TileCfg<T>;
+  static constexpr int S = Cfg::SLOTS_BWD;
+  float4 sP[Cfg::NW][32], sQ[Cfg::NW][32], sC[Cfg::NW][32];
+  uint4 sH[Cfg::NW][32];                 // staged record headers
+  int s_cb[Cfg::NW][S][Cfg::PPT][32];    // the slot's boundary candidate per pixel (-1: none)
+  float s_cacc[Cfg::NW][S][Cfg::PPT][32];  // sum of dl/dw over the slot's Gaussians per pixel
 };
 
 // Warp-wide lookup of primitive g in the warp's cache: lane s < SLOTS holds
@@ -282,18 +290,86 @@ __device__ __forceinline__ int cache_find(int ckey, int g) {
   return m ? __ffs(m) - 1 : -1;
 }
 
+// Writer of the blend records of one warp (warp-uniform state): header
+// chunks belong to one warp block, payload chunks to the warp (they persist
+// across the blocks it blends). Running out of either capacity raises
+// kStatusBlendOverflow and marks the block's records invalid.
+struct RecWriter {
+  int chunk, count;  // the block's current header chunk (-1: none) and its records
+  int pay, pay_end;  // the warp's current payload chunk [pay, pay_end)
+  bool ok;
+
+  __device__ __forceinline__ void begin_block() {
+    chunk = -1;
+    count = kRecChunk;
+    ok = true;
+  }
+
+  // record: Gaussian gi composited at the pixels k of the lanes in cm; this
+  // lane (if in cm) stores its w and boundary candidate
+  __device__ __forceinline__ void put(const Work &w, unsigned gi, unsigned cm, int k, bool mine, float wv, int best) {
+    const int lane = threadIdx.x & 31;
+    if (!ok) return;
+    if (count == kRecChunk) {
+      int id = 0;
+      if (lane == 0) {
+        id = atomicAdd(w.counters + kRecChunks, 1);
+        if (id < w.rec_chunk_cap) w.rec_prev[id] = chunk;
+      }
+      id = __shfl_sync(0xffffffffu, id, 0);
+      if (id >= w.rec_chunk_cap) {
+        fail(w);
+        return;
+      }
+      chunk = id;
+      count = 0;
+    }
+    const int n = __popc(cm);
+    if (pay + n > pay_end) {
+      int c = 0;
+      if (lane == 0) c = atomicAdd(w.counters + kPayChunks, 1);
+      c = __shfl_sync(0xffffffffu, c, 0);
+      if (c >= w.pay_chunk_cap) {
+        fail(w);
+        return;
+      }
+      pay = c * kPayChunk;
+      pay_end = pay + kPayChunk;
+    }
+    if (lane == 0) w.rec_hdr[(size_t)chunk * kRecChunk + count] = make_uint4(gi, cm, (unsigned)pay, (unsigned)k);
+    if (mine)
+      w.rec_pay[(size_t)pay + __popc(cm & ((1u << lane) - 1u))] = make_uint2(__float_as_uint(wv), (unsigned)best);
+    pay += n;
+    count++;
+  }
+
+  __device__ __forceinline__ void fail(const Work &w) {
+    ok = false;
+    if ((threadIdx.x & 31) == 0) atomicOr(w.status, kStatusBlendOverflow);
+  }
+
+  __device__ __forceinline__ void end_block(const Work &w, int blk) {
+    if ((threadIdx.x & 31) == 0)
+      w.blk_rec[blk] = ok ? make_int2(chunk, chunk >= 0 ? count : 0) : make_int2(-2, 0);
+  }
+};
+
 template <int T>
 __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_composite_fwd(Params p, Work w, float *image) {
   using Cfg = TileCfg<T>;
   constexpr int NT = Cfg::NT, PPT = Cfg::PPT, S = Cfg::SLOTS_FWD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  auto &sh = *reinterpret_cast<BlendShared<T, false> *>(smem_raw);
+  auto &sh = *reinterpret_cast<FwdShared<T> *>(smem_raw);
   auto &sP = sh.sP;
   auto &sQ = sh.sQ;
   auto &sC = sh.sC;
+  auto &sG = sh.sG;
   auto &s_cw = sh.s_cw;
+  auto &s_cb = sh.s_cb;
   auto &s_tile = sh.s_tile;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  RecWriter rw;
+  rw.pay = rw.pay_end = 0;
   if (threadIdx.x == 0) s_tile = atomicAdd(w.counters + kQueueFwd, 1);
   __syncthreads();
   for (;;) {
@@ -314,6 +390,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_compos
     bool done[PPT];
     unsigned n_sup = 0, n_comp = 0, n_cand = 0, n_visit = 0;
     int ckey = -2, cnext = 0;
+    rw.begin_block();
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
       int lx, ly;
@@ -339,7 +416,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_compos
       if (__all_sync(0xffffffffu, alldone)) break;
       const unsigned long long key = knext;
       if (c0 + 32 + lane < gn) knext = gkeys[c0 + 32 + lane];  // prefetch the next chunk's keys
-      unsigned mask = stage_chunk(w, key, c0 + lane < gn, bx0, bx1, by0, by1, sP[warp], sQ[warp], sC[warp], nullptr);
+      unsigned mask = stage_chunk(w, key, c0 + lane < gn, bx0, bx1, by0, by1, sP[warp], sQ[warp], sC[warp], sG[warp]);
       while (mask) {
         const int l = __ffs(mask) - 1;
         mask &= mask - 1;
@@ -367,14 +444,17 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_compos
           if (p.use_boundary) warp_equal_range(bl.prim, bl.n, g, lo, hi);
 #pragma unroll
           for (int k = 0; k < PPT; k++) {
-            int best;
+            int best = -1;
             s_cw[warp][slot][k][lane] = p.use_boundary
                 ? w_search<2>(bl, lo, hi, pxf[k], pyf[k], idq[k] == g, best, n_cand) : 1.0f;
+            s_cb[warp][slot][k][lane] = best;
           }
           if (lane == slot) ckey = g;
         }
+        bool comp[PPT];
 #pragma unroll
         for (int k = 0; k < PPT; k++) {
+          comp[k] = false;
           if (!cand[k]) continue;
           n_sup++;
           const float alpha = fminf(p.alpha_max, __fmul_rn(og[k], s_cw[warp][slot][k][lane]));
@@ -390,11 +470,20 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_compos
           C[k][2] = __fmaf_rn(ta, Cc.z, C[k][2]);
           Tr[k] = testT;
           last[k] = c0 + l + 1;
+          comp[k] = true;
           n_comp++;
+        }
+        // record the pixels composited for the backward pass
+#pragma unroll
+        for (int k = 0; k < PPT; k++) {
+          const unsigned cm = __ballot_sync(0xffffffffu, comp[k]);
+          if (cm)
+            rw.put(w, (unsigned)sG[warp][l], cm, k, comp[k], s_cw[warp][slot][k][lane], s_cb[warp][slot][k][lane]);
         }
       }
       __syncwarp();
     }
+    rw.end_block(w, tile * Cfg::NW + warp);
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
       if (pix[k] >= 0) {
@@ -442,9 +531,11 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float *v) {
 // the slot's w = gamma (inside g) or 1 - gamma with gamma = 2^(rho - 1) of the
 // same boundary point b for all of g's Gaussians, so their dl/dw add up
 // (sum) before dl/drho = +-ln2 gamma sum is taken through rho = |q - b| / sigma:
-// drho/db = -(q - b) / (|q - b| sigma), drho/dsigma = -rho / sigma.
+// drho/db = -(q - b) / (|q - b| sigma), drho/dsigma = -rho / sigma. brec and
+// bkeys are the tile's boundary list (records in search form after
+// to_search, keys holding the boundary point's index).
 template <int PPT>
-__device__ __forceinline__ void flush_boundary(const BList &bl, const unsigned long long *bkeys, float4 *bg_grad,
+__device__ __forceinline__ void flush_boundary(const float4 *brec, const unsigned long long *bkeys, float4 *bg_grad,
                                                const int *cb, const float *cacc, int g, const int *idq,
                                                const float *pxf, const float *pyf) {
   const float LN2 = 0.69314718055994531f;
@@ -454,9 +545,10 @@ __device__ __forceinline__ void flush_boundary(const BList &bl, const unsigned l
     const int bi = cb[k * 32 + lane];
     const float sum = cacc[k * 32 + lane];
     if (bi < 0 || sum == 0.f) continue;
-    // rho and gamma with the operations of the search
-    float isig;
-    const float4 b = bl.get(bi, isig);
+    // rho and gamma with the operations of the forward search
+    const float4 rec = brec[bi];
+    const float4 b = to_search(rec);
+    const float isig = rec.w;
     const float ex = __fsub_rn(__fsub_rn(pxf[k], b.x), b.z), ey = __fsub_rn(__fsub_rn(pyf[k], b.y), b.w);
     const float r2 = __fmul_rn(__fmaf_rn(ex, ex, __fmul_rn(ey, ey)), __fmul_rn(isig, isig));
     const float rho = sqrt_approx(r2);
@@ -472,58 +564,64 @@ __device__ __forceinline__ void flush_boundary(const BList &bl, const unsigned l
   }
 }
 
+// payload entry of this lane in record h (zeros if the lane is not in it)
+__device__ __forceinline__ uint2 record_payload(const Work &w, const uint4 &h) {
+  const int lane = threadIdx.x & 31;
+  if (!((h.y >> lane) & 1u)) return make_uint2(0u, 0u);
+  return w.rec_pay[(size_t)h.z + __popc(h.y & ((1u << lane) - 1u))];
+}
+
+// Backward pass over the forward pass's blend records. Every warp takes warp
+// blocks (tile, block) from a queue and replays the block's records back to
+// front: T_i = T_{i+1} / (1 - alpha_i) with alpha_i recomputed from the
+// recorded w by the forward pass's operations, R (colour behind) updated as
+// R <- alpha_i c_i + (1 - alpha_i) R. Per record, the per-Gaussian gradient is
+// reduced over the warp; boundary-point gradients are summed per (pixel,
+// primitive) in a cache slot and flushed on eviction and at the block's end.
 template <int T>
 __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_composite_bwd(Params p, Work w, const float *dimage) {
   using Cfg = TileCfg<T>;
-  constexpr int NT = Cfg::NT, PPT = Cfg::PPT, S = Cfg::SLOTS_BWD;
+  constexpr int PPT = Cfg::PPT, S = Cfg::SLOTS_BWD, NW = Cfg::NW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  auto &sh = *reinterpret_cast<BlendShared<T, true> *>(smem_raw);
-  auto &sP = sh.sP;
-  auto &sQ = sh.sQ;
-  auto &sC = sh.sC;
-  auto &sG = sh.sG;
-  auto &s_cw = sh.s_cw;
-  auto &s_cb = sh.s_cb;
-  auto &s_cacc = sh.s_cacc;
-  auto &s_tile = sh.s_tile;
+  auto &sh = *reinterpret_cast<BwdShared<T> *>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) s_tile = atomicAdd(w.counters + kQueueBwd, 1);
-  __syncthreads();
-  for (;;) {
-    const int tile = s_tile;
-    if (tile >= p.tiles) break;
-    const TileInfo ti = tile_info(p, w, tile);
-    const BList bl = load_boundary<NT>(ti, w, sh.s_bprim, sh.s_bloc, sh.s_bisig);
-    __syncthreads();  // boundary list staged, s_tile read by every thread
-    // the next tile, fetched while this one is blended
-    if (threadIdx.x == 0) s_tile = atomicAdd(w.counters + kQueueBwd, 1);
-    const unsigned long long *bkeys = w.bkeys + ti.bs;
-    const int wx = ti.x0 + (warp % Cfg::WPR) * Cfg::WX, wy = ti.y0 + (warp / Cfg::WPR) * Cfg::WY;
-    const float bx0 = (float)wx, bx1 = (float)(wx + Cfg::WX - 1);
-    const float by0 = (float)wy, by1 = (float)(wy + Cfg::WY - 1);
+  float4 *sP = sh.sP[warp], *sQ = sh.sQ[warp], *sC = sh.sC[warp];
+  uint4 *sH = sh.sH[warp];
+  auto &s_cb = sh.s_cb[warp];
+  auto &s_cacc = sh.s_cacc[warp];
+  const int items = p.tiles * NW;
+  int item = 0;
+  if (lane == 0) item = atomicAdd(w.counters + kQueueBwd, 1);
+  item = __shfl_sync(0xffffffffu, item, 0);
+  while (item < items) {
+    int next = 0;  // the next warp block, fetched while this one is processed
+    if (lane == 0) next = atomicAdd(w.counters + kQueueBwd, 1);
+    const int tile = item / NW, wb = item - tile * NW;
+    const int4 d = w.tile_desc[tile];
+    const int x0 = d.y & 0xffff, y0 = (int)((unsigned)d.y >> 16);
+    const int W = d.z & 0xffff, H = (int)((unsigned)d.z >> 16);
+    const bool b_over = w.b_tstart[p.tiles] > p.max_bpairs;
+    const long long bs = b_over ? 0 : w.b_tstart[tile];
+    const float4 *brec = w.bl_rec + bs;
+    const unsigned long long *bkeys = w.bkeys + bs;
+    const int2 br = w.blk_rec[item];
 
-    // R: colour behind the current pair, seen through the pairs behind it
     float Tr[PPT], R[PPT][3], dC[PPT][3], pxf[PPT], pyf[PPT];
-    int last[PPT], idq[PPT];
-    unsigned n_sup = 0, n_comp = 0, n_cand = 0, n_visit = 0;
-    int ckey = -2, cnext = 0;
-    int mylast = 0;
+    int idq[PPT];
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
       int lx, ly;
-      lane_pixel<T>(warp, lane, k, lx, ly);
-      const int px = ti.x0 + lx, py = ti.y0 + ly;
+      lane_pixel<T>(wb, lane, k, lx, ly);
+      const int px = x0 + lx, py = y0 + ly;
       pxf[k] = (float)px;
       pyf[k] = (float)py;
-      last[k] = 0;
       idq[k] = -1;
       Tr[k] = 1.f;
       R[k][0] = R[k][1] = R[k][2] = 0.f;
       dC[k][0] = dC[k][1] = dC[k][2] = 0.f;
-      if (px < ti.W && py < ti.H) {
-        const int pix = ti.pix_off + py * ti.W + px;
+      if (br.x >= 0 && px < W && py < H) {
+        const int pix = d.w + py * W + px;
         idq[k] = w.pid[pix];
-        last[k] = w.n_contrib[pix];
         Tr[k] = w.T_final[pix];
 #pragma unroll
         for (int c = 0; c < 3; c++) {
@@ -531,73 +629,47 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
           R[k][c] = p.bg[c];
         }
       }
-      mylast = max(mylast, last[k]);
     }
-    int wlast = mylast;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) wlast = max(wlast, __shfl_xor_sync(0xffffffffu, wlast, o));
-    const unsigned long long *gkeys = w.gkeys + ti.gs;
-    unsigned long long knext = (wlast > 0 && max(0, wlast - 32) + lane < wlast) ? gkeys[max(0, wlast - 32) + lane] : 0ull;
-    for (int c1 = wlast; c1 > 0; c1 -= 32) {
-      const int c0 = max(0, c1 - 32);
-      const unsigned long long key = knext;
-      if (c0 > 0) knext = gkeys[max(0, c0 - 32) + lane];  // prefetch the next (earlier) chunk's keys
-      unsigned mask = stage_chunk(w, key, c0 + lane < c1, bx0, bx1, by0, by1, sP[warp], sQ[warp], sC[warp], sG[warp]);
-      while (mask) {
-        const int l = 31 - __clz(mask);
-        mask &= ~(1u << l);
-        const int j = c0 + l;
-        const float4 P = sP[warp][l], Q = sQ[warp][l];
-        float G[PPT], og[PPT], dxs[PPT], dys[PPT];
-        bool cand[PPT];
-        bool anyc = false;
-#pragma unroll
-        for (int k = 0; k < PPT; k++) {
-          dxs[k] = __fsub_rn(__fsub_rn(pxf[k], P.x), P.z);
-          dys[k] = __fsub_rn(__fsub_rn(pyf[k], P.y), P.w);
-          G[k] = gauss(dxs[k], dys[k], Q);
-          og[k] = __fmul_rn(Q.w, G[k]);
-          cand[k] = j < last[k] && og[k] >= p.alpha_min;
-          anyc = anyc || cand[k];
-        }
-        if (!__any_sync(0xffffffffu, anyc)) continue;
-        n_visit++;
-        const float4 Cc = sC[warp][l];
+    unsigned n_comp = 0, n_rec = 0;
+    int ckey = -2, cnext = 0;
+    int chunk = br.x, n = br.y;
+    while (chunk >= 0) {
+      const int prev = w.rec_prev[chunk];
+      // stage the chunk's records: headers and their Gaussians
+      if (lane < n) {
+        const uint4 h = w.rec_hdr[(size_t)chunk * kRecChunk + lane];
+        const float4 A = w.gA[h.x];
+        const unsigned qxy = __float_as_uint(A.z);
+        sH[lane] = h;
+        sP[lane] = make_float4((float)(int)(qxy & 0xffffu), (float)(int)(qxy >> 16), A.x, A.y);
+        sQ[lane] = w.gB[h.x];
+        sC[lane] = w.gC[h.x];
+      }
+      __syncwarp();
+      uint2 pay_next = record_payload(w, sH[n - 1]);
+      for (int r = n - 1; r >= 0; r--) {
+        const uint4 h = sH[r];
+        const uint2 pay = pay_next;
+        if (r > 0) pay_next = record_payload(w, sH[r - 1]);  // prefetch
+        const bool mine = (h.y >> lane) & 1u;
+        const int rk = (int)h.w;
+        const float4 P = sP[r], Q = sQ[r], Cc = sC[r];
         const int g = __float_as_int(Cc.w);
-        int slot = cache_find(ckey, g);
-        if (slot < 0) {  // warp-uniform miss: every lane searches, coherently
-          slot = cnext;
-          cnext = (cnext + 1 == S) ? 0 : cnext + 1;
-          const int old = __shfl_sync(0xffffffffu, ckey, slot);
-          if (old >= 0 && p.use_boundary)
-            flush_boundary<PPT>(bl, bkeys, w.bg_grad, &s_cb[warp][slot][0][0], &s_cacc[warp][slot][0][0], old, idq,
-                                pxf, pyf);
-          int lo = 0, hi = 0;
-          if (p.use_boundary) warp_equal_range(bl.prim, bl.n, g, lo, hi);
-#pragma unroll
-          for (int k = 0; k < PPT; k++) {
-            int best = -1;
-            s_cw[warp][slot][k][lane] = p.use_boundary
-                ? w_search<2>(bl, lo, hi, pxf[k], pyf[k], idq[k] == g, best, n_cand) : 1.0f;
-            s_cb[warp][slot][k][lane] = best;
-            s_cacc[warp][slot][k][lane] = 0.f;
-          }
-          if (lane == slot) ckey = g;
-        }
+        n_rec++;
         float acc[9];
 #pragma unroll
         for (int q = 0; q < 9; q++) acc[q] = 0.f;
-        bool any = false;
+        float dl_dw = 0.f;
 #pragma unroll
         for (int k = 0; k < PPT; k++) {
-          if (!cand[k]) continue;
-          n_sup++;
-          const float wv = s_cw[warp][slot][k][lane];
-          const float raw = __fmul_rn(og[k], wv);
-          const float alpha = fminf(p.alpha_max, raw);
-          if (alpha < p.alpha_min) continue;
-          any = true;
+          if (k != rk || !mine) continue;
           n_comp++;
+          const float dx = __fsub_rn(__fsub_rn(pxf[k], P.x), P.z), dy = __fsub_rn(__fsub_rn(pyf[k], P.y), P.w);
+          const float G = gauss(dx, dy, Q);
+          const float og = __fmul_rn(Q.w, G);
+          const float wv = __uint_as_float(pay.x);
+          const float raw = __fmul_rn(og, wv);
+          const float alpha = fminf(p.alpha_max, raw);
           const float oma = 1.0f - alpha;
           Tr[k] = __fdividef(Tr[k], oma);  // T_i
           const float ta = Tr[k] * alpha;
@@ -614,40 +686,57 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
           }
           dl_da *= Tr[k];
           if (raw >= p.alpha_max) continue;  // clamped: alpha is constant
-          acc[5] += dl_da * wv * G[k];
-          const float dl_dw = dl_da * Q.w * G[k];
-          const float dl_dpow = dl_da * og[k] * wv;
-          const float dx = dxs[k], dy = dys[k];  // q - mu
+          acc[5] += dl_da * wv * G;
+          dl_dw = dl_da * Q.w * G;
+          const float dl_dpow = dl_da * og * wv;
           acc[2] += dl_dpow * (-0.5f * dx * dx);
           acc[3] += dl_dpow * (-dx * dy);
           acc[4] += dl_dpow * (-0.5f * dy * dy);
           acc[0] += dl_dpow * (Q.x * dx + Q.y * dy);
           acc[1] += dl_dpow * (Q.y * dx + Q.z * dy);
-          s_cacc[warp][slot][k][lane] += dl_dw;  // boundary-point gradient, taken per slot
         }
-        if (__any_sync(0xffffffffu, any)) {
-          // gradient slots: 0 dmu x, 1 dmu y, 2-4 dK, 5 do, 6-8 dcol; slots 0-7
-          // by reduce-scatter (lanes 4m hold slot m), slot 8 by a butterfly
-          const float part = warp_reduce_scatter8(acc);
-          const float s8 = warp_sum(acc[8]);
-          float *gg = w.gg + 12 * (size_t)sG[warp][l];
-          const int gslot = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-          if ((lane & 3) == 0 && part != 0.f) atomicAdd(gg + gslot, part);
-          if (lane == 1 && s8 != 0.f) atomicAdd(gg + 8, s8);
+        if (p.use_boundary) {
+          int slot = cache_find(ckey, g);
+          if (slot < 0) {  // warp-uniform miss: flush the evicted slot, start a new sum
+            slot = cnext;
+            cnext = (cnext + 1 == S) ? 0 : cnext + 1;
+            const int old = __shfl_sync(0xffffffffu, ckey, slot);
+            if (old >= 0)
+              flush_boundary<PPT>(brec, bkeys, w.bg_grad, &s_cb[slot][0][0], &s_cacc[slot][0][0], old, idq, pxf, pyf);
+#pragma unroll
+            for (int k = 0; k < PPT; k++) {
+              s_cb[slot][k][lane] = -1;
+              s_cacc[slot][k][lane] = 0.f;
+            }
+            if (lane == slot) ckey = g;
+          }
+          if (mine) {
+            s_cb[slot][rk][lane] = (int)pay.y;
+            s_cacc[slot][rk][lane] += dl_dw;
+          }
         }
+        // gradient slots: 0 dmu x, 1 dmu y, 2-4 dK, 5 do, 6-8 dcol; slots 0-7
+        // by reduce-scatter (lanes 4m hold slot m), slot 8 by a butterfly
+        const float part = warp_reduce_scatter8(acc);
+        const float s8 = warp_sum(acc[8]);
+        float *gg = w.gg + 12 * (size_t)h.x;
+        const int gslot = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+        if ((lane & 3) == 0 && part != 0.f) atomicAdd(gg + gslot, part);
+        if (lane == 1 && s8 != 0.f) atomicAdd(gg + 8, s8);
       }
       __syncwarp();
+      chunk = prev;
+      n = kRecChunk;
     }
     if (p.use_boundary) {
       for (int sl = 0; sl < S; sl++) {
         const int old = __shfl_sync(0xffffffffu, ckey, sl);
         if (old >= 0)
-          flush_boundary<PPT>(bl, bkeys, w.bg_grad, &s_cb[warp][sl][0][0], &s_cacc[warp][sl][0][0], old, idq, pxf,
-                              pyf);
+          flush_boundary<PPT>(brec, bkeys, w.bg_grad, &s_cb[sl][0][0], &s_cacc[sl][0][0], old, idq, pxf, pyf);
       }
     }
-    if (p.stats) flush_stats(w.stats, kBwdSupport, n_sup, n_comp, n_cand, n_visit);
-    __syncthreads();  // the staged boundary list is free again
+    if (p.stats) flush_stats(w.stats, kBwdSupport, n_comp, n_comp, 0u, n_rec);
+    item = __shfl_sync(0xffffffffu, next, 0);
   }
 }
 
@@ -655,7 +744,7 @@ template <int T>
 int launch_fwd_t(const Params &p, const Work &w, float *image, cudaStream_t st, int sms) {
   int grid = p.tiles < sms * 8 ? p.tiles : sms * 8;
   if (grid > 0)
-    k_composite_fwd<T><<<grid, TileCfg<T>::NT, sizeof(BlendShared<T, false>), st>>>(p, w, image);
+    k_composite_fwd<T><<<grid, TileCfg<T>::NT, sizeof(FwdShared<T>), st>>>(p, w, image);
   return grid > 0 ? 1 : 0;
 }
 
@@ -663,17 +752,17 @@ template <int T>
 int launch_bwd_t(const Params &p, const Work &w, const float *dimage, cudaStream_t st, int sms) {
   int grid = p.tiles < sms * 8 ? p.tiles : sms * 8;
   if (grid > 0)
-    k_composite_bwd<T><<<grid, TileCfg<T>::NT, sizeof(BlendShared<T, true>), st>>>(p, w, dimage);
+    k_composite_bwd<T><<<grid, TileCfg<T>::NT, sizeof(BwdShared<T>), st>>>(p, w, dimage);
   return grid > 0 ? 1 : 0;
 }
 
 template <int T>
 cudaError_t configure_t() {
   cudaError_t e = cudaFuncSetAttribute(k_composite_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(BlendShared<T, false>));
+                                       (int)sizeof(FwdShared<T>));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_composite_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(BlendShared<T, true>));
+                             (int)sizeof(BwdShared<T>));
   return e;
 }
 

@@ -46,13 +46,15 @@ class Renderer:
 
     Capacities: max_prims, max_views, max_pixels (sum of W*H of one call),
     max_pairs / max_boundary_pairs ((Gaussian, tile) and (boundary point,
-    tile) pairs; default 8 per pixel). Options: tess_level L, tile_size
+    tile) pairs; default 8 per pixel), max_blend_pairs (composited
+    (pixel, Gaussian) pairs the forward records for the backward; default
+    24 per pixel). Options: tess_level L, tile_size
     (8/16/32), use_boundary (False = the paper's "w/o B" ablation), graph
     (capture forward / backward in CUDA graphs) and the blending cutoffs.
     """
 
     def __init__(self, degree=2, max_prims=100_000, max_views=64, max_pixels=1 << 20, max_pairs=None,
-                 max_boundary_pairs=None, tess_level=8, tile_size=16, use_boundary=True, graph=False,
+                 max_boundary_pairs=None, max_blend_pairs=0, tess_level=8, tile_size=16, use_boundary=True, graph=False,
                  k_b=3.0, alpha_min=1.0 / 255.0, alpha_max=0.99, t_stop=1e-4, dilation=0.3, near_z=0.2):
         self.lib = _abi.load()
         cfg = _abi.Config()
@@ -63,6 +65,7 @@ class Renderer:
         cfg.max_pixels = max_pixels
         cfg.max_pairs = max_pairs if max_pairs is not None else 8 * max_pixels
         cfg.max_boundary_pairs = max_boundary_pairs if max_boundary_pairs is not None else 8 * max_pixels
+        cfg.max_blend_pairs = max_blend_pairs
         cfg.tess_level = tess_level
         cfg.tile_size = tile_size
         cfg.k_b, cfg.alpha_min, cfg.alpha_max = k_b, alpha_min, alpha_max
