@@ -113,11 +113,11 @@ void carve(bgt_handle *h, char *base, size_t *total) {
   w.scan_aux2 = w.scan_aux ? w.scan_aux + (T / 4096 + 4) : nullptr;
   w.big_list = c.take<int>(2 * (long long)T + 2);
   w.tile_desc = c.take<int4>(T + 1);
-  w.rec_chunk_cap = (int)(h->Bcap / 4 / bgt::kRecChunk + 1);
-  w.pay_chunk_cap = (int)(h->Bcap / bgt::kPayChunk + 1);
+  w.rec_chunk_cap = (int)(h->Bcap / 8 / bgt::kRecChunk + 1);
+  w.fill_unit_cap = (int)(h->Bcap / 24 + bgt::kFillChunk * 4);
   w.rec_hdr = c.take<uint4>((long long)w.rec_chunk_cap * bgt::kRecChunk);
   w.rec_prev = c.take<int>(w.rec_chunk_cap);
-  w.rec_pay = c.take<uint2>((long long)w.pay_chunk_cap * bgt::kPayChunk);
+  w.rec_fill = c.take<int>((long long)w.fill_unit_cap * 32);
   w.blk_rec = c.take<int2>(8 * (long long)T + 8);  // warp blocks: at most 8 per tile at any tile size
   w.gkeys = c.take<unsigned long long>(2 * K);   // second half: sort scratch
   w.bkeys = c.take<unsigned long long>(2 * Kb);  // second half: sort scratch
@@ -357,7 +357,7 @@ bgt_status bgt_create(const bgt_config *cfg, bgt_handle **out) {
   h->Kbcap = cfg->max_boundary_pairs;
   // default 24 records per pixel, at least 4M (every resident warp holds a partly used payload chunk)
   h->Bcap = cfg->max_blend_pairs > 0 ? cfg->max_blend_pairs : std::max(24 * cfg->max_pixels, 1ll << 22);
-  if (h->Bcap > (1ll << 31) - 2 * bgt::kPayChunk) h->Bcap = (1ll << 31) - 2 * bgt::kPayChunk;
+  if (h->Bcap > (1ll << 31) - 1024) h->Bcap = (1ll << 31) - 1024;
   h->Vcap = cfg->max_views;
   h->Mcap = cfg->max_prims;
   // tiles of all views at the smallest tile size: sum (W/8+1)(H/8+1) <= P (1/64 + 1/8) + 2 V

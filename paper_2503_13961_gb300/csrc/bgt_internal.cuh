@@ -31,9 +31,9 @@ constexpr int kStatusBadPrim = 16;
 constexpr int kStatusBlendOverflow = 32;  // the forward pass's blend records exceeded their capacity
 
 // blend records (forward -> backward): headers in chunks of kRecChunk per warp
-// block, payload entries in chunks of kPayChunk per warp
+// block, fill records in chunks of kFillChunk per warp
 constexpr int kRecChunk = 32;
-constexpr int kPayChunk = 256;
+constexpr int kFillChunk = 8;
 
 struct View {                 // one camera and its place in the batch (128 B)
   float R[9];                 // world -> camera rotation, row-major
@@ -110,16 +110,18 @@ struct Work {
   long long *scan_aux, *scan_aux2; // scratch of the two tile-count scans
   int *big_list;              // [2 tiles] segments too long for one warp to sort
   int4 *tile_desc;            // [tiles] view, x0 | y0 << 16, W | H << 16, view pixel offset
-  // Blend records written by the forward pass for the backward pass. One
-  // record per (warp visit of a listed Gaussian, pixel plane k) with at least
-  // one composited pixel: header (Gaussian index, lane mask of composited
-  // pixels, payload offset, k); payload per composited pixel (w bits, index of
-  // its most influential boundary point in the tile's boundary list or -1).
+  // Blend records written by the forward pass for the backward pass. A fill
+  // record is written when a warp's primitive cache takes in primitive g: per
+  // pixel plane k and lane, the index of the pixel's most influential boundary
+  // point of g in the tile's boundary list, or -1 (w follows from it). A
+  // header is written per (warp visit of a listed Gaussian, plane k) with at
+  // least one composited pixel: (Gaussian index, lane mask of the composited
+  // pixels, first unit of the fill record of its primitive, k).
   uint4 *rec_hdr;             // [rec_chunk_cap * kRecChunk]
   int *rec_prev;              // [rec_chunk_cap] previous header chunk of the same warp block, -1
-  uint2 *rec_pay;             // [pay_chunk_cap * kPayChunk]
+  int *rec_fill;              // [fill_unit_cap * 32] one unit = one plane of one fill record
   int2 *blk_rec;              // [warp blocks] last header chunk (-1 none, -2 overflow), records in it
-  int rec_chunk_cap, pay_chunk_cap;
+  int rec_chunk_cap, fill_unit_cap;
   // pairs
   unsigned long long *gkeys;  // [Kcap] depth key (FP32 bits << 5 | sub) << 27 | gaussian index
   unsigned long long *bkeys;  // [Kbcap] (prim << 32) | boundary index
@@ -146,7 +148,7 @@ constexpr int kIndexBits = 27;  // Gaussian index field of a pair key (<= 134M G
 constexpr unsigned long long kIndexMask = (1ull << kIndexBits) - 1ull;
 
 enum Counter { kF = 0, kNb = 1, kK = 2, kKb = 3, kQueueFwd = 4, kQueueBwd = 5, kQueueSort = 6, kBigCount = 7,
-               kRecChunks = 8, kPayChunks = 9 };
+               kRecChunks = 8, kFillChunks = 9 };
 
 // ---------------------------------------------------------------------------
 // small helpers

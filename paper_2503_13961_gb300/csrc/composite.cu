@@ -23,7 +23,7 @@ namespace bgt {
 
 namespace {
 
-constexpr int kBCap = 768;         // boundary candidates staged in shared memory per tile
+constexpr int kBCap = 1024;        // boundary candidates staged in shared memory per tile
 constexpr float kLog2e = 1.4426950408889634f;
 
 // Block layout: NT threads; every warp owns a WX x WY block of the tile's
@@ -38,7 +38,7 @@ struct TileCfg {
   static constexpr int WY = (T == 32) ? 8 : 4;
   static constexpr int WPR = T / WX;         // warp blocks per tile row
   // primitive cache per warp (fully associative, FIFO): slot keys one per lane
-  static constexpr int SLOTS_FWD = (PPT == 1) ? 12 : 4;
+  static constexpr int SLOTS_FWD = (PPT == 1) ? 16 : 8;
   static constexpr int SLOTS_BWD = (PPT == 1) ? 12 : 4;
   // resident blocks per SM the kernels are compiled for (their shared memory
   // allows this many; the register budget follows)
@@ -266,7 +266,6 @@ struct FwdShared {
   float4 sP[Cfg::NW][32], sQ[Cfg::NW][32], sC[Cfg::NW][32];
   float4 s_bloc[kBCap];
   float s_cw[Cfg::NW][S][Cfg::PPT][32];  // cached w per slot and pixel
-  int s_cb[Cfg::NW][S][Cfg::PPT][32];    // its boundary candidate (tile list index) or -1
   int sG[Cfg::NW][32];
   int s_bprim[kBCap];
   float s_bisig[kBCap];
@@ -279,6 +278,7 @@ struct BwdShared {
   static constexpr int S = Cfg::SLOTS_BWD;
   float4 sP[Cfg::NW][32], sQ[Cfg::NW][32], sC[Cfg::NW][32];
   uint4 sH[Cfg::NW][32];                 // staged record headers
+  float s_cw[Cfg::NW][S][Cfg::PPT][32];  // w of the slot's primitive per pixel
   int s_cb[Cfg::NW][S][Cfg::PPT][32];    // the slot's boundary candidate per pixel (-1: none)
   float s_cacc[Cfg::NW][S][Cfg::PPT][32];  // sum of dl/dw over the slot's Gaussians per pixel
 };
@@ -290,57 +290,23 @@ __device__ __forceinline__ int cache_find(int ckey, int g) {
   return m ? __ffs(m) - 1 : -1;
 }
 
-// Writer of the blend records of one warp (warp-uniform state): header
-// chunks belong to one warp block, payload chunks to the warp (they persist
-// across the blocks it blends). Running out of either capacity raises
-// kStatusBlendOverflow and marks the block's records invalid.
+// Writer of the blend records of one warp. Headers are stashed one per lane
+// (lane i holds the block's i-th pending header) and stored as one coalesced
+// chunk of kRecChunk; fill records come from chunks of kFillChunk units owned
+// by the warp across the blocks it blends. Running out of either capacity
+// raises kStatusBlendOverflow and marks the block's records invalid.
 struct RecWriter {
-  int chunk, count;  // the block's current header chunk (-1: none) and its records
-  int pay, pay_end;  // the warp's current payload chunk [pay, pay_end)
+  int chunk, last_n;  // the block's last stored header chunk (-1: none) and its headers
+  int count;          // pending headers
+  uint4 hdr;          // this lane's pending header
+  int fill, fill_end; // the warp's current fill units [fill, fill_end)
   bool ok;
 
   __device__ __forceinline__ void begin_block() {
     chunk = -1;
-    count = kRecChunk;
+    last_n = 0;
+    count = 0;
     ok = true;
-  }
-
-  // record: Gaussian gi composited at the pixels k of the lanes in cm; this
-  // lane (if in cm) stores its w and boundary candidate
-  __device__ __forceinline__ void put(const Work &w, unsigned gi, unsigned cm, int k, bool mine, float wv, int best) {
-    const int lane = threadIdx.x & 31;
-    if (!ok) return;
-    if (count == kRecChunk) {
-      int id = 0;
-      if (lane == 0) {
-        id = atomicAdd(w.counters + kRecChunks, 1);
-        if (id < w.rec_chunk_cap) w.rec_prev[id] = chunk;
-      }
-      id = __shfl_sync(0xffffffffu, id, 0);
-      if (id >= w.rec_chunk_cap) {
-        fail(w);
-        return;
-      }
-      chunk = id;
-      count = 0;
-    }
-    const int n = __popc(cm);
-    if (pay + n > pay_end) {
-      int c = 0;
-      if (lane == 0) c = atomicAdd(w.counters + kPayChunks, 1);
-      c = __shfl_sync(0xffffffffu, c, 0);
-      if (c >= w.pay_chunk_cap) {
-        fail(w);
-        return;
-      }
-      pay = c * kPayChunk;
-      pay_end = pay + kPayChunk;
-    }
-    if (lane == 0) w.rec_hdr[(size_t)chunk * kRecChunk + count] = make_uint4(gi, cm, (unsigned)pay, (unsigned)k);
-    if (mine)
-      w.rec_pay[(size_t)pay + __popc(cm & ((1u << lane) - 1u))] = make_uint2(__float_as_uint(wv), (unsigned)best);
-    pay += n;
-    count++;
   }
 
   __device__ __forceinline__ void fail(const Work &w) {
@@ -348,9 +314,54 @@ struct RecWriter {
     if ((threadIdx.x & 31) == 0) atomicOr(w.status, kStatusBlendOverflow);
   }
 
+  // first unit of a new fill record of `units` planes, or -1
+  __device__ __forceinline__ int new_fill(const Work &w, int units) {
+    if (!ok) return -1;
+    if (fill + units > fill_end) {
+      int c = 0;
+      if ((threadIdx.x & 31) == 0) c = atomicAdd(w.counters + kFillChunks, 1);
+      c = __shfl_sync(0xffffffffu, c, 0);
+      if ((long long)(c + 1) * kFillChunk * units > w.fill_unit_cap) {
+        fail(w);
+        return -1;
+      }
+      fill = c * kFillChunk * units;
+      fill_end = fill + kFillChunk * units;
+    }
+    const int f = fill;
+    fill += units;
+    return f;
+  }
+
+  __device__ __forceinline__ void flush(const Work &w) {
+    const int lane = threadIdx.x & 31;
+    if (count == 0 || !ok) return;
+    int id = 0;
+    if (lane == 0) {
+      id = atomicAdd(w.counters + kRecChunks, 1);
+      if (id < w.rec_chunk_cap) w.rec_prev[id] = chunk;
+    }
+    id = __shfl_sync(0xffffffffu, id, 0);
+    if (id >= w.rec_chunk_cap) {
+      fail(w);
+      return;
+    }
+    if (lane < count) w.rec_hdr[(size_t)id * kRecChunk + lane] = hdr;
+    chunk = id;
+    last_n = count;
+    count = 0;
+  }
+
+  // header: Gaussian gi composited at the pixels k of the lanes in cm; its
+  // primitive's fill record starts at unit f
+  __device__ __forceinline__ void put(const Work &w, unsigned gi, unsigned cm, int f, int k) {
+    if ((threadIdx.x & 31) == count) hdr = make_uint4(gi, cm, (unsigned)f, (unsigned)k);
+    if (++count == kRecChunk) flush(w);
+  }
+
   __device__ __forceinline__ void end_block(const Work &w, int blk) {
-    if ((threadIdx.x & 31) == 0)
-      w.blk_rec[blk] = ok ? make_int2(chunk, chunk >= 0 ? count : 0) : make_int2(-2, 0);
+    flush(w);
+    if ((threadIdx.x & 31) == 0) w.blk_rec[blk] = ok ? make_int2(chunk, last_n) : make_int2(-2, 0);
   }
 };
 
@@ -365,11 +376,10 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_compos
   auto &sC = sh.sC;
   auto &sG = sh.sG;
   auto &s_cw = sh.s_cw;
-  auto &s_cb = sh.s_cb;
   auto &s_tile = sh.s_tile;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   RecWriter rw;
-  rw.pay = rw.pay_end = 0;
+  rw.fill = rw.fill_end = 0;
   if (threadIdx.x == 0) s_tile = atomicAdd(w.counters + kQueueFwd, 1);
   __syncthreads();
   for (;;) {
@@ -389,7 +399,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_compos
     int last[PPT], idq[PPT], pix[PPT];
     bool done[PPT];
     unsigned n_sup = 0, n_comp = 0, n_cand = 0, n_visit = 0;
-    int ckey = -2, cnext = 0;
+    int ckey = -2, cnext = 0, cfill = -1;  // lane s: primitive and fill record of cache slot s
     rw.begin_block();
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
@@ -440,16 +450,22 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_compos
         if (slot < 0) {  // warp-uniform miss: every lane searches, coherently
           slot = cnext;
           cnext = (cnext + 1 == S) ? 0 : cnext + 1;
-          int lo = 0, hi = 0;
-          if (p.use_boundary) warp_equal_range(bl.prim, bl.n, g, lo, hi);
+          int lo = 0, hi = 0, f = -1;
+          if (p.use_boundary) {
+            warp_equal_range(bl.prim, bl.n, g, lo, hi);
+            f = rw.new_fill(w, PPT);
+          }
 #pragma unroll
           for (int k = 0; k < PPT; k++) {
             int best = -1;
             s_cw[warp][slot][k][lane] = p.use_boundary
                 ? w_search<2>(bl, lo, hi, pxf[k], pyf[k], idq[k] == g, best, n_cand) : 1.0f;
-            s_cb[warp][slot][k][lane] = best;
+            if (f >= 0) w.rec_fill[(size_t)(f + k) * 32 + lane] = best;
           }
-          if (lane == slot) ckey = g;
+          if (lane == slot) {
+            ckey = g;
+            cfill = f;
+          }
         }
         bool comp[PPT];
 #pragma unroll
@@ -474,11 +490,11 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_compos
           n_comp++;
         }
         // record the pixels composited for the backward pass
+        const int fill = __shfl_sync(0xffffffffu, cfill, slot);
 #pragma unroll
         for (int k = 0; k < PPT; k++) {
           const unsigned cm = __ballot_sync(0xffffffffu, comp[k]);
-          if (cm)
-            rw.put(w, (unsigned)sG[warp][l], cm, k, comp[k], s_cw[warp][slot][k][lane], s_cb[warp][slot][k][lane]);
+          if (cm) rw.put(w, (unsigned)sG[warp][l], cm, fill, k);
         }
       }
       __syncwarp();
@@ -564,11 +580,17 @@ __device__ __forceinline__ void flush_boundary(const float4 *brec, const unsigne
   }
 }
 
-// payload entry of this lane in record h (zeros if the lane is not in it)
-__device__ __forceinline__ uint2 record_payload(const Work &w, const uint4 &h) {
-  const int lane = threadIdx.x & 31;
-  if (!((h.y >> lane) & 1u)) return make_uint2(0u, 0u);
-  return w.rec_pay[(size_t)h.z + __popc(h.y & ((1u << lane) - 1u))];
+// w (Eq. 6-7) at pixel (px, py) for the primitive whose most influential
+// boundary point is candidate bi of the tile's list (-1: none within rho < 1),
+// with the operations of the forward search, so the value is bit-identical
+__device__ __forceinline__ float w_from_candidate(const float4 *brec, int bi, float pxf, float pyf, bool inside) {
+  if (bi < 0) return inside ? 1.0f : 0.0f;
+  const float4 rec = brec[bi];
+  const float4 b = to_search(rec);
+  const float dx = __fsub_rn(__fsub_rn(pxf, b.x), b.z), dy = __fsub_rn(__fsub_rn(pyf, b.y), b.w);
+  const float r2 = __fmul_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)), __fmul_rn(rec.w, rec.w));
+  const float gamma = gamma_of(r2);
+  return inside ? gamma : __fsub_rn(1.0f, gamma);
 }
 
 // Backward pass over the forward pass's blend records. Every warp takes warp
@@ -587,6 +609,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float4 *sP = sh.sP[warp], *sQ = sh.sQ[warp], *sC = sh.sC[warp];
   uint4 *sH = sh.sH[warp];
+  auto &s_cw = sh.s_cw[warp];
   auto &s_cb = sh.s_cb[warp];
   auto &s_cacc = sh.s_cacc[warp];
   const int items = p.tiles * NW;
@@ -646,16 +669,33 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
         sC[lane] = w.gC[h.x];
       }
       __syncwarp();
-      uint2 pay_next = record_payload(w, sH[n - 1]);
       for (int r = n - 1; r >= 0; r--) {
         const uint4 h = sH[r];
-        const uint2 pay = pay_next;
-        if (r > 0) pay_next = record_payload(w, sH[r - 1]);  // prefetch
         const bool mine = (h.y >> lane) & 1u;
         const int rk = (int)h.w;
         const float4 P = sP[r], Q = sQ[r], Cc = sC[r];
         const int g = __float_as_int(Cc.w);
         n_rec++;
+        // w of (pixel, g): from the cache slot, filled from g's fill record
+        int slot = 0;
+        if (p.use_boundary) {
+          slot = cache_find(ckey, g);
+          if (slot < 0) {  // warp-uniform miss: flush the evicted slot, take in g
+            slot = cnext;
+            cnext = (cnext + 1 == S) ? 0 : cnext + 1;
+            const int old = __shfl_sync(0xffffffffu, ckey, slot);
+            if (old >= 0)
+              flush_boundary<PPT>(brec, bkeys, w.bg_grad, &s_cb[slot][0][0], &s_cacc[slot][0][0], old, idq, pxf, pyf);
+#pragma unroll
+            for (int k = 0; k < PPT; k++) {
+              const int bi = (int)h.z >= 0 ? w.rec_fill[(size_t)((int)h.z + k) * 32 + lane] : -1;
+              s_cw[slot][k][lane] = w_from_candidate(brec, bi, pxf[k], pyf[k], idq[k] == g);
+              s_cb[slot][k][lane] = bi;
+              s_cacc[slot][k][lane] = 0.f;
+            }
+            if (lane == slot) ckey = g;
+          }
+        }
         float acc[9];
 #pragma unroll
         for (int q = 0; q < 9; q++) acc[q] = 0.f;
@@ -667,7 +707,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
           const float dx = __fsub_rn(__fsub_rn(pxf[k], P.x), P.z), dy = __fsub_rn(__fsub_rn(pyf[k], P.y), P.w);
           const float G = gauss(dx, dy, Q);
           const float og = __fmul_rn(Q.w, G);
-          const float wv = __uint_as_float(pay.x);
+          const float wv = p.use_boundary ? s_cw[slot][k][lane] : 1.0f;
           const float raw = __fmul_rn(og, wv);
           const float alpha = fminf(p.alpha_max, raw);
           const float oma = 1.0f - alpha;
@@ -695,26 +735,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
           acc[0] += dl_dpow * (Q.x * dx + Q.y * dy);
           acc[1] += dl_dpow * (Q.y * dx + Q.z * dy);
         }
-        if (p.use_boundary) {
-          int slot = cache_find(ckey, g);
-          if (slot < 0) {  // warp-uniform miss: flush the evicted slot, start a new sum
-            slot = cnext;
-            cnext = (cnext + 1 == S) ? 0 : cnext + 1;
-            const int old = __shfl_sync(0xffffffffu, ckey, slot);
-            if (old >= 0)
-              flush_boundary<PPT>(brec, bkeys, w.bg_grad, &s_cb[slot][0][0], &s_cacc[slot][0][0], old, idq, pxf, pyf);
-#pragma unroll
-            for (int k = 0; k < PPT; k++) {
-              s_cb[slot][k][lane] = -1;
-              s_cacc[slot][k][lane] = 0.f;
-            }
-            if (lane == slot) ckey = g;
-          }
-          if (mine) {
-            s_cb[slot][rk][lane] = (int)pay.y;
-            s_cacc[slot][rk][lane] += dl_dw;
-          }
-        }
+        if (p.use_boundary && mine) s_cacc[slot][rk][lane] += dl_dw;
         // gradient slots: 0 dmu x, 1 dmu y, 2-4 dK, 5 do, 6-8 dcol; slots 0-7
         // by reduce-scatter (lanes 4m hold slot m), slot 8 by a butterfly
         const float part = warp_reduce_scatter8(acc);
