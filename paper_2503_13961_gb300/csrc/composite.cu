@@ -43,7 +43,7 @@ struct TileCfg {
   // resident blocks per SM the kernels are compiled for (their shared memory
   // allows this many; the register budget follows)
   static constexpr int MINB_FWD = (T == 8) ? 6 : (T == 16) ? 4 : 2;
-  static constexpr int MINB_BWD = (T == 8) ? 6 : (T == 16) ? 3 : 2;
+  static constexpr int MINB_BWD = (T == 8) ? 6 : (T == 16) ? 4 : 2;
 };
 
 template <int T>

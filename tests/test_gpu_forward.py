@@ -235,6 +235,27 @@ def test_pair_capacity_overflow_is_reported(scenes):
     rd2.sync_status()
 
 
+def test_blend_record_capacity_overflow_is_reported(scenes):
+    """The forward pass's blend records (read by the backward pass) have their
+    own capacity; running out of it is reported and the backward pass reads
+    only complete records."""
+    import torch
+    from paper_2503_13961_gb300 import _abi
+    from paper_2503_13961_gb300 import render as R
+    sc, cams = scenes.tiny_scene("ico1", noise=0.02, size=(96, 96))
+    rd = R.Renderer(degree=2, max_prims=64, max_views=1, max_pixels=96 * 96, max_blend_pairs=1)
+    dev = R.scene_to_device(sc)
+    img = rd.forward(dev, cams)
+    with pytest.raises(_abi.BGTError) as e:
+        rd.sync_status()
+    assert e.value.status == 2
+    rd.backward(dev, cams, torch.ones_like(img))
+    torch.cuda.synchronize()
+    rd2 = make_renderer(sc, cams)
+    rd2.forward(dev, cams)
+    rd2.sync_status()
+
+
 def test_host_side_argument_errors(scenes):
     import torch
     from paper_2503_13961_gb300 import _abi
