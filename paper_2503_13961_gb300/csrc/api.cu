@@ -112,7 +112,7 @@ void carve(bgt_handle *h, char *base, size_t *total) {
   w.scan_aux = c.take<long long>(2 * (T / 4096 + 4));
   w.scan_aux2 = w.scan_aux ? w.scan_aux + (T / 4096 + 4) : nullptr;
   w.big_list = c.take<int>(2 * (long long)T + 2);
-  w.tile_desc = c.take<int4>(T + 1);
+  w.tile_desc = c.take<int4>(2 * (long long)T + 2);
   w.rec_chunk_cap = (int)(h->Bcap / 8 / bgt::kRecChunk + 1);
   w.fill_unit_cap = (int)(h->Bcap / 24 + bgt::kFillChunk * 4);
   w.rec_hdr = c.take<uint4>((long long)w.rec_chunk_cap * bgt::kRecChunk);

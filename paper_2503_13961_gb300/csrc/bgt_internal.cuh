@@ -109,7 +109,8 @@ struct Work {
   long long *g_tstart, *b_tstart;  // [tiles + 1] exclusive prefix sums (64-bit: no wrap)
   long long *scan_aux, *scan_aux2; // scratch of the two tile-count scans
   int *big_list;              // [2 tiles] segments too long for one warp to sort
-  int4 *tile_desc;            // [tiles] view, x0 | y0 << 16, W | H << 16, view pixel offset
+  int4 *tile_desc;            // [2 tiles] (view, x0 | y0 << 16, W | H << 16, view pixel offset),
+                              // (Gaussian list start, length, boundary list start, length)
   // Blend records written by the forward pass for the backward pass. A fill
   // record is written when a warp's primitive cache takes in primitive g: per
   // pixel plane k and lane, the index of the pixel's most influential boundary

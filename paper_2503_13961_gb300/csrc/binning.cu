@@ -131,8 +131,10 @@ __global__ void k_emit(Params p, Work w) {
   }
 }
 
-// per-tile descriptor, so that the blending kernels read one record instead
-// of searching the view offsets
+// per-tile descriptor, so that the blending kernels read two records instead
+// of searching the view offsets and reading the list starts: [2t] geometry,
+// [2t + 1] (Gaussian list start, length, boundary list start, length); an
+// overflowed list (its slots were not all written) has length 0
 __global__ void k_tile_desc(Params p, Work w) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= p.tiles) return;
@@ -140,8 +142,12 @@ __global__ void k_tile_desc(Params p, Work w) {
   const View &vw = w.views[view];
   const int lt = t - vw.tile_off;
   const int ty = lt / vw.tiles_x, tx = lt - ty * vw.tiles_x;
-  w.tile_desc[t] = make_int4(view, (int)((unsigned)(tx * p.tile) | ((unsigned)(ty * p.tile) << 16)),
-                             (int)((unsigned)vw.W | ((unsigned)vw.H << 16)), vw.pix_off);
+  w.tile_desc[2 * t] = make_int4(view, (int)((unsigned)(tx * p.tile) | ((unsigned)(ty * p.tile) << 16)),
+                                 (int)((unsigned)vw.W | ((unsigned)vw.H << 16)), vw.pix_off);
+  const bool g_over = w.g_tstart[p.tiles] > p.max_pairs, b_over = w.b_tstart[p.tiles] > p.max_bpairs;
+  const long long gs = w.g_tstart[t], bs = w.b_tstart[t];
+  w.tile_desc[2 * t + 1] = make_int4(g_over ? 0 : (int)gs, g_over ? 0 : (int)(w.g_tstart[t + 1] - gs),
+                                     b_over ? 0 : (int)bs, b_over ? 0 : (int)(w.b_tstart[t + 1] - bs));
 }
 
 __global__ void k_check_capacity(Params p, Work w) {

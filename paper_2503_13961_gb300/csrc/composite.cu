@@ -175,20 +175,19 @@ struct TileInfo {
 
 __device__ inline TileInfo tile_info(const Params &p, const Work &w, int tile) {
   TileInfo t;
-  const int4 d = w.tile_desc[tile];
+  const int4 d = w.tile_desc[2 * tile], r = w.tile_desc[2 * tile + 1];
   t.view = d.x;
   t.x0 = d.y & 0xffff;
   t.y0 = (int)((unsigned)d.y >> 16);
   t.W = d.z & 0xffff;
   t.H = (int)((unsigned)d.z >> 16);
   t.pix_off = d.w;
-  // an overflowed call (reported through the status word) leaves key slots
-  // unwritten: its lists are treated as empty so that no slot is read
-  const bool g_over = w.g_tstart[p.tiles] > p.max_pairs, b_over = w.b_tstart[p.tiles] > p.max_bpairs;
-  t.gs = g_over ? 0 : w.g_tstart[tile];
-  t.gn = g_over ? 0 : w.g_tstart[tile + 1] - t.gs;
-  t.bs = b_over ? 0 : w.b_tstart[tile];
-  t.bn = b_over ? 0 : w.b_tstart[tile + 1] - t.bs;
+  // an overflowed call (reported through the status word) has empty lists,
+  // so that no unwritten key slot is read
+  t.gs = r.x;
+  t.gn = r.y;
+  t.bs = r.z;
+  t.bn = r.w;
   return t;
 }
 
@@ -620,11 +619,10 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
     int next = 0;  // the next warp block, fetched while this one is processed
     if (lane == 0) next = atomicAdd(w.counters + kQueueBwd, 1);
     const int tile = item / NW, wb = item - tile * NW;
-    const int4 d = w.tile_desc[tile];
+    const int4 d = w.tile_desc[2 * tile];
     const int x0 = d.y & 0xffff, y0 = (int)((unsigned)d.y >> 16);
     const int W = d.z & 0xffff, H = (int)((unsigned)d.z >> 16);
-    const bool b_over = w.b_tstart[p.tiles] > p.max_bpairs;
-    const long long bs = b_over ? 0 : w.b_tstart[tile];
+    const long long bs = w.tile_desc[2 * tile + 1].z;
     const float4 *brec = w.bl_rec + bs;
     const unsigned long long *bkeys = w.bkeys + bs;
     const int2 br = w.blk_rec[item];
