@@ -115,7 +115,9 @@ void bgt_destroy(bgt_handle *h);
 
 /* Forward pass (Sec. 3.2 pipeline) of n_views cameras (host array) on
  * `stream`. images: device [sum W H][3], written entirely. The handle keeps
- * the rasterizer outputs, sorted lists and per-pixel final transmittance for
+ * the rasterizer outputs, sorted lists, per-pixel final transmittance and
+ * the blend records (which Gaussians each pixel composited, with their w and
+ * most influential boundary point; capacity max_blend_pairs) for
  * bgt_render_bwd (valid until the next bgt_render_fwd on the handle).
  * BGT_ERR_INVALID_ARG / BGT_ERR_CAPACITY for bad or oversized inputs (checked
  * on the host before any launch), BGT_ERR_CUDA if a launch fails. */
@@ -160,8 +162,9 @@ int bgt_get_tile_size(const bgt_handle *h);
  * [0] pairs inside a Gaussian's support (o G >= alpha_min), [1] pairs
  * composited, [2] boundary candidates scanned by the Eq. 6 search, [3]
  * warp visits (a warp of 32 pixels evaluating one listed Gaussian with at
- * least one pixel in its support), for the forward; [4]-[7] the same for
- * the backward.
+ * least one pixel in its support), for the forward; for the backward, which
+ * replays the forward's blend records: [4] and [5] pairs composited, [6]
+ * zero, [7] records replayed.
  * BGT_ERR_STATE if profiling is off or no profiled pair has run. */
 bgt_status bgt_set_profiling(bgt_handle *h, int on);
 bgt_status bgt_get_profile(bgt_handle *h, float ms[8], int *kernels_fwd, int *kernels_bwd,
