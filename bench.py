@@ -47,8 +47,9 @@ def parse():
     ap.add_argument("--tile", type=int, default=0, help="0 = autotune")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="config4", choices=["config4", "view800"],
-                    help="view800: one 800^2 view of the same scene (small case for profilers)")
+    ap.add_argument("--workload", default="config4", choices=["config4", "view800", "views1024x4"],
+                    help="view800: one 800^2 view of the same scene (small case for profilers); "
+                         "views1024x4: four 1024^2 views (inputs larger than L2, a few GB on the device)")
     return ap.parse_args()
 
 
@@ -161,6 +162,26 @@ def stage_bytes(stage, c, M, ncp, V):
     }[stage]
 
 
+# DRAM bytes (read + write) per composited pair of the blending kernels, from one
+# ncu capture of four 1024^2 views (profiles/composite_dram_views1024x4.md),
+# valid only for the kernel source they were measured on (else traffic: null)
+BLEND_TRAFFIC = {"source_sha256": "a94eb491f9d2d0fe7e79ba9500e43337c7c2eaa2ced6ca010bb02e317178329d",
+                 "composite_fwd": (132.1e6 + 154.3e6) / 50625814, "composite_bwd": (297.4e6 + 40.7e6) / 50625814}
+
+
+def blend_traffic(dom, units):
+    import hashlib
+    src = os.path.join(ROOT, "paper_2503_13961_gb300", "csrc", "composite.cu")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    if sha != BLEND_TRAFFIC["source_sha256"] or dom not in BLEND_TRAFFIC:
+        return None
+    pairs = units["fwd_composited" if dom == "composite_fwd" else "bwd_composited"]
+    return int(BLEND_TRAFFIC[dom] * pairs)
+
+
 def roofline_entry(dom, stage_ms, units, achieved_gbs, dom_bytes, peak, peak_kind, fp32_peak):
     """Roofline of the dominant kernel: the blending kernels are bound by FP32
     issue (no dense contraction, DRAM far from busy), the others by HBM."""
@@ -170,7 +191,7 @@ def roofline_entry(dom, stage_ms, units, achieved_gbs, dom_bytes, peak, peak_kin
         ach = fl / (ms * 1e-3) / 1e12
         return {"bound": "alu", "kernel": dom, "achieved": round(ach, 3), "peak": round(fp32_peak, 1),
                 "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock", "unit": "TFLOP/s",
-                "frac": round(ach / fp32_peak, 4), "traffic": None, "alg_flops_per_launch": int(fl),
+                "frac": round(ach / fp32_peak, 4), "traffic": blend_traffic(dom, units), "alg_flops_per_launch": int(fl),
                 "ms_per_launch": round(ms, 4),
                 "hbm_view": {"achieved": round(achieved_gbs, 1), "peak": peak, "unit": "GB/s",
                              "frac": round(achieved_gbs / peak, 4), "alg_bytes_per_launch": int(dom_bytes)}}
@@ -184,6 +205,8 @@ def build_workload(seed_views, rb, workload="config4"):
     sc, cams = scenes.config_scene(4, r_b=rb)
     if workload == "view800":
         return sc, [c for c in cams if c["width"] == 800][:1]
+    if workload == "views1024x4":
+        return sc, [c for c in cams if c["width"] == 1024][:4]
     if seed_views:
         # other ranks render their own 64 views of the same scene (weak scaling)
         rng = np.random.default_rng(1000 + seed_views)
@@ -338,7 +361,8 @@ def run_ours(args):
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms / args.steps, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded scene generator; stands in for Lego / NeRF-Synthetic)",
-            "config": {"workload": WORKLOAD if args.workload == "config4" else "one 800^2 view of: " + WORKLOAD,
+            "config": {"workload": WORKLOAD if args.workload == "config4" else
+                       ("one 800^2 view of: " if args.workload == "view800" else "four 1024^2 views of: ") + WORKLOAD,
                        "views": V, "pixels": P, "prims": M, "degree": 2,
                        "tile": rd.tile_size, "tile_autotune_ms": tune_ms, "graph": True,
                        "counts": {k: int(v) for k, v in counts.items()},
