@@ -200,13 +200,21 @@ struct RVert {
   bool valid;
 };
 
+// lattice coordinate k / L, correctly rounded
+__device__ inline float lattice_frac(int k, int L) { return __fdiv_rn((float)k, (float)L); }
+
+template <int N>
+__device__ inline RVert raster_vertex(const float *cp, float u, float vv, float w, const View &v, float near_z);
+
 template <int N>
 __device__ inline RVert raster_vertex(const float *cp, int a, int b, int L, const View &v, float near_z) {
+  return raster_vertex<N>(cp, lattice_frac(a, L), lattice_frac(b, L), lattice_frac(L - a - b, L), v, near_z);
+}
+
+// vertex at barycentric (u, vv, w) = (a, b, L - a - b) / L
+template <int N>
+__device__ inline RVert raster_vertex(const float *cp, float u, float vv, float w, const View &v, float near_z) {
   RVert o;
-  const float fL = (float)L;
-  const float u = __fdiv_rn((float)a, fL);
-  const float vv = __fdiv_rn((float)b, fL);
-  const float w = __fdiv_rn((float)(L - a - b), fL);
   float pu[N + 1], pv[N + 1], pw[N + 1];
   pu[0] = pv[0] = pw[0] = 1.0f;
 #pragma unroll

@@ -38,12 +38,42 @@ __global__ void __launch_bounds__(kRasterWarps * 32) k_raster(Params p, Scene s,
   __shared__ int sX[kRasterWarps][kMaxVerts];
   __shared__ int sY[kRasterWarps][kMaxVerts];
   __shared__ float sIZ[kRasterWarps][kMaxVerts];
+  // lattice tables of this launch's level L: k / L, vertex (a, b), and per flat
+  // triangle its three vertex slots and its id
+  __shared__ float s_frac[kMaxTess + 1];
+  __shared__ int s_vab[kMaxVerts];
+  __shared__ int2 s_tri[kMaxTess * kMaxTess];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long items = (long long)p.V * p.M;
   const int L = p.L;
   const int NV = (L + 1) * (L + 2) / 2;
   const int up_count = L * (L + 1) / 2;
   const int nsub = 2 * L * L;
+  for (int i = threadIdx.x; i <= L; i += blockDim.x) s_frac[i] = lattice_frac(i, L);
+  for (int vi = threadIdx.x; vi < NV; vi += blockDim.x) {
+    int a, b;
+    slot_to_ab(vi, L, a, b);
+    s_vab[vi] = a | (b << 8);
+  }
+  for (int ti = threadIdx.x; ti < L * L; ti += blockDim.x) {
+    int a, down, rem;
+    if (ti < up_count) {
+      down = 0;
+      rem = ti;
+      a = 0;
+      while (rem >= L - a) { rem -= L - a; a++; }
+    } else {
+      down = 1;
+      rem = ti - up_count;
+      a = 0;
+      while (rem >= L - 1 - a) { rem -= L - 1 - a; a++; }
+    }
+    const int sid = 2 * (a * L + rem) + down;
+    int va[3], vb[3];
+    subtri_verts(L, sid, va, vb);
+    s_tri[ti] = make_int2(vslot(va[0], vb[0], L) | (vslot(va[1], vb[1], L) << 8) | (vslot(va[2], vb[2], L) << 16), sid);
+  }
+  __syncthreads();
   for (long long item = (long long)blockIdx.x * kRasterWarps + warp; item < items;
        item += (long long)gridDim.x * kRasterWarps) {
     const int view = (int)(item / p.M);
@@ -51,9 +81,8 @@ __global__ void __launch_bounds__(kRasterWarps * 32) k_raster(Params p, Scene s,
     const View vw = w.views[view];
     const float *cp = s.ctrl + (size_t)prim * p.ncp * 3;
     for (int vi = lane; vi < NV; vi += 32) {
-      int a, b;
-      slot_to_ab(vi, L, a, b);
-      const RVert r = raster_vertex<N>(cp, a, b, L, vw, p.near_z);
+      const int ab = s_vab[vi], a = ab & 0xff, b = ab >> 8;
+      const RVert r = raster_vertex<N>(cp, s_frac[a], s_frac[b], s_frac[L - a - b], vw, p.near_z);
       sX[warp][vi] = r.valid ? r.X : INT_MIN;
       sY[warp][vi] = r.Y;
       sIZ[warp][vi] = r.iz;
@@ -62,28 +91,14 @@ __global__ void __launch_bounds__(kRasterWarps * 32) k_raster(Params p, Scene s,
     const int W = vw.W, H = vw.H;
     unsigned long long *zb = w.zbuf + vw.pix_off;
     for (int ti = lane; ti < L * L; ti += 32) {
-      int a, b, down, rem;
-      if (ti < up_count) {
-        down = 0;
-        rem = ti;
-        a = 0;
-        while (rem >= L - a) { rem -= L - a; a++; }
-      } else {
-        down = 1;
-        rem = ti - up_count;
-        a = 0;
-        while (rem >= L - 1 - a) { rem -= L - 1 - a; a++; }
-      }
-      b = rem;
-      const int sid = 2 * (a * L + b) + down;
-      int va[3], vb[3];
-      subtri_verts(L, sid, va, vb);
+      const int2 tri = s_tri[ti];
+      const int sid = tri.y;
       int X[3], Y[3];
       float IZ[3];
       bool ok = true;
 #pragma unroll
       for (int c = 0; c < 3; c++) {
-        const int sl = vslot(va[c], vb[c], L);
+        const int sl = (tri.x >> (8 * c)) & 0xff;
         X[c] = sX[warp][sl];
         Y[c] = sY[warp][sl];
         IZ[c] = sIZ[warp][sl];
