@@ -167,10 +167,13 @@ __device__ inline uint2 tile_rect(float cx, float cy, float rx, float ry, const 
 template <int N>
 __global__ void __launch_bounds__(kGenThreads) k_generate(Params p, Scene s, Work w) {
   __shared__ int s_wf[kGenThreads / 32], s_wb[kGenThreads / 32];
+  // the block's foreground pixels in pixel order: pixel, view, boundary index (-1)
+  __shared__ int s_pix[kGenPixels], s_view[kGenPixels], s_bi[kGenPixels];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  int base_f = w.blk_cnt[blockIdx.x];
-  int base_b = w.blk_cnt[w.nblk + blockIdx.x];
+  const int base_f0 = w.blk_cnt[blockIdx.x];
+  int nf = 0, base_b = w.blk_cnt[w.nblk + blockIdx.x];
   const int base = blockIdx.x * kGenPixels;
+  // compaction: ranks in pixel order give the Gaussian and boundary indices
   for (int r = 0; r < kGenRounds; r++) {
     const int pix = base + r * kGenThreads + threadIdx.x;
     bool fg, bnd;
@@ -180,19 +183,29 @@ __global__ void __launch_bounds__(kGenThreads) k_generate(Params p, Scene s, Wor
     const unsigned lt = (1u << lane) - 1u;
     if (lane == 0) { s_wf[wp] = __popc(mf); s_wb[wp] = __popc(mb); }
     __syncthreads();
-    int off_f = base_f, off_b = base_b, tot_f = 0, tot_b = 0;
+    int off_f = nf, off_b = base_b, tot_f = 0, tot_b = 0;
     for (int i = 0; i < kGenThreads / 32; i++) {
       if (i < wp) { off_f += s_wf[i]; off_b += s_wb[i]; }
       tot_f += s_wf[i];
       tot_b += s_wb[i];
     }
     __syncthreads();
-    base_f += tot_f;
+    nf += tot_f;
     base_b += tot_b;
-    if (pix < p.P) w.pix_gidx[pix] = fg ? off_f + __popc(mf & lt) : -1;
-    if (!fg) continue;
-    const int gi = off_f + __popc(mf & lt);
-    const int bi = off_b + __popc(mb & lt);
+    const int lf = off_f + __popc(mf & lt);
+    if (pix < p.P) w.pix_gidx[pix] = fg ? base_f0 + lf : -1;
+    if (fg) {
+      s_pix[lf] = pix;
+      s_view[lf] = view;
+      s_bi[lf] = bnd ? off_b + __popc(mb & lt) : -1;
+    }
+  }
+  __syncthreads();
+  // sub-primitives of the foreground pixels, all threads busy
+  for (int j = threadIdx.x; j < nf; j += kGenThreads) {
+    const int pix = s_pix[j], view = s_view[j], bi = s_bi[j];
+    const bool bnd = bi >= 0;
+    const int gi = base_f0 + j;
     const View vw = w.views[view];
     const int prim = w.pid[pix];
     const float2 uv = w.puv[pix];
