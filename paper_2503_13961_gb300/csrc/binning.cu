@@ -251,7 +251,9 @@ __device__ void radix_global(unsigned long long *keys, unsigned long long *tmp, 
 }
 
 constexpr int kWarpSortCap = 1024;  // keys a single warp sorts in its own shared memory
-constexpr int kTileSortSmem = (kSortThreads / 32) * kWarpSortCap * (int)sizeof(unsigned long long);
+constexpr int kRadixMin = 129;     // segments from this length sort by radix, shorter ones by bitonic network
+// per warp: the keys (kWarpSortCap) and 256 radix bins
+constexpr int kTileSortSmem = (kSortThreads / 32) * (kWarpSortCap * (int)sizeof(unsigned long long) + 256 * 4);
 
 __device__ inline void segment_bounds(const Params &p, const Work &w, int item, bool &bnd, long long &s0,
                                       long long &s1) {
@@ -290,6 +292,80 @@ __device__ __forceinline__ void warp_bitonic_smem(unsigned long long *sk, int N,
     }
 }
 
+// Stable LSD radix sort (8-bit digits) of sk[0, n) (n <= kWarpSortCap) by
+// one warp: the keys sit in registers, key i in lane i % 32, slot i / 32; each
+// pass histograms the digit into `bins`, scans it and scatters the keys back
+// to sk in order, ranking equal digits of a round with a match; digits that
+// are equal over the whole segment are skipped.
+__device__ __forceinline__ void warp_radix_smem(unsigned long long *sk, unsigned *bins, int n, int lane) {
+  constexpr int R = kWarpSortCap / 32;
+  const int rounds = (n + 31) >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned long long key[R];
+  unsigned long long vor = 0ull, vand = ~0ull;
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    key[r] = 0ull;
+    if (r < rounds && r * 32 + lane < n) {
+      key[r] = sk[r * 32 + lane];
+      vor |= key[r];
+      vand &= key[r];
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    vor |= __shfl_xor_sync(0xffffffffu, vor, o);
+    vand &= __shfl_xor_sync(0xffffffffu, vand, o);
+  }
+  const unsigned long long varying = vor ^ vand;
+  for (int shift = 0; shift < 64; shift += 8) {
+    if (((varying >> shift) & 0xffull) == 0ull) continue;
+    for (int d = lane; d < 256; d += 32) bins[d] = 0u;
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < R; r++)
+      if (r < rounds && r * 32 + lane < n) atomicAdd(&bins[(unsigned)(key[r] >> shift) & 0xffu], 1u);
+    __syncwarp();
+    // exclusive scan of the 256 bins: 8 consecutive bins per lane
+    unsigned c[8], tot = 0u;
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      c[q] = bins[lane * 8 + q];
+      tot += c[q];
+    }
+    unsigned inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    unsigned run = inc - tot;
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      bins[lane * 8 + q] = run;
+      run += c[q];
+    }
+    __syncwarp();
+    // stable scatter, one round of 32 keys at a time
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      if (r >= rounds) break;
+      const bool valid = r * 32 + lane < n;
+      const unsigned d = valid ? ((unsigned)(key[r] >> shift) & 0xffu) : 0x100u + lane;
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      const unsigned base = valid ? bins[d] : 0u;
+      if (valid) sk[base + __popc(peers & lt)] = key[r];
+      __syncwarp();
+      if (valid && lane == 31 - __clz(peers)) bins[d] = base + __popc(peers);
+      __syncwarp();
+    }
+#pragma unroll
+    for (int r = 0; r < R; r++)
+      if (r < rounds && r * 32 + lane < n) key[r] = sk[r * 32 + lane];
+    __syncwarp();
+  }
+}
+
 // Warps take segments from a queue. Up to 32 keys: bitonic sort across the
 // lanes' registers; up to kWarpSortCap: bitonic sort in the warp's shared
 // memory; longer segments are appended to a list for k_tile_sort_big.
@@ -299,6 +375,7 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Params p, Work w, in
   const bool g_over = w.g_tstart[p.tiles] > p.max_pairs, b_over = w.b_tstart[p.tiles] > p.max_bpairs;
   const int items = 2 * p.tiles;
   unsigned long long *sk = s_sort + wp * kWarpSortCap;
+  unsigned *bins = reinterpret_cast<unsigned *>(s_sort + (kSortThreads / 32) * kWarpSortCap) + wp * 256;
   for (;;) {
     int item = 0;
     if (lane == 0) item = atomicAdd(w.counters + kQueueSort, 1);
@@ -329,7 +406,8 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Params p, Work w, in
       while (N < n) N <<= 1;
       for (int i = lane; i < N; i += 32) sk[i] = i < n ? keys[i] : ~0ull;
       __syncwarp();
-      warp_bitonic_smem(sk, N, lane);
+      if (n >= kRadixMin) warp_radix_smem(sk, bins, n, lane);
+      else warp_bitonic_smem(sk, N, lane);
       for (int i = lane; i < n; i += 32) keys[i] = sk[i];
       __syncwarp();
     }
