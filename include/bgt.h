@@ -61,8 +61,8 @@ typedef struct {
   long long max_pairs;          /* capacity: (Gaussian, tile) pairs per call */
   long long max_boundary_pairs; /* capacity: (boundary point, tile) pairs per call */
   long long max_blend_pairs;    /* capacity: (pixel, Gaussian) pairs the forward pass composites
-                                   per call, recorded for the backward pass; 0 = 24 per pixel,
-                                   at least 2^22 */
+                                   per call, recorded for the backward pass: headers get 1/2,
+                                   fill records 1/32 of it; 0 = 32 per pixel, at least 2^22 */
   int tess_level;               /* L: each primitive becomes L^2 flat triangles (1..16) */
   int tile_size;                /* screen tile edge: 8, 16 or 32 pixels */
   float k_b;                    /* boundary radius sigma = k_b fx r_b / z (Sec. 3.2) */
@@ -143,8 +143,11 @@ const char *bgt_last_error(const bgt_handle *h);
 
 /* Counts of the last forward, after a synchronize: out[0] = foreground
  * pixels F (= Gaussians), out[1] = boundary points |B|, out[2] = Gaussian
- * tile pairs K, out[3] = boundary tile pairs Kb, out[4] = total tiles. */
-bgt_status bgt_get_counts(bgt_handle *h, long long out[5], void *stream);
+ * tile pairs K, out[3] = boundary tile pairs Kb, out[4] = total tiles,
+ * out[5] = blend-record header slots taken (capacity max_blend_pairs / 2),
+ * out[6] = blend fill-record units taken (capacity max_blend_pairs / 32);
+ * taken slots beyond a capacity were not written (BGT_ERR_CAPACITY). */
+bgt_status bgt_get_counts(bgt_handle *h, long long out[7], void *stream);
 
 /* Change the tile size (8, 16 or 32) used by later calls. Images do not
  * depend on it (every pixel composites the same pairs in the same order). */

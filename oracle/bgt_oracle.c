@@ -389,7 +389,8 @@ typedef struct {
   ogauss *G;
   obnd *Bp;
   int32_t *bptr, *bidx;  /* boundary points of each primitive (CSR, bidx order) */
-  int32_t *pptr, *pidx;  /* candidate Gaussians of each pixel (CSR, index order) */
+  int64_t *pptr;         /* candidate Gaussians of each pixel (CSR, index order) */
+  int32_t *pidx;
 } oprep;
 
 static void cam_from_f32(const float *c, int W, int H, dcam *d) {
@@ -479,8 +480,9 @@ static void prep_free(oprep *pr) {
  * lists. In all-pairs mode every Gaussian is a candidate of every pixel; in
  * box mode only those whose support box contains the pixel: outside the box
  * o G < alpha_min, and since w <= 1 the pair would be dropped anyway. */
+/* pix_mask (nullable): only these pixels get candidate lists */
 static int prepare(const oscene *sc, const dcam *c, const int32_t *id, const double *uv,
-                   const oparams *pa, oprep *pr) {
+                   const oparams *pa, const int32_t *pix_mask, oprep *pr) {
   memset(pr, 0, sizeof(*pr));
   const int W = c->W, H = c->H, n = sc->n, m = ncp(n);
   const int64_t P = (int64_t)W * H;
@@ -553,9 +555,9 @@ static int prepare(const oscene *sc, const dcam *c, const int32_t *id, const dou
   }
   /* candidate Gaussians per pixel */
   if (!pa->all_pairs) {
-    pr->pptr = (int32_t *)calloc(P + 1, sizeof(int32_t));
+    pr->pptr = (int64_t *)calloc(P + 1, sizeof(int64_t));
     for (int pass = 0; pass < 2; pass++) {
-      int32_t *fill = pass ? (int32_t *)calloc(P + 1, sizeof(int32_t)) : NULL;
+      int64_t *fill = pass ? (int64_t *)calloc(P + 1, sizeof(int64_t)) : NULL;
       for (int i = 0; i < F; i++) {
         const ogauss *G = &pr->G[i];
         if (G->rx < 0) continue;
@@ -566,6 +568,7 @@ static int prepare(const oscene *sc, const dcam *c, const int32_t *id, const dou
         for (int y = y0; y <= y1; y++)
           for (int x = x0; x <= x1; x++) {
             int64_t p = (int64_t)y * W + x;
+            if (pix_mask && !pix_mask[p]) continue;
             if (!pass) pr->pptr[p + 1]++;
             else pr->pidx[pr->pptr[p] + fill[p]++] = i;
           }
@@ -656,7 +659,7 @@ static int collect(const oprep *pr, const oparams *pa, const int32_t *id, int W,
                    pair_t **buf, int *cap, int *flags) {
   int qx = (int)(p % W), qy = (int)(p / W), idq = id[p];
   int cnt = 0;
-  int nc = pa->all_pairs ? pr->F : (pr->pptr[p + 1] - pr->pptr[p]);
+  int nc = pa->all_pairs ? pr->F : (int)(pr->pptr[p + 1] - pr->pptr[p]);
   for (int c = 0; c < nc; c++) {
     int gi = pa->all_pairs ? c : pr->pidx[pr->pptr[p] + c];
     const ogauss *G = &pr->G[gi];
@@ -768,7 +771,7 @@ int bgto_render(int n, int M, const double *ctrl, const double *color, const dou
   oparams pa;
   params_from(params, &pa);
   oprep pr;
-  int rc = prepare(&sc, &c, id, uv, &pa, &pr);
+  int rc = prepare(&sc, &c, id, uv, &pa, pix_mask, &pr);
   if (rc) { prep_free(&pr); return rc; }
   const int64_t P = (int64_t)W * H;
   uint64_t hall = 0;
@@ -847,7 +850,7 @@ int bgto_backward(int n, int M, const double *ctrl, const double *color, const d
   oparams pa;
   params_from(params, &pa);
   oprep pr;
-  int rc = prepare(&sc, &c, id, uv, &pa, &pr);
+  int rc = prepare(&sc, &c, id, uv, &pa, NULL, &pr);
   if (rc) { prep_free(&pr); return rc; }
   const int64_t P = (int64_t)W * H;
   double *gG = (double *)calloc((size_t)(pr.F > 0 ? pr.F : 1) * GG, sizeof(double));
@@ -1078,7 +1081,7 @@ int bgto_wvalues(int n, int M, const double *ctrl, const double *color, const do
   oparams pa;
   params_from(params, &pa);
   oprep pr;
-  int rc = prepare(&sc, &c, id, uv, &pa, &pr);
+  int rc = prepare(&sc, &c, id, uv, &pa, NULL, &pr);
   if (rc) { prep_free(&pr); return rc; }
   for (int i = 0; i < count; i++) {
     int p = pix[i];

@@ -113,8 +113,8 @@ void carve(bgt_handle *h, char *base, size_t *total) {
   w.scan_aux2 = w.scan_aux ? w.scan_aux + (T / 4096 + 4) : nullptr;
   w.big_list = c.take<int>(2 * (long long)T + 2);
   w.tile_desc = c.take<int4>(2 * (long long)T + 2);
-  w.rec_chunk_cap = (int)(h->Bcap / 8 / bgt::kRecChunk + 1);
-  w.fill_unit_cap = (int)(h->Bcap / 24 + bgt::kFillChunk * 4);
+  w.rec_chunk_cap = (int)(h->Bcap / 2 / bgt::kRecChunk + 1);
+  w.fill_unit_cap = (int)(h->Bcap / 32 + bgt::kFillChunk * 4 * 1024);
   w.rec_hdr = c.take<uint4>((long long)w.rec_chunk_cap * bgt::kRecChunk);
   w.rec_prev = c.take<int>(w.rec_chunk_cap);
   w.rec_fill = c.take<int>((long long)w.fill_unit_cap * 32);
@@ -355,8 +355,8 @@ bgt_status bgt_create(const bgt_config *cfg, bgt_handle **out) {
   h->Fcap = cfg->max_pixels;
   h->Kcap = cfg->max_pairs;
   h->Kbcap = cfg->max_boundary_pairs;
-  // default 24 records per pixel, at least 4M (every resident warp holds a partly used payload chunk)
-  h->Bcap = cfg->max_blend_pairs > 0 ? cfg->max_blend_pairs : std::max(24 * cfg->max_pixels, 1ll << 22);
+  // default 32 per pixel, at least 4M (every resident warp holds a partly used fill chunk)
+  h->Bcap = cfg->max_blend_pairs > 0 ? cfg->max_blend_pairs : std::max(32 * cfg->max_pixels, 1ll << 22);
   if (h->Bcap > (1ll << 31) - 1024) h->Bcap = (1ll << 31) - 1024;
   h->Vcap = cfg->max_views;
   h->Mcap = cfg->max_prims;
@@ -483,14 +483,17 @@ bgt_status bgt_sync_status(bgt_handle *h, void *stream) {
 
 const char *bgt_last_error(const bgt_handle *h) { return h ? h->err.c_str() : ""; }
 
-bgt_status bgt_get_counts(bgt_handle *h, long long out[5], void *stream) {
+bgt_status bgt_get_counts(bgt_handle *h, long long out[7], void *stream) {
   if (!h || !out) return BGT_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemcpyAsync(h->h_status + 4, h->w.counters, 4 * sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaMemcpyAsync(h->h_status + 4, h->w.counters, 10 * sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(h, e, "counter read");
   for (int i = 0; i < 4; i++) out[i] = h->h_status[4 + i];
   out[4] = h->last.tiles;
+  const int ppt = h->last.tile == 32 ? 4 : 1;
+  out[5] = (long long)h->h_status[4 + bgt::kRecChunks] * bgt::kRecChunk;
+  out[6] = (long long)h->h_status[4 + bgt::kFillChunks] * bgt::kFillChunk * ppt;
   return BGT_OK;
 }
 
@@ -657,7 +660,7 @@ extern "C" {
 bgt_status bgt_get_stage(bgt_handle *h, int which, void *dst, long long bytes, long long *written, void *stream) {
   if (!h || !dst || bytes < 0) return BGT_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  long long cnt[5];
+  long long cnt[7];
   bgt_status s = bgt_get_counts(h, cnt, stream);
   if (s != BGT_OK) return s;
   const bgt::Params &p = h->last;

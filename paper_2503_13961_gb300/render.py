@@ -48,7 +48,7 @@ class Renderer:
     max_pairs / max_boundary_pairs ((Gaussian, tile) and (boundary point,
     tile) pairs; default 8 per pixel), max_blend_pairs (composited
     (pixel, Gaussian) pairs the forward records for the backward; default
-    24 per pixel). Options: tess_level L, tile_size
+    32 per pixel). Options: tess_level L, tile_size
     (8/16/32), use_boundary (False = the paper's "w/o B" ablation), graph
     (capture forward / backward in CUDA graphs) and the blending cutoffs.
     """
@@ -134,9 +134,10 @@ class Renderer:
         return int(self.lib.bgt_sync_status(self.h, _stream(stream)))
 
     def counts(self, stream=None):
-        out = (ctypes.c_longlong * 5)()
+        out = (ctypes.c_longlong * 7)()
         self._check(self.lib.bgt_get_counts(self.h, out, _stream(stream)))
-        return {"F": out[0], "Nb": out[1], "K": out[2], "Kb": out[3], "tiles": out[4]}
+        return {"F": out[0], "Nb": out[1], "K": out[2], "Kb": out[3], "tiles": out[4], "rec_headers": out[5],
+                "rec_fill_units": out[6]}
 
     def set_tile_size(self, t):
         self._check(self.lib.bgt_set_tile_size(self.h, int(t)))
