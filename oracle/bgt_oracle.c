@@ -363,6 +363,9 @@ typedef struct {
   double K[3];     /* conic a, b, c (inverse covariance) */
   double col[3], o, depth;
   double Sig3[9];  /* 3D covariance */
+  double quat[4], lscale[3];  /* attributes interpolated from the maps (Eq. 5) */
+  int tex[3];      /* attribute-map texels of the interpolation and their weights */
+  double tw[3];
   double rx, ry;   /* support box half extents (< 0: empty support) */
 } ogauss;
 
@@ -377,6 +380,7 @@ typedef struct {
   double k_b, alpha_min, alpha_max, t_stop, dilation;
   int use_boundary, all_pairs;
   double tol_alpha, tol_T, tol_z, tol_rho, tol_d;
+  int attr_res;  /* leg resolution R of the rotation / scaling attribute maps */
 } oparams;
 
 typedef struct {
@@ -405,6 +409,7 @@ static void params_from(const double *p, oparams *o) {
   o->dilation = p[4]; o->use_boundary = (int)p[5]; o->all_pairs = (int)p[6];
   o->tol_alpha = p[7]; o->tol_T = p[8]; o->tol_z = p[9]; o->tol_rho = p[10];
   o->tol_d = p[11];
+  o->attr_res = (int)p[12];
 }
 
 /* Eq. 3 / Eq. 4: sum over control points with Bernstein weights at (u, v). */
@@ -441,6 +446,68 @@ static void cov3d(const double *quat, const double *log_scale, double *Sig) {
       for (int k = 0; k < 3; k++) s += Mx[3 * r + k] * Mx[3 * c + k];
       Sig[3 * r + c] = s;
     }
+}
+
+/* Attribute maps (Eq. 5): per primitive a triangular grid of texels at the
+ * nodes (i, j), i + j <= R - 1, of the level-(R - 1) barycentric lattice,
+ * node (i, j) at (u, v) = (i, j) / (R - 1), stored in the control-point order
+ * (i = R-1..0, then j = R-1-i..0). Theta(M, (u, v)) interpolates linearly on
+ * the lattice triangle holding (u, v) (the triangle analogue of bilinear
+ * texture filtering); R = 1 is one texel per primitive. */
+static int tex_count(int R) { return R * (R + 1) / 2; }
+
+static int tex_index(int R, int i, int j) {
+  int n = R - 1;
+  return (n - i) * (n - i + 1) / 2 + (n - i - j);
+}
+
+static void attr_weights(int R, double u, double v, int *idx, double *w) {
+  int n = R - 1;
+  if (n <= 0) {
+    idx[0] = idx[1] = idx[2] = 0;
+    w[0] = 1.0; w[1] = w[2] = 0.0;
+    return;
+  }
+  double x = u * n, y = v * n;
+  int a = (int)floor(x), b = (int)floor(y);
+  if (a < 0) a = 0;
+  if (b < 0) b = 0;
+  if (a > n - 1) a = n - 1;
+  if (b > n - 1) b = n - 1;
+  if (a + b > n - 1) a = n - 1 - b;
+  double fx = x - a, fy = y - b;
+  if (fx + fy <= 1.0) {
+    idx[0] = tex_index(R, a, b);     w[0] = 1.0 - fx - fy;
+    idx[1] = tex_index(R, a + 1, b); w[1] = fx;
+    idx[2] = tex_index(R, a, b + 1); w[2] = fy;
+  } else {
+    idx[0] = tex_index(R, a + 1, b + 1); w[0] = fx + fy - 1.0;
+    idx[1] = tex_index(R, a + 1, b);     w[1] = 1.0 - fy;
+    idx[2] = tex_index(R, a, b + 1);     w[2] = 1.0 - fx;
+  }
+}
+
+int bgto_attr_weights(int R, double u, double v, int32_t *idx, double *w) {
+  if (R < 1 || R > 16) return -1;
+  int ii[3];
+  attr_weights(R, u, v, ii, w);
+  for (int k = 0; k < 3; k++) idx[k] = ii[k];
+  return 0;
+}
+
+/* d R(q/|q|) / d q contracted with dR (3x3): dl/dq for the raw quaternion */
+static void quat_rot_grad(const double *q, const double *dR, double *dq) {
+  double nq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  double r = q[0] / nq, x = q[1] / nq, y = q[2] / nq, z = q[3] / nq;
+  double g[4];
+  g[0] = 2 * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+  g[1] = 2 * (-2 * x * dR[4] + y * dR[1] + z * dR[2] + y * dR[3] - r * dR[5] + z * dR[6] + r * dR[7] - 2 * x * dR[8]);
+  g[2] = 2 * (-2 * y * dR[0] + x * dR[1] + r * dR[2] + x * dR[3] + z * dR[5] - r * dR[6] + z * dR[7] - 2 * y * dR[8]);
+  g[3] = 2 * (-2 * z * dR[0] - r * dR[1] + x * dR[2] + r * dR[3] - 2 * z * dR[4] + y * dR[5] + x * dR[6] + y * dR[7]);
+  /* through the normalisation: (I - qh qh^T) g / |q| */
+  double qh[4] = {r, x, y, z}, d = 0;
+  for (int k = 0; k < 4; k++) d += qh[k] * g[k];
+  for (int k = 0; k < 4; k++) dq[k] = (g[k] - qh[k] * d) / nq;
 }
 
 /* Jacobian of the pinhole projection at camera point t, 2x3 row-major. */
@@ -484,6 +551,7 @@ static void prep_free(oprep *pr) {
 static int prepare(const oscene *sc, const dcam *c, const int32_t *id, const double *uv,
                    const oparams *pa, const int32_t *pix_mask, oprep *pr) {
   memset(pr, 0, sizeof(*pr));
+  if (pa->attr_res < 1 || pa->attr_res > 16) return -2;
   const int W = c->W, H = c->H, n = sc->n, m = ncp(n);
   const int64_t P = (int64_t)W * H;
   int F = 0, Nb = 0;
@@ -521,7 +589,19 @@ static int prepare(const oscene *sc, const dcam *c, const int32_t *id, const dou
     G->depth = G->t[2];
     G->mu[0] = c->fx * G->t[0] / G->t[2] + c->cx;
     G->mu[1] = c->fy * G->t[1] / G->t[2] + c->cy;
-    cov3d(sc->quat + 4 * (size_t)g, sc->log_scale + 3 * (size_t)g, G->Sig3);
+    {
+      const int R = pa->attr_res, nt = tex_count(R);
+      attr_weights(R, u, v, G->tex, G->tw);
+      for (int k = 0; k < 4; k++) G->quat[k] = 0.0;
+      for (int k = 0; k < 3; k++) G->lscale[k] = 0.0;
+      for (int e = 0; e < 3; e++) {
+        const double *qt = sc->quat + 4 * ((size_t)g * nt + G->tex[e]);
+        const double *st = sc->log_scale + 3 * ((size_t)g * nt + G->tex[e]);
+        for (int k = 0; k < 4; k++) G->quat[k] += G->tw[e] * qt[k];
+        for (int k = 0; k < 3; k++) G->lscale[k] += G->tw[e] * st[k];
+      }
+      cov3d(G->quat, G->lscale, G->Sig3);
+    }
     double Tm[6];
     cov2d(c, G->t, G->Sig3, pa->dilation, G->cov, Tm);
     double det = G->cov[0] * G->cov[2] - G->cov[1] * G->cov[1];
@@ -841,7 +921,8 @@ int bgto_backward(int n, int M, const double *ctrl, const double *color, const d
                   const double *r_b, const double *log_scale, const double *quat, const double *bg,
                   const float *camf, int W, int H, const int32_t *id, const double *uv,
                   const double *params, const double *dLdC, double *g_ctrl, double *g_color,
-                  double *g_opacity, double *g_rb, double *out_ggrad, double *out_bgrad) {
+                  double *g_opacity, double *g_rb, double *out_ggrad, double *out_bgrad,
+                  double *g_log_scale, double *g_quat) {
   if (n < 1 || n > MAXN || W < 0 || H < 0) return -1;
   oscene sc;
   scene_from(n, M, ctrl, color, opacity, r_b, log_scale, quat, bg, &sc);
@@ -949,6 +1030,47 @@ int bgto_backward(int n, int M, const double *ctrl, const double *color, const d
     for (int r = 0; r < 2; r++)
       for (int kk = 0; kk < 3; kk++)
         GT[3 * r + kk] = 2.0 * (GSs[2 * r] * TS[kk] + GSs[2 * r + 1] * TS[3 + kk]);
+    /* attribute maps: dl/dSigma3D = T^T dl/dSigma2D T, Sigma3D = M M^T with
+     * M = R(q) diag(exp(s)): dl/dM = 2 dl/dSigma3D M, then through R(q) and
+     * exp to the interpolated q and s, and with the texel weights to the maps */
+    if (g_log_scale || g_quat) {
+      double GS3[9];
+      for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+          double acc = 0.0;
+          for (int r = 0; r < 2; r++)
+            for (int s2 = 0; s2 < 2; s2++) acc += Tm[3 * r + a] * GSs[2 * r + s2] * Tm[3 * s2 + b];
+          GS3[3 * a + b] = acc;
+        }
+      double Rq[9], sc3[3], Mx[9], GM[9], GR[9], gls[3], gq[4];
+      quat_rot(G->quat, Rq);
+      for (int k = 0; k < 3; k++) sc3[k] = exp(G->lscale[k]);
+      for (int r = 0; r < 3; r++)
+        for (int cc = 0; cc < 3; cc++) Mx[3 * r + cc] = Rq[3 * r + cc] * sc3[cc];
+      for (int r = 0; r < 3; r++)
+        for (int cc = 0; cc < 3; cc++) {
+          double acc = 0.0;
+          for (int k = 0; k < 3; k++) acc += (GS3[3 * r + k] + GS3[3 * k + r]) * Mx[3 * k + cc];
+          GM[3 * r + cc] = acc;
+        }
+      for (int cc = 0; cc < 3; cc++) {
+        double ds = 0.0;
+        for (int r = 0; r < 3; r++) {
+          GR[3 * r + cc] = GM[3 * r + cc] * sc3[cc];
+          ds += GM[3 * r + cc] * Rq[3 * r + cc];
+        }
+        gls[cc] = ds * sc3[cc];
+      }
+      quat_rot_grad(G->quat, GR, gq);
+      const int nt = tex_count(pa.attr_res);
+      for (int e = 0; e < 3; e++) {
+        const size_t t = (size_t)g * nt + G->tex[e];
+        if (g_log_scale)
+          for (int k = 0; k < 3; k++) g_log_scale[3 * t + k] += G->tw[e] * gls[k];
+        if (g_quat)
+          for (int k = 0; k < 4; k++) g_quat[4 * t + k] += G->tw[e] * gq[k];
+      }
+    }
     /* dl/dJ = dl/dT W^T */
     double GJ[6];
     for (int r = 0; r < 2; r++)

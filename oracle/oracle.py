@@ -74,7 +74,8 @@ def lib():
             L.bgto_render.argtypes = [i32, i32, P, P, P, P, P, P, P, P, i32, i32, P, P, P, P,
                                       P, P, P, P, P, P, P, P]
             L.bgto_backward.argtypes = [i32, i32, P, P, P, P, P, P, P, P, i32, i32, P, P, P, P,
-                                        P, P, P, P, P, P]
+                                        P, P, P, P, P, P, P, P]
+            L.bgto_attr_weights.argtypes = [i32, f64, f64, P, P]
             L.bgto_pixel_lists.argtypes = [i32, i32, i32, P, P, P, P, P, P, f64, P, P, i64]
             L.bgto_pixel_lists.restype = i64
             L.bgto_num_threads.restype = i32
@@ -101,12 +102,23 @@ def cam_array(cam):
     return np.ascontiguousarray(v, np.float32)
 
 
-def _params(opts):
+def _params(opts, scene=None):
     o = dict(DEFAULTS)
     o.update(opts or {})
+    R = int(scene.get("attr_res", 1)) if scene is not None else 1
     return o, np.array([o["k_b"], o["alpha_min"], o["alpha_max"], o["t_stop"], o["dilation"],
                         o["use_boundary"], o["all_pairs"], o["tol_alpha"], o["tol_T"], o["tol_z"],
-                        o["tol_rho"], o["tol_d"]], np.float64)
+                        o["tol_rho"], o["tol_d"], R], np.float64)
+
+
+def attr_weights(R, u, v):
+    """Eq. 5 texture interpolation Theta on a leg-R triangular attribute map:
+    (texel indices [3], weights [3]) of the lattice triangle holding (u, v)."""
+    idx = np.zeros(3, np.int32)
+    w = np.zeros(3, np.float64)
+    rc = lib().bgto_attr_weights(int(R), float(u), float(v), _p(idx), _p(w))
+    assert rc == 0, rc
+    return idx, w
 
 
 def bernstein(n, u, v, w):
@@ -151,7 +163,7 @@ def render(scene, cam, idm=None, uv=None, opts=None, pixels=None, records=False,
     idm / uv default to bgto_raster's output. `pixels` (bool [H,W]) limits
     compositing to those pixels. `scene64` overrides the parameters with FP64
     arrays (finite differences)."""
-    o, par = _params(opts)
+    o, par = _params(opts, scene)
     W, H = cam["width"], cam["height"]
     if idm is None:
         idm, uv, _ = raster(scene, cam, o["tess_level"], o["near_z"])
@@ -183,9 +195,10 @@ def render(scene, cam, idm=None, uv=None, opts=None, pixels=None, records=False,
 
 def backward(scene, cam, dLdC, idm=None, uv=None, opts=None, scene64=None, intermediates=False):
     """Gradients of l = sum dLdC * C with the raster and all discrete choices frozen.
-    Returns dict ctrl [M,Ncp,3], color [M,Ncp,3], opacity [M], r_b [M]
+    Returns dict ctrl [M,Ncp,3], color [M,Ncp,3], opacity [M], r_b [M],
+    log_scale and quat (shaped like the scene's attribute maps)
     (+ ggrad [F,9], bgrad [Nb,3] if intermediates)."""
-    o, par = _params(opts)
+    o, par = _params(opts, scene)
     W, H = cam["width"], cam["height"]
     if idm is None:
         idm, uv, _ = raster(scene, cam, o["tess_level"], o["near_z"])
@@ -201,12 +214,14 @@ def backward(scene, cam, dLdC, idm=None, uv=None, opts=None, scene64=None, inter
     dl = np.ascontiguousarray(dLdC, np.float64).reshape(H, W, 3)
     idm = np.ascontiguousarray(idm, np.int32)
     uv = np.ascontiguousarray(uv, np.float64)
+    gls = np.zeros(s["log_scale"].shape, np.float64)
+    gq = np.zeros(s["quat"].shape, np.float64)
     rc = lib().bgto_backward(scene["degree"], M, _p(s["ctrl"]), _p(s["color"]), _p(s["opacity"]),
                              _p(s["r_b"]), _p(s["log_scale"]), _p(s["quat"]), _p(s["bg"]),
                              _p(cam_array(cam)), W, H, _p(idm), _p(uv), _p(par), _p(dl), _p(gc),
-                             _p(gcol), _p(go), _p(grb), _p(gg), _p(gb))
+                             _p(gcol), _p(go), _p(grb), _p(gg), _p(gb), _p(gls), _p(gq))
     assert rc == 0, rc
-    out = {"ctrl": gc, "color": gcol, "opacity": go, "r_b": grb}
+    out = {"ctrl": gc, "color": gcol, "opacity": go, "r_b": grb, "log_scale": gls, "quat": gq}
     if intermediates:
         F = int((idm >= 0).sum())
         out["ggrad"] = gg[:F].copy()
@@ -241,7 +256,7 @@ def gamma(d, sigma):
 def wvalues(scene, cam, pix, prim, idm=None, uv=None, opts=None):
     """Eq. 6 coefficient w(q, g) for pixel indices `pix` and primitives `prim`.
     Returns (w, most influential boundary index)."""
-    o, par = _params(opts)
+    o, par = _params(opts, scene)
     W, H = cam["width"], cam["height"]
     if idm is None:
         idm, uv, _ = raster(scene, cam, o["tess_level"], o["near_z"])

@@ -21,6 +21,10 @@ Every array is float32 and C-contiguous; a scene is a plain dict:
   log_scale [M, 3]       log of the sub-primitive Gaussian scales
   quat      [M, 4]       sub-primitive rotation, (w, x, y, z)
   bg        [3]          background colour
+  attr_res  int R        (optional, default 1) leg resolution of the rotation
+                         and scaling attribute maps (Sec. 3.2, Eq. 5); with
+                         R > 1, log_scale is [M, T, 3] and quat [M, T, 4] over
+                         the T = R (R + 1) / 2 texels (see with_attribute_maps)
 A camera is a dict with R [3,3], t [3] (world -> camera, x right, y down,
 z forward), fx, fy, cx, cy (pixels, pixel centres at integer coordinates)
 and width, height.
@@ -388,6 +392,27 @@ def _room_mesh(rng):
         centres.append(c)
         mesh.add_object(("sphere", c, r), latlong_tris(c, (r, r, r), 22, 14))
     return mesh, centres
+
+
+def with_attribute_maps(scene, R, seed=0, scale_noise=0.3, rot_noise=0.3):
+    """The scene with rotation and scaling attribute maps of leg resolution R
+    (Eq. 5): T = R (R + 1) / 2 texels per primitive at the nodes (i, j),
+    i + j <= R - 1, of the level-(R - 1) barycentric lattice, in control-point
+    order. Each texel is the primitive's attribute plus seeded noise (normal,
+    std scale_noise on the log scales, rot_noise on the raw quaternion), so
+    that the interpolation varies across a primitive."""
+    rng = np.random.default_rng(1000 + seed)
+    M = scene["ctrl"].shape[0]
+    T = R * (R + 1) // 2
+    ls = np.asarray(scene["log_scale"], np.float64).reshape(M, -1, 3)[:, :1, :]
+    q = np.asarray(scene["quat"], np.float64).reshape(M, -1, 4)[:, :1, :]
+    ls = np.repeat(ls, T, axis=1) + rng.normal(0.0, scale_noise, size=(M, T, 3))
+    q = np.repeat(q, T, axis=1) + rng.normal(0.0, rot_noise, size=(M, T, 4))
+    out = dict(scene)
+    out["attr_res"] = int(R)
+    out["log_scale"] = np.ascontiguousarray(ls, np.float32)
+    out["quat"] = np.ascontiguousarray(q, np.float32)
+    return out
 
 
 def config_scene(cfg, seed=0, r_b=None):

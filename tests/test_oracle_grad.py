@@ -17,7 +17,7 @@ import pytest
 H_STEP = 1e-6
 
 
-def fd_check(oracle, scene, cam, opts, nparams, seed):
+def fd_check(oracle, scene, cam, opts, nparams, seed, kinds=("ctrl", "color", "opacity", "r_b")):
     opts = dict(opts, tol_d=1e-2)
     idm, uv, _ = oracle.raster(scene, cam)
     rng = np.random.default_rng(seed)
@@ -30,12 +30,14 @@ def fd_check(oracle, scene, cam, opts, nparams, seed):
     M, m = s64["ctrl"].shape[:2]
     out = []
     tries = 0
-    kinds = ["ctrl", "color", "opacity", "r_b"]
     while len(out) < nparams and tries < 20 * nparams:
-        kind = kinds[tries % 4]
+        kind = kinds[tries % len(kinds)]
         tries += 1
         if kind in ("ctrl", "color"):
             idx = (int(rng.integers(M)), int(rng.integers(m)), int(rng.integers(3)))
+        elif kind in ("log_scale", "quat"):
+            shp = s64[kind].shape
+            idx = tuple(int(rng.integers(d)) for d in shp)
         else:
             idx = (int(rng.integers(M)),)
         vals = []
@@ -84,3 +86,20 @@ def test_config1_gradient(oracle, scenes):
     assert gmax > 0
     for kind_, idx, an, num in res:
         assert abs(an - num) <= 1e-5 * max(abs(num), 1e-3 * gmax), (kind_, idx, an, num)
+
+
+@pytest.mark.parametrize("R", [1, 3])
+def test_attribute_map_gradients_match_central_differences(oracle, scenes, R):
+    """Rotation and scaling attribute maps (Eq. 5, leg resolution R): the
+    analytic gradient of the maps' texels through Sigma3D, EWA and the blending
+    equals central differences of the oracle's forward pass."""
+    sc, cams = scenes.tiny_scene("ico1", noise=0.04, size=(44, 44), r_b=2e-2)
+    sc = scenes.with_attribute_maps(sc, R, seed=R)
+    res, g = fd_check(oracle, sc, cams[0], {}, 40, seed=7 + R,
+                      kinds=("log_scale", "quat", "log_scale", "quat", "ctrl", "color"))
+    assert len(res) >= 32
+    gmax = max(abs(r[3]) for r in res)
+    for kind_, idx, an, num in res:
+        err = abs(an - num) / max(abs(num), 1e-3 * gmax)
+        assert err < 1e-5, (kind_, idx, an, num)
+    assert np.abs(g["log_scale"]).max() > 0 and np.abs(g["quat"]).max() > 0
