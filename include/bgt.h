@@ -86,10 +86,17 @@ typedef struct {
   const float *color;     /* [M][Ncp][3] colour control points p^c_ijk (Eq. 4) */
   const float *opacity;   /* [M] opacity o (Eq. 8) */
   const float *r_b;       /* [M] boundary scale r_b (Sec. 3.2) */
-  const float *log_scale; /* [M][3] log scales of the sub-primitive Gaussians (Eq. 5, one texel) */
-  const float *quat;      /* [M][4] rotation (w, x, y, z) of the sub-primitive Gaussians */
+  const float *log_scale; /* [M][T][3] scaling attribute maps: log scales of the sub-primitive
+                             Gaussians (Sec. 3.2, Eq. 5), T = R (R + 1) / 2 texels */
+  const float *quat;      /* [M][T][4] rotation attribute maps, (w, x, y, z), normalised after
+                             interpolation */
   int num_prims;          /* M */
   float bg[3];            /* background colour c_bg */
+  int attr_res;           /* R, leg resolution of the attribute maps (1..16; 0 counts as 1).
+                             Texel (i, j), i + j <= R - 1, sits at (u, v) = (i, j) / (R - 1),
+                             stored in the control-point order (i = R-1..0, then
+                             j = R-1-i..0); Theta interpolates linearly on the lattice
+                             triangle holding I_uv (R = 1: one texel per primitive) */
 } bgt_scene;
 
 typedef struct {
@@ -97,6 +104,8 @@ typedef struct {
   float *color;   /* [M][Ncp][3] dl/dp^c_ijk */
   float *opacity; /* [M] dl/do */
   float *r_b;     /* [M] dl/dr_b */
+  float *log_scale; /* [M][T][3] dl/d scaling map texels, or NULL (not computed) */
+  float *quat;      /* [M][T][4] dl/d rotation map texels (raw quaternion), or NULL */
 } bgt_grads;
 
 /* Fill *cfg with the defaults named above (n = 2, L = 8, tile 16, 1/255, 0.99,

@@ -85,7 +85,6 @@ void carve(bgt_handle *h, char *base, size_t *total) {
   w.counters = c.take<int>(16);
   w.stats = c.take<unsigned long long>(8);
   w.status = c.take<int>(1);
-  w.sig3 = c.take<float>(6 * (long long)h->Mcap);
   w.gA = c.take<float4>(F);
   w.gB = c.take<float4>(F);
   w.gC = c.take<float4>(F);
@@ -157,6 +156,8 @@ bgt_status setup_call(bgt_handle *h, const bgt_scene *sc, const bgt_camera *cams
   if (sc->num_prims < 0 || sc->num_prims > h->Mcap) return fail(h, BGT_ERR_CAPACITY, "num_prims exceeds max_prims");
   if (sc->num_prims > 0 && (!sc->ctrl || !sc->color || !sc->opacity || !sc->r_b || !sc->log_scale || !sc->quat))
     return fail(h, BGT_ERR_INVALID_ARG, "null scene array");
+  const int R = sc->attr_res == 0 ? 1 : sc->attr_res;
+  if (R < 1 || R > 16) return fail(h, BGT_ERR_INVALID_ARG, "attr_res must be 0..16");
   const int t = h->tile;
   cudaError_t e = cudaEventSynchronize(h->staged);  // previous upload has left the staging buffer
   if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
@@ -216,6 +217,8 @@ bgt_status setup_call(bgt_handle *h, const bgt_scene *sc, const bgt_camera *cams
   p.max_pairs = h->Kcap;
   p.max_bpairs = h->Kbcap;
   p.stats = h->profiling ? 1 : 0;
+  p.attr_res = R;
+  p.ntex = R * (R + 1) / 2;
   return BGT_OK;
 }
 
@@ -245,7 +248,7 @@ cudaError_t enqueue_fwd(bgt_handle *h, const bgt::Params &p, const bgt::Scene &s
   cudaMemsetAsync(w.b_tcount, 0, tb, st);
   cudaMemsetAsync(w.b_tfill, 0, tb, st);
   cudaMemsetAsync(w.counters, 0, 16 * sizeof(int), st);
-  int k = bgt::launch_prim_prep(p, s, w, st);
+  int k = 0;
   mark(h, 1, st);
   k += bgt::launch_raster(p, s, w, st);
   mark(h, 2, st);
@@ -271,6 +274,8 @@ cudaError_t enqueue_bwd(bgt_handle *h, const bgt::Params &p, const bgt::Scene &s
     cudaMemsetAsync(g.color, 0, cp, st);
     cudaMemsetAsync(g.opacity, 0, sizeof(float) * (size_t)p.M, st);
     cudaMemsetAsync(g.r_b, 0, sizeof(float) * (size_t)p.M, st);
+    if (g.log_scale) cudaMemsetAsync(g.log_scale, 0, sizeof(float) * 3 * (size_t)p.M * p.ntex, st);
+    if (g.quat) cudaMemsetAsync(g.quat, 0, sizeof(float) * 4 * (size_t)p.M * p.ntex, st);
   }
   int k = bgt::launch_composite_bwd(p, w, dimg, st);
   mark(h, 8, st);
@@ -283,8 +288,8 @@ cudaError_t enqueue_bwd(bgt_handle *h, const bgt::Params &p, const bgt::Scene &s
 std::string graph_key(const bgt::Params &p, const void *a, const void *b, const void *c, const void *d,
                       const void *e, const bgt_camera *cams, int n) {
   char buf[256];
-  snprintf(buf, sizeof(buf), "%p|%p|%p|%p|%p|%d|%d|%d|%d|%d|%d|", a, b, c, d, e, p.M, p.V, p.P, p.tiles, p.tile,
-           p.use_boundary);
+  snprintf(buf, sizeof(buf), "%p|%p|%p|%p|%p|%d|%d|%d|%d|%d|%d|%d|", a, b, c, d, e, p.M, p.V, p.P, p.tiles, p.tile,
+           p.use_boundary, p.attr_res);
   std::string k(buf);
   for (int v = 0; v < n; v++) k += std::to_string(cams[v].width) + "x" + std::to_string(cams[v].height) + ",";
   // the parameters passed by value to kernels are part of the graph
@@ -452,11 +457,13 @@ bgt_status bgt_render_bwd(bgt_handle *h, const bgt_scene *scene, const bgt_camer
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const bgt::Params p = h->last;
   const bgt::Scene sc = to_scene(scene);
-  const bgt::Grads g{grads->ctrl, grads->color, grads->opacity, grads->r_b};
+  const bgt::Grads g{grads->ctrl, grads->color, grads->opacity, grads->r_b, grads->log_scale, grads->quat};
   cudaError_t e;
   if ((h->cfg.flags & BGT_FLAG_GRAPH) && st != nullptr) {
     const std::string key = graph_key(p, scene->ctrl, d_images, grads->ctrl, grads->color, grads->opacity, cams,
-                                      n_views) + std::to_string((size_t)grads->r_b) + (h->profiling ? "P" : "-");
+                                      n_views) + std::to_string((size_t)grads->r_b) +
+                            std::to_string((size_t)grads->log_scale) + std::to_string((size_t)grads->quat) +
+                            (h->profiling ? "P" : "-");
     e = run_graph(&h->g_bwd, &h->g_bwd_key, key, st, [&]() { return enqueue_bwd(h, p, sc, d_images, g, st); });
   } else {
     e = enqueue_bwd(h, p, sc, d_images, g, st);

@@ -57,6 +57,7 @@ struct Params {
   float bg[3];
   long long max_pairs, max_bpairs;
   int stats;                  // 1: blending kernels count their work units into Work::stats
+  int attr_res, ntex;         // attribute maps: leg resolution R, texels R (R + 1) / 2
 };
 
 struct Scene {                // device pointers, caller-owned
@@ -65,6 +66,7 @@ struct Scene {                // device pointers, caller-owned
 
 struct Grads {                // device pointers, caller-owned outputs
   float *ctrl, *color, *opacity, *r_b;
+  float *log_scale, *quat;    // attribute-map texel gradients, nullable
 };
 
 // Gaussian record (one per foreground pixel), three float4 per Gaussian:
@@ -87,7 +89,6 @@ struct Work {
   int *counters;              // [16] F, Nb, K, Kb, queue heads...
   int *status;                // [1]
   // per primitive
-  float *sig3;                // [M][6] 3D covariance (xx, xy, xz, yy, yz, zz)
   // gaussians
   float4 *gA, *gB, *gC;       // [Fcap]
   int *g_pix;                 // [Fcap] global pixel index
@@ -277,6 +278,83 @@ __device__ inline void subtri_verts(int L, int s, int *va, int *vb) {
 }
 
 // ---------------------------------------------------------------------------
+// Attribute maps (Sec. 3.2, Eq. 5): per primitive T = R (R + 1) / 2 texels at
+// the nodes (i, j), i + j <= R - 1, of the level-(R - 1) barycentric lattice,
+// in control-point order; Theta interpolates linearly on the lattice triangle
+// holding (u, v). Rotation maps hold raw quaternions (w, x, y, z), normalised
+// after interpolation; scaling maps hold log scales.
+// ---------------------------------------------------------------------------
+__device__ inline int tex_index(int R, int i, int j) {
+  const int n = R - 1;
+  return (n - i) * (n - i + 1) / 2 + (n - i - j);
+}
+
+__device__ inline void attr_weights(int R, float u, float v, int *idx, float *w) {
+  const int n = R - 1;
+  if (n <= 0) {
+    idx[0] = idx[1] = idx[2] = 0;
+    w[0] = 1.f;
+    w[1] = w[2] = 0.f;
+    return;
+  }
+  const float x = u * (float)n, y = v * (float)n;
+  int a = (int)floorf(x), b = (int)floorf(y);
+  a = max(0, min(a, n - 1));
+  b = max(0, min(b, n - 1));
+  if (a + b > n - 1) a = n - 1 - b;
+  const float fx = x - (float)a, fy = y - (float)b;
+  if (fx + fy <= 1.f) {
+    idx[0] = tex_index(R, a, b);     w[0] = 1.f - fx - fy;
+    idx[1] = tex_index(R, a + 1, b); w[1] = fx;
+    idx[2] = tex_index(R, a, b + 1); w[2] = fy;
+  } else {
+    idx[0] = tex_index(R, a + 1, b + 1); w[0] = fx + fy - 1.f;
+    idx[1] = tex_index(R, a + 1, b);     w[1] = 1.f - fy;
+    idx[2] = tex_index(R, a, b + 1);     w[2] = 1.f - fx;
+  }
+}
+
+// interpolated raw quaternion and log scales of the Gaussian of primitive g at (u, v)
+__device__ inline void gauss_attrs(const float *quat, const float *log_scale, int R, int T, int g, float u, float v,
+                                   float *q, float *ls, int *tex, float *tw) {
+  attr_weights(R, u, v, tex, tw);
+  q[0] = q[1] = q[2] = q[3] = 0.f;
+  ls[0] = ls[1] = ls[2] = 0.f;
+#pragma unroll
+  for (int e = 0; e < 3; e++) {
+    if (tw[e] == 0.f) continue;
+    const size_t t = (size_t)g * T + tex[e];
+#pragma unroll
+    for (int k = 0; k < 4; k++) q[k] = fmaf(tw[e], __ldg(quat + 4 * t + k), q[k]);
+#pragma unroll
+    for (int k = 0; k < 3; k++) ls[k] = fmaf(tw[e], __ldg(log_scale + 3 * t + k), ls[k]);
+  }
+}
+
+// Sigma3D = (R(q) S)(R(q) S)^T, S = diag(exp(ls)): upper triangle (xx, xy, xz,
+// yy, yz, zz); Rm and sc receive R(q / |q|) and exp(ls)
+__device__ inline void cov3d_f32(const float *q, const float *ls, float *S6, float *Rm, float *sc) {
+  const float nq = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  const float r = q[0] * nq, x = q[1] * nq, y = q[2] * nq, z = q[3] * nq;
+  Rm[0] = 1.f - 2.f * (y * y + z * z); Rm[1] = 2.f * (x * y - r * z);       Rm[2] = 2.f * (x * z + r * y);
+  Rm[3] = 2.f * (x * y + r * z);       Rm[4] = 1.f - 2.f * (x * x + z * z); Rm[5] = 2.f * (y * z - r * x);
+  Rm[6] = 2.f * (x * z - r * y);       Rm[7] = 2.f * (y * z + r * x);       Rm[8] = 1.f - 2.f * (x * x + y * y);
+  sc[0] = expf(ls[0]);
+  sc[1] = expf(ls[1]);
+  sc[2] = expf(ls[2]);
+  float Mx[9];
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) Mx[3 * i + j] = Rm[3 * i + j] * sc[j];
+  int k = 0;
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int j = i; j < 3; j++) S6[k++] = Mx[3 * i] * Mx[3 * j] + Mx[3 * i + 1] * Mx[3 * j + 1] + Mx[3 * i + 2] * Mx[3 * j + 2];
+}
+
+// ---------------------------------------------------------------------------
 // double-float arithmetic (Dekker 1971 / Knuth TAOCP vol. 2, 4.2.2): a value
 // is hi + lo with |lo| <= ulp(hi) / 2. Used to place Gaussian means and
 // boundary points to ~1e-12 px before storing them relative to their pixel.
@@ -395,7 +473,6 @@ __device__ inline float2 project_offset(const df *t, const View &vw, int qx, int
 // host-side launchers (one per kernel family)
 // ---------------------------------------------------------------------------
 // host-side launchers; each returns the number of kernels it enqueued
-int launch_prim_prep(const Params &p, const Scene &s, const Work &w, cudaStream_t st);
 int launch_raster(const Params &p, const Scene &s, const Work &w, cudaStream_t st);
 int launch_resolve(const Params &p, const Scene &s, const Work &w, cudaStream_t st);
 int launch_generate(const Params &p, const Scene &s, const Work &w, cudaStream_t st);

@@ -82,6 +82,9 @@ __global__ void __launch_bounds__(256) k_chain_gauss(Params p, Scene s, Work w, 
     bool active = i < F;
     int g = -1;
     float gS[3] = {0.f, 0.f, 0.f}, gcol[3] = {0.f, 0.f, 0.f}, gop = 0.f;
+    float gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};  // map gradients (interpolated attrs)
+    int tex[3] = {0, 0, 0};
+    float tw[3] = {0.f, 0.f, 0.f};
     float B[m];
     if (active) {
       const float *gg = w.gg + 12 * (size_t)i;
@@ -117,8 +120,51 @@ __global__ void __launch_bounds__(256) k_chain_gauss(Params p, Scene s, Work w, 
           T0[k] = j00 * vw.R[k] + j02 * vw.R[6 + k];
           T1[k] = j11 * vw.R[3 + k] + j12 * vw.R[6 + k];
         }
-        const float *S3 = w.sig3 + 6 * g;
+        // Sigma3D from the attribute maps at I_uv (Eq. 5), as in the forward
+        float qa[4], lsa[3], Rm[9], sc3[3], S3[6];
+        gauss_attrs(s.quat, s.log_scale, p.attr_res, p.ntex, g, uv.x, uv.y, qa, lsa, tex, tw);
+        cov3d_f32(qa, lsa, S3, Rm, sc3);
         const float Sg[9] = {S3[0], S3[1], S3[2], S3[1], S3[3], S3[4], S3[2], S3[4], S3[5]};
+        if (out.log_scale || out.quat) {
+          // dl/dSigma3D = T^T dl/dSigma2D T; Sigma3D = M M^T, M = R(q) diag(exp(s)):
+          // dl/dM = 2 dl/dSigma3D M, dl/ds_c = exp(s_c) sum_r dM_rc R_rc,
+          // dl/dR_rc = dM_rc exp(s_c), then through the normalised quaternion
+          float G3[9];
+#pragma unroll
+          for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int b = 0; b < 3; b++)
+              G3[3 * a + b] = GS00 * T0[a] * T0[b] + GS01 * (T0[a] * T1[b] + T1[a] * T0[b]) + GS11 * T1[a] * T1[b];
+          float GR[9];
+#pragma unroll
+          for (int c = 0; c < 3; c++) {
+            float ds = 0.f;
+#pragma unroll
+            for (int r = 0; r < 3; r++) {
+              float dm = 0.f;
+#pragma unroll
+              for (int k = 0; k < 3; k++) dm += 2.f * G3[3 * r + k] * Rm[3 * k + c] * sc3[c];
+              GR[3 * r + c] = dm * sc3[c];
+              ds += dm * Rm[3 * r + c];
+            }
+            gls[c] = ds * sc3[c];
+          }
+          const float nq = rsqrtf(qa[0] * qa[0] + qa[1] * qa[1] + qa[2] * qa[2] + qa[3] * qa[3]);
+          const float r = qa[0] * nq, x = qa[1] * nq, y = qa[2] * nq, z = qa[3] * nq;
+          float h[4];
+          h[0] = 2.f * (-z * GR[1] + y * GR[2] + z * GR[3] - x * GR[5] - y * GR[6] + x * GR[7]);
+          h[1] = 2.f * (-2.f * x * GR[4] + y * GR[1] + z * GR[2] + y * GR[3] - r * GR[5] + z * GR[6] + r * GR[7] -
+                        2.f * x * GR[8]);
+          h[2] = 2.f * (-2.f * y * GR[0] + x * GR[1] + r * GR[2] + x * GR[3] + z * GR[5] - r * GR[6] + z * GR[7] -
+                        2.f * y * GR[8]);
+          h[3] = 2.f * (-2.f * z * GR[0] - r * GR[1] + x * GR[2] + r * GR[3] - 2.f * z * GR[4] + y * GR[5] +
+                        x * GR[6] + y * GR[7]);
+          const float dot = r * h[0] + x * h[1] + y * h[2] + z * h[3];
+          gq[0] = (h[0] - r * dot) * nq;
+          gq[1] = (h[1] - x * dot) * nq;
+          gq[2] = (h[2] - y * dot) * nq;
+          gq[3] = (h[3] - z * dot) * nq;
+        }
         float TS0[3], TS1[3];
 #pragma unroll
         for (int k = 0; k < 3; k++) {
@@ -155,6 +201,31 @@ __global__ void __launch_bounds__(256) k_chain_gauss(Params p, Scene s, Work w, 
     scatter_cp<m>(out.color, g, B, gcol, sg, nz);
     const float so = seg_sum(nz ? gop : 0.f, sg);
     if (sg.tail && nz && so != 0.f) atomicAdd(out.opacity + g, so);
+    if (out.log_scale || out.quat) {
+      // the map texels of the interpolation, with their weights; runs of equal
+      // (primitive, texel) are summed before one atomic each
+      const bool nm = active && (gls[0] != 0.f || gls[1] != 0.f || gls[2] != 0.f || gq[0] != 0.f ||
+                                 gq[1] != 0.f || gq[2] != 0.f || gq[3] != 0.f);
+#pragma unroll
+      for (int e = 0; e < 3; e++) {
+        const bool on = nm && tw[e] != 0.f;
+        if (!__any_sync(0xffffffffu, on)) continue;
+        const int t = g * p.ntex + tex[e];
+        const Seg st = seg_info(on ? t : -1 - lane);
+        if (out.log_scale)
+#pragma unroll
+          for (int c = 0; c < 3; c++) {
+            const float v = seg_sum(on ? tw[e] * gls[c] : 0.f, st);
+            if (st.tail && on && v != 0.f) atomicAdd(out.log_scale + 3 * (size_t)t + c, v);
+          }
+        if (out.quat)
+#pragma unroll
+          for (int c = 0; c < 4; c++) {
+            const float v = seg_sum(on ? tw[e] * gq[c] : 0.f, st);
+            if (st.tail && on && v != 0.f) atomicAdd(out.quat + 4 * (size_t)t + c, v);
+          }
+      }
+    }
   }
 }
 

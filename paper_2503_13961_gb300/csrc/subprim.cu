@@ -24,31 +24,6 @@ constexpr int kGenThreads = 256;
 constexpr int kGenRounds = 4;  // pixels per thread; block covers 1024 pixels
 constexpr int kGenPixels = kGenThreads * kGenRounds;
 
-__global__ void k_prim_prep(Params p, Scene s, Work w) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= p.M) return;
-  const float q0 = s.quat[4 * g], q1 = s.quat[4 * g + 1], q2 = s.quat[4 * g + 2], q3 = s.quat[4 * g + 3];
-  const float nq = rsqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
-  const float r = q0 * nq, x = q1 * nq, y = q2 * nq, z = q3 * nq;
-  const float R[9] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - r * z), 2.f * (x * z + r * y),
-                      2.f * (x * y + r * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - r * x),
-                      2.f * (x * z - r * y), 2.f * (y * z + r * x), 1.f - 2.f * (x * x + y * y)};
-  const float sc[3] = {expf(s.log_scale[3 * g]), expf(s.log_scale[3 * g + 1]), expf(s.log_scale[3 * g + 2])};
-  float Mx[9];
-#pragma unroll
-  for (int i = 0; i < 3; i++)
-#pragma unroll
-    for (int j = 0; j < 3; j++) Mx[3 * i + j] = R[3 * i + j] * sc[j];
-  float S[6];
-  int k = 0;
-#pragma unroll
-  for (int i = 0; i < 3; i++)
-#pragma unroll
-    for (int j = i; j < 3; j++) S[k++] = Mx[3 * i] * Mx[3 * j] + Mx[3 * i + 1] * Mx[3 * j + 1] + Mx[3 * i + 2] * Mx[3 * j + 2];
-#pragma unroll
-  for (int i = 0; i < 6; i++) w.sig3[6 * g + i] = S[i];
-}
-
 // foreground / boundary flags of global pixel `pix`
 __device__ inline void pixel_flags(const Params &p, const Work &w, int pix, bool &fg, bool &bnd,
                                    int &view) {
@@ -239,7 +214,14 @@ __global__ void __launch_bounds__(kGenThreads) k_generate(Params p, Scene s, Wor
       T0[k] = j00 * vw.R[k] + j02 * vw.R[6 + k];
       T1[k] = j11 * vw.R[3 + k] + j12 * vw.R[6 + k];
     }
-    const float *S3 = w.sig3 + 6 * prim;
+    // Sigma3D from the attribute maps interpolated at I_uv (Eq. 5)
+    float S3[6];
+    {
+      float qa[4], ls[3], Rm[9], sc3[3], tw[3];
+      int tex[3];
+      gauss_attrs(s.quat, s.log_scale, p.attr_res, p.ntex, prim, uv.x, uv.y, qa, ls, tex, tw);
+      cov3d_f32(qa, ls, S3, Rm, sc3);
+    }
     const float Sxx = S3[0], Sxy = S3[1], Sxz = S3[2], Syy = S3[3], Syz = S3[4], Szz = S3[5];
     const float a0 = T0[0] * Sxx + T0[1] * Sxy + T0[2] * Sxz;
     const float a1 = T0[0] * Sxy + T0[1] * Syy + T0[2] * Syz;
@@ -311,12 +293,6 @@ __global__ void __launch_bounds__(kGenThreads) k_generate(Params p, Scene s, Wor
 }
 
 }  // namespace
-
-int launch_prim_prep(const Params &p, const Scene &s, const Work &w, cudaStream_t st) {
-  if (p.M == 0) return 0;
-  k_prim_prep<<<(p.M + 127) / 128, 128, 0, st>>>(p, s, w);
-  return 1;
-}
 
 int launch_generate(const Params &p, const Scene &s, const Work &w, cudaStream_t st) {
   const int nblk = (p.P + kGenPixels - 1) / kGenPixels;

@@ -13,7 +13,7 @@ import torch
 from . import _abi
 
 SCENE_KEYS = ("ctrl", "color", "opacity", "r_b", "log_scale", "quat")
-GRAD_KEYS = ("ctrl", "color", "opacity", "r_b")
+GRAD_KEYS = ("ctrl", "color", "opacity", "r_b", "log_scale", "quat")
 
 STAGE_ID = {"id": 0, "uv": 1, "gauss": 2, "bnd": 3, "g_ranges": 4, "g_keys": 5, "b_ranges": 6,
             "b_keys": 7, "T": 8, "n": 9, "ggrad": 10, "bgrad": 11}
@@ -34,7 +34,13 @@ def scene_to_device(scene, device="cuda"):
            for k in SCENE_KEYS}
     out["degree"] = int(scene["degree"])
     out["bg"] = [float(x) for x in np.asarray(scene["bg"]).ravel()]
+    out["attr_res"] = int(scene.get("attr_res", 1))
     return out
+
+
+def _grads_struct(grads):
+    """bgt_grads of a dict of tensors; absent keys (or None) are not computed."""
+    return _abi.Grads(*((grads[k].data_ptr() if grads.get(k) is not None else None) for k in GRAD_KEYS))
 
 
 def view_pixels(cams):
@@ -97,6 +103,7 @@ class Renderer:
             setattr(s, k, t.data_ptr())
         s.num_prims = int(sc["ctrl"].shape[0])
         s.bg[:] = [float(x) for x in sc["bg"]]
+        s.attr_res = int(sc.get("attr_res", 1))
         return s
 
     def _check(self, st):
@@ -116,11 +123,12 @@ class Renderer:
         return images
 
     def backward(self, scene, cams, d_images, grads=None, stream=None):
-        """dl/d(ctrl, color, opacity, r_b) for the last forward, given dl/dimages."""
+        """dl/d(ctrl, color, opacity, r_b, log_scale, quat) for the last forward,
+        given dl/dimages; keys missing from `grads` are not computed."""
         if grads is None:
             grads = {k: torch.empty_like(scene[k]) for k in GRAD_KEYS}
         d_images = d_images.contiguous()
-        g = _abi.Grads(*(grads[k].data_ptr() for k in GRAD_KEYS))
+        g = _grads_struct(grads)
         sc = self._scene(scene)
         cam_arr = _abi.camera_array(cams)
         self._check(self.lib.bgt_render_bwd(self.h, ctypes.byref(sc), cam_arr, len(cams), _ptr(d_images),
@@ -149,7 +157,7 @@ class Renderer:
     def autotune(self, scene, cams, images, d_images, grads, iters=3, stream=None):
         best = ctypes.c_int(0)
         ms = (ctypes.c_float * 3)()
-        g = _abi.Grads(*(grads[k].data_ptr() for k in GRAD_KEYS))
+        g = _grads_struct(grads)
         self._check(self.lib.bgt_autotune(self.h, ctypes.byref(self._scene(scene)), _abi.camera_array(cams),
                                           len(cams), _ptr(images), _ptr(d_images), ctypes.byref(g), iters,
                                           ctypes.byref(best), ms, _stream(stream)))
@@ -241,13 +249,13 @@ class _RenderFn(torch.autograd.Function):
     @staticmethod
     def backward(ctx, d_img):
         g = ctx.renderer.backward(ctx.scene, ctx.cams, d_img.contiguous())
-        return None, None, None, g["ctrl"], g["color"], g["opacity"], g["r_b"], None, None
+        return None, None, None, g["ctrl"], g["color"], g["opacity"], g["r_b"], g["log_scale"], g["quat"]
 
 
 def render(renderer, scene, cams):
     """Differentiable render: images [sum W*H, 3]; gradients flow to
-    scene['ctrl'], ['color'], ['opacity'], ['r_b']."""
-    meta = {"degree": scene["degree"], "bg": scene["bg"]}
+    scene['ctrl'], ['color'], ['opacity'], ['r_b'], ['log_scale'], ['quat']."""
+    meta = {"degree": scene["degree"], "bg": scene["bg"], "attr_res": scene.get("attr_res", 1)}
     return _RenderFn.apply(renderer, cams, meta, scene["ctrl"], scene["color"], scene["opacity"], scene["r_b"],
                            scene["log_scale"], scene["quat"])
 

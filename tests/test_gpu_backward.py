@@ -44,7 +44,7 @@ def _run(oracle, sc, cams, seed=0, tile=16, use_boundary=True):
         r = oracle.backward(sc, c, dl, opts=opts, intermediates=True)
         inter.append(r)
         if ref_g is None:
-            ref_g = {k: r[k].copy() for k in ("ctrl", "color", "opacity", "r_b")}
+            ref_g = {k: r[k].copy() for k in ("ctrl", "color", "opacity", "r_b", "log_scale", "quat")}
         else:
             for k in ref_g:
                 ref_g[k] += r[k]
@@ -211,3 +211,16 @@ def test_l1_loss_helper(scenes):
     assert torch.allclose(d, 0.5 * torch.sign(a - b))
     assert torch.allclose(loss, 0.5 * (a - b).abs().sum(), rtol=1e-5)
     del R
+
+
+@pytest.mark.parametrize("R", [1, 3])
+def test_attribute_map_gradients_match_oracle(oracle, scenes, R):
+    """Rotation / scaling attribute maps of leg resolution R (Eq. 5): gradients
+    of their texels (and of the other parameters) against the oracle."""
+    sc, cams = scenes.tiny_scene("ico1", noise=0.04, size=(90, 70), r_b=0.04)
+    sc = scenes.with_attribute_maps(sc, R, seed=R)
+    _, got, ref, _, _ = _run(oracle, sc, cams, seed=5)
+    for k in ("ctrl", "color", "opacity", "r_b", "log_scale", "quat"):
+        assert got[k].shape == ref[k].shape, k
+        _assert_close(got[k], ref[k], k)
+    assert np.abs(ref["log_scale"]).max() > 0 and np.abs(ref["quat"]).max() > 0
