@@ -364,6 +364,7 @@ typedef struct {
   double col[3], o, depth;
   double Sig3[9];  /* 3D covariance */
   double quat[4], lscale[3];  /* attributes interpolated from the maps (Eq. 5) */
+  double S[3];     /* world position S_q (kept for the SH direction) */
   int tex[3];      /* attribute-map texels of the interpolation and their weights */
   double tw[3];
   double rx, ry;   /* support box half extents (< 0: empty support) */
@@ -381,11 +382,13 @@ typedef struct {
   int use_boundary, all_pairs;
   double tol_alpha, tol_T, tol_z, tol_rho, tol_d;
   int attr_res;  /* leg resolution R of the rotation / scaling attribute maps */
+  int sh_deg;    /* D, degree of the view-dependent SH colour (0: none) */
 } oparams;
 
 typedef struct {
   int n, M;
   const double *ctrl, *color, *opacity, *r_b, *log_scale, *quat, *bg;
+  const double *sh;  /* [M][K][3] SH coefficients of bands 1..D per primitive, K = (D+1)^2 - 1 */
 } oscene;
 
 typedef struct {
@@ -410,6 +413,7 @@ static void params_from(const double *p, oparams *o) {
   o->tol_alpha = p[7]; o->tol_T = p[8]; o->tol_z = p[9]; o->tol_rho = p[10];
   o->tol_d = p[11];
   o->attr_res = (int)p[12];
+  o->sh_deg = (int)p[13];
 }
 
 /* Eq. 3 / Eq. 4: sum over control points with Bernstein weights at (u, v). */
@@ -510,6 +514,61 @@ static void quat_rot_grad(const double *q, const double *dR, double *dq) {
   for (int k = 0; k < 4; k++) dq[k] = (g[k] - qh[k] * d) / nq;
 }
 
+/* Real spherical harmonics of bands 1..D at the unit direction d, from their
+ * definition: Y_l^0 = K_l^0 P_l^0(cos t), Y_l^m = sqrt(2) K_l^m cos(m p) P_l^m(cos t),
+ * Y_l^-m = sqrt(2) K_l^m sin(m p) P_l^m(cos t) (m > 0), K_l^m =
+ * sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!), P_l^m the associated Legendre functions
+ * with the Condon-Shortley phase (three-term recurrence), t the polar angle
+ * from +z and p = atan2(y, x). Y[k] for k = l^2 - 1 + (m + l), m = -l..l. */
+static double factorial_d(int k) {
+  double f = 1.0;
+  for (int i = 2; i <= k; i++) f *= i;
+  return f;
+}
+
+static double assoc_legendre(int l, int m, double x) {
+  double pmm = 1.0, somx2 = sqrt(fmax(0.0, 1.0 - x * x));
+  for (int i = 1; i <= m; i++) pmm *= -(2.0 * i - 1.0) * somx2;
+  if (l == m) return pmm;
+  double pmm1 = x * (2.0 * m + 1.0) * pmm;
+  if (l == m + 1) return pmm1;
+  double pll = 0.0;
+  for (int ll = m + 2; ll <= l; ll++) {
+    pll = ((2.0 * ll - 1.0) * x * pmm1 - (ll + m - 1.0) * pmm) / (ll - m);
+    pmm = pmm1;
+    pmm1 = pll;
+  }
+  return pll;
+}
+
+static void sh_basis(int D, const double *dir, double *Y) {
+  const double PI = 3.14159265358979323846;
+  double nd = sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+  double x = dir[0] / nd, y = dir[1] / nd, z = dir[2] / nd;
+  double ph = atan2(y, x);
+  for (int l = 1; l <= D; l++)
+    for (int m = -l; m <= l; m++) {
+      int am = m < 0 ? -m : m;
+      double K = sqrt((2.0 * l + 1.0) / (4.0 * PI) * factorial_d(l - am) / factorial_d(l + am));
+      double P = assoc_legendre(l, am, z), val;
+      if (m == 0) val = K * P;
+      else if (m > 0) val = sqrt(2.0) * K * cos(am * ph) * P;
+      else val = sqrt(2.0) * K * sin(am * ph) * P;
+      Y[l * l - 1 + (m + l)] = val;
+    }
+}
+
+int bgto_sh_basis(int D, const double *dir, double *Y) {
+  if (D < 0 || D > 3) return -1;
+  sh_basis(D, dir, Y);
+  return 0;
+}
+
+/* camera centre in world coordinates, C = -R^T t */
+static void cam_centre(const dcam *c, double *C) {
+  for (int k = 0; k < 3; k++) C[k] = -(c->R[k] * c->t[0] + c->R[3 + k] * c->t[1] + c->R[6 + k] * c->t[2]);
+}
+
 /* Jacobian of the pinhole projection at camera point t, 2x3 row-major. */
 static void proj_jac(const dcam *c, const double *t, double *J) {
   double tz = t[2];
@@ -552,6 +611,7 @@ static int prepare(const oscene *sc, const dcam *c, const int32_t *id, const dou
                    const oparams *pa, const int32_t *pix_mask, oprep *pr) {
   memset(pr, 0, sizeof(*pr));
   if (pa->attr_res < 1 || pa->attr_res > 16) return -2;
+  if (pa->sh_deg < 0 || pa->sh_deg > 3 || (pa->sh_deg > 0 && !sc->sh)) return -3;
   const int W = c->W, H = c->H, n = sc->n, m = ncp(n);
   const int64_t P = (int64_t)W * H;
   int F = 0, Nb = 0;
@@ -609,6 +669,18 @@ static int prepare(const oscene *sc, const dcam *c, const int32_t *id, const dou
     G->K[1] = -G->cov[1] / det;
     G->K[2] = G->cov[0] / det;
     interp(n, sc->color + (size_t)g * m * 3, u, v, G->col);
+    if (pa->sh_deg > 0) {
+      /* view-dependent colour: diffuse (Eq. 4) plus SH bands 1..D of the
+       * primitive's coefficients at the direction from the camera to S_q */
+      const int K = (pa->sh_deg + 1) * (pa->sh_deg + 1) - 1;
+      double C0[3], dir[3], Y[15];
+      cam_centre(c, C0);
+      for (int k = 0; k < 3; k++) dir[k] = S[k] - C0[k];
+      sh_basis(pa->sh_deg, dir, Y);
+      for (int k = 0; k < K; k++)
+        for (int ch = 0; ch < 3; ch++) G->col[ch] += Y[k] * sc->sh[((size_t)g * K + k) * 3 + ch];
+      for (int k = 0; k < 3; k++) G->S[k] = S[k];
+    }
     G->o = sc->opacity[g];
     if (G->o > pa->alpha_min) {
       double lvl = 2.0 * log(G->o / pa->alpha_min);
@@ -828,9 +900,9 @@ static int composite(const pair_t *s, int cnt, const oprep *pr, const oparams *p
 
 static void scene_from(int n, int M, const double *ctrl, const double *color, const double *opacity,
                        const double *r_b, const double *log_scale, const double *quat,
-                       const double *bg, oscene *s) {
+                       const double *bg, const double *sh, oscene *s) {
   s->n = n; s->M = M; s->ctrl = ctrl; s->color = color; s->opacity = opacity; s->r_b = r_b;
-  s->log_scale = log_scale; s->quat = quat; s->bg = bg;
+  s->log_scale = log_scale; s->quat = quat; s->bg = bg; s->sh = sh;
 }
 
 /* Forward pass from given raster outputs (id, uv). pix_mask (nullable)
@@ -839,13 +911,14 @@ static void scene_from(int n, int M, const double *ctrl, const double *color, co
  * sub-primitive and boundary records; out_counts = {F, Nb}. */
 int bgto_render(int n, int M, const double *ctrl, const double *color, const double *opacity,
                 const double *r_b, const double *log_scale, const double *quat, const double *bg,
+                const double *sh,
                 const float *camf, int W, int H, const int32_t *id, const double *uv,
                 const double *params, const int32_t *pix_mask, double *out_img, double *out_T,
                 int32_t *out_n, int32_t *out_flags, uint64_t *out_hash, double *out_gauss,
                 double *out_bnd, int32_t *out_counts) {
   if (n < 1 || n > MAXN || W < 0 || H < 0) return -1;
   oscene sc;
-  scene_from(n, M, ctrl, color, opacity, r_b, log_scale, quat, bg, &sc);
+  scene_from(n, M, ctrl, color, opacity, r_b, log_scale, quat, bg, sh, &sc);
   dcam c;
   cam_from_f32(camf, W, H, &c);
   oparams pa;
@@ -919,13 +992,14 @@ static void add_atomic(double *dst, double v) {
  * gradients. */
 int bgto_backward(int n, int M, const double *ctrl, const double *color, const double *opacity,
                   const double *r_b, const double *log_scale, const double *quat, const double *bg,
+                const double *sh,
                   const float *camf, int W, int H, const int32_t *id, const double *uv,
                   const double *params, const double *dLdC, double *g_ctrl, double *g_color,
                   double *g_opacity, double *g_rb, double *out_ggrad, double *out_bgrad,
-                  double *g_log_scale, double *g_quat) {
+                  double *g_log_scale, double *g_quat, double *g_sh) {
   if (n < 1 || n > MAXN || W < 0 || H < 0) return -1;
   oscene sc;
-  scene_from(n, M, ctrl, color, opacity, r_b, log_scale, quat, bg, &sc);
+  scene_from(n, M, ctrl, color, opacity, r_b, log_scale, quat, bg, sh, &sc);
   dcam c;
   cam_from_f32(camf, W, H, &c);
   oparams pa;
@@ -1088,6 +1162,34 @@ int bgto_backward(int n, int M, const double *ctrl, const double *color, const d
     gt[2] += -gg[0] * fx * tx / tz2 - gg[1] * fy * ty / tz2;
     double gS[3];
     for (int kk = 0; kk < 3; kk++) gS[kk] = c.R[kk] * gt[0] + c.R[3 + kk] * gt[1] + c.R[6 + kk] * gt[2];
+    if (pa.sh_deg > 0) {
+      /* SH colour: dl/dk = Y(d) dl/dc; the direction d = (S_q - C) / |S_q - C|
+       * moves with S_q: its basis derivative by FP64 central differences */
+      const int K = (pa.sh_deg + 1) * (pa.sh_deg + 1) - 1;
+      double C0[3], v0[3], Y[15], wk[15];
+      cam_centre(&c, C0);
+      for (int kk = 0; kk < 3; kk++) v0[kk] = G->S[kk] - C0[kk];
+      sh_basis(pa.sh_deg, v0, Y);
+      for (int k = 0; k < K; k++) {
+        wk[k] = 0.0;
+        for (int ch = 0; ch < 3; ch++) {
+          const double coef = sc.sh[((size_t)g * K + k) * 3 + ch];
+          wk[k] += gg[5 + ch] * coef;
+          if (g_sh) g_sh[((size_t)g * K + k) * 3 + ch] += Y[k] * gg[5 + ch];
+        }
+      }
+      const double hv = 1e-6 * sqrt(v0[0] * v0[0] + v0[1] * v0[1] + v0[2] * v0[2]);
+      for (int j = 0; j < 3; j++) {
+        double vp[3] = {v0[0], v0[1], v0[2]}, vm[3] = {v0[0], v0[1], v0[2]}, Yp[15], Ym[15];
+        vp[j] += hv;
+        vm[j] -= hv;
+        sh_basis(pa.sh_deg, vp, Yp);
+        sh_basis(pa.sh_deg, vm, Ym);
+        double dj = 0.0;
+        for (int k = 0; k < K; k++) dj += wk[k] * (Yp[k] - Ym[k]) / (2.0 * hv);
+        gS[j] += dj;
+      }
+    }
     double B[MAXCP];
     bernstein(n, G->u, G->v, 1.0 - G->u - G->v, B);
     for (int a = 0; a < m; a++)
@@ -1193,11 +1295,12 @@ double bgto_gamma(double d, double sigma) { return gamma_fn(d, sigma); }
  * of the most influential boundary point (-1 if none). */
 int bgto_wvalues(int n, int M, const double *ctrl, const double *color, const double *opacity,
                  const double *r_b, const double *log_scale, const double *quat, const double *bg,
+                const double *sh,
                  const float *camf, int W, int H, const int32_t *id, const double *uv,
                  const double *params, int count, const int32_t *pix, const int32_t *prim,
                  double *out_w, int32_t *out_b) {
   oscene sc;
-  scene_from(n, M, ctrl, color, opacity, r_b, log_scale, quat, bg, &sc);
+  scene_from(n, M, ctrl, color, opacity, r_b, log_scale, quat, bg, sh, &sc);
   dcam c;
   cam_from_f32(camf, W, H, &c);
   oparams pa;

@@ -71,17 +71,18 @@ def lib():
             L.bgto_bernstein.argtypes = [i32, f64, f64, f64, P]
             L.bgto_decasteljau.argtypes = [i32, P, f64, f64, f64, P]
             L.bgto_raster.argtypes = [i32, i32, P, i32, P, i32, i32, f32, i32, P, P, P, P]
-            L.bgto_render.argtypes = [i32, i32, P, P, P, P, P, P, P, P, i32, i32, P, P, P, P,
+            L.bgto_render.argtypes = [i32, i32, P, P, P, P, P, P, P, P, P, i32, i32, P, P, P, P,
                                       P, P, P, P, P, P, P, P]
-            L.bgto_backward.argtypes = [i32, i32, P, P, P, P, P, P, P, P, i32, i32, P, P, P, P,
-                                        P, P, P, P, P, P, P, P]
+            L.bgto_backward.argtypes = [i32, i32, P, P, P, P, P, P, P, P, P, i32, i32, P, P, P, P,
+                                        P, P, P, P, P, P, P, P, P]
+            L.bgto_sh_basis.argtypes = [i32, P, P]
             L.bgto_attr_weights.argtypes = [i32, f64, f64, P, P]
             L.bgto_pixel_lists.argtypes = [i32, i32, i32, P, P, P, P, P, P, f64, P, P, i64]
             L.bgto_pixel_lists.restype = i64
             L.bgto_num_threads.restype = i32
             L.bgto_gamma.argtypes = [f64, f64]
             L.bgto_gamma.restype = f64
-            L.bgto_wvalues.argtypes = [i32, i32, P, P, P, P, P, P, P, P, i32, i32, P, P, P, i32,
+            L.bgto_wvalues.argtypes = [i32, i32, P, P, P, P, P, P, P, P, P, i32, i32, P, P, P, i32,
                                        P, P, P, P]
             _LIB = L
     return _LIB
@@ -106,9 +107,10 @@ def _params(opts, scene=None):
     o = dict(DEFAULTS)
     o.update(opts or {})
     R = int(scene.get("attr_res", 1)) if scene is not None else 1
+    D = int(scene.get("sh_degree", 0)) if scene is not None else 0
     return o, np.array([o["k_b"], o["alpha_min"], o["alpha_max"], o["t_stop"], o["dilation"],
                         o["use_boundary"], o["all_pairs"], o["tol_alpha"], o["tol_T"], o["tol_z"],
-                        o["tol_rho"], o["tol_d"], R], np.float64)
+                        o["tol_rho"], o["tol_d"], R, D], np.float64)
 
 
 def attr_weights(R, u, v):
@@ -119,6 +121,16 @@ def attr_weights(R, u, v):
     rc = lib().bgto_attr_weights(int(R), float(u), float(v), _p(idx), _p(w))
     assert rc == 0, rc
     return idx, w
+
+
+def sh_basis(D, direction):
+    """Real spherical harmonics of bands 1..D at a direction (the SH colour's
+    basis, from the associated Legendre definition), [(D + 1)^2 - 1]."""
+    Y = np.zeros(max((D + 1) ** 2 - 1, 1), np.float64)
+    d = np.ascontiguousarray(direction, np.float64)
+    rc = lib().bgto_sh_basis(int(D), _p(d), _p(Y))
+    assert rc == 0, rc
+    return Y[:(D + 1) ** 2 - 1]
 
 
 def bernstein(n, u, v, w):
@@ -153,7 +165,10 @@ def raster(scene, cam, tess_level=None, near_z=None, ztest=True, cover=False):
 
 def _scene64(scene):
     f = lambda k: np.ascontiguousarray(scene[k], np.float64)
-    return {k: f(k) for k in ("ctrl", "color", "opacity", "r_b", "log_scale", "quat", "bg")}
+    out = {k: f(k) for k in ("ctrl", "color", "opacity", "r_b", "log_scale", "quat", "bg")}
+    if scene.get("sh_degree", 0) > 0:
+        out["sh"] = f("sh")
+    return out
 
 
 def render(scene, cam, idm=None, uv=None, opts=None, pixels=None, records=False, scene64=None):
@@ -181,7 +196,7 @@ def render(scene, cam, idm=None, uv=None, opts=None, pixels=None, records=False,
     idm = np.ascontiguousarray(idm, np.int32)
     uv = np.ascontiguousarray(uv, np.float64)
     rc = lib().bgto_render(scene["degree"], M, _p(s["ctrl"]), _p(s["color"]), _p(s["opacity"]),
-                           _p(s["r_b"]), _p(s["log_scale"]), _p(s["quat"]), _p(s["bg"]),
+                           _p(s["r_b"]), _p(s["log_scale"]), _p(s["quat"]), _p(s["bg"]), _p(s.get("sh")),
                            _p(cam_array(cam)), W, H, _p(idm), _p(uv), _p(par), _p(mask), _p(img),
                            _p(T), _p(nn), _p(fl), _p(hsh), _p(grec), _p(brec), _p(cnt))
     assert rc == 0, rc
@@ -216,12 +231,15 @@ def backward(scene, cam, dLdC, idm=None, uv=None, opts=None, scene64=None, inter
     uv = np.ascontiguousarray(uv, np.float64)
     gls = np.zeros(s["log_scale"].shape, np.float64)
     gq = np.zeros(s["quat"].shape, np.float64)
+    gsh = np.zeros(s["sh"].shape, np.float64) if "sh" in s else None
     rc = lib().bgto_backward(scene["degree"], M, _p(s["ctrl"]), _p(s["color"]), _p(s["opacity"]),
-                             _p(s["r_b"]), _p(s["log_scale"]), _p(s["quat"]), _p(s["bg"]),
+                             _p(s["r_b"]), _p(s["log_scale"]), _p(s["quat"]), _p(s["bg"]), _p(s.get("sh")),
                              _p(cam_array(cam)), W, H, _p(idm), _p(uv), _p(par), _p(dl), _p(gc),
-                             _p(gcol), _p(go), _p(grb), _p(gg), _p(gb), _p(gls), _p(gq))
+                             _p(gcol), _p(go), _p(grb), _p(gg), _p(gb), _p(gls), _p(gq), _p(gsh))
     assert rc == 0, rc
     out = {"ctrl": gc, "color": gcol, "opacity": go, "r_b": grb, "log_scale": gls, "quat": gq}
+    if gsh is not None:
+        out["sh"] = gsh
     if intermediates:
         F = int((idm >= 0).sum())
         out["ggrad"] = gg[:F].copy()
@@ -267,7 +285,7 @@ def wvalues(scene, cam, pix, prim, idm=None, uv=None, opts=None):
     b = np.zeros(len(pix), np.int32)
     rc = lib().bgto_wvalues(scene["degree"], s["ctrl"].shape[0], _p(s["ctrl"]), _p(s["color"]),
                             _p(s["opacity"]), _p(s["r_b"]), _p(s["log_scale"]), _p(s["quat"]),
-                            _p(s["bg"]), _p(cam_array(cam)), W, H,
+                            _p(s["bg"]), _p(s.get("sh")), _p(cam_array(cam)), W, H,
                             _p(np.ascontiguousarray(idm, np.int32)),
                             _p(np.ascontiguousarray(uv, np.float64)), _p(par), len(pix), _p(pix),
                             _p(prim), _p(w), _p(b))

@@ -25,6 +25,9 @@ Every array is float32 and C-contiguous; a scene is a plain dict:
                          and scaling attribute maps (Sec. 3.2, Eq. 5); with
                          R > 1, log_scale is [M, T, 3] and quat [M, T, 4] over
                          the T = R (R + 1) / 2 texels (see with_attribute_maps)
+  sh_degree int D        (optional, default 0) degree of the view-dependent
+                         colour; with D > 0, sh [M, (D+1)^2 - 1, 3] holds the
+                         coefficients of SH bands 1..D per primitive (see with_sh)
 A camera is a dict with R [3,3], t [3] (world -> camera, x right, y down,
 z forward), fx, fy, cx, cy (pixels, pixel centres at integer coordinates)
 and width, height.
@@ -412,6 +415,19 @@ def with_attribute_maps(scene, R, seed=0, scale_noise=0.3, rot_noise=0.3):
     out["attr_res"] = int(R)
     out["log_scale"] = np.ascontiguousarray(ls, np.float32)
     out["quat"] = np.ascontiguousarray(q, np.float32)
+    return out
+
+
+def with_sh(scene, D, seed=0, scale=0.2):
+    """The scene with view-dependent colour of SH degree D: per primitive the
+    coefficients of the real SH bands 1..D for each RGB channel, normal with
+    std `scale`, added to the diffuse colour of Eq. 4."""
+    rng = np.random.default_rng(2000 + seed)
+    M = scene["ctrl"].shape[0]
+    K = (D + 1) ** 2 - 1
+    out = dict(scene)
+    out["sh_degree"] = int(D)
+    out["sh"] = np.ascontiguousarray(rng.normal(0.0, scale, size=(M, K, 3)), np.float32)
     return out
 
 

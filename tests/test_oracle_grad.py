@@ -35,7 +35,7 @@ def fd_check(oracle, scene, cam, opts, nparams, seed, kinds=("ctrl", "color", "o
         tries += 1
         if kind in ("ctrl", "color"):
             idx = (int(rng.integers(M)), int(rng.integers(m)), int(rng.integers(3)))
-        elif kind in ("log_scale", "quat"):
+        elif kind in ("log_scale", "quat", "sh"):
             shp = s64[kind].shape
             idx = tuple(int(rng.integers(d)) for d in shp)
         else:
