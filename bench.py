@@ -237,7 +237,7 @@ def run_ours(args):
         images = torch.empty((P, 3), device="cuda")
         target = torch.rand((P, 3), device="cuda", generator=gen)
         dimg = torch.zeros((P, 3), device="cuda")
-        grads = {k: torch.empty_like(dev[k]) for k in R.GRAD_KEYS}
+        grads = {k: torch.empty_like(dev[k]) for k in R.GRAD_KEYS if k in dev}
         loss = torch.zeros(1, device="cuda")
     torch.cuda.synchronize()  # scene tensors were filled on the default stream
     scale = 1.0 / (3 * P)
@@ -305,7 +305,7 @@ def run_ours(args):
 
     # end to end: parameters from pinned host memory in, gradients + loss out, every step
     host_in = {k: dev[k].cpu().pin_memory() for k in R.SCENE_KEYS}
-    host_out = {k: torch.empty(grads[k].shape, dtype=torch.float32).pin_memory() for k in R.GRAD_KEYS}
+    host_out = {k: torch.empty(grads[k].shape, dtype=torch.float32).pin_memory() for k in grads}
     host_loss = torch.empty(1).pin_memory()
     h2d = sum(t.numel() * 4 for t in host_in.values())
     d2h = sum(t.numel() * 4 for t in host_out.values()) + 4
@@ -314,7 +314,7 @@ def run_ours(args):
         for k in R.SCENE_KEYS:
             dev[k].copy_(host_in[k], non_blocking=True)
         step()
-        for k in R.GRAD_KEYS:
+        for k in grads:
             host_out[k].copy_(grads[k], non_blocking=True)
         host_loss.copy_(loss, non_blocking=True)
 
@@ -394,7 +394,7 @@ def run_plain(rd_ctx, args):
             n = c["width"] * c["height"]
             bufs.append((torch.empty((n, 3), device="cuda"), torch.rand((n, 3), device="cuda", generator=gen),
                          torch.zeros((n, 3), device="cuda")))
-        grads = {k: torch.empty_like(dev[k]) for k in R.GRAD_KEYS}
+        grads = {k: torch.empty_like(dev[k]) for k in R.GRAD_KEYS if k in dev}
 
     def step():
         for c, (img, tgt, d) in zip(cams, bufs):

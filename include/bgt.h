@@ -97,6 +97,11 @@ typedef struct {
                              stored in the control-point order (i = R-1..0, then
                              j = R-1-i..0); Theta interpolates linearly on the lattice
                              triangle holding I_uv (R = 1: one texel per primitive) */
+  const float *sh;        /* [M][K][3] view-dependent colour: coefficients of the real spherical
+                             harmonics of bands 1..D per primitive and RGB channel, K = (D+1)^2 - 1,
+                             added to the diffuse colour at the direction from the camera centre
+                             to S_q (Sec. 3.2, "SH coefficients"); NULL when D = 0 */
+  int sh_degree;          /* D = 0..3 */
 } bgt_scene;
 
 typedef struct {
@@ -106,6 +111,7 @@ typedef struct {
   float *r_b;     /* [M] dl/dr_b */
   float *log_scale; /* [M][T][3] dl/d scaling map texels, or NULL (not computed) */
   float *quat;      /* [M][T][4] dl/d rotation map texels (raw quaternion), or NULL */
+  float *sh;        /* [M][K][3] dl/d SH coefficients, or NULL (not computed) */
 } bgt_grads;
 
 /* Fill *cfg with the defaults named above (n = 2, L = 8, tile 16, 1/255, 0.99,

@@ -41,12 +41,12 @@ class Camera(ctypes.Structure):
 class Scene(ctypes.Structure):
     _fields_ = [("ctrl", c_void_p), ("color", c_void_p), ("opacity", c_void_p), ("r_b", c_void_p),
                 ("log_scale", c_void_p), ("quat", c_void_p), ("num_prims", c_int), ("bg", c_float * 3),
-                ("attr_res", c_int)]
+                ("attr_res", c_int), ("sh", c_void_p), ("sh_degree", c_int)]
 
 
 class Grads(ctypes.Structure):
     _fields_ = [("ctrl", c_void_p), ("color", c_void_p), ("opacity", c_void_p), ("r_b", c_void_p),
-                ("log_scale", c_void_p), ("quat", c_void_p)]
+                ("log_scale", c_void_p), ("quat", c_void_p), ("sh", c_void_p)]
 
 
 class BGTError(RuntimeError):

@@ -158,6 +158,8 @@ bgt_status setup_call(bgt_handle *h, const bgt_scene *sc, const bgt_camera *cams
     return fail(h, BGT_ERR_INVALID_ARG, "null scene array");
   const int R = sc->attr_res == 0 ? 1 : sc->attr_res;
   if (R < 1 || R > 16) return fail(h, BGT_ERR_INVALID_ARG, "attr_res must be 0..16");
+  if (sc->sh_degree < 0 || sc->sh_degree > 3) return fail(h, BGT_ERR_INVALID_ARG, "sh_degree must be 0..3");
+  if (sc->sh_degree > 0 && sc->num_prims > 0 && !sc->sh) return fail(h, BGT_ERR_INVALID_ARG, "null sh array");
   const int t = h->tile;
   cudaError_t e = cudaEventSynchronize(h->staged);  // previous upload has left the staging buffer
   if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
@@ -219,11 +221,13 @@ bgt_status setup_call(bgt_handle *h, const bgt_scene *sc, const bgt_camera *cams
   p.stats = h->profiling ? 1 : 0;
   p.attr_res = R;
   p.ntex = R * (R + 1) / 2;
+  p.sh_deg = sc->sh_degree;
+  p.sh_k = (sc->sh_degree + 1) * (sc->sh_degree + 1) - 1;
   return BGT_OK;
 }
 
 bgt::Scene to_scene(const bgt_scene *s) {
-  return bgt::Scene{s->ctrl, s->color, s->opacity, s->r_b, s->log_scale, s->quat};
+  return bgt::Scene{s->ctrl, s->color, s->opacity, s->r_b, s->log_scale, s->quat, s->sh_degree > 0 ? s->sh : nullptr};
 }
 
 // stage boundaries recorded when profiling: 0 fwd start, 1 after prep, 2 raster,
@@ -276,6 +280,7 @@ cudaError_t enqueue_bwd(bgt_handle *h, const bgt::Params &p, const bgt::Scene &s
     cudaMemsetAsync(g.r_b, 0, sizeof(float) * (size_t)p.M, st);
     if (g.log_scale) cudaMemsetAsync(g.log_scale, 0, sizeof(float) * 3 * (size_t)p.M * p.ntex, st);
     if (g.quat) cudaMemsetAsync(g.quat, 0, sizeof(float) * 4 * (size_t)p.M * p.ntex, st);
+    if (g.sh && p.sh_k > 0) cudaMemsetAsync(g.sh, 0, sizeof(float) * 3 * (size_t)p.M * p.sh_k, st);
   }
   int k = bgt::launch_composite_bwd(p, w, dimg, st);
   mark(h, 8, st);
@@ -288,8 +293,8 @@ cudaError_t enqueue_bwd(bgt_handle *h, const bgt::Params &p, const bgt::Scene &s
 std::string graph_key(const bgt::Params &p, const void *a, const void *b, const void *c, const void *d,
                       const void *e, const bgt_camera *cams, int n) {
   char buf[256];
-  snprintf(buf, sizeof(buf), "%p|%p|%p|%p|%p|%d|%d|%d|%d|%d|%d|%d|", a, b, c, d, e, p.M, p.V, p.P, p.tiles, p.tile,
-           p.use_boundary, p.attr_res);
+  snprintf(buf, sizeof(buf), "%p|%p|%p|%p|%p|%d|%d|%d|%d|%d|%d|%d|%d|", a, b, c, d, e, p.M, p.V, p.P, p.tiles,
+           p.tile, p.use_boundary, p.attr_res, p.sh_deg);
   std::string k(buf);
   for (int v = 0; v < n; v++) k += std::to_string(cams[v].width) + "x" + std::to_string(cams[v].height) + ",";
   // the parameters passed by value to kernels are part of the graph
@@ -422,7 +427,7 @@ bgt_status bgt_render_fwd(bgt_handle *h, const bgt_scene *scene, const bgt_camer
   if ((h->cfg.flags & BGT_FLAG_GRAPH) && st != nullptr) {
     const std::string key = graph_key(p, scene->ctrl, scene->color, scene->opacity, scene->r_b, images, cams, n_views) +
                             std::to_string((size_t)scene->quat) + std::to_string((size_t)scene->log_scale) +
-                            (h->profiling ? "P" : "-");
+                            std::to_string((size_t)scene->sh) + (h->profiling ? "P" : "-");
     e = run_graph(&h->g_fwd, &h->g_fwd_key, key, st, [&]() { return enqueue_fwd(h, p, sc, images, st); });
   } else {
     e = enqueue_fwd(h, p, sc, images, st);
@@ -457,13 +462,14 @@ bgt_status bgt_render_bwd(bgt_handle *h, const bgt_scene *scene, const bgt_camer
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const bgt::Params p = h->last;
   const bgt::Scene sc = to_scene(scene);
-  const bgt::Grads g{grads->ctrl, grads->color, grads->opacity, grads->r_b, grads->log_scale, grads->quat};
+  const bgt::Grads g{grads->ctrl, grads->color, grads->opacity, grads->r_b, grads->log_scale, grads->quat,
+                     scene->sh_degree > 0 ? grads->sh : nullptr};
   cudaError_t e;
   if ((h->cfg.flags & BGT_FLAG_GRAPH) && st != nullptr) {
     const std::string key = graph_key(p, scene->ctrl, d_images, grads->ctrl, grads->color, grads->opacity, cams,
                                       n_views) + std::to_string((size_t)grads->r_b) +
                             std::to_string((size_t)grads->log_scale) + std::to_string((size_t)grads->quat) +
-                            (h->profiling ? "P" : "-");
+                            std::to_string((size_t)grads->sh) + (h->profiling ? "P" : "-");
     e = run_graph(&h->g_bwd, &h->g_bwd_key, key, st, [&]() { return enqueue_bwd(h, p, sc, d_images, g, st); });
   } else {
     e = enqueue_bwd(h, p, sc, d_images, g, st);

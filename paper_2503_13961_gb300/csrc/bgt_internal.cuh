@@ -58,15 +58,18 @@ struct Params {
   long long max_pairs, max_bpairs;
   int stats;                  // 1: blending kernels count their work units into Work::stats
   int attr_res, ntex;         // attribute maps: leg resolution R, texels R (R + 1) / 2
+  int sh_deg, sh_k;           // SH colour: degree D, coefficients per channel (D + 1)^2 - 1
 };
 
 struct Scene {                // device pointers, caller-owned
   const float *ctrl, *color, *opacity, *r_b, *log_scale, *quat;
+  const float *sh;            // [M][K][3] SH coefficients of bands 1..D, or null
 };
 
 struct Grads {                // device pointers, caller-owned outputs
   float *ctrl, *color, *opacity, *r_b;
   float *log_scale, *quat;    // attribute-map texel gradients, nullable
+  float *sh;                  // SH coefficient gradients, nullable
 };
 
 // Gaussian record (one per foreground pixel), three float4 per Gaussian:
@@ -352,6 +355,54 @@ __device__ inline void cov3d_f32(const float *q, const float *ls, float *S6, flo
   for (int i = 0; i < 3; i++)
 #pragma unroll
     for (int j = i; j < 3; j++) S6[k++] = Mx[3 * i] * Mx[3 * j] + Mx[3 * i + 1] * Mx[3 * j + 1] + Mx[3 * i + 2] * Mx[3 * j + 2];
+}
+
+// ---------------------------------------------------------------------------
+// View-dependent colour: real spherical harmonics of bands 1..D (D <= 3) at a
+// unit direction (x, y, z), in the Cartesian forms that the associated
+// Legendre definition (Condon-Shortley phase) gives on the unit sphere, order
+// m = -l..l within a band; constants sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!) times
+// the Legendre factors, as noted.
+// ---------------------------------------------------------------------------
+__device__ inline void sh_eval(int D, float x, float y, float z, float *Y) {
+  const float c1 = 0.48860251190291992f;   // sqrt(3 / (4 pi))
+  const float c2a = 1.09254843059207907f;  // sqrt(15 / (4 pi))
+  const float c2b = 0.31539156525252005f;  // sqrt(5 / (16 pi))
+  const float c2c = 0.54627421529603959f;  // sqrt(15 / (16 pi))
+  const float c3a = 0.59004358992664352f;  // sqrt(35 / (32 pi))
+  const float c3b = 2.89061144264055405f;  // sqrt(105 / (4 pi))
+  const float c3c = 0.45704579946446574f;  // sqrt(21 / (32 pi))
+  const float c3d = 0.37317633259011540f;  // sqrt(7 / (16 pi))
+  const float c3e = 1.44530572132027703f;  // sqrt(105 / (16 pi))
+  Y[0] = -c1 * y; Y[1] = c1 * z; Y[2] = -c1 * x;
+  if (D < 2) return;
+  Y[3] = c2a * x * y; Y[4] = -c2a * y * z; Y[5] = c2b * (3.f * z * z - 1.f); Y[6] = -c2a * x * z;
+  Y[7] = c2c * (x * x - y * y);
+  if (D < 3) return;
+  Y[8] = -c3a * y * (3.f * x * x - y * y); Y[9] = c3b * x * y * z; Y[10] = -c3c * y * (5.f * z * z - 1.f);
+  Y[11] = c3d * z * (5.f * z * z - 3.f); Y[12] = -c3c * x * (5.f * z * z - 1.f); Y[13] = c3e * z * (x * x - y * y);
+  Y[14] = -c3a * x * (x * x - 3.f * y * y);
+}
+
+// g = sum_k w_k grad P_k(x, y, z) of the Cartesian forms above
+__device__ inline void sh_grad(int D, float x, float y, float z, const float *w, float *g) {
+  const float c1 = 0.48860251190291992f, c2a = 1.09254843059207907f, c2b = 0.31539156525252005f;
+  const float c2c = 0.54627421529603959f, c3a = 0.59004358992664352f, c3b = 2.89061144264055405f;
+  const float c3c = 0.45704579946446574f, c3d = 0.37317633259011540f, c3e = 1.44530572132027703f;
+  g[0] = -c1 * w[2];
+  g[1] = -c1 * w[0];
+  g[2] = c1 * w[1];
+  if (D < 2) return;
+  g[0] += c2a * y * w[3] - c2a * z * w[6] + 2.f * c2c * x * w[7];
+  g[1] += c2a * x * w[3] - c2a * z * w[4] - 2.f * c2c * y * w[7];
+  g[2] += -c2a * y * w[4] + 6.f * c2b * z * w[5] - c2a * x * w[6];
+  if (D < 3) return;
+  g[0] += -6.f * c3a * x * y * w[8] + c3b * y * z * w[9] - c3c * (5.f * z * z - 1.f) * w[12] +
+          2.f * c3e * x * z * w[13] - 3.f * c3a * (x * x - y * y) * w[14];
+  g[1] += -3.f * c3a * (x * x - y * y) * w[8] + c3b * x * z * w[9] - c3c * (5.f * z * z - 1.f) * w[10] -
+          2.f * c3e * y * z * w[13] + 6.f * c3a * x * y * w[14];
+  g[2] += c3b * x * y * w[9] - 10.f * c3c * y * z * w[10] + c3d * (15.f * z * z - 3.f) * w[11] -
+          10.f * c3c * x * z * w[12] + c3e * (x * x - y * y) * w[13];
 }
 
 // ---------------------------------------------------------------------------

@@ -229,6 +229,70 @@ __global__ void __launch_bounds__(256) k_chain_gauss(Params p, Scene s, Work w, 
   }
 }
 
+// View-dependent colour (SH bands 1..D, one coefficient set per primitive):
+// dl/dk = Y(d) dl/dc summed per primitive, and the direction d = v / |v|,
+// v = R^T t from the camera centre to S_q, moves with S_q:
+// dl/dv = (I - d d^T) / |v| sum_k (sum_c dl/dc_c k_kc) grad Y_k(d), taken to
+// the control points with the Bernstein weights (Eq. 3).
+template <int N>
+__global__ void __launch_bounds__(256) k_chain_sh(Params p, Scene s, Work w, Grads out) {
+  const int F = w.counters[kF];
+  const int lane = threadIdx.x & 31;
+  const int warps_total = gridDim.x * (blockDim.x >> 5);
+  constexpr int m = SurfPoint<N>::M;
+  for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < F; base += warps_total * 32) {
+    const int i = base + lane;
+    const bool active = i < F;
+    int g = -1;
+    float gS[3] = {0.f, 0.f, 0.f}, gcol[3] = {0.f, 0.f, 0.f}, Y[15], B[m];
+    if (active) {
+      const float *gg = w.gg + 12 * (size_t)i;
+      gcol[0] = gg[6];
+      gcol[1] = gg[7];
+      gcol[2] = gg[8];
+      g = __float_as_int(w.gC[i].w);
+      const View vw = w.views[w.g_view[i]];
+      const float2 uv = w.g_uv[i];
+      float t[3], dv[3];
+      camera_point_f32<N>(s.ctrl + (size_t)g * m * 3, uv.x, uv.y, vw, B, t);
+#pragma unroll
+      for (int k = 0; k < 3; k++) dv[k] = vw.R[k] * t[0] + vw.R[3 + k] * t[1] + vw.R[6 + k] * t[2];
+      const float inv = rsqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+      const float d0 = dv[0] * inv, d1 = dv[1] * inv, d2 = dv[2] * inv;
+      sh_eval(p.sh_deg, d0, d1, d2, Y);
+      const float *shp = s.sh + (size_t)g * p.sh_k * 3;
+      float wk[15];
+#pragma unroll
+      for (int k = 0; k < 15; k++) {
+        wk[k] = 0.f;
+        if (k < p.sh_k)
+          wk[k] = gcol[0] * __ldg(shp + 3 * k) + gcol[1] * __ldg(shp + 3 * k + 1) + gcol[2] * __ldg(shp + 3 * k + 2);
+      }
+      float gd[3];
+      sh_grad(p.sh_deg, d0, d1, d2, wk, gd);
+      const float dot = d0 * gd[0] + d1 * gd[1] + d2 * gd[2];
+      gS[0] = (gd[0] - d0 * dot) * inv;
+      gS[1] = (gd[1] - d1 * dot) * inv;
+      gS[2] = (gd[2] - d2 * dot) * inv;
+    }
+    const bool nz = active && (gcol[0] != 0.f || gcol[1] != 0.f || gcol[2] != 0.f);
+    if (!__any_sync(0xffffffffu, nz)) continue;
+    const Seg sg = seg_info(nz ? g : -1 - lane);
+    scatter_cp<m>(out.ctrl, g, B, gS, sg, nz);
+    if (out.sh) {
+#pragma unroll
+      for (int k = 0; k < 15; k++) {
+        if (k >= p.sh_k) break;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          const float v = seg_sum(nz ? Y[k] * gcol[c] : 0.f, sg);
+          if (sg.tail && nz && v != 0.f) atomicAdd(out.sh + ((size_t)g * p.sh_k + k) * 3 + c, v);
+        }
+      }
+    }
+  }
+}
+
 template <int N>
 __global__ void __launch_bounds__(256) k_chain_bnd(Params p, Scene s, Work w, Grads out) {
   const int Nb = w.counters[kNb];
@@ -286,8 +350,9 @@ int launch_chain(const Params &p, const Scene &s, const Work &w, const Grads &g,
   dispatch_degree(p.n, [&](auto d) {
     k_chain_gauss<decltype(d)::value><<<grid, 256, 0, st>>>(p, s, w, g);
     k_chain_bnd<decltype(d)::value><<<grid, 256, 0, st>>>(p, s, w, g);
+    if (p.sh_deg > 0) k_chain_sh<decltype(d)::value><<<grid, 256, 0, st>>>(p, s, w, g);
   });
-  return 2;
+  return p.sh_deg > 0 ? 3 : 2;
 }
 
 int launch_l1_grad(const float *img, const float *target, long long n, float scale, float *dimg, float *loss,

@@ -294,6 +294,45 @@ __global__ void __launch_bounds__(kGenThreads) k_generate(Params p, Scene s, Wor
 
 }  // namespace
 
+// View-dependent colour (SH bands 1..D of the primitive) added to the diffuse
+// colour of every Gaussian, at the direction from the camera centre to S_q
+// (R^T t in world coordinates, t the camera-space point of Eq. 3)
+template <int N>
+__global__ void __launch_bounds__(256) k_sh_color(Params p, Scene s, Work w) {
+  const int F = w.counters[kF];
+  constexpr int m = SurfPoint<N>::M;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < F; i += gridDim.x * blockDim.x) {
+    float4 C = w.gC[i];
+    const int g = __float_as_int(C.w);
+    const View &vw = w.views[w.g_view[i]];
+    const float2 uv = w.g_uv[i];
+    float B[m], S[3] = {0.f, 0.f, 0.f};
+    bernstein_f32<N>(uv.x, uv.y, B);
+    const float *cp = s.ctrl + (size_t)g * m * 3;
+#pragma unroll
+    for (int a = 0; a < m; a++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) S[c] = fmaf(B[a], __ldg(cp + 3 * a + c), S[c]);
+    float t[3], dv[3];
+#pragma unroll
+    for (int r = 0; r < 3; r++) t[r] = vw.R[3 * r] * S[0] + vw.R[3 * r + 1] * S[1] + vw.R[3 * r + 2] * S[2] + vw.t[r];
+#pragma unroll
+    for (int k = 0; k < 3; k++) dv[k] = vw.R[k] * t[0] + vw.R[3 + k] * t[1] + vw.R[6 + k] * t[2];
+    const float inv = rsqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+    float Y[15];
+    sh_eval(p.sh_deg, dv[0] * inv, dv[1] * inv, dv[2] * inv, Y);
+    const float *shp = s.sh + (size_t)g * p.sh_k * 3;
+#pragma unroll
+    for (int k = 0; k < 15; k++) {
+      if (k >= p.sh_k) break;
+      C.x = fmaf(Y[k], __ldg(shp + 3 * k + 0), C.x);
+      C.y = fmaf(Y[k], __ldg(shp + 3 * k + 1), C.y);
+      C.z = fmaf(Y[k], __ldg(shp + 3 * k + 2), C.z);
+    }
+    w.gC[i] = C;
+  }
+}
+
 int launch_generate(const Params &p, const Scene &s, const Work &w, cudaStream_t st) {
   const int nblk = (p.P + kGenPixels - 1) / kGenPixels;
   if (nblk == 0) {
@@ -303,6 +342,10 @@ int launch_generate(const Params &p, const Scene &s, const Work &w, cudaStream_t
   k_count<<<nblk, kGenThreads, 0, st>>>(p, w);
   k_scan_blocks<<<1, 1024, 0, st>>>(w, nblk);
   dispatch_degree(p.n, [&](auto d) { k_generate<decltype(d)::value><<<nblk, kGenThreads, 0, st>>>(p, s, w); });
+  if (p.sh_deg > 0) {
+    dispatch_degree(p.n, [&](auto d) { k_sh_color<decltype(d)::value><<<152 * 8, 256, 0, st>>>(p, s, w); });
+    return 4;
+  }
   return 3;
 }
 

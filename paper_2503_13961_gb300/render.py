@@ -13,7 +13,7 @@ import torch
 from . import _abi
 
 SCENE_KEYS = ("ctrl", "color", "opacity", "r_b", "log_scale", "quat")
-GRAD_KEYS = ("ctrl", "color", "opacity", "r_b", "log_scale", "quat")
+GRAD_KEYS = ("ctrl", "color", "opacity", "r_b", "log_scale", "quat", "sh")
 
 STAGE_ID = {"id": 0, "uv": 1, "gauss": 2, "bnd": 3, "g_ranges": 4, "g_keys": 5, "b_ranges": 6,
             "b_keys": 7, "T": 8, "n": 9, "ggrad": 10, "bgrad": 11}
@@ -35,6 +35,9 @@ def scene_to_device(scene, device="cuda"):
     out["degree"] = int(scene["degree"])
     out["bg"] = [float(x) for x in np.asarray(scene["bg"]).ravel()]
     out["attr_res"] = int(scene.get("attr_res", 1))
+    out["sh_degree"] = int(scene.get("sh_degree", 0))
+    if out["sh_degree"] > 0:
+        out["sh"] = torch.as_tensor(np.ascontiguousarray(scene["sh"]), dtype=torch.float32, device=device)
     return out
 
 
@@ -104,6 +107,11 @@ class Renderer:
         s.num_prims = int(sc["ctrl"].shape[0])
         s.bg[:] = [float(x) for x in sc["bg"]]
         s.attr_res = int(sc.get("attr_res", 1))
+        s.sh_degree = int(sc.get("sh_degree", 0))
+        if s.sh_degree > 0:
+            t = sc["sh"]
+            assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous(), "sh"
+            s.sh = t.data_ptr()
         return s
 
     def _check(self, st):
@@ -123,10 +131,10 @@ class Renderer:
         return images
 
     def backward(self, scene, cams, d_images, grads=None, stream=None):
-        """dl/d(ctrl, color, opacity, r_b, log_scale, quat) for the last forward,
-        given dl/dimages; keys missing from `grads` are not computed."""
+        """dl/d(ctrl, color, opacity, r_b, log_scale, quat[, sh]) for the last
+        forward, given dl/dimages; keys missing from `grads` are not computed."""
         if grads is None:
-            grads = {k: torch.empty_like(scene[k]) for k in GRAD_KEYS}
+            grads = {k: torch.empty_like(scene[k]) for k in GRAD_KEYS if scene.get(k) is not None}
         d_images = d_images.contiguous()
         g = _grads_struct(grads)
         sc = self._scene(scene)
@@ -240,8 +248,10 @@ class Renderer:
 
 class _RenderFn(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, renderer, cams, scene_meta, ctrl, color, opacity, r_b, log_scale, quat):
+    def forward(ctx, renderer, cams, scene_meta, ctrl, color, opacity, r_b, log_scale, quat, sh):
         scene = dict(scene_meta, ctrl=ctrl, color=color, opacity=opacity, r_b=r_b, log_scale=log_scale, quat=quat)
+        if scene_meta.get("sh_degree", 0) > 0:
+            scene["sh"] = sh
         img = renderer.forward(scene, cams)
         ctx.renderer, ctx.cams, ctx.scene = renderer, cams, scene
         return img
@@ -249,15 +259,20 @@ class _RenderFn(torch.autograd.Function):
     @staticmethod
     def backward(ctx, d_img):
         g = ctx.renderer.backward(ctx.scene, ctx.cams, d_img.contiguous())
-        return None, None, None, g["ctrl"], g["color"], g["opacity"], g["r_b"], g["log_scale"], g["quat"]
+        return (None, None, None, g["ctrl"], g["color"], g["opacity"], g["r_b"], g["log_scale"], g["quat"],
+                g.get("sh"))
 
 
 def render(renderer, scene, cams):
     """Differentiable render: images [sum W*H, 3]; gradients flow to
-    scene['ctrl'], ['color'], ['opacity'], ['r_b'], ['log_scale'], ['quat']."""
-    meta = {"degree": scene["degree"], "bg": scene["bg"], "attr_res": scene.get("attr_res", 1)}
+    scene['ctrl'], ['color'], ['opacity'], ['r_b'], ['log_scale'], ['quat'] and ['sh']."""
+    meta = {"degree": scene["degree"], "bg": scene["bg"], "attr_res": scene.get("attr_res", 1),
+            "sh_degree": scene.get("sh_degree", 0)}
+    sh = scene.get("sh")
+    if sh is None:
+        sh = scene["opacity"].new_zeros(0)
     return _RenderFn.apply(renderer, cams, meta, scene["ctrl"], scene["color"], scene["opacity"], scene["r_b"],
-                           scene["log_scale"], scene["quat"])
+                           scene["log_scale"], scene["quat"], sh)
 
 
 def split_views(images, cams):

@@ -44,7 +44,8 @@ def _run(oracle, sc, cams, seed=0, tile=16, use_boundary=True):
         r = oracle.backward(sc, c, dl, opts=opts, intermediates=True)
         inter.append(r)
         if ref_g is None:
-            ref_g = {k: r[k].copy() for k in ("ctrl", "color", "opacity", "r_b", "log_scale", "quat")}
+            ref_g = {k: r[k].copy() for k in ("ctrl", "color", "opacity", "r_b", "log_scale", "quat", "sh")
+                     if k in r}
         else:
             for k in ref_g:
                 ref_g[k] += r[k]
@@ -224,3 +225,15 @@ def test_attribute_map_gradients_match_oracle(oracle, scenes, R):
         assert got[k].shape == ref[k].shape, k
         _assert_close(got[k], ref[k], k)
     assert np.abs(ref["log_scale"]).max() > 0 and np.abs(ref["quat"]).max() > 0
+
+
+@pytest.mark.parametrize("D", [1, 3])
+def test_sh_colour_gradients_match_oracle(oracle, scenes, D):
+    """View-dependent colour of SH degree D: gradients of the coefficients and
+    of the control points (which move the view direction) against the oracle."""
+    sc, cams = scenes.tiny_scene("ico1", noise=0.04, size=(90, 70), r_b=0.04)
+    sc = scenes.with_sh(sc, D, seed=D)
+    _, got, ref, _, _ = _run(oracle, sc, cams, seed=9)
+    for k in ("ctrl", "color", "opacity", "r_b", "sh"):
+        assert got[k].shape == ref[k].shape, k
+        _assert_close(got[k], ref[k], k)

@@ -31,6 +31,8 @@ def _cases():
     out.append(("degree4", sc, cams))
     sc, cams = S.tiny_scene("ico1", noise=0.04, size=(100, 75), r_b=0.03)
     out.append(("attr_maps_R3", S.with_attribute_maps(sc, 3), cams))
+    sc, cams = S.tiny_scene("ico1", noise=0.04, size=(90, 70), r_b=0.03)
+    out.append(("sh_degree3", S.with_sh(sc, 3), cams))
     sc, cams, _ = S.config_scene(2)
     out.append(("config2_crop", sc, [S.crop_camera(cams[0], 300, 330, 160, 121)]))
     sc, cams = S.config_scene(4)
@@ -51,7 +53,7 @@ def cases():
 
 
 CASE_NAMES = ["config1_64", "two_ragged", "ico1_100x75", "degree3", "degree1", "degree4", "attr_maps_R3",
-              "config2_crop", "config4_multiview"]
+              "sh_degree3", "config2_crop", "config4_multiview"]
 
 
 @pytest.fixture(scope="module")
