@@ -203,6 +203,24 @@ bgt_status bgt_autotune(bgt_handle *h, const bgt_scene *scene, const bgt_camera 
 bgt_status bgt_l1_loss_grad(const float *images, const float *target, long long n, float scale,
                             float *d_images, float *loss, void *stream);
 
+/* Photometric training loss of Sec. 3.3, Eq. 9, and its gradient, fused.
+ * images, target: device, the renderer's image layout ([sum W H][3] float,
+ * view v an [H_v][W_v][3] block); sizes: host [n_views][2] = (W_v, H_v).
+ * For each view
+ *   L_v = (1 - lambda) * L2 + lambda * (1 - SSIM),
+ * L2 the mean of (images - target)^2 over the view's 3 W H values and SSIM
+ * the mean over its pixels and channels of the SSIM map (11 x 11 Gaussian
+ * window of sigma 1.5 normalised to one, values outside the image taken as
+ * zero, C1 = 0.01^2, C2 = 0.03^2, each channel on its own); the paper uses
+ * lambda = 0.2. Writes scale * dL_v/dC to d_images (same layout, written
+ * entirely) and atomically adds scale * sum_v L_v to *loss (device float,
+ * may be NULL; the caller zeroes it). d_images must not overlap images or
+ * target. BGT_ERR_INVALID_ARG for negative sizes, a view of more than
+ * 2^31 / 3 pixels, lambda outside [0, 1], a non-finite scale, missing or
+ * aliased buffers (checked on the host before any launch). */
+bgt_status bgt_l2_dssim_loss_grad(const float *images, const float *target, int n_views, const int *sizes,
+                                  float lambda, float scale, float *d_images, float *loss, void *stream);
+
 /* Intermediate buffers of the last forward, copied to host memory for stage
  * tests. `which`: 0 I_id int32[P]; 1 I_uv float[P][2]; 2 Gaussian records
  * float[F][12] (off_x, off_y, K_a, K_b, K_c, o, bits(qx|qy<<16), bits(prim),

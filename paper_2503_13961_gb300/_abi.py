@@ -72,6 +72,7 @@ def _declare(L):
     L.bgt_autotune.argtypes = [P, ctypes.POINTER(Scene), ctypes.POINTER(Camera), c_int, P, P, ctypes.POINTER(Grads),
                                c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_float), P]
     L.bgt_l1_loss_grad.argtypes = [P, P, c_ll, c_float, P, P, P]
+    L.bgt_l2_dssim_loss_grad.argtypes = [P, P, c_int, P, c_float, c_float, P, P, P]
     L.bgt_get_stage.argtypes = [P, c_int, P, c_ll, ctypes.POINTER(c_ll), P]
     L.bgt_bin_sort.argtypes = [P, c_int, c_int, c_int, P, P, P, P, P, P]
     L.bgt_bin_sort_static.argtypes = [c_int, c_int, c_int, c_int, P, P, P, P, P, c_float, P, P, c_ll, P]

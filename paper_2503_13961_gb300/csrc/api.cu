@@ -601,6 +601,23 @@ bgt_status bgt_l1_loss_grad(const float *images, const float *target, long long 
   return cudaGetLastError() == cudaSuccess ? BGT_OK : BGT_ERR_CUDA;
 }
 
+bgt_status bgt_l2_dssim_loss_grad(const float *images, const float *target, int n_views, const int *sizes,
+                                  float lambda, float scale, float *d_images, float *loss, void *stream) {
+  if (n_views < 0 || (n_views > 0 && !sizes)) return BGT_ERR_INVALID_ARG;
+  if (!(lambda >= 0.f && lambda <= 1.f) || !std::isfinite(scale)) return BGT_ERR_INVALID_ARG;
+  long long n = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const int W = sizes[2 * v], H = sizes[2 * v + 1];
+    if (W < 0 || H < 0 || (long long)W * H > (1LL << 31) / 3) return BGT_ERR_INVALID_ARG;
+    n += 3LL * W * H;
+  }
+  if (n > 0 && (!images || !target || !d_images)) return BGT_ERR_INVALID_ARG;
+  if (n > 0 && (d_images == images || d_images == target)) return BGT_ERR_INVALID_ARG;
+  bgt::launch_l2_dssim_grad(images, target, n_views, sizes, lambda, scale, d_images, loss,
+                            static_cast<cudaStream_t>(stream));
+  return cudaGetLastError() == cudaSuccess ? BGT_OK : BGT_ERR_CUDA;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

@@ -535,6 +535,8 @@ int launch_composite_bwd(const Params &p, const Work &w, const float *dimage, cu
 int launch_chain(const Params &p, const Scene &s, const Work &w, const Grads &g, cudaStream_t st);
 int launch_l1_grad(const float *img, const float *target, long long n, float scale, float *dimg,
                    float *loss, cudaStream_t st);
+int launch_l2_dssim_grad(const float *img, const float *gt, int n_views, const int *sizes, float lambda,
+                         float scale, float *dimg, float *loss, cudaStream_t st);
 int launch_exclusive_scan(const int *in, long long *out, int n, long long *aux, cudaStream_t st);
 int launch_bin_sort_only(const Params &p, const Work &w, cudaStream_t st);
 

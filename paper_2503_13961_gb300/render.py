@@ -196,6 +196,19 @@ class Renderer:
                                              _ptr(d_images), _ptr(loss), _stream(stream)))
         return d_images
 
+    def l2_dssim_loss_grad(self, images, target, cams, lam=0.2, scale=1.0, d_images=None, loss=None, stream=None):
+        """Eq. 9 per view of `images` (the forward's layout, views sized by `cams`): writes
+        scale * dL/dC to d_images and adds scale * the sum of the views' losses to `loss`."""
+        if d_images is None:
+            d_images = torch.empty_like(images)
+        sizes = (ctypes.c_int * (2 * len(cams)))(*[int(x) for c in cams for x in (c["width"], c["height"])])
+        n = 3 * sum(c["width"] * c["height"] for c in cams)
+        if images.numel() != n or target.numel() != n or d_images.numel() != n:
+            raise ValueError("images, target and d_images must hold the views of `cams`")
+        _abi.check(self.lib.bgt_l2_dssim_loss_grad(_ptr(images), _ptr(target), len(cams), sizes, float(lam),
+                                                   float(scale), _ptr(d_images), _ptr(loss), _stream(stream)))
+        return d_images
+
     def stage(self, name, stream=None):
         """Copy an intermediate buffer of the last forward to a numpy array."""
         which = STAGE_ID[name]

@@ -564,3 +564,27 @@ def triangles_scene(tris, n=1, seed=0, **kw):
     mesh = _Mesh()
     mesh.add_object(("flat",), [tuple(np.asarray(p, np.float64) for p in t) for t in tris])
     return make_scene(mesh, n, 0.0, seed, **kw)
+
+
+def photo_pair(rng, width, height, noise=0.05):
+    """A rendered-looking image and a target to train it against, [H, W, 3]
+    float32 in [0, 1], for the photometric loss (Sec. 3.3, Eq. 9).
+
+    The image is a flat background with a few flat rectangles (sharp edges,
+    the flat areas where windowed variances are small) and sparse pixel
+    noise; the target is the image with Gaussian noise of std `noise`,
+    clipped, and one flat stripe every seventh row (structure that differs).
+    """
+    img = np.empty((height, width, 3), np.float64)
+    img[:] = rng.uniform(0.0, 1.0, size=3)
+    for _ in range(4):
+        y0, x0 = rng.integers(0, max(1, height), 2) if height and width else (0, 0)
+        y1 = y0 + rng.integers(1, max(2, height // 2 + 1))
+        x1 = x0 + rng.integers(1, max(2, width // 2 + 1))
+        img[y0:y1, x0:x1] = rng.uniform(0.0, 1.0, size=3)
+    speck = rng.uniform(size=(height, width, 1)) < 0.3
+    img += rng.normal(scale=0.02, size=img.shape) * speck
+    img = np.clip(img, 0.0, 1.0)
+    gt = np.clip(img + rng.normal(scale=noise, size=img.shape), 0.0, 1.0)
+    gt[::7] = rng.uniform(0.0, 1.0, size=3)
+    return img.astype(np.float32), gt.astype(np.float32)
