@@ -394,7 +394,49 @@ def run_ours(args):
             "work_units": units,
             "stages": per_stage,
         }
+    if rank == 0:
+        out["split_prune"] = run_split_prune((rd, dev, cams, sc, stream), grads)
     return out, (rd, dev, cams, sc, stream)
+
+
+def run_split_prune(rd_ctx, grads):
+    """Splitting / pruning geometry on the workload's primitives (Sec. 3.3):
+    the per-primitive measures and flags with the step's control-point
+    gradients, and the 1 -> 4 split of every primitive; CUDA-event times and
+    the HBM fraction of their algorithmic bytes."""
+    import torch
+    from paper_2503_13961_gb300 import render as R
+    _, dev, _, sc, stream = rd_ctx
+    M, ncp = sc["ctrl"].shape[0], sc["ctrl"].shape[1]
+    T = int(dev.get("attr_res", 1)) * (int(dev.get("attr_res", 1)) + 1) // 2
+    sel = torch.arange(M, dtype=torch.int32, device="cuda")
+    peak, _, _ = peaks()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+    # algorithmic bytes: metrics read ctrl + gradient and write 13 B per primitive;
+    # the split reads the parent's control points, colours and attributes and
+    # writes four pieces
+    work = {
+        "prim_metrics": (lambda: R.prim_metrics(dev, grads["ctrl"], stream=stream), M * (24 * ncp + 13)),
+        "subdivide": (lambda: R.subdivide(dev, sel, stream=stream),
+                      M * (4 + 24 * ncp + 8 + 28 * T) + 4 * M * (24 * ncp + 8 + 28 * T)),
+    }
+    with torch.cuda.stream(stream):
+        for name, (fn, nbytes) in work.items():
+            for _ in range(3):
+                fn()
+            reps = 20
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            res[name] = {"ms": round(ms, 4), "alg_bytes": int(nbytes),
+                         "GBps": round(nbytes / (ms * 1e-3) / 1e9, 1),
+                         "hbm_frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4)}
+    res["prims"] = M
+    return res
 
 
 def run_plain(rd_ctx, args):

@@ -221,6 +221,55 @@ bgt_status bgt_l1_loss_grad(const float *images, const float *target, long long 
 bgt_status bgt_l2_dssim_loss_grad(const float *images, const float *target, int n_views, const int *sizes,
                                   float lambda, float scale, float *d_images, float *loss, void *stream);
 
+/* Output arrays of bgt_subdivide (device memory, caller-owned), laid out like
+ * the bgt_scene arrays of 4 * n_sel primitives with the input's degree,
+ * attr_res and sh_degree. sh may be NULL when sh_degree = 0. */
+typedef struct {
+  float *ctrl;      /* [4 n_sel][Ncp][3] */
+  float *color;     /* [4 n_sel][Ncp][3] */
+  float *opacity;   /* [4 n_sel] */
+  float *r_b;       /* [4 n_sel] */
+  float *log_scale; /* [4 n_sel][T][3] */
+  float *quat;      /* [4 n_sel][T][4] */
+  float *sh;        /* [4 n_sel][K][3] */
+} bgt_prims;
+
+/* Measures of the pruning and splitting criteria (Sec. 3.3 "Splitting and
+ * Pruning") for the num_prims degree-`degree` primitives of `scene` (device
+ * arrays; only ctrl is read):
+ *   area[m]   sum of the areas of the four planar triangles through the three
+ *             corners and the surface points at the edge midpoints, in the
+ *             pattern of the midpoint split;
+ *   aspect[m] longer / shorter side of the bounding rectangle of the control
+ *             points in the plane of the three corners, its first axis along
+ *             the longest corner edge (+inf when the corners are collinear);
+ *   grad[m]   mean over the control points of |dl/dp_ijk| from g_ctrl
+ *             ([M][Ncp][3] device, e.g. bgt_grads.ctrl; may be NULL);
+ *   flags[m]  bit 0 = prune (area < tau_a or aspect > tau_s; the paper uses
+ *             3e-4 and 10), bit 1 = split (grad > tau_g, the paper's 0.0018;
+ *             never set without g_ctrl).
+ * Each output (device, M entries) may be NULL. BGT_ERR_INVALID_ARG for a
+ * degree outside 1..4, a NULL scene or a NULL ctrl with M > 0. */
+bgt_status bgt_prim_metrics(int degree, const bgt_scene *scene, const float *g_ctrl, float tau_a, float tau_s,
+                            float tau_g, float *area, float *aspect, float *grad, unsigned char *flags,
+                            void *stream);
+
+/* The 1 -> 4 split of Sec. 3.3 ("Splitting and Pruning"): each primitive
+ * sel[s] (device int array of n_sel indices into scene) becomes the pieces
+ * 4 s + p, p = U corner, V corner, W corner, middle, with corners (U, M_uv,
+ * M_uw), (M_uv, V, M_vw), (M_uw, M_vw, W), (M_vw, M_uw, M_uv) of its
+ * parameter domain (M the edge midpoints; every piece keeps the parent's
+ * orientation). Control points and colour control points are the exact
+ * restriction of the degree-n Bezier patch to the piece (its polar form at
+ * the piece's corners); opacity, r_b and SH coefficients are copied; each
+ * texel of a piece's rotation / scaling maps (attr_res R > 1) is the
+ * parent map's Eq. 5 interpolation at the texel's node. The pieces of an
+ * index outside [0, num_prims) are written as NaN. `out` must not overlap
+ * the scene's arrays. BGT_ERR_INVALID_ARG for a degree outside 1..4, n_sel
+ * < 0 or > 2^28, or NULL arrays that the call needs. */
+bgt_status bgt_subdivide(int degree, const bgt_scene *scene, const int *sel, int n_sel, const bgt_prims *out,
+                         void *stream);
+
 /* Intermediate buffers of the last forward, copied to host memory for stage
  * tests. `which`: 0 I_id int32[P]; 1 I_uv float[P][2]; 2 Gaussian records
  * float[F][12] (off_x, off_y, K_a, K_b, K_c, o, bits(qx|qy<<16), bits(prim),

@@ -49,6 +49,14 @@ class Grads(ctypes.Structure):
                 ("log_scale", c_void_p), ("quat", c_void_p), ("sh", c_void_p)]
 
 
+PRIMS_KEYS = ("ctrl", "color", "opacity", "r_b", "log_scale", "quat", "sh")
+
+
+class Prims(ctypes.Structure):
+    """bgt_prims: output arrays of bgt_subdivide."""
+    _fields_ = [(k, c_void_p) for k in PRIMS_KEYS]
+
+
 class BGTError(RuntimeError):
     def __init__(self, status, msg=""):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -73,6 +81,8 @@ def _declare(L):
                                c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_float), P]
     L.bgt_l1_loss_grad.argtypes = [P, P, c_ll, c_float, P, P, P]
     L.bgt_l2_dssim_loss_grad.argtypes = [P, P, c_int, P, c_float, c_float, P, P, P]
+    L.bgt_prim_metrics.argtypes = [c_int, ctypes.POINTER(Scene), P, c_float, c_float, c_float, P, P, P, P, P]
+    L.bgt_subdivide.argtypes = [c_int, ctypes.POINTER(Scene), P, c_int, ctypes.POINTER(Prims), P]
     L.bgt_get_stage.argtypes = [P, c_int, P, c_ll, ctypes.POINTER(c_ll), P]
     L.bgt_bin_sort.argtypes = [P, c_int, c_int, c_int, P, P, P, P, P, P]
     L.bgt_bin_sort_static.argtypes = [c_int, c_int, c_int, c_int, P, P, P, P, P, c_float, P, P, c_ll, P]

@@ -10,6 +10,12 @@
 #include "../../include/bgt.h"
 #include "bgt_internal.cuh"
 
+namespace bgt {
+// split.cu (its arguments are the C-ABI structs)
+int launch_subdivide(int degree, const bgt_scene &sc, const int *sel, int n_sel, const bgt_prims &out,
+                     cudaStream_t st);
+}  // namespace bgt
+
 using bgt::View;
 
 struct bgt_handle {
@@ -615,6 +621,36 @@ bgt_status bgt_l2_dssim_loss_grad(const float *images, const float *target, int 
   if (n > 0 && (d_images == images || d_images == target)) return BGT_ERR_INVALID_ARG;
   bgt::launch_l2_dssim_grad(images, target, n_views, sizes, lambda, scale, d_images, loss,
                             static_cast<cudaStream_t>(stream));
+  return cudaGetLastError() == cudaSuccess ? BGT_OK : BGT_ERR_CUDA;
+}
+
+bgt_status bgt_prim_metrics(int degree, const bgt_scene *scene, const float *g_ctrl, float tau_a, float tau_s,
+                            float tau_g, float *area, float *aspect, float *grad, unsigned char *flags,
+                            void *stream) {
+  if (degree < 1 || degree > bgt::kMaxDegree || !scene || scene->num_prims < 0) return BGT_ERR_INVALID_ARG;
+  if (scene->num_prims > 0 && !scene->ctrl) return BGT_ERR_INVALID_ARG;
+  bgt::launch_prim_metrics(degree, scene->ctrl, scene->num_prims, g_ctrl, tau_a, tau_s, tau_g, area, aspect, grad,
+                           flags, static_cast<cudaStream_t>(stream));
+  return cudaGetLastError() == cudaSuccess ? BGT_OK : BGT_ERR_CUDA;
+}
+
+bgt_status bgt_subdivide(int degree, const bgt_scene *scene, const int *sel, int n_sel, const bgt_prims *out,
+                         void *stream) {
+  if (degree < 1 || degree > bgt::kMaxDegree || !scene || scene->num_prims < 0) return BGT_ERR_INVALID_ARG;
+  if (n_sel < 0 || n_sel > (1 << 28)) return BGT_ERR_INVALID_ARG;
+  if (n_sel == 0) return BGT_OK;
+  const int R = scene->attr_res <= 0 ? 1 : scene->attr_res;
+  if (R > 16 || scene->sh_degree < 0 || scene->sh_degree > 3) return BGT_ERR_INVALID_ARG;
+  if (!sel || !out || !out->ctrl || !out->color || !out->opacity || !out->r_b || !out->log_scale || !out->quat)
+    return BGT_ERR_INVALID_ARG;
+  if (scene->sh_degree > 0 && !out->sh) return BGT_ERR_INVALID_ARG;
+  if (scene->num_prims > 0 && (!scene->ctrl || !scene->color || !scene->opacity || !scene->r_b ||
+                               !scene->log_scale || !scene->quat || (scene->sh_degree > 0 && !scene->sh)))
+    return BGT_ERR_INVALID_ARG;
+  if (out->ctrl == scene->ctrl || out->color == scene->color || out->log_scale == scene->log_scale ||
+      out->quat == scene->quat)
+    return BGT_ERR_INVALID_ARG;
+  bgt::launch_subdivide(degree, *scene, sel, n_sel, *out, static_cast<cudaStream_t>(stream));
   return cudaGetLastError() == cudaSuccess ? BGT_OK : BGT_ERR_CUDA;
 }
 

@@ -537,6 +537,8 @@ int launch_l1_grad(const float *img, const float *target, long long n, float sca
                    float *loss, cudaStream_t st);
 int launch_l2_dssim_grad(const float *img, const float *gt, int n_views, const int *sizes, float lambda,
                          float scale, float *dimg, float *loss, cudaStream_t st);
+int launch_prim_metrics(int degree, const float *ctrl, int M, const float *g_ctrl, float tau_a, float tau_s,
+                        float tau_g, float *area, float *aspect, float *grad, unsigned char *flags, cudaStream_t st);
 int launch_exclusive_scan(const int *in, long long *out, int n, long long *aux, cudaStream_t st);
 int launch_bin_sort_only(const Params &p, const Work &w, cudaStream_t st);
 

@@ -46,6 +46,67 @@ def _grads_struct(grads):
     return _abi.Grads(*((grads[k].data_ptr() if grads.get(k) is not None else None) for k in GRAD_KEYS))
 
 
+def _scene_struct(sc):
+    """bgt_scene of a device scene dict (see scene_to_device)."""
+    s = _abi.Scene()
+    for k in SCENE_KEYS:
+        t = sc[k]
+        assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous(), k
+        setattr(s, k, t.data_ptr())
+    s.num_prims = int(sc["ctrl"].shape[0])
+    s.bg[:] = [float(x) for x in sc["bg"]]
+    s.attr_res = int(sc.get("attr_res", 1))
+    s.sh_degree = int(sc.get("sh_degree", 0))
+    if s.sh_degree > 0:
+        t = sc["sh"]
+        assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous(), "sh"
+        s.sh = t.data_ptr()
+    return s
+
+
+# thresholds of the splitting and pruning criteria (Sec. 3.3 and its implementation details)
+TAU_A, TAU_S, TAU_G = 3e-4, 10.0, 0.0018
+
+
+def prim_metrics(scene, g_ctrl=None, tau_a=TAU_A, tau_s=TAU_S, tau_g=TAU_G, stream=None):
+    """Area, aspect ratio, mean control-point gradient and prune / split flags
+    (bit 0 / bit 1) of every primitive of a device scene (bgt_prim_metrics)."""
+    lib = _abi.load()
+    M = int(scene["ctrl"].shape[0])
+    dev = scene["ctrl"].device
+    out = {"area": torch.empty(M, device=dev), "aspect": torch.empty(M, device=dev),
+           "flags": torch.empty(M, dtype=torch.uint8, device=dev)}
+    if g_ctrl is not None:
+        assert g_ctrl.is_contiguous() and g_ctrl.shape == scene["ctrl"].shape
+        out["grad"] = torch.empty(M, device=dev)
+    sc = _scene_struct(scene)
+    _abi.check(lib.bgt_prim_metrics(int(scene["degree"]), ctypes.byref(sc), _ptr(g_ctrl), float(tau_a), float(tau_s),
+                                    float(tau_g), _ptr(out["area"]), _ptr(out["aspect"]), _ptr(out.get("grad")),
+                                    _ptr(out["flags"]), _stream(stream)))
+    return out
+
+
+def subdivide(scene, sel, stream=None):
+    """Device scene of the 1 -> 4 midpoint split of the primitives `sel`
+    (int32 CUDA tensor): piece 4 s + p of sel[s], p = U, V, W corner, middle
+    (bgt_subdivide)."""
+    lib = _abi.load()
+    sel = sel.to(dtype=torch.int32).contiguous()
+    n = int(sel.numel())
+    out = {"degree": scene["degree"], "bg": list(scene["bg"]), "attr_res": int(scene.get("attr_res", 1)),
+           "sh_degree": int(scene.get("sh_degree", 0))}
+    for k in SCENE_KEYS + (("sh",) if out["sh_degree"] > 0 else ()):
+        t = scene[k]
+        out[k] = torch.empty((4 * n,) + tuple(t.shape[1:]), dtype=torch.float32, device=t.device)
+    if n == 0:
+        return out
+    sc = _scene_struct(scene)
+    pr = _abi.Prims(*(out[k].data_ptr() if k in out else None for k in _abi.PRIMS_KEYS))
+    _abi.check(lib.bgt_subdivide(int(scene["degree"]), ctypes.byref(sc), _ptr(sel), n, ctypes.byref(pr),
+                                 _stream(stream)))
+    return out
+
+
 def view_pixels(cams):
     return int(sum(int(c["width"]) * int(c["height"]) for c in cams))
 
@@ -99,20 +160,7 @@ class Renderer:
 
     # -- marshalling -----------------------------------------------------
     def _scene(self, sc):
-        s = _abi.Scene()
-        for k in SCENE_KEYS:
-            t = sc[k]
-            assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous(), k
-            setattr(s, k, t.data_ptr())
-        s.num_prims = int(sc["ctrl"].shape[0])
-        s.bg[:] = [float(x) for x in sc["bg"]]
-        s.attr_res = int(sc.get("attr_res", 1))
-        s.sh_degree = int(sc.get("sh_degree", 0))
-        if s.sh_degree > 0:
-            t = sc["sh"]
-            assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous(), "sh"
-            s.sh = t.data_ptr()
-        return s
+        return _scene_struct(sc)
 
     def _check(self, st):
         _abi.check(st, self.h)

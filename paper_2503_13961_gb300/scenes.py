@@ -588,3 +588,30 @@ def photo_pair(rng, width, height, noise=0.05):
     gt = np.clip(img + rng.normal(scale=noise, size=img.shape), 0.0, 1.0)
     gt[::7] = rng.uniform(0.0, 1.0, size=3)
     return img.astype(np.float32), gt.astype(np.float32)
+
+
+def mixed_shapes_scene(count, n, seed=0, curve=0.15):
+    """`count` degree-n primitives of mixed size and shape for the split and
+    prune geometry (Sec. 3.3): corner triangles with longest edge log-uniform
+    in [1e-3, 1] and height / edge log-uniform in [1e-3, 1] (from tiny to
+    sliver-like), randomly oriented and placed in [-2, 2]^3, control points
+    moved by N(0, curve * edge) (curved patches), colour control points
+    U[0, 1] each, opacity U[0.5, 1], r_b U[5e-3, 2e-2], attribute maps of
+    leg 1."""
+    rng = np.random.default_rng(seed)
+    tris = []
+    for _ in range(count):
+        e = 10.0 ** rng.uniform(-3.0, 0.0)
+        h = e * 10.0 ** rng.uniform(-3.0, 0.0)
+        t = rng.uniform(-0.5, 1.5)
+        local = np.array([[0.0, 0.0, 0.0], [e, 0.0, 0.0], [t * e, h, 0.0]])
+        q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        tris.append(local @ q.T + rng.uniform(-2.0, 2.0, size=3))
+    sc = triangles_scene(tris, n=n, seed=seed)
+    m = ncp(n)
+    edge = np.array([np.linalg.norm(np.asarray(tr)[1] - np.asarray(tr)[0]) for tr in tris])
+    noise = rng.normal(size=(count, m, 3)) * (curve * edge)[:, None, None]
+    sc["ctrl"] = np.ascontiguousarray(sc["ctrl"] + noise, np.float32)
+    sc["color"] = np.ascontiguousarray(rng.uniform(0.0, 1.0, size=(count, m, 3)), np.float32)
+    sc["r_b"] = np.ascontiguousarray(rng.uniform(5e-3, 2e-2, size=count), np.float32)
+    return sc
