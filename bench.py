@@ -5,8 +5,9 @@ Workload (the batched configuration of the metric): 20,000 degree-2
 BG-triangles (icosphere + three ellipsoids, control-point noise N(0, 0.02)),
 64 views of mixed size {256, 512, 800, 1024}^2 on a radius 3.5..5 sphere,
 boundary scale r_b = 1e-2. One step = forward of all 64 views in one batched
-call, the photometric loss of Eq. 9 (L2 + D-SSIM, lambda 0.2) and its
-gradient against a fixed target, backward to the primitive parameters. Metric: renders/s, one render = one view forward + backward.
+call, L1 loss gradient against a fixed target, backward to the primitive
+parameters (the metric's fwd+bwd step). Beside it, the training step with
+the paper's photometric loss (Eq. 9, L2 + D-SSIM, lambda 0.2) in place of L1. Metric: renders/s, one render = one view forward + backward.
 The step's inputs (~0.5 GB of pixels and pairs) exceed the 129 MB L2.
 
 Beside it: the plain single-view path on the same 64 views, one 800^2 view,
@@ -34,7 +35,7 @@ import numpy as np  # noqa: E402
 
 METRIC = "fwd+bwd renders/s at 800² (20k BG-triangles) batched vs plain; % HBM peak"
 WORKLOAD = ("20k degree-2 BG-triangles (icosphere f20 + 3 ellipsoids, noise 0.02), 64 views mixed "
-            "{256,512,800,1024}^2, radius U[3.5,5], r_b=1e-2, batched fwd + L2/D-SSIM loss (Eq. 9) + bwd")
+            "{256,512,800,1024}^2, radius U[3.5,5], r_b=1e-2, batched fwd+L1+bwd")
 
 
 def parse():
@@ -73,7 +74,6 @@ def peaks():
 SMS, FP32_LANES = 152, 128
 
 LAMBDA = 0.2      # weight of the D-SSIM term of Eq. 9
-LOSS_VIEWS = 112  # views per launch of the fused loss kernel
 # Algorithmic FP32 operations per pixel and channel of the fused loss: the
 # separable 11-tap window over five moments (2 x 5 x 11 FMA) and over three
 # SSIM partials (2 x 3 x 11 FMA), SSIM and its partials (~20), the gradient (6)
@@ -166,8 +166,6 @@ def stage_bytes(stage, c, M, ncp, V):
         # per-Gaussian / boundary gradients read, parameter gradients written
         "chain": 48 * F + 16 * Nb + 8 * F + 4 * (2 * 3 * ncp + 2) * M,
         "prep": 8 * P,
-        # image + target read, dl/dC written (3 floats each per pixel)
-        "loss": 36 * P,
     }[stage]
 
 
@@ -249,7 +247,7 @@ def run_ours(args):
         grads = {k: torch.empty_like(dev[k]) for k in R.GRAD_KEYS if k in dev}
         loss = torch.zeros(1, device="cuda")
     torch.cuda.synchronize()  # scene tensors were filled on the default stream
-    scale = 1.0 / V  # mean over views of each view's Eq. 9 loss
+    scale = 1.0 / (3 * P)
     tune_ms = None
     if args.tile:
         rd.set_tile_size(args.tile)
@@ -258,8 +256,7 @@ def run_ours(args):
 
     def step():
         rd.forward(dev, cams, images, stream=stream)
-        loss.zero_()
-        rd.l2_dssim_loss_grad(images, target, cams, LAMBDA, scale, dimg, loss, stream=stream)
+        rd.l1_loss_grad(images, target, scale, dimg, loss, stream=stream)
         rd.backward(dev, cams, dimg, grads, stream=stream)
 
     for _ in range(max(args.warmup, 3)):
@@ -294,15 +291,12 @@ def run_ours(args):
     prof_rd = R.Renderer(degree=2, max_prims=M, max_views=V, max_pixels=P, max_pairs=6 * P,
                          max_boundary_pairs=6 * P, tile_size=rd.tile_size, graph=False)
     prof_rd.set_profiling(True)
-    loss_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     stage_ms = {}
     units = {}
     nprof = max(3, min(args.steps, 8))
     for i in range(nprof + 1):
         prof_rd.forward(dev, cams, images, stream=stream)
-        loss_ev[0].record(stream)
-        prof_rd.l2_dssim_loss_grad(images, target, cams, LAMBDA, scale, dimg, loss, stream=stream)
-        loss_ev[1].record(stream)
+        prof_rd.l1_loss_grad(images, target, scale, dimg, loss, stream=stream)
         prof_rd.backward(dev, cams, dimg, grads, stream=stream)
         stream.synchronize()
         prof, kf, kb, u = prof_rd.profile()
@@ -310,12 +304,11 @@ def run_ours(args):
             continue  # warm-up
         for k, v in prof.items():
             stage_ms[k] = stage_ms.get(k, 0.0) + v / nprof
-        stage_ms["loss"] = stage_ms.get("loss", 0.0) + loss_ev[0].elapsed_time(loss_ev[1]) / nprof
         units = u
     prof_rd.sync_status(stream)
     prof_rd.close()
     del prof_rd
-    launches_per_step = kf + kb + (V + LOSS_VIEWS - 1) // LOSS_VIEWS  # + the fused loss kernel
+    launches_per_step = kf + kb + 1  # + the L1 loss-gradient kernel
 
     # end to end: parameters from pinned host memory in, gradients + loss out, every step
     host_in = {k: dev[k].cpu().pin_memory() for k in R.SCENE_KEYS}
@@ -368,11 +361,6 @@ def run_ours(args):
                 per_stage[s_name]["alg_flops"] = int(fl)
                 per_stage[s_name]["TFLOPs"] = round(fl / (s_ms * 1e-3) / 1e12, 3)
                 per_stage[s_name]["alu_frac"] = round(fl / (s_ms * 1e-3) / 1e12 / fp32_peak, 4)
-            if s_name == "loss" and s_ms > 0:
-                fl = LOSS_FLOPS_PER_VALUE * 3 * P
-                per_stage[s_name]["alg_flops"] = int(fl)
-                per_stage[s_name]["TFLOPs"] = round(fl / (s_ms * 1e-3) / 1e12, 3)
-                per_stage[s_name]["alu_frac"] = round(fl / (s_ms * 1e-3) / 1e12 / fp32_peak, 4)
         dom_bytes = stage_bytes(dom, counts, M, ncp, V)
         achieved = dom_bytes / (stage_ms[dom] * 1e-3) / 1e9
         out = {
@@ -395,8 +383,55 @@ def run_ours(args):
             "stages": per_stage,
         }
     if rank == 0:
+        out["train_step_eq9"] = run_eq9_step((rd, dev, cams, sc, stream), images, target, dimg, grads, args)
         out["split_prune"] = run_split_prune((rd, dev, cams, sc, stream), grads)
     return out, (rd, dev, cams, sc, stream)
+
+
+def run_eq9_step(rd_ctx, images, target, dimg, grads, args):
+    """The training step with the paper's photometric loss (Eq. 9, L2 +
+    D-SSIM, lambda 0.2) in place of L1: renders/s of forward + loss +
+    backward, and the loss kernel alone (CUDA events, roofline figures)."""
+    import torch
+    rd, dev, cams, _, stream = rd_ctx
+    V = len(cams)
+    P = images.shape[0]
+    loss = torch.zeros(1, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def step():
+        rd.forward(dev, cams, images, stream=stream)
+        loss.zero_()
+        rd.l2_dssim_loss_grad(images, target, cams, LAMBDA, 1.0 / V, dimg, loss, stream=stream)
+        rd.backward(dev, cams, dimg, grads, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            step()
+        steps = max(3, args.steps)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        for _ in range(3):
+            rd.l2_dssim_loss_grad(images, target, cams, LAMBDA, 1.0 / V, dimg, loss, stream=stream)
+        e0.record(stream)
+        for _ in range(10):
+            rd.l2_dssim_loss_grad(images, target, cams, LAMBDA, 1.0 / V, dimg, loss, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        lms = e0.elapsed_time(e1) / 10
+    rd.sync_status(stream)
+    peak, _, sm_mhz = peaks()
+    fp32_peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+    fl = LOSS_FLOPS_PER_VALUE * 3 * P
+    return {"value": round(V / (ms * 1e-3), 2), "unit": "renders/s", "ms_per_step": round(ms, 4),
+            "loss_kernel": {"ms": round(lms, 4), "alg_bytes": 36 * P, "alg_flops": int(fl),
+                            "TFLOPs": round(fl / (lms * 1e-3) / 1e12, 3),
+                            "alu_frac": round(fl / (lms * 1e-3) / 1e12 / fp32_peak, 4),
+                            "hbm_frac": round(36 * P / (lms * 1e-3) / 1e9 / peak, 4)}}
 
 
 def run_split_prune(rd_ctx, grads):
@@ -460,7 +495,7 @@ def run_plain(rd_ctx, args):
     def step():
         for c, (img, tgt, d) in zip(cams, bufs):
             rd.forward(dev, [c], img, stream=stream)
-            rd.l2_dssim_loss_grad(img, tgt, [c], LAMBDA, 1.0, d, stream=stream)
+            rd.l1_loss_grad(img, tgt, 1.0 / img.numel(), d, stream=stream)
             rd.backward(dev, [c], d, grads, stream=stream)
 
     step()
@@ -484,13 +519,13 @@ def run_plain(rd_ctx, args):
         img, tgt, d = bufs[i800[0]]
         for _ in range(3):
             rd.forward(dev, c800, img, stream=stream)
-            rd.l2_dssim_loss_grad(img, tgt, c800, LAMBDA, 1.0, d, stream=stream)
+            rd.l1_loss_grad(img, tgt, 1.0 / img.numel(), d, stream=stream)
             rd.backward(dev, c800, d, grads, stream=stream)
         n = 20
         e0.record(stream)
         for _ in range(n):
             rd.forward(dev, c800, img, stream=stream)
-            rd.l2_dssim_loss_grad(img, tgt, c800, LAMBDA, 1.0, d, stream=stream)
+            rd.l1_loss_grad(img, tgt, 1.0 / img.numel(), d, stream=stream)
             rd.backward(dev, c800, d, grads, stream=stream)
         e1.record(stream)
         e1.synchronize()
@@ -502,8 +537,7 @@ def run_plain(rd_ctx, args):
 
 def cpu_baseline(budget_s, rb):
     """The FP64 oracle on the host cores: whole views of the workload (forward,
-    Eq. 9 loss + backward) until the time budget is used; renders/s."""
-    from oracle import loss as oracle_loss
+    L1 loss gradient, backward) until the time budget is used; renders/s."""
     from oracle import oracle
     from paper_2503_13961_gb300 import scenes
     sc, cams = scenes.config_scene(4, r_b=rb)
@@ -515,7 +549,7 @@ def cpu_baseline(budget_s, rb):
         idm, uv, _ = oracle.raster(sc, c)
         img = oracle.render(sc, c, idm, uv)["image"]
         gt = rng.uniform(size=img.shape)
-        dl = oracle_loss.loss_grad(img, gt, LAMBDA) / len(cams)
+        dl = np.sign(img - gt) / img.size  # the L1 loss gradient of the GPU step
         oracle.backward(sc, c, dl, idm, uv)
         done += 1
         pix += c["width"] * c["height"]
@@ -523,7 +557,7 @@ def cpu_baseline(budget_s, rb):
             break
     dt = time.perf_counter() - t0
     return {"value": round(done / dt, 4), "unit": "renders/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{done} whole views ({pix} px) of the 64-view workload, smallest first, fwd + Eq. 9 loss + bwd, "
+            "sample": f"{done} whole views ({pix} px) of the 64-view workload, smallest first, fwd+L1+bwd, "
                       f"FP64, {dt:.1f} s"}
 
 
