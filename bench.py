@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--tile", type=int, default=0, help="0 = autotune")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--sh-degree", type=int, default=0,
+                    help="add view-dependent SH colour of this degree (1..3) to the scene")
+    ap.add_argument("--attr-res", type=int, default=1,
+                    help="rotation / scaling attribute maps of this leg resolution (paper: 3)")
     ap.add_argument("--workload", default="config4", choices=["config4", "view800", "views1024x4"],
                     help="view800: one 800^2 view of the same scene (small case for profilers); "
                          "views1024x4: four 1024^2 views (inputs larger than L2, a few GB on the device)")
@@ -207,9 +211,13 @@ def roofline_entry(dom, stage_ms, units, achieved_gbs, dom_bytes, peak, peak_kin
             "alg_bytes_per_launch": int(dom_bytes), "ms_per_launch": round(ms, 4)}
 
 
-def build_workload(seed_views, rb, workload="config4"):
+def build_workload(seed_views, rb, workload="config4", sh_degree=0, attr_res=1):
     from paper_2503_13961_gb300 import scenes
     sc, cams = scenes.config_scene(4, r_b=rb)
+    if attr_res > 1:
+        sc = scenes.with_attribute_maps(sc, attr_res)
+    if sh_degree > 0:
+        sc = scenes.with_sh(sc, sh_degree)
     if workload == "view800":
         return sc, [c for c in cams if c["width"] == 800][:1]
     if workload == "views1024x4":
@@ -231,7 +239,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    sc, cams = build_workload(rank, args.rb, args.workload)
+    sc, cams = build_workload(rank, args.rb, args.workload, args.sh_degree, args.attr_res)
     V = len(cams)
     P = sum(c["width"] * c["height"] for c in cams)
     M, ncp = sc["ctrl"].shape[0], sc["ctrl"].shape[1]
@@ -371,6 +379,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD if args.workload == "config4" else
                        ("one 800^2 view of: " if args.workload == "view800" else "four 1024^2 views of: ") + WORKLOAD,
                        "views": V, "pixels": P, "prims": M, "degree": 2,
+                       "sh_degree": args.sh_degree, "attr_res": args.attr_res,
                        "tile": rd.tile_size, "tile_autotune_ms": tune_ms, "graph": True,
                        "counts": {k: int(v) for k, v in counts.items()},
                        "l2": "inputs larger than L2 (no flush needed)", "parallelism": f"replicas x{world}"},
@@ -535,12 +544,16 @@ def run_plain(rd_ctx, args):
     return plain, v800
 
 
-def cpu_baseline(budget_s, rb):
+def cpu_baseline(budget_s, rb, sh_degree=0, attr_res=1):
     """The FP64 oracle on the host cores: whole views of the workload (forward,
     L1 loss gradient, backward) until the time budget is used; renders/s."""
     from oracle import oracle
     from paper_2503_13961_gb300 import scenes
     sc, cams = scenes.config_scene(4, r_b=rb)
+    if attr_res > 1:
+        sc = scenes.with_attribute_maps(sc, attr_res)
+    if sh_degree > 0:
+        sc = scenes.with_sh(sc, sh_degree)
     order = sorted(range(len(cams)), key=lambda i: cams[i]["width"])
     rng = np.random.default_rng(0)
     done, t0, pix = 0, time.perf_counter(), 0
@@ -573,9 +586,9 @@ def main():
         ms_steps = []
         base = None
         for _ in range(args.warmup):
-            cpu_baseline(1.0, args.rb)
+            cpu_baseline(1.0, args.rb, args.sh_degree, args.attr_res)
         for _ in range(args.steps):
-            base = cpu_baseline(args.cpu_seconds / max(args.steps, 1), args.rb)
+            base = cpu_baseline(args.cpu_seconds / max(args.steps, 1), args.rb, args.sh_degree, args.attr_res)
             ms_steps.append(base["value"])
         val = statistics.mean(ms_steps)
         print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": "renders/s",
@@ -595,7 +608,7 @@ def main():
             out["batched_over_plain"] = round(out["value"] / plain["value"], 3)
             out["view_800"] = v800
         if world == 1:
-            out["cpu_baseline"] = cpu_baseline(args.cpu_seconds, args.rb)
+            out["cpu_baseline"] = cpu_baseline(args.cpu_seconds, args.rb, args.sh_degree, args.attr_res)
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist
