@@ -336,6 +336,27 @@ def render(renderer, scene, cams):
                            scene["log_scale"], scene["quat"], sh)
 
 
+class _LossFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, renderer, cams, lam, images, target):
+        loss = images.new_zeros(1)
+        d = renderer.l2_dssim_loss_grad(images.contiguous(), target.contiguous(), cams, lam, 1.0, loss=loss)
+        ctx.save_for_backward(d)
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, g):
+        (d,) = ctx.saved_tensors
+        return None, None, None, d * g, None
+
+
+def photometric_loss(renderer, images, target, cams, lam=0.2):
+    """Differentiable Eq. 9 loss, (1 - lam) L2 + lam (1 - SSIM) summed over the
+    views of `images` (the forward's layout); its gradient with respect to
+    `images` comes from the same fused kernel call as the value."""
+    return _LossFn.apply(renderer, cams, float(lam), images, target)
+
+
 def split_views(images, cams):
     """Packed images [sum W*H, 3] -> list of [H, W, 3] views."""
     out, off = [], 0

@@ -171,3 +171,28 @@ def test_full_size_batch_sampled_against_the_oracle(scenes):
     per_view = sum(_run(rd, [pairs[v]], [cams[v]], 0.2)[1] for v in range(len(cams))) / len(cams)
     assert abs(total - per_view) <= 1e-5 * per_view
     rd.close()
+
+
+def test_autograd_loss_feeds_the_differentiable_render(scenes):
+    # render() + photometric_loss() + .backward() gives the gradients of the
+    # explicit calls: forward, loss gradient, backward
+    import torch
+    from paper_2503_13961_gb300 import render as R
+    from tests.gpu_util import make_renderer
+    sc, cams = scenes.config_scene(1)
+    rd = make_renderer(sc, cams)
+    dev = R.scene_to_device(sc)
+    leaf = {k: (v.clone().requires_grad_(True) if torch.is_tensor(v) else v) for k, v in dev.items()}
+    img = R.render(rd, leaf, cams)
+    target = torch.rand(img.shape, device="cuda", generator=torch.Generator(device="cuda").manual_seed(5))
+    loss = R.photometric_loss(rd, img, target, cams)
+    loss.backward()
+    img2 = rd.forward(dev, cams)
+    d = rd.l2_dssim_loss_grad(img2, target, cams)
+    g = rd.backward(dev, cams, d)
+    torch.cuda.synchronize()
+    for k in ("ctrl", "color", "opacity", "r_b"):
+        a, b = leaf[k].grad, g[k]
+        assert torch.allclose(a, b, rtol=1e-5, atol=1e-7 * float(b.abs().max())), k
+    assert float(g["ctrl"].abs().max()) > 0
+    rd.close()
