@@ -25,6 +25,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -111,8 +112,8 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else f"/tmp/bgt_clocks_{os.getpid()}.csv"
+        self.path = os.environ.get("BGT_CLOCKS_CSV") or os.path.join(
+            tempfile.gettempdir(), f"bgt_clocks_{os.getpid()}_{index}.csv")
 
     def start(self):
         try:
