@@ -237,3 +237,43 @@ def test_sh_colour_gradients_match_oracle(oracle, scenes, D):
     for k in ("ctrl", "color", "opacity", "r_b", "sh"):
         assert got[k].shape == ref[k].shape, k
         _assert_close(got[k], ref[k], k)
+
+
+def test_full_size_batched_backward_equals_the_plain_path(scenes):
+    # the benchmark's launch configuration (64 views of mixed size in one
+    # graph-captured call, tile 16): its gradients are the sum over the views
+    # of the plain single-view path, which the crops above check against the
+    # oracle; views are independent given the parameters, so only the FP32
+    # summation order differs
+    import torch
+    from paper_2503_13961_gb300 import render as R
+    sc, cams = scenes.config_scene(4)
+    P = sum(c["width"] * c["height"] for c in cams)
+    rd = make_renderer(sc, cams, graph=True, tile=16)
+    dev = R.scene_to_device(sc)
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    dl = torch.randn((P, 3), device="cuda", generator=gen) / P
+    rd.forward(dev, cams)
+    g_all = rd.backward(dev, cams, dl)
+    rd.sync_status()
+    Pmax = max(c["width"] * c["height"] for c in cams)
+    one = R.Renderer(degree=2, max_prims=sc["ctrl"].shape[0], max_views=1, max_pixels=Pmax,
+                     max_pairs=8 * Pmax, max_boundary_pairs=8 * Pmax, tile_size=16)
+    acc = {k: torch.zeros_like(v) for k, v in g_all.items()}
+    off = 0
+    for c in cams:
+        n = c["width"] * c["height"]
+        one.forward(dev, [c])
+        g = one.backward(dev, [c], dl[off:off + n].contiguous())
+        for k in acc:
+            acc[k] += g[k]
+        off += n
+    one.sync_status()
+    torch.cuda.synchronize()
+    for k in ("ctrl", "color", "opacity", "r_b"):
+        a, b = g_all[k].double().cpu().numpy(), acc[k].double().cpu().numpy()
+        assert np.abs(b).max() > 0, k
+        rel = grad_rel(a, b)
+        assert rel < 1e-4, (k, rel)
+    rd.close()
+    one.close()
