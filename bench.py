@@ -66,6 +66,20 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(x, device):
+    """The largest of every rank's x (the job's time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, views_per_rank, steps, ms):
+    """Whole-job renders/s: every rank renders its own views (weak scaling)."""
+    return world * views_per_rank * steps / (ms / 1e3)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -288,12 +302,10 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     torch.cuda.synchronize()
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, "cuda")
         dist.barrier()
     rd.sync_status(stream)
-    value = world * V * args.steps / (ms / 1e3)
+    value = job_value(world, V, args.steps, ms)
 
     # per-stage device time of the same step: a second handle (no graph, same
     # tile size) records CUDA events between the stages on the same stream
@@ -347,10 +359,8 @@ def run_ours(args):
         wall = time.perf_counter() - t0
     e2e_ms = max(e0.elapsed_time(e1), wall * 1e3)
     if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * V * args.steps / (e2e_ms / 1e3)
+        e2e_ms = max_over_ranks(e2e_ms, "cuda")
+    e2e_value = job_value(world, V, args.steps, e2e_ms)
     rd.sync_status(stream)
 
     out = None
