@@ -196,3 +196,20 @@ def test_autograd_loss_feeds_the_differentiable_render(scenes):
         assert torch.allclose(a, b, rtol=1e-5, atol=1e-7 * float(b.abs().max())), k
     assert float(g["ctrl"].abs().max()) > 0
     rd.close()
+
+
+def test_more_views_than_one_launch_holds():
+    # 130 small views: the view table of one launch holds 112, so the call
+    # takes two launches; every view must still match the oracle
+    from oracle import loss as L
+    rng = np.random.default_rng(9)
+    sizes = [(int(w), int(h)) for w, h in zip(rng.integers(1, 40, 130), rng.integers(1, 40, 130))]
+    pairs, cams = _views(9, sizes)
+    rd = _renderer()
+    grads, total = _run(rd, pairs, cams, 0.2)
+    want = 0.0
+    for (img, gt), g in zip(pairs, grads):
+        want += L.loss(img, gt)
+        _check_grad(g, L.loss_grad(img, gt))
+    assert abs(total - want) <= LOSS_TOL * want
+    rd.close()
