@@ -77,7 +77,9 @@ def prim_metrics(scene, g_ctrl=None, tau_a=TAU_A, tau_s=TAU_S, tau_g=TAU_G, stre
     out = {"area": torch.empty(M, device=dev), "aspect": torch.empty(M, device=dev),
            "flags": torch.empty(M, dtype=torch.uint8, device=dev)}
     if g_ctrl is not None:
-        assert g_ctrl.is_contiguous() and g_ctrl.shape == scene["ctrl"].shape
+        if not (g_ctrl.is_cuda and g_ctrl.dtype == torch.float32 and g_ctrl.is_contiguous()
+                and g_ctrl.shape == scene["ctrl"].shape):
+            raise ValueError("g_ctrl must be a contiguous float32 CUDA tensor shaped like scene['ctrl']")
         out["grad"] = torch.empty(M, device=dev)
     sc = _scene_struct(scene)
     _abi.check(lib.bgt_prim_metrics(int(scene["degree"]), ctypes.byref(sc), _ptr(g_ctrl), float(tau_a), float(tau_s),
@@ -91,7 +93,7 @@ def subdivide(scene, sel, stream=None):
     (int32 CUDA tensor): piece 4 s + p of sel[s], p = U, V, W corner, middle
     (bgt_subdivide)."""
     lib = _abi.load()
-    sel = sel.to(dtype=torch.int32).contiguous()
+    sel = torch.as_tensor(sel).to(device=scene["ctrl"].device, dtype=torch.int32).contiguous()
     n = int(sel.numel())
     out = {"degree": scene["degree"], "bg": list(scene["bg"]), "attr_res": int(scene.get("attr_res", 1)),
            "sh_degree": int(scene.get("sh_degree", 0))}
