@@ -46,6 +46,18 @@ def _grads_struct(grads):
     return _abi.Grads(*((grads[k].data_ptr() if grads.get(k) is not None else None) for k in GRAD_KEYS))
 
 
+def _device_f32(t, name, numel=None):
+    """A contiguous float32 CUDA tensor (the library writes or reads it on the
+    device), of `numel` elements if given; else ValueError."""
+    if t is None:
+        return None
+    if not (torch.is_tensor(t) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must hold {numel} floats, not {t.numel()}")
+    return t
+
+
 def _scene_struct(sc):
     """bgt_scene of a device scene dict (see scene_to_device)."""
     s = _abi.Scene()
@@ -174,6 +186,7 @@ class Renderer:
         self._last_pixels = P
         if images is None:
             images = torch.empty((P, 3), dtype=torch.float32, device=scene["ctrl"].device)
+        _device_f32(images, "images", 3 * P)
         cam_arr = _abi.camera_array(cams)
         sc = self._scene(scene)
         self._check(self.lib.bgt_render_fwd(self.h, ctypes.byref(sc), cam_arr, len(cams), _ptr(images),
@@ -185,7 +198,10 @@ class Renderer:
         forward, given dl/dimages; keys missing from `grads` are not computed."""
         if grads is None:
             grads = {k: torch.empty_like(scene[k]) for k in GRAD_KEYS if scene.get(k) is not None}
-        d_images = d_images.contiguous()
+        d_images = _device_f32(d_images.contiguous(), "d_images", 3 * view_pixels(cams))
+        for k, t in grads.items():
+            if t is not None:
+                _device_f32(t, f"grads[{k!r}]", scene[k].numel())
         g = _grads_struct(grads)
         sc = self._scene(scene)
         cam_arr = _abi.camera_array(cams)
@@ -242,6 +258,9 @@ class Renderer:
     def l1_loss_grad(self, images, target, scale, d_images=None, loss=None, stream=None):
         if d_images is None:
             d_images = torch.empty_like(images)
+        for name, t in (("images", images), ("target", target), ("d_images", d_images)):
+            _device_f32(t, name, images.numel())
+        _device_f32(loss, "loss", 1)
         _abi.check(self.lib.bgt_l1_loss_grad(_ptr(images), _ptr(target), images.numel(), float(scale),
                                              _ptr(d_images), _ptr(loss), _stream(stream)))
         return d_images
@@ -253,8 +272,9 @@ class Renderer:
             d_images = torch.empty_like(images)
         sizes = (ctypes.c_int * (2 * len(cams)))(*[int(x) for c in cams for x in (c["width"], c["height"])])
         n = 3 * sum(c["width"] * c["height"] for c in cams)
-        if images.numel() != n or target.numel() != n or d_images.numel() != n:
-            raise ValueError("images, target and d_images must hold the views of `cams`")
+        for name, t in (("images", images), ("target", target), ("d_images", d_images)):
+            _device_f32(t, name, n)
+        _device_f32(loss, "loss", 1)
         _abi.check(self.lib.bgt_l2_dssim_loss_grad(_ptr(images), _ptr(target), len(cams), sizes, float(lam),
                                                    float(scale), _ptr(d_images), _ptr(loss), _stream(stream)))
         return d_images

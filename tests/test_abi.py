@@ -65,3 +65,15 @@ def test_product_path_has_no_oracle_dependency():
         if f.endswith((".py", ".cu", ".cuh", ".h")):
             src = open(f).read()
             assert not re.search(r"(from|import)\s+oracle|bgt_oracle|bgto_", src), f
+
+
+def test_binding_rejects_host_tensors_before_any_call():
+    # the library reads and writes these through device pointers: a host
+    # tensor (or a wrong dtype, layout or size) is refused in Python first
+    import pytest
+    import torch
+    from paper_2503_13961_gb300 import render as R
+    for t in (torch.zeros(6), torch.zeros(6, dtype=torch.float64), torch.zeros(3, 2).t()):
+        with pytest.raises(ValueError):
+            R._device_f32(t, "x")
+    assert R._device_f32(None, "x") is None
