@@ -7,7 +7,10 @@
   * the area estimate from four planar triangles and the bounding-box aspect
     ratio that the pruning criteria threshold (tau_a = 3e-4, tau_s = 10);
   * the average control-point gradient that the split criterion thresholds
-    (tau_g = 0.0018).
+    (tau_g = 0.0018);
+  * the visibility measures of the other two pruning criteria: in how many
+    training views a primitive owns pixels of I_id (tau_v = 0.08 of them)
+    and how much of its visibility texture is seen (tau_r = 0.4).
 
 TEST INFRASTRUCTURE: imported only by tests/. The CUDA library never imports
 it, and it shares no code with it.
@@ -179,3 +182,42 @@ def decisions(ctrl, n, g_ctrl=None, tau_a=TAU_A, tau_s=TAU_S, tau_g=TAU_G):
     prune = area(ctrl, n) < tau_a or aspect(ctrl, n) > tau_s
     split = g_ctrl is not None and avg_grad(g_ctrl) > tau_g
     return prune, split
+
+
+TAU_V = 0.08
+TAU_R = 0.4
+
+
+def visibility(rasters, M, tess_level=8):
+    """Visibility measures of the pruning criteria from the raster of each
+    training view: rasters = [(I_id [H, W], key [H, W]), ...], key the depth
+    key whose low 32 bits are prim * 2 L^2 + sub-triangle id.
+
+    Readings: a primitive is visible in a view when it owns at least one
+    pixel of I_id there (view_count = number of such views); its visibility
+    texture has one cell per flat triangle of the level-L lattice (the L^2
+    sub-triangles of the raster, id 2 (a L + b) + down), and a cell is
+    visible when the primitive owns a pixel through that flat triangle in
+    any view. Returns (view_count [M] int, cells: list of M sets of ids)."""
+    L = tess_level
+    nsub = 2 * L * L
+    count = np.zeros(M, np.int64)
+    cells = [set() for _ in range(M)]
+    for idm, key in rasters:
+        fg = idm >= 0
+        ids = idm[fg].astype(np.int64)
+        sub = (key[fg].astype(np.uint64) & np.uint64(0xFFFFFFFF)).astype(np.int64) - ids * nsub
+        for m in np.unique(ids):
+            count[m] += 1
+        for m, s in zip(ids.tolist(), sub.tolist()):
+            cells[m].add(s)
+    return count, cells
+
+
+def occluded(view_count, n_views, cells, tess_level=8, tau_v=TAU_V, tau_r=TAU_R):
+    """(seen in too few views, too little of the texture visible) per
+    primitive: view_count / n_views < tau_v, |cells| / L^2 < tau_r."""
+    L2 = tess_level * tess_level
+    by_views = [n_views > 0 and c / n_views < tau_v for c in view_count]
+    by_area = [len(s) / L2 < tau_r for s in cells]
+    return by_views, by_area
