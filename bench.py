@@ -455,10 +455,11 @@ def run_eq9_step(rd_ctx, images, target, dimg, grads, args):
 
 
 def run_split_prune(rd_ctx, grads):
-    """Splitting / pruning geometry on the workload's primitives (Sec. 3.3):
-    the per-primitive measures and flags with the step's control-point
-    gradients, and the 1 -> 4 split of every primitive; CUDA-event times and
-    the HBM fraction of their algorithmic bytes."""
+    """Splitting / pruning on the workload's primitives (Sec. 3.3): the
+    visibility measures of the step's views, the per-primitive measures and
+    flags with the step's control-point gradients, and the 1 -> 4 split of
+    every primitive; CUDA-event times and the HBM fraction of their
+    algorithmic bytes."""
     import torch
     from paper_2503_13961_gb300 import render as R
     _, dev, _, sc, stream = rd_ctx
@@ -471,7 +472,13 @@ def run_split_prune(rd_ctx, grads):
     # algorithmic bytes: metrics read ctrl + gradient and write 13 B per primitive;
     # the split reads the parent's control points, colours and attributes and
     # writes four pieces
+    rd = rd_ctx[0]
+    P = sum(c["width"] * c["height"] for c in rd_ctx[2])
+    vc = torch.zeros(M, dtype=torch.int32, device="cuda")
+    cm = torch.zeros((M, 2), dtype=torch.int64, device="cuda")
     work = {
+        # the last forward's I_id and depth keys read, per-primitive counts and masks updated
+        "visibility": (lambda: rd.visibility(M, vc, cm, stream=stream), 12 * P + 24 * M),
         "prim_metrics": (lambda: R.prim_metrics(dev, grads["ctrl"], stream=stream), M * (24 * ncp + 13)),
         "subdivide": (lambda: R.subdivide(dev, sel, stream=stream),
                       M * (4 + 24 * ncp + 8 + 28 * T) + 4 * M * (24 * ncp + 8 + 28 * T)),

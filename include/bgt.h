@@ -247,12 +247,31 @@ typedef struct {
  *             ([M][Ncp][3] device, e.g. bgt_grads.ctrl; may be NULL);
  *   flags[m]  bit 0 = prune (area < tau_a or aspect > tau_s; the paper uses
  *             3e-4 and 10), bit 1 = split (grad > tau_g, the paper's 0.0018;
- *             never set without g_ctrl).
+ *             never set without g_ctrl), bit 2 = occluded in the views
+ *             (view_count[m] < tau_v n_views, the paper's 0.08), bit 3 =
+ *             occluded in its visibility texture (set bits of its cell_mask
+ *             words < tau_r L^2, the paper's 0.4, L = tess_level); bits 2 and
+ *             3 need view_count / cell_mask (from bgt_visibility, device).
  * Each output (device, M entries) may be NULL. BGT_ERR_INVALID_ARG for a
- * degree outside 1..4, a NULL scene or a NULL ctrl with M > 0. */
+ * degree outside 1..4, a NULL scene or ctrl with M > 0, n_views < 0 or a
+ * tess_level outside 1..16 with a cell_mask. */
 bgt_status bgt_prim_metrics(int degree, const bgt_scene *scene, const float *g_ctrl, float tau_a, float tau_s,
-                            float tau_g, float *area, float *aspect, float *grad, unsigned char *flags,
-                            void *stream);
+                            float tau_g, const int *view_count, int n_views, const unsigned long long *cell_mask,
+                            int tess_level, float tau_v, float tau_r, float *area, float *aspect, float *grad,
+                            unsigned char *flags, void *stream);
+
+/* Visibility measures of the pruning criteria (Sec. 3.3 "Splitting and
+ * Pruning"), from the raster of the last bgt_render_fwd on the handle:
+ * view_count[m] += the number of its views in which primitive m owns at
+ * least one pixel of I_id; cell_mask[m * words + s / 64] |= 1 << (s % 64) for
+ * every flat triangle s = 2 (a L + b) + down of its level-L lattice (the
+ * raster's sub-triangles, L = tess_level) through which it owns a pixel in
+ * one of the views: its visibility texture, words = ceil(2 L^2 / 64). Device
+ * arrays of num_prims (cell_mask: num_prims * words) entries, accumulated
+ * across calls, so that views rendered in several forwards add up (the
+ * caller zeroes them when a tracking period starts); either may be NULL.
+ * BGT_ERR_STATE without a forward; BGT_ERR_CUDA if a launch fails. */
+bgt_status bgt_visibility(bgt_handle *h, int *view_count, unsigned long long *cell_mask, void *stream);
 
 /* The 1 -> 4 split of Sec. 3.3 ("Splitting and Pruning"): each primitive
  * sel[s] (device int array of n_sel indices into scene) becomes the pieces

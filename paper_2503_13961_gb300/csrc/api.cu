@@ -83,6 +83,7 @@ void carve(bgt_handle *h, char *base, size_t *total) {
   h->d_offs = c.take<int>(2 * (h->Vcap + 1));
   w.zbuf = c.take<unsigned long long>(P);
   w.pid = c.take<int>(P);
+  w.vis_seen = c.take<unsigned long long>(h->Mcap);
   w.puv = c.take<float2>(P);
   w.pix_gidx = c.take<int>(P);
   w.T_final = c.take<float>(P);
@@ -625,13 +626,27 @@ bgt_status bgt_l2_dssim_loss_grad(const float *images, const float *target, int 
 }
 
 bgt_status bgt_prim_metrics(int degree, const bgt_scene *scene, const float *g_ctrl, float tau_a, float tau_s,
-                            float tau_g, float *area, float *aspect, float *grad, unsigned char *flags,
-                            void *stream) {
+                            float tau_g, const int *view_count, int n_views, const unsigned long long *cell_mask,
+                            int tess_level, float tau_v, float tau_r, float *area, float *aspect, float *grad,
+                            unsigned char *flags, void *stream) {
   if (degree < 1 || degree > bgt::kMaxDegree || !scene || scene->num_prims < 0) return BGT_ERR_INVALID_ARG;
   if (scene->num_prims > 0 && !scene->ctrl) return BGT_ERR_INVALID_ARG;
-  bgt::launch_prim_metrics(degree, scene->ctrl, scene->num_prims, g_ctrl, tau_a, tau_s, tau_g, area, aspect, grad,
-                           flags, static_cast<cudaStream_t>(stream));
+  if (n_views < 0 || (cell_mask && (tess_level < 1 || tess_level > bgt::kMaxTess))) return BGT_ERR_INVALID_ARG;
+  bgt::launch_prim_metrics(degree, scene->ctrl, scene->num_prims, g_ctrl, tau_a, tau_s, tau_g, view_count, n_views,
+                           cell_mask, cell_mask ? tess_level : 1, tau_v, tau_r, area, aspect, grad, flags,
+                           static_cast<cudaStream_t>(stream));
   return cudaGetLastError() == cudaSuccess ? BGT_OK : BGT_ERR_CUDA;
+}
+
+bgt_status bgt_visibility(bgt_handle *h, int *view_count, unsigned long long *cell_mask, void *stream) {
+  if (!h) return BGT_ERR_INVALID_ARG;
+  if (!h->fwd_valid) return fail(h, BGT_ERR_STATE, "visibility without a forward");
+  const bgt::Params &p = h->last;
+  std::vector<int> off(p.V + 1, 0);
+  for (int v = 0; v < p.V; v++) off[v + 1] = off[v] + h->fwd_shapes[2 * v] * h->fwd_shapes[2 * v + 1];
+  bgt::launch_visibility(p, h->w, off.data(), view_count, cell_mask, static_cast<cudaStream_t>(stream));
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? BGT_OK : cuda_fail(h, e, "visibility");
 }
 
 bgt_status bgt_subdivide(int degree, const bgt_scene *scene, const int *sel, int n_sel, const bgt_prims *out,

@@ -86,6 +86,7 @@ struct Work {
   const int *view_tile_off;   // V + 1 entries
   unsigned long long *zbuf;   // [P] depth key of the nearest flat triangle
   int *pid;                   // [P] I_id, -1 background
+  unsigned long long *vis_seen;  // [M] views (bit v - v0) a primitive owns pixels in, for the visibility measures
   float2 *puv;                // [P] I_uv (u, v)
   int *pix_gidx;              // [P] gaussian index of a foreground pixel, else -1
   int *blk_cnt;               // [2][nblk] per-block foreground / boundary counts
@@ -538,7 +539,11 @@ int launch_l1_grad(const float *img, const float *target, long long n, float sca
 int launch_l2_dssim_grad(const float *img, const float *gt, int n_views, const int *sizes, float lambda,
                          float scale, float *dimg, float *loss, cudaStream_t st);
 int launch_prim_metrics(int degree, const float *ctrl, int M, const float *g_ctrl, float tau_a, float tau_s,
-                        float tau_g, float *area, float *aspect, float *grad, unsigned char *flags, cudaStream_t st);
+                        float tau_g, const int *view_count, int n_views, const unsigned long long *cell_mask,
+                        int tess_level, float tau_v, float tau_r, float *area, float *aspect, float *grad,
+                        unsigned char *flags, cudaStream_t st);
+int launch_visibility(const Params &p, const Work &w, const int *view_off, int *view_count,
+                      unsigned long long *cell_mask, cudaStream_t st);
 int launch_exclusive_scan(const int *in, long long *out, int n, long long *aux, cudaStream_t st);
 int launch_bin_sort_only(const Params &p, const Work &w, cudaStream_t st);
 

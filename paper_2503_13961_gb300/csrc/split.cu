@@ -1,7 +1,9 @@
-// Geometry of splitting and pruning (Sec. 3.3 "Splitting and Pruning"):
-// the per-primitive area / aspect / gradient measures that the criteria
-// threshold, and the exact 1 -> 4 midpoint subdivision of the selected
-// primitives.
+// Splitting and pruning (Sec. 3.3 "Splitting and Pruning"): the
+// per-primitive area / aspect / gradient measures that the criteria
+// threshold, the visibility measures (views in which a primitive owns pixels
+// of I_id, and its visibility texture: the flat triangles of its lattice it
+// is seen through) gathered from a forward's raster, and the exact 1 -> 4
+// midpoint subdivision of the selected primitives.
 //
 // A piece of the split is the parent patch restricted to a sub-triangle
 // (A, B, C) of its parameter domain; its control point q_ijk is the polar
@@ -155,6 +157,11 @@ struct MetricArgs {
   const float *ctrl, *g_ctrl;
   int M;
   float tau_a, tau_s, tau_g;
+  const int *view_count;
+  int n_views;
+  const unsigned long long *cell_mask;
+  int words, cells;  // mask words per primitive, lattice cells L^2
+  float tau_v, tau_r;
   float *area, *aspect, *grad;
   unsigned char *flags;
 };
@@ -244,9 +251,54 @@ __global__ void __launch_bounds__(256) k_prim_metrics(const MetricArgs s) {
   if (s.area) s.area[m] = area;
   if (s.aspect) s.aspect[m] = aspect;
   if (s.grad && s.g_ctrl) s.grad[m] = grad;
-  if (s.flags)
-    s.flags[m] = (unsigned char)((area < s.tau_a || aspect > s.tau_s ? 1 : 0) |
-                                 (s.g_ctrl && grad > s.tau_g ? 2 : 0));
+  if (s.flags) {
+    unsigned char f = (unsigned char)((area < s.tau_a || aspect > s.tau_s ? 1 : 0) |
+                                      (s.g_ctrl && grad > s.tau_g ? 2 : 0));
+    // visibility ratios compared in FP64: integer counts over integer totals
+    if (s.view_count && s.n_views > 0 && (double)s.view_count[m] < (double)s.tau_v * (double)s.n_views) f |= 4;
+    if (s.cell_mask) {
+      int seen = 0;
+      for (int k = 0; k < s.words; ++k) seen += __popcll(s.cell_mask[(size_t)m * s.words + k]);
+      if ((double)seen < (double)s.tau_r * (double)s.cells) f |= 8;
+    }
+    s.flags[m] = f;
+  }
+}
+
+// Visibility measures from the raster of views [v0, v0 + 64): per foreground
+// pixel, the bit of the flat triangle it is seen through (the low 32 bits of
+// its depth key are prim * nsub + sub-triangle) in cell_mask[prim], and bit
+// v - v0 in seen[prim]. A bit already set is read, not written again.
+__global__ void __launch_bounds__(256) k_vis_pixels(const int *pid, const unsigned long long *zbuf,
+                                                    const int *view_off, int V, int pix0, int pix1, int v0,
+                                                    int nsub, int words, unsigned long long *cell_mask,
+                                                    unsigned long long *seen) {
+  const int pix = pix0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= pix1) return;
+  const int id = pid[pix];
+  if (id < 0) return;
+  if (cell_mask) {
+    const int sub = (int)((unsigned)(zbuf[pix] & 0xffffffffull) - (unsigned)id * (unsigned)nsub);
+    unsigned long long *c = cell_mask + (size_t)id * words + (sub >> 6);
+    const unsigned long long bit = 1ull << (sub & 63);
+    if (!(*c & bit)) atomicOr(c, bit);
+  }
+  if (seen) {
+    const int view = find_view(view_off, V, pix);
+    const unsigned long long bit = 1ull << (view - v0);
+    if (!(seen[id] & bit)) atomicOr(seen + id, bit);
+  }
+}
+
+// view_count[m] += the views of the group primitive m was seen in; clears seen
+__global__ void __launch_bounds__(256) k_vis_count(int M, unsigned long long *seen, int *view_count) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  const unsigned long long v = seen[m];
+  if (v) {
+    view_count[m] += __popcll(v);
+    seen[m] = 0ull;
+  }
 }
 
 }  // namespace
@@ -277,12 +329,41 @@ int launch_subdivide(int degree, const bgt_scene &sc, const int *sel, int n_sel,
 }
 
 int launch_prim_metrics(int degree, const float *ctrl, int M, const float *g_ctrl, float tau_a, float tau_s,
-                        float tau_g, float *area, float *aspect, float *grad, unsigned char *flags,
-                        cudaStream_t st) {
+                        float tau_g, const int *view_count, int n_views, const unsigned long long *cell_mask,
+                        int tess_level, float tau_v, float tau_r, float *area, float *aspect, float *grad,
+                        unsigned char *flags, cudaStream_t st) {
   if (M <= 0) return 0;
-  MetricArgs s{ctrl, g_ctrl, M, tau_a, tau_s, tau_g, area, aspect, grad, flags};
+  const int nsub = 2 * tess_level * tess_level;
+  MetricArgs s{ctrl, g_ctrl, M, tau_a, tau_s, tau_g, view_count, n_views, cell_mask, (nsub + 63) / 64,
+               tess_level * tess_level, tau_v, tau_r, area, aspect, grad, flags};
   dispatch_degree(degree, [&](auto d) { k_prim_metrics<decltype(d)::value><<<(M + 255) / 256, 256, 0, st>>>(s); });
   return 1;
+}
+
+int launch_visibility(const Params &p, const Work &w, const int *view_off, int *view_count,
+                      unsigned long long *cell_mask, cudaStream_t st) {
+  // view_off: host copy of the forward's pixel offsets per view (V + 1)
+  const int nsub = 2 * p.L * p.L, words = (nsub + 63) / 64;
+  int launches = 0;
+  if (view_count && p.M > 0) {
+    cudaMemsetAsync(w.vis_seen, 0, sizeof(unsigned long long) * (size_t)p.M, st);
+    launches++;
+  }
+  for (int v0 = 0; v0 < p.V; v0 += 64) {
+    const int v1 = v0 + 64 < p.V ? v0 + 64 : p.V;
+    const int pix0 = view_off[v0], pix1 = view_off[v1];
+    if (pix1 > pix0) {
+      k_vis_pixels<<<(pix1 - pix0 + 255) / 256, 256, 0, st>>>(w.pid, w.zbuf, w.view_pix_off, p.V, pix0, pix1, v0,
+                                                             nsub, words, cell_mask,
+                                                             view_count ? w.vis_seen : nullptr);
+      launches++;
+    }
+    if (view_count && p.M > 0) {
+      k_vis_count<<<(p.M + 255) / 256, 256, 0, st>>>(p.M, w.vis_seen, view_count);
+      launches++;
+    }
+  }
+  return launches;
 }
 
 }  // namespace bgt

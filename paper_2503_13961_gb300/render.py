@@ -80,9 +80,16 @@ def _scene_struct(sc):
 TAU_A, TAU_S, TAU_G = 3e-4, 10.0, 0.0018
 
 
-def prim_metrics(scene, g_ctrl=None, tau_a=TAU_A, tau_s=TAU_S, tau_g=TAU_G, stream=None):
-    """Area, aspect ratio, mean control-point gradient and prune / split flags
-    (bit 0 / bit 1) of every primitive of a device scene (bgt_prim_metrics)."""
+TAU_V, TAU_R = 0.08, 0.4
+
+
+def prim_metrics(scene, g_ctrl=None, tau_a=TAU_A, tau_s=TAU_S, tau_g=TAU_G, view_count=None, n_views=0,
+                 cell_mask=None, tess_level=8, tau_v=TAU_V, tau_r=TAU_R, stream=None):
+    """Area, aspect ratio, mean control-point gradient and the flags of the
+    splitting and pruning criteria (bit 0 prune by area / aspect, bit 1
+    split, bit 2 occluded in the views, bit 3 occluded in the visibility
+    texture) of every primitive of a device scene (bgt_prim_metrics);
+    view_count / cell_mask come from Renderer.visibility over n_views views."""
     lib = _abi.load()
     M = int(scene["ctrl"].shape[0])
     dev = scene["ctrl"].device
@@ -93,10 +100,14 @@ def prim_metrics(scene, g_ctrl=None, tau_a=TAU_A, tau_s=TAU_S, tau_g=TAU_G, stre
                 and g_ctrl.shape == scene["ctrl"].shape):
             raise ValueError("g_ctrl must be a contiguous float32 CUDA tensor shaped like scene['ctrl']")
         out["grad"] = torch.empty(M, device=dev)
+    for name, t, dt in (("view_count", view_count, torch.int32), ("cell_mask", cell_mask, torch.int64)):
+        if t is not None and not (t.is_cuda and t.dtype == dt and t.is_contiguous() and t.shape[0] == M):
+            raise ValueError(f"{name} must be a contiguous {dt} CUDA tensor with one row per primitive")
     sc = _scene_struct(scene)
     _abi.check(lib.bgt_prim_metrics(int(scene["degree"]), ctypes.byref(sc), _ptr(g_ctrl), float(tau_a), float(tau_s),
-                                    float(tau_g), _ptr(out["area"]), _ptr(out["aspect"]), _ptr(out.get("grad")),
-                                    _ptr(out["flags"]), _stream(stream)))
+                                    float(tau_g), _ptr(view_count), int(n_views), _ptr(cell_mask), int(tess_level),
+                                    float(tau_v), float(tau_r), _ptr(out["area"]), _ptr(out["aspect"]),
+                                    _ptr(out.get("grad")), _ptr(out["flags"]), _stream(stream)))
     return out
 
 
@@ -151,6 +162,7 @@ class Renderer:
         cfg.max_boundary_pairs = max_boundary_pairs if max_boundary_pairs is not None else 8 * max_pixels
         cfg.max_blend_pairs = max_blend_pairs
         cfg.tess_level = tess_level
+        self.tess_level = int(tess_level)
         cfg.tile_size = tile_size
         cfg.k_b, cfg.alpha_min, cfg.alpha_max = k_b, alpha_min, alpha_max
         cfg.t_stop, cfg.dilation, cfg.near_z = t_stop, dilation, near_z
@@ -278,6 +290,28 @@ class Renderer:
         _abi.check(self.lib.bgt_l2_dssim_loss_grad(_ptr(images), _ptr(target), len(cams), sizes, float(lam),
                                                    float(scale), _ptr(d_images), _ptr(loss), _stream(stream)))
         return d_images
+
+    def visibility(self, num_prims, view_count=None, cell_mask=None, stream=None):
+        """Visibility measures of the last forward's views (bgt_visibility),
+        accumulated into view_count [M] int32 and cell_mask [M, words] int64
+        (zeros when not given; words = ceil(2 L^2 / 64) of the tessellation
+        level L): views a primitive owns pixels in, and the lattice flat
+        triangles it is seen through."""
+        L = self.tess_level
+        words = (2 * L * L + 63) // 64
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if view_count is None:
+            view_count = torch.zeros(num_prims, dtype=torch.int32, device=dev)
+        if cell_mask is None:
+            cell_mask = torch.zeros((num_prims, words), dtype=torch.int64, device=dev)
+        if not (view_count.is_cuda and view_count.dtype == torch.int32 and view_count.is_contiguous()
+                and view_count.numel() == num_prims):
+            raise ValueError("view_count must be a contiguous int32 CUDA tensor of num_prims entries")
+        if not (cell_mask.is_cuda and cell_mask.dtype == torch.int64 and cell_mask.is_contiguous()
+                and cell_mask.numel() == num_prims * words):
+            raise ValueError(f"cell_mask must be a contiguous int64 CUDA tensor of num_prims x {words}")
+        self._check(self.lib.bgt_visibility(self.h, _ptr(view_count), _ptr(cell_mask), _stream(stream)))
+        return view_count, cell_mask
 
     def stage(self, name, stream=None):
         """Copy an intermediate buffer of the last forward to a numpy array."""

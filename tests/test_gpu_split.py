@@ -207,3 +207,68 @@ def test_pieces_of_flat_patches_share_the_area():
         c = sc["ctrl"][m].astype(np.float64)
         tol = 1e-5 * a1[m] + 2 * _tolerances(c, 3, 1.0)[0]
         assert np.abs(a2[m] - a1[m] / 4).max() <= tol, (m, a2[m], a1[m])
+
+
+def _expected_masks(cells, M, words):
+    want = np.zeros((M, words), np.uint64)
+    for m, cs in enumerate(cells):
+        for c in cs:
+            want[m, c >> 6] |= np.uint64(1) << np.uint64(c & 63)
+    return want
+
+
+def test_visibility_measures_match_the_oracle(oracle, scenes):
+    # 8 views of mixed size of the benchmark scene in one forward: the views
+    # each primitive is seen in and its visibility texture, bit-exact (the
+    # raster is); a second forward of 8 other views accumulates; the
+    # occlusion flags follow the oracle's ratios
+    import torch
+    from oracle import split as S
+    from paper_2503_13961_gb300 import render as R
+    from tests.gpu_util import make_renderer
+    sc, cams = scenes.config_scene(4)
+    M = sc["ctrl"].shape[0]
+    dev = _dev(sc)
+    rd = make_renderer(sc, cams[:16])  # capacities of both forwards
+    vc = cm = None
+    rasters = []
+    for part in (cams[:8], cams[8:16]):
+        rd.forward(dev, part)
+        rd.sync_status()
+        vc, cm = rd.visibility(M, vc, cm)
+        rasters += [oracle.raster(sc, c)[0::2] for c in part]
+        count, cells = S.visibility(rasters, M)
+        torch.cuda.synchronize()
+        assert np.array_equal(vc.cpu().numpy(), count)
+        assert np.array_equal(cm.cpu().numpy().view(np.uint64), _expected_masks(cells, M, 2))
+    assert 0 < int((count > 0).sum()) < M  # some primitives seen, some hidden
+    out = R.prim_metrics(dev, view_count=vc, n_views=16, cell_mask=cm, tess_level=8)
+    torch.cuda.synchronize()
+    flags = out["flags"].cpu().numpy()
+    by_v, by_a = S.occluded(count, 16, cells)
+    assert np.array_equal((flags & 4) != 0, np.array(by_v))
+    assert np.array_equal((flags & 8) != 0, np.array(by_a))
+    assert 0 < int(np.sum(by_a)) < M
+    rd.close()
+
+
+def test_visibility_over_more_than_64_views(oracle, scenes):
+    # 140 small views in one forward: the view bits go in groups of 64, and
+    # primitives are seen in more than 64 of them
+    import torch
+    from oracle import split as S
+    from tests.gpu_util import make_renderer
+    sc, _ = scenes.config_scene(1)
+    rng = np.random.default_rng(12)
+    cams = scenes.make_views(rng, [(32, 24)] * 140, 3.0, 4.5)
+    M = sc["ctrl"].shape[0]
+    dev = _dev(sc)
+    rd = make_renderer(sc, cams)
+    rd.forward(dev, cams)
+    rd.sync_status()
+    vc, cm = rd.visibility(M)
+    torch.cuda.synchronize()
+    count, cells = S.visibility([oracle.raster(sc, c)[0::2] for c in cams], M)
+    assert np.array_equal(vc.cpu().numpy(), count) and int(count.max()) > 64
+    assert np.array_equal(cm.cpu().numpy().view(np.uint64), _expected_masks(cells, M, 2))
+    rd.close()
