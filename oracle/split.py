@@ -10,7 +10,9 @@
     (tau_g = 0.0018);
   * the visibility measures of the other two pruning criteria: in how many
     training views a primitive owns pixels of I_id (tau_v = 0.08 of them)
-    and how much of its visibility texture is seen (tau_r = 0.4).
+    and how much of its visibility texture is seen (tau_r = 0.4);
+  * the edge prior of the split criterion: edge magnitudes of the training
+    images back-projected onto the primitives through I_id (tau_b = 13).
 
 TEST INFRASTRUCTURE: imported only by tests/. The CUDA library never imports
 it, and it shares no code with it.
@@ -221,3 +223,46 @@ def occluded(view_count, n_views, cells, tess_level=8, tau_v=TAU_V, tau_r=TAU_R)
     by_views = [n_views > 0 and c / n_views < tau_v for c in view_count]
     by_area = [len(s) / L2 < tau_r for s in cells]
     return by_views, by_area
+
+
+TAU_B = 13.0
+LUMA = (0.299, 0.587, 0.114)
+
+
+def edge_magnitude(img):
+    """Edge prior of the split criterion: the Sobel gradient magnitude of a
+    training image's luma in 8-bit units. Readings (the paper names an edge
+    detector, not which): luma 255 (0.299 R + 0.587 G + 0.114 B) of an
+    [H, W, 3] image in [0, 1]; the unnormalised 3 x 3 Sobel pair
+    Gx = [1 2 1]^T [-1 0 1], Gy its transpose, with the border replicated;
+    magnitude sqrt(Gx^2 + Gy^2). Returns [H, W]."""
+    img = np.asarray(img, np.float64)
+    y = 255.0 * (LUMA[0] * img[..., 0] + LUMA[1] * img[..., 1] + LUMA[2] * img[..., 2])
+    H, W = y.shape
+    p = np.pad(y, 1, mode="edge")
+
+    def at(dy, dx):
+        return p[1 + dy:1 + dy + H, 1 + dx:1 + dx + W]
+
+    gx = (at(-1, 1) - at(-1, -1)) + 2 * (at(0, 1) - at(0, -1)) + (at(1, 1) - at(1, -1))
+    gy = (at(1, -1) - at(-1, -1)) + 2 * (at(1, 0) - at(-1, 0)) + (at(1, 1) - at(-1, 1))
+    return np.sqrt(gx * gx + gy * gy)
+
+
+def edge_prior(ids, edges, M):
+    """Edge values back-projected onto the primitives through I_id: per
+    primitive the sum of the edge magnitudes of the pixels it owns and their
+    count, over the views (ids, edges: lists of [H, W] arrays)."""
+    s = np.zeros(M)
+    n = np.zeros(M, np.int64)
+    for idm, e in zip(ids, edges):
+        fg = idm >= 0
+        np.add.at(s, idm[fg], e[fg])
+        np.add.at(n, idm[fg], 1)
+    return s, n
+
+
+def split_by_edges(edge_sum, edge_count, tau_b=TAU_B):
+    """Split criterion of the edge prior: the accumulated average edge value
+    of a primitive exceeds tau_b."""
+    return [c > 0 and s / c > tau_b for s, c in zip(edge_sum, edge_count)]

@@ -59,3 +59,35 @@ def test_cell_of_a_pixel_holds_its_uv(oracle, scenes):
     far = (np.minimum(np.minimum(fu, fv), np.abs(fu + fv - 1)) > 1e-3) & (fu < 1 - 1e-3) & (fv < 1 - 1e-3)
     assert far.sum() > 1000
     assert np.array_equal(sub[far], want[far])
+
+
+def test_sobel_edge_magnitude_closed_forms():
+    H, W = 12, 10
+    # constant image: no edges
+    assert np.abs(S.edge_magnitude(np.full((H, W, 3), 0.3))).max() == 0.0
+    # a luma ramp of slope s per pixel along x: 8 s inside, 4 s at the replicated border
+    s = 0.01
+    ramp = np.repeat((s * np.arange(W))[None, :, None], H, axis=0).repeat(3, axis=2)
+    e = S.edge_magnitude(ramp)
+    assert np.allclose(e[:, 1:-1], 8 * s * 255) and np.allclose(e[:, [0, -1]], 4 * s * 255)
+    # a vertical step of luma h: 4 h on the two columns beside it, 0 elsewhere
+    step = np.zeros((H, W, 3))
+    step[:, 5:] = 0.5
+    e = S.edge_magnitude(step)
+    assert np.allclose(e[:, 4], 4 * 0.5 * 255) and np.allclose(e[:, 5], 4 * 0.5 * 255)
+    assert np.abs(np.delete(e, [4, 5], axis=1)).max() == 0.0
+    # transposing the image transposes the magnitude; colour weights are the luma's
+    rng = np.random.default_rng(0)
+    img = rng.uniform(size=(9, 11, 3))
+    assert np.allclose(S.edge_magnitude(img.transpose(1, 0, 2)), S.edge_magnitude(img).T)
+    red = np.zeros((H, W, 3))
+    red[:, 5:, 0] = 1.0
+    assert np.allclose(S.edge_magnitude(red)[:, 4], 4 * 0.299 * 255)
+
+
+def test_edge_prior_back_projects_through_the_index_map():
+    ids = [np.array([[0, 0, 1], [-1, 1, 1]]), np.array([[1, -1, 0], [0, 0, 0]])]
+    edges = [np.array([[1.0, 3.0, 5.0], [7.0, 9.0, 11.0]]), np.array([[2.0, 4.0, 6.0], [8.0, 10.0, 12.0]])]
+    s, n = S.edge_prior(ids, edges, 3)
+    assert s.tolist() == [1 + 3 + 6 + 8 + 10 + 12, 5 + 9 + 11 + 2, 0.0] and n.tolist() == [6, 4, 0]
+    assert S.split_by_edges(s, n, tau_b=6.0) == [True, True, False]
