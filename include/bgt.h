@@ -246,19 +246,43 @@ typedef struct {
  *   grad[m]   mean over the control points of |dl/dp_ijk| from g_ctrl
  *             ([M][Ncp][3] device, e.g. bgt_grads.ctrl; may be NULL);
  *   flags[m]  bit 0 = prune (area < tau_a or aspect > tau_s; the paper uses
- *             3e-4 and 10), bit 1 = split (grad > tau_g, the paper's 0.0018;
- *             never set without g_ctrl), bit 2 = occluded in the views
+ *             3e-4 and 10), bit 1 = split (grad > tau_g, the paper's 0.0018,
+ *             with g_ctrl; or edge_sum[m] > tau_b edge_count[m], the
+ *             accumulated average of the edge prior above the paper's 13,
+ *             with edge_sum / edge_count from bgt_edge_prior), bit 2 = occluded in the views
  *             (view_count[m] < tau_v n_views, the paper's 0.08), bit 3 =
  *             occluded in its visibility texture (set bits of its cell_mask
  *             words < tau_r L^2, the paper's 0.4, L = tess_level); bits 2 and
  *             3 need view_count / cell_mask (from bgt_visibility, device).
  * Each output (device, M entries) may be NULL. BGT_ERR_INVALID_ARG for a
- * degree outside 1..4, a NULL scene or ctrl with M > 0, n_views < 0 or a
- * tess_level outside 1..16 with a cell_mask. */
+ * degree outside 1..4, a NULL scene or ctrl with M > 0, n_views < 0, a
+ * tess_level outside 1..16 with a cell_mask, or only one of edge_sum and
+ * edge_count. */
 bgt_status bgt_prim_metrics(int degree, const bgt_scene *scene, const float *g_ctrl, float tau_a, float tau_s,
-                            float tau_g, const int *view_count, int n_views, const unsigned long long *cell_mask,
-                            int tess_level, float tau_v, float tau_r, float *area, float *aspect, float *grad,
-                            unsigned char *flags, void *stream);
+                            float tau_g, const float *edge_sum, const int *edge_count, float tau_b,
+                            const int *view_count, int n_views, const unsigned long long *cell_mask, int tess_level,
+                            float tau_v, float tau_r, float *area, float *aspect, float *grad, unsigned char *flags,
+                            void *stream);
+
+/* Edge prior of the split criterion (Sec. 3.3 "Splitting and Pruning"),
+ * step 1: the edge magnitude of training images, the Sobel gradient magnitude
+ * sqrt(Gx^2 + Gy^2) of the 8-bit luma 255 (0.299 R + 0.587 G + 0.114 B) with
+ * the unnormalised 3 x 3 Sobel pair and the border replicated. images:
+ * device, the renderer's layout ([sum W H][3], view v an [H_v][W_v][3]
+ * block, values in [0, 1]); sizes: host [n_views][2] = (W_v, H_v); edges:
+ * device [sum W H], written entirely. BGT_ERR_INVALID_ARG for negative sizes,
+ * more than 2^31 / 3 pixels or missing buffers. */
+bgt_status bgt_edge_magnitude(const float *images, int n_views, const int *sizes, float *edges, void *stream);
+
+/* Edge prior, step 2: edges ([sum W H] device, e.g. from
+ * bgt_edge_magnitude of the training images of the views of the last
+ * bgt_render_fwd on the handle) back-projected onto the primitives through
+ * that forward's I_id: edge_sum[m] += the sum of edges over the pixels
+ * primitive m owns, edge_count[m] += their number (device arrays of
+ * num_prims, accumulated across calls; either may be NULL). The split
+ * criterion of bgt_prim_metrics compares edge_sum / edge_count with tau_b
+ * (the paper's 13). BGT_ERR_STATE without a forward. */
+bgt_status bgt_edge_prior(bgt_handle *h, const float *edges, float *edge_sum, int *edge_count, void *stream);
 
 /* Visibility measures of the pruning criteria (Sec. 3.3 "Splitting and
  * Pruning"), from the raster of the last bgt_render_fwd on the handle:

@@ -81,8 +81,10 @@ def _declare(L):
                                c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_float), P]
     L.bgt_l1_loss_grad.argtypes = [P, P, c_ll, c_float, P, P, P]
     L.bgt_l2_dssim_loss_grad.argtypes = [P, P, c_int, P, c_float, c_float, P, P, P]
-    L.bgt_prim_metrics.argtypes = [c_int, ctypes.POINTER(Scene), P, c_float, c_float, c_float, P, c_int, P, c_int,
-                                   c_float, c_float, P, P, P, P, P]
+    L.bgt_prim_metrics.argtypes = [c_int, ctypes.POINTER(Scene), P, c_float, c_float, c_float, P, P, c_float, P,
+                                   c_int, P, c_int, c_float, c_float, P, P, P, P, P]
+    L.bgt_edge_magnitude.argtypes = [P, c_int, P, P, P]
+    L.bgt_edge_prior.argtypes = [P, P, P, P, P]
     L.bgt_visibility.argtypes = [P, P, P, P]
     L.bgt_subdivide.argtypes = [c_int, ctypes.POINTER(Scene), P, c_int, ctypes.POINTER(Prims), P]
     L.bgt_get_stage.argtypes = [P, c_int, P, c_ll, ctypes.POINTER(c_ll), P]

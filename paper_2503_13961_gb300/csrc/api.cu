@@ -626,16 +626,40 @@ bgt_status bgt_l2_dssim_loss_grad(const float *images, const float *target, int 
 }
 
 bgt_status bgt_prim_metrics(int degree, const bgt_scene *scene, const float *g_ctrl, float tau_a, float tau_s,
-                            float tau_g, const int *view_count, int n_views, const unsigned long long *cell_mask,
-                            int tess_level, float tau_v, float tau_r, float *area, float *aspect, float *grad,
-                            unsigned char *flags, void *stream) {
+                            float tau_g, const float *edge_sum, const int *edge_count, float tau_b,
+                            const int *view_count, int n_views, const unsigned long long *cell_mask, int tess_level,
+                            float tau_v, float tau_r, float *area, float *aspect, float *grad, unsigned char *flags,
+                            void *stream) {
   if (degree < 1 || degree > bgt::kMaxDegree || !scene || scene->num_prims < 0) return BGT_ERR_INVALID_ARG;
   if (scene->num_prims > 0 && !scene->ctrl) return BGT_ERR_INVALID_ARG;
   if (n_views < 0 || (cell_mask && (tess_level < 1 || tess_level > bgt::kMaxTess))) return BGT_ERR_INVALID_ARG;
-  bgt::launch_prim_metrics(degree, scene->ctrl, scene->num_prims, g_ctrl, tau_a, tau_s, tau_g, view_count, n_views,
-                           cell_mask, cell_mask ? tess_level : 1, tau_v, tau_r, area, aspect, grad, flags,
-                           static_cast<cudaStream_t>(stream));
+  if ((edge_sum == nullptr) != (edge_count == nullptr)) return BGT_ERR_INVALID_ARG;
+  bgt::launch_prim_metrics(degree, scene->ctrl, scene->num_prims, g_ctrl, tau_a, tau_s, tau_g, edge_sum, edge_count,
+                           tau_b, view_count, n_views, cell_mask, cell_mask ? tess_level : 1, tau_v, tau_r, area,
+                           aspect, grad, flags, static_cast<cudaStream_t>(stream));
   return cudaGetLastError() == cudaSuccess ? BGT_OK : BGT_ERR_CUDA;
+}
+
+bgt_status bgt_edge_magnitude(const float *images, int n_views, const int *sizes, float *edges, void *stream) {
+  if (n_views < 0 || (n_views > 0 && !sizes)) return BGT_ERR_INVALID_ARG;
+  long long n = 0;
+  for (int v = 0; v < n_views; ++v) {
+    if (sizes[2 * v] < 0 || sizes[2 * v + 1] < 0) return BGT_ERR_INVALID_ARG;
+    n += (long long)sizes[2 * v] * sizes[2 * v + 1];
+  }
+  if (n > (1LL << 31) / 3) return BGT_ERR_INVALID_ARG;
+  if (n > 0 && (!images || !edges)) return BGT_ERR_INVALID_ARG;
+  bgt::launch_edge_magnitude(images, n_views, sizes, edges, static_cast<cudaStream_t>(stream));
+  return cudaGetLastError() == cudaSuccess ? BGT_OK : BGT_ERR_CUDA;
+}
+
+bgt_status bgt_edge_prior(bgt_handle *h, const float *edges, float *edge_sum, int *edge_count, void *stream) {
+  if (!h) return BGT_ERR_INVALID_ARG;
+  if (!h->fwd_valid) return fail(h, BGT_ERR_STATE, "edge prior without a forward");
+  if (h->last.P > 0 && !edges) return fail(h, BGT_ERR_INVALID_ARG, "null edges");
+  bgt::launch_edge_prior(h->last, h->w, edges, edge_sum, edge_count, static_cast<cudaStream_t>(stream));
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? BGT_OK : cuda_fail(h, e, "edge prior");
 }
 
 bgt_status bgt_visibility(bgt_handle *h, int *view_count, unsigned long long *cell_mask, void *stream) {

@@ -177,6 +177,37 @@ __host__ __device__ constexpr float multinom(int n, int i, int j, int k) {
   return (float)(factorial(n) / (factorial(i) * factorial(j) * factorial(k)));
 }
 
+// Warp-segmented sums: lanes holding equal keys in a run of consecutive
+// lanes form a segment; seg_sum leaves the segment's sum (inclusive scan) in
+// its last lane (tail), so that one atomic per run replaces one per lane.
+struct Seg {
+  int start;
+  bool tail;
+};
+
+__device__ inline Seg seg_info(int key) {
+  const int lane = threadIdx.x & 31;
+  const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+  const int next = __shfl_down_sync(0xffffffffu, key, 1);
+  const bool head = lane == 0 || prev != key;
+  const unsigned heads = __ballot_sync(0xffffffffu, head);
+  const unsigned upto = (lane == 31) ? 0xffffffffu : ((2u << lane) - 1u);
+  Seg s;
+  s.start = 31 - __clz(heads & upto);
+  s.tail = lane == 31 || next != key;
+  return s;
+}
+
+__device__ inline float seg_sum(float v, const Seg &s) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane - o >= s.start) v += y;
+  }
+  return v;
+}
+
 // Calls f(Degree<N>()) for the degree n (1..kMaxDegree), so that every loop
 // over Bernstein terms is unrolled at compile time.
 template <int N> struct Degree { static constexpr int value = N; };
@@ -539,9 +570,13 @@ int launch_l1_grad(const float *img, const float *target, long long n, float sca
 int launch_l2_dssim_grad(const float *img, const float *gt, int n_views, const int *sizes, float lambda,
                          float scale, float *dimg, float *loss, cudaStream_t st);
 int launch_prim_metrics(int degree, const float *ctrl, int M, const float *g_ctrl, float tau_a, float tau_s,
-                        float tau_g, const int *view_count, int n_views, const unsigned long long *cell_mask,
-                        int tess_level, float tau_v, float tau_r, float *area, float *aspect, float *grad,
-                        unsigned char *flags, cudaStream_t st);
+                        float tau_g, const float *edge_sum, const int *edge_count, float tau_b,
+                        const int *view_count, int n_views, const unsigned long long *cell_mask, int tess_level,
+                        float tau_v, float tau_r, float *area, float *aspect, float *grad, unsigned char *flags,
+                        cudaStream_t st);
+int launch_edge_magnitude(const float *img, int n_views, const int *sizes, float *edges, cudaStream_t st);
+int launch_edge_prior(const Params &p, const Work &w, const float *edges, float *edge_sum, int *edge_count,
+                      cudaStream_t st);
 int launch_visibility(const Params &p, const Work &w, const int *view_off, int *view_count,
                       unsigned long long *cell_mask, cudaStream_t st);
 int launch_exclusive_scan(const int *in, long long *out, int n, long long *aux, cudaStream_t st);

@@ -18,34 +18,6 @@ namespace bgt {
 
 namespace {
 
-struct Seg {
-  int start;
-  bool tail;
-};
-
-__device__ inline Seg seg_info(int key) {
-  const int lane = threadIdx.x & 31;
-  const int prev = __shfl_up_sync(0xffffffffu, key, 1);
-  const int next = __shfl_down_sync(0xffffffffu, key, 1);
-  const bool head = lane == 0 || prev != key;
-  const unsigned heads = __ballot_sync(0xffffffffu, head);
-  const unsigned upto = (lane == 31) ? 0xffffffffu : ((2u << lane) - 1u);
-  Seg s;
-  s.start = 31 - __clz(heads & upto);
-  s.tail = lane == 31 || next != key;
-  return s;
-}
-
-__device__ inline float seg_sum(float v, const Seg &s) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const float y = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane - o >= s.start) v += y;
-  }
-  return v;
-}
-
 template <int N>
 __device__ inline void camera_point_f32(const float *cp, float u, float v, const View &vw, float *B, float *t) {
   bernstein_f32<N>(u, v, B);

@@ -157,6 +157,9 @@ struct MetricArgs {
   const float *ctrl, *g_ctrl;
   int M;
   float tau_a, tau_s, tau_g;
+  const float *edge_sum;
+  const int *edge_count;
+  float tau_b;
   const int *view_count;
   int n_views;
   const unsigned long long *cell_mask;
@@ -252,8 +255,11 @@ __global__ void __launch_bounds__(256) k_prim_metrics(const MetricArgs s) {
   if (s.aspect) s.aspect[m] = aspect;
   if (s.grad && s.g_ctrl) s.grad[m] = grad;
   if (s.flags) {
+    // split: the mean control-point gradient, or the accumulated average edge value
+    const bool by_edges = s.edge_sum && s.edge_count && s.edge_count[m] > 0 &&
+                          (double)s.edge_sum[m] > (double)s.tau_b * (double)s.edge_count[m];
     unsigned char f = (unsigned char)((area < s.tau_a || aspect > s.tau_s ? 1 : 0) |
-                                      (s.g_ctrl && grad > s.tau_g ? 2 : 0));
+                                      ((s.g_ctrl && grad > s.tau_g) || by_edges ? 2 : 0));
     // visibility ratios compared in FP64: integer counts over integer totals
     if (s.view_count && s.n_views > 0 && (double)s.view_count[m] < (double)s.tau_v * (double)s.n_views) f |= 4;
     if (s.cell_mask) {
@@ -301,6 +307,66 @@ __global__ void __launch_bounds__(256) k_vis_count(int M, unsigned long long *se
   }
 }
 
+constexpr int kMaxEdgeViews = 200;  // views per launch: the table stays in 4 KB of parameters
+
+struct EdgeArgs {
+  const float *img;
+  float *edges;
+  int n_views;
+  int off[kMaxEdgeViews + 1];  // first pixel of each view of the launch, last: end
+  int W[kMaxEdgeViews];
+};
+static_assert(sizeof(EdgeArgs) <= 4000, "kernel parameters");
+
+// 8-bit luma of pixel (x, y) of a W-wide view at pixel offset base (clamped to the view)
+__device__ __forceinline__ float luma255(const float *img, int base, int W, int H, int x, int y) {
+  x = min(max(x, 0), W - 1);
+  y = min(max(y, 0), H - 1);
+  const float *c = img + 3 * ((size_t)base + (size_t)y * W + x);
+  return 255.0f * (0.299f * __ldg(c) + 0.587f * __ldg(c + 1) + 0.114f * __ldg(c + 2));
+}
+
+// Edge prior of the split criterion: Sobel gradient magnitude of the 8-bit
+// luma, border replicated, one thread per pixel of the launch's views
+__global__ void __launch_bounds__(256) k_edge_magnitude(const __grid_constant__ EdgeArgs a) {
+  const int i = a.off[0] + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.off[a.n_views]) return;
+  int lo = 0, hi = a.n_views - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.off[mid] <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  const int base = a.off[lo], W = a.W[lo], H = (a.off[lo + 1] - base) / W;
+  const int y = (i - base) / W, x = (i - base) - y * W;
+  float p[3][3];
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) p[dy + 1][dx + 1] = luma255(a.img, base, W, H, x + dx, y + dy);
+  const float gx = (p[0][2] - p[0][0]) + 2.0f * (p[1][2] - p[1][0]) + (p[2][2] - p[2][0]);
+  const float gy = (p[2][0] - p[0][0]) + 2.0f * (p[2][1] - p[0][1]) + (p[2][2] - p[0][2]);
+  a.edges[i] = sqrtf(gx * gx + gy * gy);
+}
+
+// edge values back-projected through I_id of the last forward: per run of
+// consecutive pixels of one primitive, one atomic for the sum and one for the count
+__global__ void __launch_bounds__(256) k_edge_prior(const int *pid, const float *edges, int P, float *edge_sum,
+                                                    int *edge_count) {
+  const int lane = threadIdx.x & 31;
+  const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+  const int id = pix < P ? pid[pix] : -1;
+  const bool on = id >= 0;
+  if (!__any_sync(0xffffffffu, on)) return;
+  const Seg sg = seg_info(on ? id : -1 - lane);
+  const float e = seg_sum(on ? edges[pix] : 0.f, sg);
+  const float c = seg_sum(on ? 1.f : 0.f, sg);
+  if (sg.tail && on) {
+    if (edge_sum) atomicAdd(edge_sum + id, e);
+    if (edge_count) atomicAdd(edge_count + id, (int)c);
+  }
+}
+
 }  // namespace
 
 int launch_subdivide(int degree, const bgt_scene &sc, const int *sel, int n_sel, const bgt_prims &out,
@@ -329,14 +395,47 @@ int launch_subdivide(int degree, const bgt_scene &sc, const int *sel, int n_sel,
 }
 
 int launch_prim_metrics(int degree, const float *ctrl, int M, const float *g_ctrl, float tau_a, float tau_s,
-                        float tau_g, const int *view_count, int n_views, const unsigned long long *cell_mask,
-                        int tess_level, float tau_v, float tau_r, float *area, float *aspect, float *grad,
-                        unsigned char *flags, cudaStream_t st) {
+                        float tau_g, const float *edge_sum, const int *edge_count, float tau_b,
+                        const int *view_count, int n_views, const unsigned long long *cell_mask, int tess_level,
+                        float tau_v, float tau_r, float *area, float *aspect, float *grad, unsigned char *flags,
+                        cudaStream_t st) {
   if (M <= 0) return 0;
   const int nsub = 2 * tess_level * tess_level;
-  MetricArgs s{ctrl, g_ctrl, M, tau_a, tau_s, tau_g, view_count, n_views, cell_mask, (nsub + 63) / 64,
-               tess_level * tess_level, tau_v, tau_r, area, aspect, grad, flags};
+  MetricArgs s{ctrl, g_ctrl, M, tau_a, tau_s, tau_g, edge_sum, edge_count, tau_b, view_count, n_views, cell_mask,
+               (nsub + 63) / 64, tess_level * tess_level, tau_v, tau_r, area, aspect, grad, flags};
   dispatch_degree(degree, [&](auto d) { k_prim_metrics<decltype(d)::value><<<(M + 255) / 256, 256, 0, st>>>(s); });
+  return 1;
+}
+
+int launch_edge_magnitude(const float *img, int n_views, const int *sizes, float *edges, cudaStream_t st) {
+  EdgeArgs a;
+  a.img = img;
+  a.edges = edges;
+  int launches = 0, off = 0;
+  for (int v0 = 0; v0 < n_views; v0 += kMaxEdgeViews) {
+    a.n_views = 0;
+    const int first = off;
+    for (int v = v0; v < n_views && v < v0 + kMaxEdgeViews; ++v) {
+      const int W = sizes[2 * v], H = sizes[2 * v + 1];
+      if (W > 0 && H > 0) {
+        a.off[a.n_views] = off;
+        a.W[a.n_views] = W;
+        a.n_views++;
+      }
+      off += W * H;
+    }
+    a.off[a.n_views] = off;
+    if (a.n_views == 0 || off == first) continue;
+    k_edge_magnitude<<<(off - first + 255) / 256, 256, 0, st>>>(a);
+    ++launches;
+  }
+  return launches;
+}
+
+int launch_edge_prior(const Params &p, const Work &w, const float *edges, float *edge_sum, int *edge_count,
+                      cudaStream_t st) {
+  if (p.P <= 0) return 0;
+  k_edge_prior<<<(p.P + 255) / 256, 256, 0, st>>>(w.pid, edges, p.P, edge_sum, edge_count);
   return 1;
 }
 

@@ -80,16 +80,18 @@ def _scene_struct(sc):
 TAU_A, TAU_S, TAU_G = 3e-4, 10.0, 0.0018
 
 
-TAU_V, TAU_R = 0.08, 0.4
+TAU_V, TAU_R, TAU_B = 0.08, 0.4, 13.0
 
 
 def prim_metrics(scene, g_ctrl=None, tau_a=TAU_A, tau_s=TAU_S, tau_g=TAU_G, view_count=None, n_views=0,
-                 cell_mask=None, tess_level=8, tau_v=TAU_V, tau_r=TAU_R, stream=None):
+                 cell_mask=None, tess_level=8, tau_v=TAU_V, tau_r=TAU_R, edge_sum=None, edge_count=None,
+                 tau_b=TAU_B, stream=None):
     """Area, aspect ratio, mean control-point gradient and the flags of the
     splitting and pruning criteria (bit 0 prune by area / aspect, bit 1
-    split, bit 2 occluded in the views, bit 3 occluded in the visibility
-    texture) of every primitive of a device scene (bgt_prim_metrics);
-    view_count / cell_mask come from Renderer.visibility over n_views views."""
+    split by gradient or edge prior, bit 2 occluded in the views, bit 3
+    occluded in the visibility texture) of every primitive of a device scene
+    (bgt_prim_metrics); view_count / cell_mask come from Renderer.visibility
+    over n_views views, edge_sum / edge_count from Renderer.edge_prior."""
     lib = _abi.load()
     M = int(scene["ctrl"].shape[0])
     dev = scene["ctrl"].device
@@ -100,15 +102,33 @@ def prim_metrics(scene, g_ctrl=None, tau_a=TAU_A, tau_s=TAU_S, tau_g=TAU_G, view
                 and g_ctrl.shape == scene["ctrl"].shape):
             raise ValueError("g_ctrl must be a contiguous float32 CUDA tensor shaped like scene['ctrl']")
         out["grad"] = torch.empty(M, device=dev)
-    for name, t, dt in (("view_count", view_count, torch.int32), ("cell_mask", cell_mask, torch.int64)):
+    if (edge_sum is None) != (edge_count is None):
+        raise ValueError("edge_sum and edge_count go together")
+    for name, t, dt in (("view_count", view_count, torch.int32), ("cell_mask", cell_mask, torch.int64),
+                        ("edge_sum", edge_sum, torch.float32), ("edge_count", edge_count, torch.int32)):
         if t is not None and not (t.is_cuda and t.dtype == dt and t.is_contiguous() and t.shape[0] == M):
             raise ValueError(f"{name} must be a contiguous {dt} CUDA tensor with one row per primitive")
     sc = _scene_struct(scene)
     _abi.check(lib.bgt_prim_metrics(int(scene["degree"]), ctypes.byref(sc), _ptr(g_ctrl), float(tau_a), float(tau_s),
-                                    float(tau_g), _ptr(view_count), int(n_views), _ptr(cell_mask), int(tess_level),
+                                    float(tau_g), _ptr(edge_sum), _ptr(edge_count), float(tau_b),
+                                    _ptr(view_count), int(n_views), _ptr(cell_mask), int(tess_level),
                                     float(tau_v), float(tau_r), _ptr(out["area"]), _ptr(out["aspect"]),
                                     _ptr(out.get("grad")), _ptr(out["flags"]), _stream(stream)))
     return out
+
+
+def edge_magnitude(images, cams, edges=None, stream=None):
+    """Sobel magnitude of the 8-bit luma of training images in the renderer's
+    layout (bgt_edge_magnitude): [sum W H] float32."""
+    lib = _abi.load()
+    n = sum(int(c["width"]) * int(c["height"]) for c in cams)
+    _device_f32(images, "images", 3 * n)
+    if edges is None:
+        edges = torch.empty(n, dtype=torch.float32, device=images.device)
+    _device_f32(edges, "edges", n)
+    sizes = (ctypes.c_int * (2 * len(cams)))(*[int(x) for c in cams for x in (c["width"], c["height"])])
+    _abi.check(lib.bgt_edge_magnitude(_ptr(images), len(cams), sizes, _ptr(edges), _stream(stream)))
+    return edges
 
 
 def subdivide(scene, sel, stream=None):
@@ -312,6 +332,23 @@ class Renderer:
             raise ValueError(f"cell_mask must be a contiguous int64 CUDA tensor of num_prims x {words}")
         self._check(self.lib.bgt_visibility(self.h, _ptr(view_count), _ptr(cell_mask), _stream(stream)))
         return view_count, cell_mask
+
+    def edge_prior(self, edges, num_prims, edge_sum=None, edge_count=None, stream=None):
+        """Edge values of the last forward's views back-projected onto the
+        primitives through I_id (bgt_edge_prior), accumulated into edge_sum
+        [M] float32 and edge_count [M] int32 (zeros when not given)."""
+        dev = edges.device
+        if edge_sum is None:
+            edge_sum = torch.zeros(num_prims, dtype=torch.float32, device=dev)
+        if edge_count is None:
+            edge_count = torch.zeros(num_prims, dtype=torch.int32, device=dev)
+        _device_f32(edges, "edges", self._last_pixels)
+        _device_f32(edge_sum, "edge_sum", num_prims)
+        if not (edge_count.is_cuda and edge_count.dtype == torch.int32 and edge_count.is_contiguous()
+                and edge_count.numel() == num_prims):
+            raise ValueError("edge_count must be a contiguous int32 CUDA tensor of num_prims entries")
+        self._check(self.lib.bgt_edge_prior(self.h, _ptr(edges), _ptr(edge_sum), _ptr(edge_count), _stream(stream)))
+        return edge_sum, edge_count
 
     def stage(self, name, stream=None):
         """Copy an intermediate buffer of the last forward to a numpy array."""

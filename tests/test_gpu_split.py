@@ -272,3 +272,52 @@ def test_visibility_over_more_than_64_views(oracle, scenes):
     assert np.array_equal(vc.cpu().numpy(), count) and int(count.max()) > 64
     assert np.array_equal(cm.cpu().numpy().view(np.uint64), _expected_masks(cells, M, 2))
     rd.close()
+
+
+def test_edge_prior_matches_the_oracle(oracle, scenes):
+    # training images of 6 views of the benchmark scene: edge magnitudes per
+    # pixel, their back-projection onto the primitives through I_id, and the
+    # split flag of the edge prior
+    import torch
+    from oracle import split as S
+    from paper_2503_13961_gb300 import render as R
+    from tests.gpu_util import make_renderer
+    sc, cams = scenes.config_scene(4)
+    cams = cams[:6]
+    M = sc["ctrl"].shape[0]
+    rng = np.random.default_rng(31)
+    imgs = [scenes.photo_pair(rng, c["width"], c["height"])[0] for c in cams]
+    train = torch.as_tensor(np.concatenate([i.reshape(-1, 3) for i in imgs]), device="cuda")
+    edges = R.edge_magnitude(train, cams)
+    torch.cuda.synchronize()
+    got = edges.cpu().numpy().astype(np.float64)
+    off = 0
+    per_view = []
+    for c, img in zip(cams, imgs):
+        n = c["width"] * c["height"]
+        want = S.edge_magnitude(img)
+        g = got[off:off + n].reshape(want.shape)
+        assert np.all(np.abs(g - want) <= 1e-5 * want + 2e-3), c["width"]
+        per_view.append(g)
+        off += n
+    dev = _dev(sc)
+    rd = make_renderer(sc, cams)
+    rd.forward(dev, cams)
+    rd.sync_status()
+    es, ec = rd.edge_prior(edges, M)
+    torch.cuda.synchronize()
+    ids = [oracle.raster(sc, c)[0] for c in cams]
+    s_ref, n_ref = S.edge_prior(ids, per_view, M)
+    assert np.array_equal(ec.cpu().numpy(), n_ref)
+    es = es.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(es - s_ref) <= 1e-5 * s_ref + 1e-3)
+    out = R.prim_metrics(dev, edge_sum=torch.as_tensor(es, dtype=torch.float32, device="cuda"),
+                         edge_count=ec)
+    torch.cuda.synchronize()
+    split = (out["flags"].cpu().numpy() & 2) != 0
+    want = np.array(S.split_by_edges(s_ref, n_ref))
+    avg = s_ref / np.maximum(n_ref, 1)
+    far = np.abs(avg - S.TAU_B) > 1e-4 * S.TAU_B
+    assert np.array_equal(split[far], want[far])
+    assert 100 < int(want.sum()) < int((n_ref > 0).sum()) - 100
+    rd.close()
