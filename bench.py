@@ -476,9 +476,18 @@ def run_split_prune(rd_ctx, grads):
     P = sum(c["width"] * c["height"] for c in rd_ctx[2])
     vc = torch.zeros(M, dtype=torch.int32, device="cuda")
     cm = torch.zeros((M, 2), dtype=torch.int64, device="cuda")
+    cams = rd_ctx[2]
+    train = torch.rand((P, 3), device="cuda", generator=torch.Generator(device="cuda").manual_seed(77))
+    edges = torch.empty(P, device="cuda")
+    es = torch.zeros(M, device="cuda")
+    ec = torch.zeros(M, dtype=torch.int32, device="cuda")
     work = {
         # the last forward's I_id and depth keys read, per-primitive counts and masks updated
         "visibility": (lambda: rd.visibility(M, vc, cm, stream=stream), 12 * P + 24 * M),
+        # training image read (3 floats per pixel), edge magnitude written
+        "edge_magnitude": (lambda: R.edge_magnitude(train, cams, edges, stream=stream), 16 * P),
+        # edge magnitude and I_id read, per-primitive sums and counts updated
+        "edge_prior": (lambda: rd.edge_prior(edges, M, es, ec, stream=stream), 8 * P + 16 * M),
         "prim_metrics": (lambda: R.prim_metrics(dev, grads["ctrl"], stream=stream), M * (24 * ncp + 13)),
         "subdivide": (lambda: R.subdivide(dev, sel, stream=stream),
                       M * (4 + 24 * ncp + 8 + 28 * T) + 4 * M * (24 * ncp + 8 + 28 * T)),
