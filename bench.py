@@ -255,6 +255,7 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     sc, cams = build_workload(rank, args.rb, args.workload, args.sh_degree, args.attr_res)
+    cams = R.Cameras(cams)  # the C camera array is built once for the whole run
     V = len(cams)
     P = sum(c["width"] * c["height"] for c in cams)
     M, ncp = sc["ctrl"].shape[0], sc["ctrl"].shape[1]

@@ -153,7 +153,24 @@ def subdivide(scene, sel, stream=None):
 
 
 def view_pixels(cams):
+    if isinstance(cams, Cameras):
+        return cams.pixels
     return int(sum(int(c["width"]) * int(c["height"]) for c in cams))
+
+
+class Cameras(list):
+    """A list of camera dicts whose C array is built once, for loops that
+    render the same views every step (a snapshot: later edits of the dicts
+    are not seen)."""
+
+    def __init__(self, cams):
+        super().__init__(cams)
+        self.array = _abi.camera_array(self)
+        self.pixels = int(sum(int(c["width"]) * int(c["height"]) for c in self))
+
+
+def _camera_array(cams):
+    return cams.array if isinstance(cams, Cameras) else _abi.camera_array(cams)
 
 
 class Renderer:
@@ -219,7 +236,7 @@ class Renderer:
         if images is None:
             images = torch.empty((P, 3), dtype=torch.float32, device=scene["ctrl"].device)
         _device_f32(images, "images", 3 * P)
-        cam_arr = _abi.camera_array(cams)
+        cam_arr = _camera_array(cams)
         sc = self._scene(scene)
         self._check(self.lib.bgt_render_fwd(self.h, ctypes.byref(sc), cam_arr, len(cams), _ptr(images),
                                             _stream(stream)))
@@ -236,7 +253,7 @@ class Renderer:
                 _device_f32(t, f"grads[{k!r}]", scene[k].numel())
         g = _grads_struct(grads)
         sc = self._scene(scene)
-        cam_arr = _abi.camera_array(cams)
+        cam_arr = _camera_array(cams)
         self._check(self.lib.bgt_render_bwd(self.h, ctypes.byref(sc), cam_arr, len(cams), _ptr(d_images),
                                             ctypes.byref(g), _stream(stream)))
         return grads
@@ -264,7 +281,7 @@ class Renderer:
         best = ctypes.c_int(0)
         ms = (ctypes.c_float * 3)()
         g = _grads_struct(grads)
-        self._check(self.lib.bgt_autotune(self.h, ctypes.byref(self._scene(scene)), _abi.camera_array(cams),
+        self._check(self.lib.bgt_autotune(self.h, ctypes.byref(self._scene(scene)), _camera_array(cams),
                                           len(cams), _ptr(images), _ptr(d_images), ctypes.byref(g), iters,
                                           ctypes.byref(best), ms, _stream(stream)))
         return best.value, {8: ms[0], 16: ms[1], 32: ms[2]}

@@ -77,3 +77,14 @@ def test_binding_rejects_host_tensors_before_any_call():
         with pytest.raises(ValueError):
             R._device_f32(t, "x")
     assert R._device_f32(None, "x") is None
+
+
+def test_prebuilt_camera_batch_equals_the_per_call_array():
+    import ctypes
+    from paper_2503_13961_gb300 import _abi, scenes
+    from paper_2503_13961_gb300 import render as R
+    _, cams = scenes.config_scene(4)
+    batch = R.Cameras(cams)
+    arr = _abi.camera_array(cams)
+    assert len(batch) == len(cams) and R.view_pixels(batch) == R.view_pixels(list(cams))
+    assert ctypes.string_at(batch.array, ctypes.sizeof(batch.array)) == ctypes.string_at(arr, ctypes.sizeof(arr))
