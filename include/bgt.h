@@ -140,8 +140,9 @@ bgt_status bgt_render_fwd(bgt_handle *h, const bgt_scene *scene, const bgt_camer
                           float *images, void *stream);
 
 /* Backward pass for the last forward on this handle: d_images is dl/dC in
- * the image layout (device). Overwrites the four gradient arrays of *grads
- * (device, zeroed first) with dl/dparameters summed over all views, holding
+ * the image layout (device). Overwrites the gradient arrays of *grads
+ * (device, zeroed first; ctrl, color, opacity and r_b always, log_scale, quat
+ * and sh when not NULL) with dl/dparameters summed over all views, holding
  * I_id, I_uv, B and the per-pixel survivor lists of the forward fixed
  * (supplementary "Backward Derivative"). The scene and cameras must be those
  * of the forward; BGT_ERR_STATE otherwise or without a forward. */
