@@ -193,7 +193,7 @@ def test_autograd_loss_feeds_the_differentiable_render(scenes):
     torch.cuda.synchronize()
     for k in ("ctrl", "color", "opacity", "r_b"):
         a, b = leaf[k].grad, g[k]
-        assert torch.allclose(a, b, rtol=1e-5, atol=1e-7 * float(b.abs().max())), k
+        assert torch.allclose(a, b, rtol=1e-4, atol=1e-6 * float(b.abs().max())), k
     assert float(g["ctrl"].abs().max()) > 0
     rd.close()
 
