@@ -195,20 +195,48 @@ BLEND_TRAFFIC = {"source_sha256": "a94eb491f9d2d0fe7e79ba9500e43337c7c2eaa2ced6c
                  "composite_fwd": (132.1e6 + 154.3e6) / 50625814, "composite_bwd": (297.4e6 + 40.7e6) / 50625814}
 
 
-def blend_traffic(dom, units):
+# Warp instructions per warp visit of the blending kernels (a visit: one warp,
+# one listed Gaussian forward; one replayed record backward), from one ncu
+# capture of four 1024^2 views (profiles/composite_blend_views1024x4.md): both
+# kernels keep the instruction issue slots 80-85 % busy, so issue is the
+# ceiling that binds them; same source check as the traffic
+BLEND_ISSUE = {"source_sha256": BLEND_TRAFFIC["source_sha256"],
+               "composite_fwd": 780578445 / 5419084, "composite_bwd": 911759901 / 4948871}
+
+
+def _blend_source_matches():
     import hashlib
     src = os.path.join(ROOT, "paper_2503_13961_gb300", "csrc", "composite.cu")
     try:
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
     except OSError:
-        return None
-    if sha != BLEND_TRAFFIC["source_sha256"] or dom not in BLEND_TRAFFIC:
+        return False
+    return sha == BLEND_TRAFFIC["source_sha256"]
+
+
+def blend_traffic(dom, units):
+    if not _blend_source_matches() or dom not in BLEND_TRAFFIC:
         return None
     pairs = units["fwd_composited" if dom == "composite_fwd" else "bwd_composited"]
     return int(BLEND_TRAFFIC[dom] * pairs)
 
 
-def roofline_entry(dom, stage_ms, units, achieved_gbs, dom_bytes, peak, peak_kind, fp32_peak):
+def blend_issue(dom, units, ms, sm_mhz):
+    """Instruction-issue view of a blending kernel: warp instructions per launch
+    (captured per warp visit, scaled by this run's visits) over the live
+    duration, against 152 SMs x 4 schedulers x 1 warp instruction per cycle."""
+    if not _blend_source_matches() or dom not in BLEND_ISSUE:
+        return None
+    visits = units["fwd_warp_visits" if dom == "composite_fwd" else "bwd_warp_visits"]
+    instr = BLEND_ISSUE[dom] * visits
+    peak = SMS * 4 * sm_mhz * 1e6
+    ach = instr / (ms * 1e-3)
+    return {"achieved": round(ach / 1e12, 4), "peak": round(peak / 1e12, 4), "unit": "T warp-instr/s",
+            "frac": round(ach / peak, 4), "warp_instr_per_launch": int(instr),
+            "peak_kind": "derived: 152 SMs x 4 schedulers x 1 instruction per cycle x max SM clock"}
+
+
+def roofline_entry(dom, stage_ms, units, achieved_gbs, dom_bytes, peak, peak_kind, fp32_peak, sm_mhz):
     """Roofline of the dominant kernel: the blending kernels are bound by FP32
     issue (no dense contraction, DRAM far from busy), the others by HBM."""
     ms = stage_ms[dom]
@@ -220,7 +248,8 @@ def roofline_entry(dom, stage_ms, units, achieved_gbs, dom_bytes, peak, peak_kin
                 "frac": round(ach / fp32_peak, 4), "traffic": blend_traffic(dom, units), "alg_flops_per_launch": int(fl),
                 "ms_per_launch": round(ms, 4),
                 "hbm_view": {"achieved": round(achieved_gbs, 1), "peak": peak, "unit": "GB/s",
-                             "frac": round(achieved_gbs / peak, 4), "alg_bytes_per_launch": int(dom_bytes)}}
+                             "frac": round(achieved_gbs / peak, 4), "alg_bytes_per_launch": int(dom_bytes)},
+                "issue_view": blend_issue(dom, units, ms, sm_mhz)}
     return {"bound": "hbm", "kernel": dom, "achieved": round(achieved_gbs, 1), "peak": peak, "peak_kind": peak_kind,
             "unit": "GB/s", "frac": round(achieved_gbs / peak, 4), "traffic": None,
             "alg_bytes_per_launch": int(dom_bytes), "ms_per_launch": round(ms, 4)}
@@ -399,7 +428,7 @@ def run_ours(args):
             "e2e": {"value": round(e2e_value, 2), "unit": "renders/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches_per_step * args.steps),
-            "roofline": roofline_entry(dom, stage_ms, units, achieved, dom_bytes, peak, peak_kind, fp32_peak),
+            "roofline": roofline_entry(dom, stage_ms, units, achieved, dom_bytes, peak, peak_kind, fp32_peak, sm_mhz),
             "work_units": units,
             "stages": per_stage,
         }
