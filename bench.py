@@ -53,8 +53,9 @@ def parse():
                     help="add view-dependent SH colour of this degree (1..3) to the scene")
     ap.add_argument("--attr-res", type=int, default=1,
                     help="rotation / scaling attribute maps of this leg resolution (paper: 3)")
-    ap.add_argument("--workload", default="config4", choices=["config4", "view800", "views1024x4"],
+    ap.add_argument("--workload", default="config4", choices=["config4", "view800", "views1024x4", "room8"],
                     help="view800: one 800^2 view of the same scene (small case for profilers); "
+                         "room8: the 100k degree-3 room under eight 1600x1200 views (large scale); "
                          "views1024x4: four 1024^2 views (inputs larger than L2, a few GB on the device)")
     return ap.parse_args()
 
@@ -257,6 +258,8 @@ def roofline_entry(dom, stage_ms, units, achieved_gbs, dom_bytes, peak, peak_kin
 
 def build_workload(seed_views, rb, workload="config4", sh_degree=0, attr_res=1):
     from paper_2503_13961_gb300 import scenes
+    if workload == "room8":
+        return scenes.config_scene(5, r_b=rb)[:2]
     sc, cams = scenes.config_scene(4, r_b=rb)
     if attr_res > 1:
         sc = scenes.with_attribute_maps(sc, attr_res)
@@ -288,7 +291,9 @@ def run_ours(args):
     V = len(cams)
     P = sum(c["width"] * c["height"] for c in cams)
     M, ncp = sc["ctrl"].shape[0], sc["ctrl"].shape[1]
-    rd = R.Renderer(degree=2, max_prims=M, max_views=V, max_pixels=P, max_pairs=6 * P, max_boundary_pairs=6 * P,
+    n = int(sc["degree"])
+    ppp = 32 if args.workload == "room8" else 6  # pair capacity per pixel (the room is dense)
+    rd = R.Renderer(degree=n, max_prims=M, max_views=V, max_pixels=P, max_pairs=ppp * P, max_boundary_pairs=ppp * P,
                     tile_size=16, graph=True)
     dev = R.scene_to_device(sc)
     stream = torch.cuda.Stream()
@@ -339,8 +344,8 @@ def run_ours(args):
 
     # per-stage device time of the same step: a second handle (no graph, same
     # tile size) records CUDA events between the stages on the same stream
-    prof_rd = R.Renderer(degree=2, max_prims=M, max_views=V, max_pixels=P, max_pairs=6 * P,
-                         max_boundary_pairs=6 * P, tile_size=rd.tile_size, graph=False)
+    prof_rd = R.Renderer(degree=n, max_prims=M, max_views=V, max_pixels=P, max_pairs=ppp * P,
+                         max_boundary_pairs=ppp * P, tile_size=rd.tile_size, graph=False)
     prof_rd.set_profiling(True)
     stage_ms = {}
     units = {}
@@ -418,8 +423,11 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded scene generator; stands in for Lego / NeRF-Synthetic)",
             "config": {"workload": WORKLOAD if args.workload == "config4" else
-                       ("one 800^2 view of: " if args.workload == "view800" else "four 1024^2 views of: ") + WORKLOAD,
-                       "views": V, "pixels": P, "prims": M, "degree": 2,
+                       ("100k degree-3 BG-triangles (10^3 room of 19,200 + 100 cubes + 100 spheres, noise 0.01, "
+                        "opacity Beta(5,1)), eight 1600x1200 views, batched fwd+L1+bwd" if args.workload == "room8"
+                        else ("one 800^2 view of: " if args.workload == "view800" else "four 1024^2 views of: ")
+                        + WORKLOAD),
+                       "views": V, "pixels": P, "prims": M, "degree": n,
                        "sh_degree": args.sh_degree, "attr_res": args.attr_res,
                        "tile": rd.tile_size, "tile_autotune_ms": tune_ms, "graph": True,
                        "counts": {k: int(v) for k, v in counts.items()},
@@ -547,8 +555,9 @@ def run_plain(rd_ctx, args):
     _, dev, cams, sc, stream = rd_ctx
     M = sc["ctrl"].shape[0]
     Pmax = max(c["width"] * c["height"] for c in cams)
-    rd = R.Renderer(degree=2, max_prims=M, max_views=1, max_pixels=Pmax, max_pairs=6 * Pmax,
-                    max_boundary_pairs=6 * Pmax, tile_size=16, graph=False)
+    ppp = 32 if args.workload == "room8" else 6
+    rd = R.Renderer(degree=int(sc["degree"]), max_prims=M, max_views=1, max_pixels=Pmax, max_pairs=ppp * Pmax,
+                    max_boundary_pairs=ppp * Pmax, tile_size=16, graph=False)
     bufs = []
     gen = torch.Generator(device="cuda").manual_seed(99)
     with torch.cuda.stream(stream):
