@@ -169,17 +169,18 @@ __device__ void bitonic_smem(unsigned long long *s, int n) {
   while (N < n) N <<= 1;
   for (int i = n + threadIdx.x; i < N; i += blockDim.x) s[i] = ~0ull;
   __syncthreads();
+  // every thread takes compare-exchange pairs (i, i + j): pair p has
+  // i = (p with a zero bit inserted at j), so no thread idles on the
+  // upper half of a pair
   for (int k = 2; k <= N; k <<= 1)
     for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        const int ixj = i ^ j;
-        if (ixj > i) {
-          const unsigned long long a = s[i], b = s[ixj];
-          const bool up = (i & k) == 0;
-          if ((a > b) == up) {
-            s[i] = b;
-            s[ixj] = a;
-          }
+      for (int q = threadIdx.x; q < (N >> 1); q += blockDim.x) {
+        const int i = ((q & ~(j - 1)) << 1) | (q & (j - 1));
+        const unsigned long long a = s[i], b = s[i + j];
+        const bool up = (i & k) == 0;
+        if ((a > b) == up) {
+          s[i] = b;
+          s[i + j] = a;
         }
       }
       __syncthreads();
