@@ -14,6 +14,8 @@
 // the edge midpoints, so every weight is 0, 1/2 or 1.
 #include <cmath>
 
+#include <cuda/atomic>
+
 #include "../../include/bgt.h"
 #include "bgt_internal.cuh"
 
@@ -271,6 +273,12 @@ __global__ void __launch_bounds__(256) k_prim_metrics(const MetricArgs s) {
   }
 }
 
+// a word other threads set bits of: a relaxed atomic read (a stale value
+// only costs one redundant atomicOr)
+__device__ __forceinline__ unsigned long long relaxed_load(unsigned long long *p) {
+  return cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>(*p).load(cuda::memory_order_relaxed);
+}
+
 // Visibility measures from the raster of views [v0, v0 + 64): per foreground
 // pixel, the bit of the flat triangle it is seen through (the low 32 bits of
 // its depth key are prim * nsub + sub-triangle) in cell_mask[prim], and bit
@@ -287,12 +295,12 @@ __global__ void __launch_bounds__(256) k_vis_pixels(const int *pid, const unsign
     const int sub = (int)((unsigned)(zbuf[pix] & 0xffffffffull) - (unsigned)id * (unsigned)nsub);
     unsigned long long *c = cell_mask + (size_t)id * words + (sub >> 6);
     const unsigned long long bit = 1ull << (sub & 63);
-    if (!(*c & bit)) atomicOr(c, bit);
+    if (!(relaxed_load(c) & bit)) atomicOr(c, bit);
   }
   if (seen) {
     const int view = find_view(view_off, V, pix);
     const unsigned long long bit = 1ull << (view - v0);
-    if (!(seen[id] & bit)) atomicOr(seen + id, bit);
+    if (!(relaxed_load(seen + id) & bit)) atomicOr(seen + id, bit);
   }
 }
 
