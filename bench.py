@@ -20,7 +20,6 @@ region, and the FP64 CPU oracle timed on a bounded sample of views.
 """
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess

@@ -14,7 +14,7 @@ elementwise bound) and to central finite differences of the oracle.
 import numpy as np
 import pytest
 
-from tests.gpu_util import GRAD_TOL, gpu_forward, grad_rel, make_renderer, split_flat
+from tests.gpu_util import GRAD_TOL, gpu_forward, grad_rel, make_renderer
 
 pytestmark = pytest.mark.gpu
 

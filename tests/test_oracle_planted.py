@@ -4,7 +4,6 @@ only) and checks that the pin that guards it fails, while the oracle as
 committed passes it.
 """
 import numpy as np
-import pytest
 
 from oracle import loss as L
 from oracle import split as S
