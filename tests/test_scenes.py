@@ -43,3 +43,27 @@ def test_shared_edges_share_control_points(scenes):
 def test_random_gaussians_have_ties(scenes):
     g = scenes.random_gaussians(0, 40, 30, 400)
     assert len(np.unique(g["depth"])) < 400
+
+
+def test_photo_pairs_are_seeded_and_in_range(scenes):
+    import numpy as np
+    a = scenes.photo_pair(np.random.default_rng(3), 37, 21)
+    b = scenes.photo_pair(np.random.default_rng(3), 37, 21)
+    for x, y in zip(a, b):
+        assert x.shape == (21, 37, 3) and x.dtype == np.float32 and np.array_equal(x, y)
+        assert x.min() >= 0.0 and x.max() <= 1.0
+    img, gt = a
+    assert np.abs(img - gt).max() > 0  # the target differs from the image
+    assert np.array_equal(gt[7], np.broadcast_to(gt[7, 0], gt[7].shape))  # a flat stripe every seventh row
+
+
+def test_mixed_shapes_cover_the_prune_thresholds(scenes):
+    import numpy as np
+    sc = scenes.mixed_shapes_scene(300, 2, seed=4)
+    assert sc["ctrl"].shape == (300, 6, 3) and sc["color"].shape == (300, 6, 3)
+    assert np.array_equal(sc["ctrl"], scenes.mixed_shapes_scene(300, 2, seed=4)["ctrl"])
+    corners = sc["ctrl"][:, [0, 3, 5]].astype(np.float64)
+    edge = np.linalg.norm(corners[:, 1] - corners[:, 0], axis=1)
+    # edges spread over three decades: tiny and large primitives both present
+    assert edge.min() < 1e-2 and edge.max() > 0.3
+    assert (sc["r_b"] >= 5e-3).all() and (sc["r_b"] <= 2e-2).all()
