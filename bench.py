@@ -52,10 +52,14 @@ def parse():
                     help="add view-dependent SH colour of this degree (1..3) to the scene")
     ap.add_argument("--attr-res", type=int, default=1,
                     help="rotation / scaling attribute maps of this leg resolution (paper: 3)")
-    ap.add_argument("--workload", default="config4", choices=["config4", "view800", "views1024x4", "room8"],
+    ap.add_argument("--workload", default="config4",
+                    choices=["config4", "view800", "views1024x4", "room8", "views800x64"],
                     help="view800: one 800^2 view of the same scene (small case for profilers); "
                          "room8: the 100k degree-3 room under eight 1600x1200 views (large scale); "
-                         "views1024x4: four 1024^2 views (inputs larger than L2, a few GB on the device)")
+                         "views1024x4: four 1024^2 views (inputs larger than L2, a few GB on the device); "
+                         "views800x64: 64 views of 800^2 of the same scene (the metric's resolution, batched)")
+    ap.add_argument("--no-rows", action="store_true",
+                    help="skip the rows reported beside the headline (r_b = 1e-3, 64 x 800^2 batched vs plain)")
     return ap.parse_args()
 
 
@@ -268,12 +272,105 @@ def build_workload(seed_views, rb, workload="config4", sh_degree=0, attr_res=1):
         return sc, [c for c in cams if c["width"] == 800][:1]
     if workload == "views1024x4":
         return sc, [c for c in cams if c["width"] == 1024][:4]
+    if workload == "views800x64":
+        return sc, views800x64(seed_views)
     if seed_views:
         # other ranks render their own 64 views of the same scene (weak scaling)
         rng = np.random.default_rng(1000 + seed_views)
         sizes = [(c["width"], c["height"]) for c in cams]
         cams = scenes.make_views(rng, sizes, 3.5, 5.0)
     return sc, cams
+
+
+def workload_name(workload, rb=1e-2):
+    if workload == "room8":
+        return ("100k degree-3 BG-triangles (10^3 room of 19,200 + 100 cubes + 100 spheres, noise 0.01, "
+                "opacity Beta(5,1)), eight 1600x1200 views, batched fwd+L1+bwd")
+    return {"config4": "", "view800": "one 800^2 view of: ", "views1024x4": "four 1024^2 views of: ",
+            "views800x64": "64 views of 800^2 (radius U[3.5,5]) of: "}[workload] + WORKLOAD.replace(
+                "r_b=1e-2", f"r_b={rb:g}")
+
+
+def views800x64(seed=0):
+    """64 views of 800^2 of the config-4 scene, directions uniform on S^2,
+    radius U[3.5, 5] (the metric's resolution at the batch size of config 4)."""
+    from paper_2503_13961_gb300 import scenes
+    rng = np.random.default_rng(800 + seed)
+    return scenes.make_views(rng, [(800, 800)] * 64, 3.5, 5.0)
+
+
+def time_batched(R, sc, cams, tile, steps, stream, ppp=6, plain=False):
+    """renders/s of the batched fwd + L1 + bwd step on `cams` (graph, one
+    handle for all views), or of the plain single-view path (one call per
+    view) with plain=True; CUDA events on `stream` after 3 warm-up steps."""
+    import torch
+    dev = R.scene_to_device(sc)
+    M = sc["ctrl"].shape[0]
+    sizes = [c["width"] * c["height"] for c in cams]
+    P = sum(sizes)
+    cap = max(sizes) if plain else P
+    rd = R.Renderer(degree=int(sc["degree"]), max_prims=M, max_views=1 if plain else len(cams), max_pixels=cap,
+                    max_pairs=ppp * cap, max_boundary_pairs=ppp * cap, tile_size=tile, graph=not plain)
+    gen = torch.Generator(device="cuda").manual_seed(4321)
+    with torch.cuda.stream(stream):
+        images = torch.empty((P, 3), device="cuda")
+        target = torch.rand((P, 3), device="cuda", generator=gen)
+        dimg = torch.zeros((P, 3), device="cuda")
+        grads = {k: torch.empty_like(dev[k]) for k in R.GRAD_KEYS if k in dev}
+    torch.cuda.synchronize()
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    ccams = R.Cameras(cams)
+    one = [R.Cameras([c]) for c in cams]
+
+    def step():
+        if plain:
+            for v in range(len(cams)):
+                a, b = int(offs[v]), int(offs[v + 1])
+                rd.forward(dev, one[v], images[a:b], stream=stream)
+                rd.l1_loss_grad(images[a:b], target[a:b], 1.0 / (3 * (b - a)), dimg[a:b], stream=stream)
+                rd.backward(dev, one[v], dimg[a:b], grads, stream=stream)
+        else:
+            rd.forward(dev, ccams, images, stream=stream)
+            rd.l1_loss_grad(images, target, 1.0 / (3 * P), dimg, stream=stream)
+            rd.backward(dev, ccams, dimg, grads, stream=stream)
+
+    for _ in range(3):
+        step()
+    rd.sync_status(stream)
+    counts = rd.counts(stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    rd.sync_status(stream)
+    rd.close()
+    return {"value": round(len(cams) / (ms * 1e-3), 2), "unit": "renders/s", "ms_per_step": round(ms, 4),
+            "views": len(cams), "pixels": int(P), "tile": tile, "graph": not plain,
+            "counts": {k: int(v) for k, v in counts.items()}}
+
+
+def run_rows(args, tile, stream):
+    """Rows reported beside the headline: the batched step at the paper's
+    other boundary scale r_b = 1e-3 (Table 4), and 64 views of 800^2 (the
+    metric's resolution) batched against the plain single-view path."""
+    from paper_2503_13961_gb300 import render as R
+    from paper_2503_13961_gb300 import scenes
+    steps = max(3, min(args.steps, 10))
+    sc3, cams3 = scenes.config_scene(4, r_b=1e-3)
+    rows = {"rb_1e-3": time_batched(R, sc3, cams3, tile, steps, stream)}
+    rows["rb_1e-3"]["workload"] = WORKLOAD.replace("r_b=1e-2", "r_b=1e-3")
+    sc, _ = scenes.config_scene(4, r_b=args.rb)
+    c800 = views800x64()
+    b = time_batched(R, sc, c800, tile, steps, stream)
+    pl = time_batched(R, sc, c800, 16, max(2, steps // 2), stream, plain=True)
+    b["workload"] = pl["workload"] = "64 views of 800^2 of the config-4 scene (radius U[3.5,5]), fwd+L1+bwd"
+    rows["batched_800x64"] = b
+    rows["plain_800x64"] = pl
+    rows["batched_over_plain_800x64"] = round(b["value"] / pl["value"], 3)
+    return rows
 
 
 def run_ours(args):
@@ -421,11 +518,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms / args.steps, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded scene generator; stands in for Lego / NeRF-Synthetic)",
-            "config": {"workload": WORKLOAD if args.workload == "config4" else
-                       ("100k degree-3 BG-triangles (10^3 room of 19,200 + 100 cubes + 100 spheres, noise 0.01, "
-                        "opacity Beta(5,1)), eight 1600x1200 views, batched fwd+L1+bwd" if args.workload == "room8"
-                        else ("one 800^2 view of: " if args.workload == "view800" else "four 1024^2 views of: ")
-                        + WORKLOAD),
+            "config": {"workload": workload_name(args.workload, args.rb),
                        "views": V, "pixels": P, "prims": M, "degree": n,
                        "sh_degree": args.sh_degree, "attr_res": args.attr_res,
                        "tile": rd.tile_size, "tile_autotune_ms": tune_ms, "graph": True,
@@ -442,6 +535,8 @@ def run_ours(args):
     if rank == 0:
         out["train_step_eq9"] = run_eq9_step((rd, dev, cams, sc, stream), images, target, dimg, grads, args)
         out["split_prune"] = run_split_prune((rd, dev, cams, sc, stream), grads)
+        if args.workload == "config4" and world == 1 and not args.no_rows:
+            out["rows"] = run_rows(args, rd.tile_size, stream)
     return out, (rd, dev, cams, sc, stream)
 
 
@@ -609,61 +704,102 @@ def run_plain(rd_ctx, args):
     return plain, v800
 
 
-def cpu_baseline(budget_s, rb, sh_degree=0, attr_res=1):
-    """The FP64 oracle on the host cores: whole views of the workload (forward,
-    L1 loss gradient, backward) until the time budget is used; renders/s."""
+def sample_views(cams):
+    """The CPU sample of a mixed-size workload: the first view of each size
+    (256, 512, 800 and 1024 squared in config 4), largest first, so that
+    every resolution of the mix is timed."""
+    first = {}
+    for i, c in enumerate(cams):
+        first.setdefault((c["width"], c["height"]), i)
+    return sorted(first.values(), key=lambda i: -cams[i]["width"] * cams[i]["height"])
+
+
+def oracle_views(sc, cams, idx, rng):
+    """Forward, L1 loss gradient and backward of the views `idx` with the FP64
+    oracle; returns the pixels processed."""
     from oracle import oracle
-    from paper_2503_13961_gb300 import scenes
-    sc, cams = scenes.config_scene(4, r_b=rb)
-    if attr_res > 1:
-        sc = scenes.with_attribute_maps(sc, attr_res)
-    if sh_degree > 0:
-        sc = scenes.with_sh(sc, sh_degree)
-    order = sorted(range(len(cams)), key=lambda i: cams[i]["width"])
-    rng = np.random.default_rng(0)
-    done, t0, pix = 0, time.perf_counter(), 0
-    for i in order:
+    pix = 0
+    for i in idx:
         c = cams[i]
         idm, uv, _ = oracle.raster(sc, c)
         img = oracle.render(sc, c, idm, uv)["image"]
         gt = rng.uniform(size=img.shape)
         dl = np.sign(img - gt) / img.size  # the L1 loss gradient of the GPU step
         oracle.backward(sc, c, dl, idm, uv)
-        done += 1
         pix += c["width"] * c["height"]
+    return pix
+
+
+def cpu_workload(rb, sh_degree=0, attr_res=1):
+    from paper_2503_13961_gb300 import scenes
+    sc, cams = scenes.config_scene(4, r_b=rb)
+    if attr_res > 1:
+        sc = scenes.with_attribute_maps(sc, attr_res)
+    if sh_degree > 0:
+        sc = scenes.with_sh(sc, sh_degree)
+    return sc, cams
+
+
+def sample_text(cams, idx, passes, dt):
+    names = ", ".join(f"#{i} ({cams[i]['width']}^2)" for i in idx)
+    return (f"{passes} pass(es) over views {names} of the 64-view workload (one view of each size), "
+            f"fwd+L1+bwd, FP64, {dt:.1f} s")
+
+
+def cpu_baseline(budget_s, rb, sh_degree=0, attr_res=1):
+    """The FP64 oracle on the host cores: passes over the stratified sample of
+    the workload (one view of each size) until the time budget is used;
+    renders/s and pixels/s."""
+    from oracle import oracle
+    sc, cams = cpu_workload(rb, sh_degree, attr_res)
+    idx = sample_views(cams)
+    rng = np.random.default_rng(0)
+    passes, t0, pix = 0, time.perf_counter(), 0
+    while True:
+        pix += oracle_views(sc, cams, idx, rng)
+        passes += 1
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": round(done / dt, 4), "unit": "renders/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{done} whole views ({pix} px) of the 64-view workload, smallest first, fwd+L1+bwd, "
-                      f"FP64, {dt:.1f} s"}
+    return {"value": round(passes * len(idx) / dt, 4), "unit": "renders/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "pixels_per_s": round(pix / dt, 1), "sample": sample_text(cams, idx, passes, dt)}
+
+
+def run_reference(args, world):
+    """The reference arm: the FP64 oracle (the paper publishes no code), each
+    step one pass over the same stratified sample as cpu_baseline."""
+    from oracle import oracle
+    oracle.build()
+    sc, cams = cpu_workload(args.rb, args.sh_degree, args.attr_res)
+    idx = sample_views(cams)
+    rng = np.random.default_rng(0)
+    for _ in range(args.warmup):
+        oracle_views(sc, cams, idx[-1:], rng)  # the smallest view: page in, spawn the thread pool
+    t0 = time.perf_counter()
+    pix = 0
+    for _ in range(args.steps):
+        pix += oracle_views(sc, cams, idx, rng)
+    dt = time.perf_counter() - t0
+    val = args.steps * len(idx) / dt
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": "renders/s",
+                      "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": round(dt * 1e3 / max(args.steps, 1), 2),
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic", "config": {"workload": workload_name("config4", args.rb)},
+                      "cpu_baseline": {"kind": "oracle", "cores": oracle.num_threads(),
+                                       "sample": sample_text(cams, idx, args.steps, dt),
+                                       "value": round(val, 4), "unit": "renders/s",
+                                       "pixels_per_s": round(pix / dt, 1)},
+                      "e2e": {"value": round(val, 4), "unit": "renders/s", "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}), flush=True)
 
 
 def main():
     args = parse()
     world, rank, _ = dist_env()
     if args.impl == "reference":
-        # the reference arm is the FP64 oracle (the paper publishes no code)
-        if rank != 0:
-            return
-        from oracle import oracle
-        oracle.build()
-        ms_steps = []
-        base = None
-        for _ in range(args.warmup):
-            cpu_baseline(1.0, args.rb, args.sh_degree, args.attr_res)
-        for _ in range(args.steps):
-            base = cpu_baseline(args.cpu_seconds / max(args.steps, 1), args.rb, args.sh_degree, args.attr_res)
-            ms_steps.append(base["value"])
-        val = statistics.mean(ms_steps)
-        print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": "renders/s",
-                          "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                          "data": "synthetic", "config": {"workload": WORKLOAD},
-                          "cpu_baseline": {"kind": "oracle", "cores": base["cores"], "sample": base["sample"],
-                                           "value": round(val, 4), "unit": "renders/s"},
-                          "e2e": {"value": round(val, 4), "unit": "renders/s", "h2d_bytes_per_step": 0,
-                                  "d2h_bytes_per_step": 0}}), flush=True)
+        if rank == 0:
+            run_reference(args, world)
         return
     out, ctx = run_ours(args)
     if rank == 0:

@@ -341,9 +341,9 @@ bgt_status bgt_bin_sort(bgt_handle *h, int width, int height, int count, const i
 
 /* Binning + per-tile sort without any device allocation. The paper has no
  * counterpart: this entry exists for callers that cannot call cudaMalloc --
- * code running inside another framework's memory pool, plugins whose device
- * memory is fixed when they are loaded, or loops that must not synchronize
- * the device at run time (an allocation can) -- and so cannot create a handle.
+ * code running inside another framework's memory pool (whose allocator owns
+ * the device memory), or plugins whose device memory is fixed when they are
+ * loaded -- and so cannot create a handle.
  *
  * It computes what bgt_bin_sort computes (same Gaussians in, same tile
  * ranges and sorted keys out), for one width x height view with tiles of
@@ -357,11 +357,13 @@ bgt_status bgt_bin_sort(bgt_handle *h, int width, int height, int count, const i
  * loads the library until the process exits. Limits: count <= 65,536
  * Gaussians, tiles <= 16,384, total keys <= 262,144; larger inputs return
  * BGT_ERR_CAPACITY (count and tiles before any work, the key total after the
- * counting pass). The call waits for `stream` once (to read the key total)
- * and returns after the sort is enqueued. The first call on a device looks
- * up the array's device address; make that first call before any stream
- * capture. Calls share the array: two calls that overlap on the GPU (other
- * streams, other threads) race and corrupt each other's results. */
+ * counting pass). Every call waits for `stream` once, on the host, to read
+ * the key total, and returns after the sort is enqueued. The first call on a
+ * device looks up the array's device address and keeps it for the life of
+ * the CUDA context (do not use the library across a cudaDeviceReset); make
+ * that first call before any stream capture. Calls share the array: two
+ * calls that overlap on the GPU (other streams, other threads) race and
+ * corrupt each other's results. */
 bgt_status bgt_bin_sort_static(int width, int height, int tile_size, int count, const int *qxy,
                                const float *off, const float *conic, const float *opacity,
                                const float *depth, float alpha_min, long long *out_ranges,

@@ -737,24 +737,15 @@ __global__ void k_load_gaussians(bgt::Params p, bgt::Work w, int count, const in
   w.gC[i] = make_float4(0.f, 0.f, 0.f, __int_as_float(0));
   w.g_depth[i] = depth[i];
   w.g_view[i] = 0;
-  w.g_dsub[i] = 16;
-  uint2 rect = make_uint2(1u, 0u);
-  const float det = Ka * Kc - Kb * Kb;
-  if (o > p.alpha_min && det > 0.f) {
-    const float lvl = 2.0f * (logf(o) - p.log_alpha_min);
-    const float rx = sqrtf(lvl * Kc / det) * 1.0001f + 1e-3f;
-    const float ry = sqrtf(lvl * Ka / det) * 1.0001f + 1e-3f;
-    const float cx = (float)(q & 0xffffu) + off[2 * i], cy = (float)(q >> 16) + off[2 * i + 1];
-    int x0 = (int)ceilf(cx - rx), x1 = (int)floorf(cx + rx), y0 = (int)ceilf(cy - ry), y1 = (int)floorf(cy + ry);
-    x0 = max(x0, 0); y0 = max(y0, 0); x1 = min(x1, vw.W - 1); y1 = min(y1, vw.H - 1);
-    if (x0 <= x1 && y0 <= y1) {
-      x0 /= p.tile; x1 /= p.tile; y0 /= p.tile; y1 /= p.tile;
-      rect = make_uint2((unsigned)x0 | ((unsigned)y0 << 16), (unsigned)x1 | ((unsigned)y1 << 16));
-      w.gA[i].w = fmaxf(rx, ry);
-      for (int ty = y0; ty <= y1; ty++)
-        for (int tx = x0; tx <= x1; tx++) atomicAdd(w.g_tcount + ty * vw.tiles_x + tx, 1);
-    }
-  }
+  w.g_dsub[i] = (unsigned char)(bgt::plain_depth_key(depth[i]) & 31ull);
+  const bgt::ConicBox box = bgt::conic_support_box(Ka, Kb, Kc, o, (float)(q & 0xffffu) + off[2 * i],
+                                                   (float)(q >> 16) + off[2 * i + 1], vw.W, vw.H, p.tile,
+                                                   p.alpha_min, p.log_alpha_min);
+  const uint2 rect = box.rect;
+  w.gA[i].w = box.r;
+  const int x0 = rect.x & 0xffff, y0 = rect.x >> 16, x1 = rect.y & 0xffff, y1 = rect.y >> 16;
+  for (int ty = y0; ty <= y1; ty++)
+    for (int tx = x0; tx <= x1; tx++) atomicAdd(w.g_tcount + ty * vw.tiles_x + tx, 1);
   w.g_rect[i] = rect;
 }
 

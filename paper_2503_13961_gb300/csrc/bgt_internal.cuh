@@ -553,6 +553,45 @@ __device__ inline float2 project_offset(const df *t, const View &vw, int qx, int
 }
 
 // ---------------------------------------------------------------------------
+// Support box of a projected Gaussian given by its conic K = Sigma2D^-1 and
+// opacity o, for the binning stage run on its own (bgt_bin_sort and its
+// allocation-free variant, which must agree bit for bit): the support
+// {o G >= alpha_min} lies inside |dx| <= sqrt(lvl Sigma_xx), |dy| <= sqrt(lvl
+// Sigma_yy), lvl = 2 ln(o / alpha_min), widened slightly, clipped to the W x H
+// view; rect = tile rect (x0 | y0 << 16, x1 | y1 << 16) at tile size t, empty
+// as x0 = 1 > x1 = 0; r = the box's larger half-width, or -1 when empty.
+// ---------------------------------------------------------------------------
+struct ConicBox {
+  uint2 rect;
+  float r;
+};
+
+__device__ inline ConicBox conic_support_box(float Ka, float Kb, float Kc, float o, float cx, float cy, int W,
+                                             int H, int t, float alpha_min, float log_alpha_min) {
+  ConicBox b;
+  b.rect = make_uint2(1u, 0u);
+  b.r = -1.0f;
+  const float det = Ka * Kc - Kb * Kb;
+  if (!(o > alpha_min && det > 0.f)) return b;
+  const float lvl = 2.0f * (logf(o) - log_alpha_min);
+  const float rx = sqrtf(lvl * Kc / det) * 1.0001f + 1e-3f;
+  const float ry = sqrtf(lvl * Ka / det) * 1.0001f + 1e-3f;
+  int x0 = (int)ceilf(cx - rx), x1 = (int)floorf(cx + rx), y0 = (int)ceilf(cy - ry), y1 = (int)floorf(cy + ry);
+  x0 = max(x0, 0); y0 = max(y0, 0); x1 = min(x1, W - 1); y1 = min(y1, H - 1);
+  if (x0 > x1 || y0 > y1) return b;
+  x0 /= t; x1 /= t; y0 /= t; y1 /= t;
+  b.rect = make_uint2((unsigned)x0 | ((unsigned)y0 << 16), (unsigned)x1 | ((unsigned)y1 << 16));
+  b.r = fmaxf(rx, ry);
+  return b;
+}
+
+// depth key of a Gaussian given only its FP32 depth: the exact depth is the
+// FP32 value itself, the middle (16) of the 32 finer sub-steps
+__device__ inline unsigned long long plain_depth_key(float depth) {
+  return ((unsigned long long)__float_as_uint(depth) << 5) | 16ull;
+}
+
+// ---------------------------------------------------------------------------
 // host-side launchers (one per kernel family)
 // ---------------------------------------------------------------------------
 // host-side launchers; each returns the number of kernels it enqueued

@@ -1,22 +1,27 @@
 // Discontinuity-aware alpha blending, forward and backward (Sec. 3.2, Eq. 6-8;
 // supplementary "Backward Derivative").
 //
-// One CTA per screen tile, persistent over a work queue of tiles. The tile's
-// Gaussian list (sorted by depth, index) is staged in shared memory in
-// batches; its boundary list (sorted by primitive, index) is staged once. For
-// pixel q and a Gaussian of primitive g, the coefficient w (Eq. 6) is
-// gamma* = min over g's boundary points b of gamma(|q - b|; sigma_b) (Eq. 7),
-// found by a binary search for g in the tile's list; w = gamma* if I_id(q) = g
-// else 1 - gamma*. alpha = min(alpha_max, o w G) (Eq. 8); pairs with
-// alpha < alpha_min are skipped; blending stops before the pair that would
-// take T below t_stop. Pair evaluation uses explicit IEEE-rounded intrinsics
-// so that the backward pass reproduces the forward decisions exactly.
+// Forward: persistent CTAs take screen tiles from an atomic queue. The tile's
+// boundary list (sorted by primitive, index) is staged once in shared memory;
+// each warp owns an 8 x 4 (16 x 8 at tile 32) block of the tile's pixels and
+// walks the tile's Gaussian list (sorted by depth, index) in chunks of 32,
+// culling each chunk against its block with one ballot. For pixel q and a
+// Gaussian of primitive g, w (Eq. 6) is gamma* = min over g's boundary points b
+// of gamma(|q - b|; sigma_b) (Eq. 7), w = gamma* if I_id(q) = g else 1 - gamma*;
+// a warp-parallel search finds g's range in the boundary list, and a per-warp
+// cache keyed by primitive keeps w per pixel for the primitives seen last.
+// alpha = min(alpha_max, o w G) (Eq. 8); pairs with alpha < alpha_min are
+// skipped; blending stops before the pair that would take T below t_stop.
+// Every composited (warp visit, Gaussian) is recorded for the backward pass:
+// a header (Gaussian, lane mask of the composited pixels, fill record) and,
+// per cache fill, each pixel's most influential boundary point.
 //
-// The backward pass re-traverses each pixel's list back to front from its
-// last composited entry, recovering T_i = T_{i+1} / (1 - alpha_i), and
-// accumulates per-Gaussian gradients (mean, conic, opacity, colour; warp-
-// reduced before the atomics) and per-boundary-point gradients (position,
-// radius).
+// Backward: warps take warp blocks from a queue and replay the block's
+// records back to front: w is rebuilt from the recorded boundary point with
+// the forward's operations, alpha recomputed bit for bit, T_i recovered as
+// T_{i+1} / (1 - alpha_i); per-Gaussian gradients (mean, conic, opacity,
+// colour) are reduced over the warp before the atomics, per-boundary-point
+// gradients (position, radius) summed per (pixel, primitive) in the cache.
 #include "bgt_internal.cuh"
 
 namespace bgt {

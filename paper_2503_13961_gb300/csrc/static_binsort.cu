@@ -62,26 +62,15 @@ __global__ void k_sb_load(Scratch s, int count, int W, int H, int t, int tiles_x
                           const float *opac, const float *depth) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
-  const float Ka = conic[3 * i], Kb = conic[3 * i + 1], Kc = conic[3 * i + 2];
-  const float o = opac[i];
   const unsigned q = (unsigned)qxy[i];
-  s.dkey[i] = ((unsigned long long)__float_as_uint(depth[i]) << 5) | 16ull;
-  uint2 rect = make_uint2(1u, 0u);
-  const float det = Ka * Kc - Kb * Kb;
-  if (o > alpha_min && det > 0.f) {
-    const float lvl = 2.0f * (logf(o) - log_alpha_min);
-    const float rx = sqrtf(lvl * Kc / det) * 1.0001f + 1e-3f;
-    const float ry = sqrtf(lvl * Ka / det) * 1.0001f + 1e-3f;
-    const float cx = (float)(q & 0xffffu) + off[2 * i], cy = (float)(q >> 16) + off[2 * i + 1];
-    int x0 = (int)ceilf(cx - rx), x1 = (int)floorf(cx + rx), y0 = (int)ceilf(cy - ry), y1 = (int)floorf(cy + ry);
-    x0 = max(x0, 0); y0 = max(y0, 0); x1 = min(x1, W - 1); y1 = min(y1, H - 1);
-    if (x0 <= x1 && y0 <= y1) {
-      x0 /= t; x1 /= t; y0 /= t; y1 /= t;
-      rect = make_uint2((unsigned)x0 | ((unsigned)y0 << 16), (unsigned)x1 | ((unsigned)y1 << 16));
-      for (int ty = y0; ty <= y1; ty++)
-        for (int tx = x0; tx <= x1; tx++) atomicAdd(s.count + ty * tiles_x + tx, 1);
-    }
-  }
+  s.dkey[i] = bgt::plain_depth_key(depth[i]);
+  const bgt::ConicBox box = bgt::conic_support_box(conic[3 * i], conic[3 * i + 1], conic[3 * i + 2], opac[i],
+                                                   (float)(q & 0xffffu) + off[2 * i], (float)(q >> 16) + off[2 * i + 1],
+                                                   W, H, t, alpha_min, log_alpha_min);
+  const uint2 rect = box.rect;
+  const int x0 = rect.x & 0xffff, y0 = rect.x >> 16, x1 = rect.y & 0xffff, y1 = rect.y >> 16;
+  for (int ty = y0; ty <= y1; ty++)
+    for (int tx = x0; tx <= x1; tx++) atomicAdd(s.count + ty * tiles_x + tx, 1);
   s.rect[i] = rect;
 }
 
@@ -176,9 +165,13 @@ __global__ void __launch_bounds__(kThreads) k_sb_sort(Scratch s, int tiles, cons
   }
 }
 
-// device address of the static scratch, looked up once per device
+// Device address of the static scratch, looked up on the first call on each
+// device and kept: the address stays valid while the CUDA context that loaded
+// the module lives (a cudaDeviceReset destroys it; the library must not be
+// used across one).
+constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-unsigned char *g_addr[64] = {};
+unsigned char *g_addr[kMaxDevices] = {};
 
 }  // namespace
 
@@ -195,7 +188,7 @@ extern "C" bgt_status bgt_bin_sort_static(int width, int height, int tile_size, 
   const long long tiles = (long long)tiles_x * tiles_y;
   if (count > kMaxGauss || tiles > kMaxTiles) return BGT_ERR_CAPACITY;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return BGT_ERR_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return BGT_ERR_CUDA;
   unsigned char *base = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);

@@ -335,10 +335,14 @@ def test_full_size_config5_room_100k_degree3(oracle, scenes):
     assert float(grads["opacity"].abs().sum()) > 0
 
 
-def test_full_size_batched_64_views(oracle, scenes):
+@pytest.mark.parametrize("r_b", [1e-2, 1e-3])
+def test_full_size_batched_64_views(oracle, scenes, r_b):
+    """The benchmark's launch configuration (64 views of mixed size, graph,
+    tile 16) at both boundary scales of the paper's Table 4; at r_b = 1e-3
+    the boundary radius is sub-pixel (0.2-0.7 px)."""
     import torch
     from paper_2503_13961_gb300 import render as R
-    sc, cams = scenes.config_scene(4)
+    sc, cams = scenes.config_scene(4, r_b=r_b)
     rd = make_renderer(sc, cams, graph=True, tile=16)
     dev = R.scene_to_device(sc)
     s = torch.cuda.Stream()

@@ -4,12 +4,18 @@ allocate device memory (no handle; scratch in a static device array).
 Its tile ranges and sorted keys must equal those of bgt_bin_sort (integer
 outputs: exact) on the same Gaussians, for two calls in a row (the second on
 different inputs, so nothing left in the shared scratch may leak into it),
-and inputs beyond its limits must be rejected. This file is collected last.
+and must pass the same check against the oracle's per-pixel lists as the
+handle's binning (every Gaussian whose FP64 support holds a pixel listed in
+the pixel's tile in the oracle's (depth, index) order, every other entry
+valid); inputs beyond its limits must be rejected. This file is collected
+last.
 """
 import ctypes
 
 import numpy as np
 import pytest
+
+from tests.test_gpu_sort import _check_lists
 
 pytestmark = pytest.mark.gpu
 
@@ -40,7 +46,7 @@ def _static_call(lib, d, count, W, H, tile, alpha_min, cap):
 
 
 @pytest.mark.parametrize("W,H,n,tile,radius", [(70, 45, 700, 16, (0.5, 3.0)), (40, 36, 9000, 32, (2.0, 5.0))])
-def test_static_entry_matches_bin_sort_twice(scenes, W, H, n, tile, radius):
+def test_static_entry_matches_bin_sort_twice(oracle, scenes, W, H, n, tile, radius):
     from paper_2503_13961_gb300 import _abi
     from paper_2503_13961_gb300 import render as R
     lib = _abi.load()
@@ -55,6 +61,8 @@ def test_static_entry_matches_bin_sort_twice(scenes, W, H, n, tile, radius):
         assert rc == 0, _abi.STATUS_NAMES.get(rc, rc)
         assert np.array_equal(ranges, ref["ranges"])
         assert np.array_equal(keys, ref["keys"])
+        ptr, idx = oracle.pixel_lists(g, W, H, alpha_min=am)
+        _check_lists(g, W, H, tile, ranges, keys, ptr, idx, am)
     rd.close()
 
 
