@@ -247,10 +247,10 @@ __device__ inline RVert raster_vertex(const float *cp, int a, int b, int L, cons
   return raster_vertex<N>(cp, lattice_frac(a, L), lattice_frac(b, L), lattice_frac(L - a - b, L), v, near_z);
 }
 
-// vertex at barycentric (u, vv, w) = (a, b, L - a - b) / L
+// Bernstein weights ((coef u^i) v^j) w^k of a lattice vertex, in control-point
+// order, each product one IEEE rounding
 template <int N>
-__device__ inline RVert raster_vertex(const float *cp, float u, float vv, float w, const View &v, float near_z) {
-  RVert o;
+__device__ inline void lattice_bernstein(float u, float vv, float w, float *B) {
   float pu[N + 1], pv[N + 1], pw[N + 1];
   pu[0] = pv[0] = pw[0] = 1.0f;
 #pragma unroll
@@ -259,19 +259,29 @@ __device__ inline RVert raster_vertex(const float *cp, float u, float vv, float 
     pv[m] = __fmul_rn(pv[m - 1], vv);
     pw[m] = __fmul_rn(pw[m - 1], w);
   }
-  float Sx = 0.f, Sy = 0.f, Sz = 0.f;
   int idx = 0;
 #pragma unroll
   for (int i = N; i >= 0; i--)
 #pragma unroll
     for (int j = N - i; j >= 0; j--) {
       const int k = N - i - j;
-      const float B = __fmul_rn(__fmul_rn(__fmul_rn(multinom(N, i, j, k), pu[i]), pv[j]), pw[k]);
-      Sx = __fmaf_rn(B, __ldg(cp + 3 * idx + 0), Sx);
-      Sy = __fmaf_rn(B, __ldg(cp + 3 * idx + 1), Sy);
-      Sz = __fmaf_rn(B, __ldg(cp + 3 * idx + 2), Sz);
-      idx++;
+      B[idx++] = __fmul_rn(__fmul_rn(__fmul_rn(multinom(N, i, j, k), pu[i]), pv[j]), pw[k]);
     }
+}
+
+// The vertex of Bernstein weights B (lattice_bernstein) of control points
+// cp[Ncp][3]: fused multiply-add accumulation in control-point order, camera
+// transform, projection and snap. cp may point to registers or memory.
+template <int N>
+__device__ inline RVert vertex_from_weights(const float *B, const float *cp, const View &v, float near_z) {
+  RVert o;
+  float Sx = 0.f, Sy = 0.f, Sz = 0.f;
+#pragma unroll
+  for (int idx = 0; idx < (N + 1) * (N + 2) / 2; idx++) {
+    Sx = __fmaf_rn(B[idx], cp[3 * idx + 0], Sx);
+    Sy = __fmaf_rn(B[idx], cp[3 * idx + 1], Sy);
+    Sz = __fmaf_rn(B[idx], cp[3 * idx + 2], Sz);
+  }
   float Xc = __fmul_rn(v.R[0], Sx); Xc = __fmaf_rn(v.R[1], Sy, Xc); Xc = __fmaf_rn(v.R[2], Sz, Xc); Xc = __fadd_rn(Xc, v.t[0]);
   float Yc = __fmul_rn(v.R[3], Sx); Yc = __fmaf_rn(v.R[4], Sy, Yc); Yc = __fmaf_rn(v.R[5], Sz, Yc); Yc = __fadd_rn(Yc, v.t[1]);
   float Zc = __fmul_rn(v.R[6], Sx); Zc = __fmaf_rn(v.R[7], Sy, Zc); Zc = __fmaf_rn(v.R[8], Sz, Zc); Zc = __fadd_rn(Zc, v.t[2]);
@@ -288,6 +298,17 @@ __device__ inline RVert raster_vertex(const float *cp, float u, float vv, float 
     o.X = o.Y = 0;
   }
   return o;
+}
+
+// vertex at barycentric (u, vv, w) = (a, b, L - a - b) / L
+template <int N>
+__device__ inline RVert raster_vertex(const float *cp, float u, float vv, float w, const View &v, float near_z) {
+  float B[(N + 1) * (N + 2) / 2];
+  lattice_bernstein<N>(u, vv, w, B);
+  float c[3 * (N + 1) * (N + 2) / 2];
+#pragma unroll
+  for (int k = 0; k < 3 * (N + 1) * (N + 2) / 2; k++) c[k] = __ldg(cp + k);
+  return vertex_from_weights<N>(B, c, v, near_z);
 }
 
 // exact edge function (b - a) x (P - a) on the fixed-point grid

@@ -6,9 +6,16 @@
 // is kept by a 64-bit atomicMin on (depth bits << 32 | sub-triangle id). The
 // resolve pass turns the winning key into I_id and perspective-correct I_uv.
 //
-// One warp per (view, primitive): the lanes evaluate the (L+1)(L+2)/2 lattice
-// vertices into shared memory once, then each lane rasterizes its flat
-// triangles. Every operation that decides coverage or the depth order is an
+// Grid: one block row per view (blockIdx.y), warps take primitives of that
+// view. Per block, the Bernstein weights of the (L+1)(L+2)/2 lattice vertices
+// and the vertex slots of the L^2 flat triangles are tabulated once in shared
+// memory. Per primitive, the lanes evaluate its lattice vertices from the
+// table and its control points (held in registers) into shared memory; then
+// each lane rasterizes its flat triangles: an empty pixel box is rejected
+// before any edge function, and the pixel centres of the box are walked with
+// incrementally updated edge functions, in 32-bit integers when the box is
+// under 125 px (exact: every product stays below 2^30) and in 64-bit ones
+// otherwise. Every operation that decides coverage or the depth order is an
 // explicit IEEE-rounded intrinsic, so the result is reproducible bit for bit.
 #include <climits>
 
@@ -19,7 +26,9 @@ namespace bgt {
 namespace {
 
 constexpr int kRasterWarps = 4;
+constexpr int kPrimsPerWarp = 8;  // primitives each warp rasterizes per block (amortises the tables)
 constexpr int kMaxVerts = (kMaxTess + 1) * (kMaxTess + 2) / 2;
+constexpr int kSpan32 = 32000;    // box spans (1/256 px) below which edge functions fit 32 bits
 
 __device__ inline int vslot(int a, int b, int L) { return a * (L + 1) - a * (a - 1) / 2 + b; }
 
@@ -33,27 +42,71 @@ __device__ inline void slot_to_ab(int vi, int L, int &a, int &b) {
   b = rem;
 }
 
+__device__ __forceinline__ float to_f32(int x) { return __int2float_rn(x); }
+__device__ __forceinline__ float to_f32(long long x) { return __ll2float_rn(x); }
+
+// Pixel centres of the box [px0, px1] x [py0, py1] inside the flat triangle
+// (X, Y, IZ) (counter-clockwise after the swap, area2 > 0, fill-rule flags
+// t0..t2 of the edges 1-2, 2-0, 0-1): edge functions (b - a) x (P - a) start
+// at the box corner and step by their constant differences; I is int when
+// every value stays below 2^31 (box span < kSpan32), else long long. Covered
+// pixels take the depth test with the interpolated depth 1 / sum(l_i / z_i).
+template <typename I>
+__device__ __forceinline__ void raster_box(const int *X, const int *Y, const float *IZ, bool t0, bool t1, bool t2,
+                                           float af, int px0, int px1, int py0, int py1, unsigned gid,
+                                           unsigned long long *zb, int W) {
+  const I a0 = (I)(X[2] - X[1]), b0 = (I)(Y[2] - Y[1]);
+  const I a1 = (I)(X[0] - X[2]), b1 = (I)(Y[0] - Y[2]);
+  const I a2 = (I)(X[1] - X[0]), b2 = (I)(Y[1] - Y[0]);
+  const int Px0 = px0 * 256, Py0 = py0 * 256;
+  I r0 = a0 * (I)(Py0 - Y[1]) - b0 * (I)(Px0 - X[1]);
+  I r1 = a1 * (I)(Py0 - Y[2]) - b1 * (I)(Px0 - X[2]);
+  I r2 = a2 * (I)(Py0 - Y[0]) - b2 * (I)(Px0 - X[0]);
+  const I sx0 = b0 * (I)256, sx1 = b1 * (I)256, sx2 = b2 * (I)256;  // per pixel step in x (subtracted)
+  const I sy0 = a0 * (I)256, sy1 = a1 * (I)256, sy2 = a2 * (I)256;  // per pixel step in y (added)
+  for (int py = py0; py <= py1; py++) {
+    I e0 = r0, e1 = r1, e2 = r2;
+    for (int px = px0; px <= px1; px++) {
+      if ((e0 > 0 || (e0 == 0 && t0)) && (e1 > 0 || (e1 == 0 && t1)) && (e2 > 0 || (e2 == 0 && t2))) {
+        const float l0 = __fdiv_rn(to_f32(e0), af);
+        const float l1 = __fdiv_rn(to_f32(e1), af);
+        const float l2 = __fdiv_rn(to_f32(e2), af);
+        float sd = __fmul_rn(l0, IZ[0]);
+        sd = __fmaf_rn(l1, IZ[1], sd);
+        sd = __fmaf_rn(l2, IZ[2], sd);
+        const float z = __fdiv_rn(1.0f, sd);
+        atomicMin(zb + (size_t)py * W + px, ((unsigned long long)__float_as_uint(z) << 32) | (unsigned long long)gid);
+      }
+      e0 -= sx0;
+      e1 -= sx1;
+      e2 -= sx2;
+    }
+    r0 += sy0;
+    r1 += sy1;
+    r2 += sy2;
+  }
+}
+
 template <int N>
-__global__ void __launch_bounds__(kRasterWarps * 32) k_raster(Params p, Scene s, Work w) {
+__global__ void __launch_bounds__(kRasterWarps * 32, N <= 2 ? 8 : 6) k_raster(Params p, Scene s, Work w) {
+  constexpr int NCP = (N + 1) * (N + 2) / 2;
+  __shared__ float sB[kMaxVerts * NCP];  // Bernstein weights of the lattice vertices
+  __shared__ int2 s_tri[kMaxTess * kMaxTess];  // vertex slots (8 bits each) and sub-triangle id
   __shared__ int sX[kRasterWarps][kMaxVerts];
   __shared__ int sY[kRasterWarps][kMaxVerts];
   __shared__ float sIZ[kRasterWarps][kMaxVerts];
-  // lattice tables of this launch's level L: k / L, vertex (a, b), and per flat
-  // triangle its three vertex slots and its id
-  __shared__ float s_frac[kMaxTess + 1];
-  __shared__ int s_vab[kMaxVerts];
-  __shared__ int2 s_tri[kMaxTess * kMaxTess];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long items = (long long)p.V * p.M;
   const int L = p.L;
   const int NV = (L + 1) * (L + 2) / 2;
   const int up_count = L * (L + 1) / 2;
   const int nsub = 2 * L * L;
-  for (int i = threadIdx.x; i <= L; i += blockDim.x) s_frac[i] = lattice_frac(i, L);
   for (int vi = threadIdx.x; vi < NV; vi += blockDim.x) {
     int a, b;
     slot_to_ab(vi, L, a, b);
-    s_vab[vi] = a | (b << 8);
+    float Bw[NCP];
+    lattice_bernstein<N>(lattice_frac(a, L), lattice_frac(b, L), lattice_frac(L - a - b, L), Bw);
+#pragma unroll
+    for (int t = 0; t < NCP; t++) sB[vi * NCP + t] = Bw[t];
   }
   for (int ti = threadIdx.x; ti < L * L; ti += blockDim.x) {
     int a, down, rem;
@@ -74,37 +127,41 @@ __global__ void __launch_bounds__(kRasterWarps * 32) k_raster(Params p, Scene s,
     s_tri[ti] = make_int2(vslot(va[0], vb[0], L) | (vslot(va[1], vb[1], L) << 8) | (vslot(va[2], vb[2], L) << 16), sid);
   }
   __syncthreads();
-  for (long long item = (long long)blockIdx.x * kRasterWarps + warp; item < items;
-       item += (long long)gridDim.x * kRasterWarps) {
-    const int view = (int)(item / p.M);
-    const int prim = (int)(item - (long long)view * p.M);
-    const View vw = w.views[view];
-    const float *cp = s.ctrl + (size_t)prim * p.ncp * 3;
+  const View vw = w.views[blockIdx.y];
+  const int W = vw.W, H = vw.H;
+  unsigned long long *zb = w.zbuf + vw.pix_off;
+  for (int prim = blockIdx.x * kRasterWarps + warp; prim < p.M; prim += gridDim.x * kRasterWarps) {
+    const float *cp = s.ctrl + (size_t)prim * NCP * 3;
+    float c[3 * NCP];
+#pragma unroll
+    for (int k = 0; k < 3 * NCP; k++) c[k] = __ldg(cp + k);
     for (int vi = lane; vi < NV; vi += 32) {
-      const int ab = s_vab[vi], a = ab & 0xff, b = ab >> 8;
-      const RVert r = raster_vertex<N>(cp, s_frac[a], s_frac[b], s_frac[L - a - b], vw, p.near_z);
+      const RVert r = vertex_from_weights<N>(sB + vi * NCP, c, vw, p.near_z);
       sX[warp][vi] = r.valid ? r.X : INT_MIN;
       sY[warp][vi] = r.Y;
       sIZ[warp][vi] = r.iz;
     }
     __syncwarp();
-    const int W = vw.W, H = vw.H;
-    unsigned long long *zb = w.zbuf + vw.pix_off;
     for (int ti = lane; ti < L * L; ti += 32) {
       const int2 tri = s_tri[ti];
-      const int sid = tri.y;
       int X[3], Y[3];
       float IZ[3];
       bool ok = true;
 #pragma unroll
-      for (int c = 0; c < 3; c++) {
-        const int sl = (tri.x >> (8 * c)) & 0xff;
-        X[c] = sX[warp][sl];
-        Y[c] = sY[warp][sl];
-        IZ[c] = sIZ[warp][sl];
-        ok = ok && (X[c] != INT_MIN);
+      for (int k = 0; k < 3; k++) {
+        const int sl = (tri.x >> (8 * k)) & 0xff;
+        X[k] = sX[warp][sl];
+        Y[k] = sY[warp][sl];
+        IZ[k] = sIZ[warp][sl];
+        ok = ok && (X[k] != INT_MIN);
       }
       if (!ok) continue;
+      const int xmin = min(X[0], min(X[1], X[2])), xmax = max(X[0], max(X[1], X[2]));
+      const int ymin = min(Y[0], min(Y[1], Y[2])), ymax = max(Y[0], max(Y[1], Y[2]));
+      // pixel range: ceil(xmin / 256) .. floor(xmax / 256) (arithmetic shift = floor)
+      const int px0 = max(-((-xmin) >> 8), 0), px1 = min(xmax >> 8, W - 1);
+      const int py0 = max(-((-ymin) >> 8), 0), py1 = min(ymax >> 8, H - 1);
+      if (px0 > px1 || py0 > py1) continue;  // no pixel centre in the box
       long long area2 = edge_fn(X[0], Y[0], X[1], Y[1], X[2], Y[2]);
       if (area2 == 0) continue;
       if (area2 < 0) {
@@ -113,41 +170,15 @@ __global__ void __launch_bounds__(kRasterWarps * 32) k_raster(Params p, Scene s,
         const float tz = IZ[1]; IZ[1] = IZ[2]; IZ[2] = tz;
         area2 = -area2;
       }
-      const int xmin = min(X[0], min(X[1], X[2])), xmax = max(X[0], max(X[1], X[2]));
-      const int ymin = min(Y[0], min(Y[1], Y[2])), ymax = max(Y[0], max(Y[1], Y[2]));
-      // pixel range: ceil(xmin / 256) .. floor(xmax / 256) (arithmetic shift = floor)
-      int px0 = -((-xmin) >> 8), px1 = xmax >> 8;
-      int py0 = -((-ymin) >> 8), py1 = ymax >> 8;
-      px0 = max(px0, 0); py0 = max(py0, 0);
-      px1 = min(px1, W - 1); py1 = min(py1, H - 1);
-      if (px0 > px1 || py0 > py1) continue;
       const bool t0 = owns_zero_edge(X[1], Y[1], X[2], Y[2]);
       const bool t1 = owns_zero_edge(X[2], Y[2], X[0], Y[0]);
       const bool t2 = owns_zero_edge(X[0], Y[0], X[1], Y[1]);
       const float af = __ll2float_rn(area2);
-      const unsigned int gid = (unsigned int)prim * (unsigned int)nsub + (unsigned int)sid;
-      for (int py = py0; py <= py1; py++) {
-        const int Py = py * 256;
-        for (int px = px0; px <= px1; px++) {
-          const int Px = px * 256;
-          const long long e0 = edge_fn(X[1], Y[1], X[2], Y[2], Px, Py);
-          const long long e1 = edge_fn(X[2], Y[2], X[0], Y[0], Px, Py);
-          const long long e2 = edge_fn(X[0], Y[0], X[1], Y[1], Px, Py);
-          const bool in = (e0 > 0 || (e0 == 0 && t0)) && (e1 > 0 || (e1 == 0 && t1)) &&
-                          (e2 > 0 || (e2 == 0 && t2));
-          if (!in) continue;
-          const float l0 = __fdiv_rn(__ll2float_rn(e0), af);
-          const float l1 = __fdiv_rn(__ll2float_rn(e1), af);
-          const float l2 = __fdiv_rn(__ll2float_rn(e2), af);
-          float sd = __fmul_rn(l0, IZ[0]);
-          sd = __fmaf_rn(l1, IZ[1], sd);
-          sd = __fmaf_rn(l2, IZ[2], sd);
-          const float z = __fdiv_rn(1.0f, sd);
-          const unsigned long long key =
-              ((unsigned long long)__float_as_uint(z) << 32) | (unsigned long long)gid;
-          atomicMin(zb + (size_t)py * W + px, key);
-        }
-      }
+      const unsigned gid = (unsigned)prim * (unsigned)nsub + (unsigned)tri.y;
+      if (xmax - xmin < kSpan32 && ymax - ymin < kSpan32)
+        raster_box<int>(X, Y, IZ, t0, t1, t2, af, px0, px1, py0, py1, gid, zb, W);
+      else
+        raster_box<long long>(X, Y, IZ, t0, t1, t2, af, px0, px1, py0, py1, gid, zb, W);
     }
     __syncwarp();
   }
@@ -207,11 +238,10 @@ __global__ void k_resolve(Params p, Scene s, Work w) {
 }  // namespace
 
 int launch_raster(const Params &p, const Scene &s, const Work &w, cudaStream_t st) {
-  const long long items = (long long)p.V * p.M;
-  if (items == 0) return 0;
-  long long blocks = (items + kRasterWarps - 1) / kRasterWarps;
-  if (blocks > (1ll << 30)) blocks = 1ll << 30;
-  dispatch_degree(p.n, [&](auto d) { k_raster<decltype(d)::value><<<(unsigned)blocks, kRasterWarps * 32, 0, st>>>(p, s, w); });
+  if (p.V == 0 || p.M == 0) return 0;
+  const int per_block = kRasterWarps * kPrimsPerWarp;
+  const dim3 grid((unsigned)((p.M + per_block - 1) / per_block), (unsigned)p.V);
+  dispatch_degree(p.n, [&](auto d) { k_raster<decltype(d)::value><<<grid, kRasterWarps * 32, 0, st>>>(p, s, w); });
   return 1;
 }
 
