@@ -299,7 +299,7 @@ def views800x64(seed=0):
     return scenes.make_views(rng, [(800, 800)] * 64, 3.5, 5.0)
 
 
-def time_batched(R, sc, cams, tile, steps, stream, ppp=6, plain=False):
+def time_batched(R, sc, cams, tuning, steps, stream, ppp=6, plain=False):
     """renders/s of the batched fwd + L1 + bwd step on `cams` (graph, one
     handle for all views), or of the plain single-view path (one call per
     view) with plain=True; CUDA events on `stream` after 3 warm-up steps."""
@@ -310,7 +310,8 @@ def time_batched(R, sc, cams, tile, steps, stream, ppp=6, plain=False):
     P = sum(sizes)
     cap = max(sizes) if plain else P
     rd = R.Renderer(degree=int(sc["degree"]), max_prims=M, max_views=1 if plain else len(cams), max_pixels=cap,
-                    max_pairs=ppp * cap, max_boundary_pairs=ppp * cap, tile_size=tile, graph=not plain)
+                    max_pairs=ppp * cap, max_boundary_pairs=ppp * cap, graph=not plain)
+    rd.set_tuning(**tuning)
     gen = torch.Generator(device="cuda").manual_seed(4321)
     with torch.cuda.stream(stream):
         images = torch.empty((P, 3), device="cuda")
@@ -348,11 +349,11 @@ def time_batched(R, sc, cams, tile, steps, stream, ppp=6, plain=False):
     rd.sync_status(stream)
     rd.close()
     return {"value": round(len(cams) / (ms * 1e-3), 2), "unit": "renders/s", "ms_per_step": round(ms, 4),
-            "views": len(cams), "pixels": int(P), "tile": tile, "graph": not plain,
+            "views": len(cams), "pixels": int(P), "tuning": tuning, "graph": not plain,
             "counts": {k: int(v) for k, v in counts.items()}}
 
 
-def run_rows(args, tile, stream):
+def run_rows(args, tuning, stream):
     """Rows reported beside the headline: the batched step at the paper's
     other boundary scale r_b = 1e-3 (Table 4), and 64 views of 800^2 (the
     metric's resolution) batched against the plain single-view path."""
@@ -360,12 +361,12 @@ def run_rows(args, tile, stream):
     from paper_2503_13961_gb300 import scenes
     steps = max(3, min(args.steps, 10))
     sc3, cams3 = scenes.config_scene(4, r_b=1e-3)
-    rows = {"rb_1e-3": time_batched(R, sc3, cams3, tile, steps, stream)}
+    rows = {"rb_1e-3": time_batched(R, sc3, cams3, tuning, steps, stream)}
     rows["rb_1e-3"]["workload"] = WORKLOAD.replace("r_b=1e-2", "r_b=1e-3")
     sc, _ = scenes.config_scene(4, r_b=args.rb)
     c800 = views800x64()
-    b = time_batched(R, sc, c800, tile, steps, stream)
-    pl = time_batched(R, sc, c800, 16, max(2, steps // 2), stream, plain=True)
+    b = time_batched(R, sc, c800, tuning, steps, stream)
+    pl = time_batched(R, sc, c800, dict(tuning, tile_size=16), max(2, steps // 2), stream, plain=True)
     b["workload"] = pl["workload"] = "64 views of 800^2 of the config-4 scene (radius U[3.5,5]), fwd+L1+bwd"
     rows["batched_800x64"] = b
     rows["plain_800x64"] = pl
@@ -442,6 +443,7 @@ def run_ours(args):
     # tile size) records CUDA events between the stages on the same stream
     prof_rd = R.Renderer(degree=n, max_prims=M, max_views=V, max_pixels=P, max_pairs=ppp * P,
                          max_boundary_pairs=ppp * P, tile_size=rd.tile_size, graph=False)
+    prof_rd.set_tuning(**rd.tuning())
     prof_rd.set_profiling(True)
     stage_ms = {}
     units = {}
@@ -521,7 +523,7 @@ def run_ours(args):
             "config": {"workload": workload_name(args.workload, args.rb),
                        "views": V, "pixels": P, "prims": M, "degree": n,
                        "sh_degree": args.sh_degree, "attr_res": args.attr_res,
-                       "tile": rd.tile_size, "tile_autotune_ms": tune_ms, "graph": True,
+                       "tile": rd.tile_size, "tile_autotune_ms": tune_ms, "tuning": rd.tuning(), "graph": True,
                        "counts": {k: int(v) for k, v in counts.items()},
                        "l2": "inputs larger than L2 (no flush needed)", "parallelism": f"replicas x{world}"},
             "clocks": clk,
@@ -536,7 +538,7 @@ def run_ours(args):
         out["train_step_eq9"] = run_eq9_step((rd, dev, cams, sc, stream), images, target, dimg, grads, args)
         out["split_prune"] = run_split_prune((rd, dev, cams, sc, stream), grads)
         if args.workload == "config4" and world == 1 and not args.no_rows:
-            out["rows"] = run_rows(args, rd.tile_size, stream)
+            out["rows"] = run_rows(args, rd.tuning(), stream)
     return out, (rd, dev, cams, sc, stream)
 
 

@@ -62,7 +62,10 @@ typedef struct {
   long long max_boundary_pairs; /* capacity: (boundary point, tile) pairs per call */
   long long max_blend_pairs;    /* capacity: (pixel, Gaussian) pairs the forward pass composites
                                    per call, recorded for the backward pass: headers get 1/2,
-                                   fill records 1/32 of it; 0 = 32 per pixel, at least 2^22 */
+                                   fill records 1/32 of it; 0 = 8 per pixel, at least 2^22.
+                                   Warp blocks whose records do not fit are differentiated by
+                                   re-walking their tile lists (bgt_get_counts out[7]): not an
+                                   error, only slower */
   int tess_level;               /* L: each primitive becomes L^2 flat triangles (1..16) */
   int tile_size;                /* screen tile edge: 8, 16 or 32 pixels */
   float k_b;                    /* boundary radius sigma = k_b fx r_b / z (Sec. 3.2) */
@@ -151,7 +154,8 @@ bgt_status bgt_render_bwd(bgt_handle *h, const bgt_scene *scene, const bgt_camer
 
 /* Wait for `stream`, then report and clear the device status word:
  * BGT_ERR_CAPACITY (pairs or boundary pairs exceeded their capacity),
- * BGT_ERR_NONFINITE, or BGT_OK. */
+ * BGT_ERR_NONFINITE, or BGT_OK. Blend records that did not fit are not an
+ * error (see max_blend_pairs). */
 bgt_status bgt_sync_status(bgt_handle *h, void *stream);
 
 /* Text of the last error on this handle ("" if none). Owned by the handle. */
@@ -161,9 +165,12 @@ const char *bgt_last_error(const bgt_handle *h);
  * pixels F (= Gaussians), out[1] = boundary points |B|, out[2] = Gaussian
  * tile pairs K, out[3] = boundary tile pairs Kb, out[4] = total tiles,
  * out[5] = blend-record header slots taken (capacity max_blend_pairs / 2),
- * out[6] = blend fill-record units taken (capacity max_blend_pairs / 32);
- * taken slots beyond a capacity were not written (BGT_ERR_CAPACITY). */
-bgt_status bgt_get_counts(bgt_handle *h, long long out[7], void *stream);
+ * out[6] = blend fill-record units taken (capacity max_blend_pairs / 32),
+ * out[7] = warp blocks (32 pixels, 128 at tile 32) whose records did not
+ * fit: the backward pass re-walks their tile lists instead of replaying
+ * records (same gradients, slower); taken slots beyond a capacity were not
+ * written. */
+bgt_status bgt_get_counts(bgt_handle *h, long long out[8], void *stream);
 
 /* Change the tile size (8, 16 or 32) used by later calls. Images do not
  * depend on it (every pixel composites the same pairs in the same order). */
@@ -189,10 +196,33 @@ bgt_status bgt_set_profiling(bgt_handle *h, int on);
 bgt_status bgt_get_profile(bgt_handle *h, float ms[8], int *kernels_fwd, int *kernels_bwd,
                            unsigned long long units[8]);
 
+/* Scheduling of the batched launches: the tile size and the work each
+ * queue dequeue or persistent block takes. No knob changes an image (every
+ * pixel composites the same pairs in the same order); gradients change only
+ * by the summation order of FP32 atomics. */
+typedef struct {
+  int tile_size;           /* screen tile edge: 8, 16 or 32 pixels */
+  int raster_prims;        /* primitives each rasterizer warp takes per block, 1..64 (default 8) */
+  int bwd_dequeue;         /* warp blocks a backward-blending warp takes per queue dequeue, 1..8 (default 1) */
+  int chain_blocks_per_sm; /* persistent blocks per SM of the chain-rule kernels, 1..32 (default 8) */
+} bgt_tuning;
+
+/* Current scheduling of the handle. BGT_ERR_INVALID_ARG for NULL. */
+bgt_status bgt_get_tuning(const bgt_handle *h, bgt_tuning *out);
+
+/* Set the scheduling used by later calls; BGT_ERR_INVALID_ARG (nothing
+ * changed) for a value out of its range. A backward must follow a forward
+ * of the same tile size (changing the tile size invalidates the forward). */
+bgt_status bgt_set_tuning(bgt_handle *h, const bgt_tuning *t);
+
 /* Autotuner: time `iters` forward + backward passes of this workload at each
  * tile size in {8, 16, 32} with CUDA events on `stream`, keep the fastest and
- * return it in *best (ms per pass of each size in ms_out[3] if non-NULL).
- * Buffers as for bgt_render_fwd / bgt_render_bwd. */
+ * return it in *best (ms per pass of each size in ms_out[3] if non-NULL);
+ * then, at that tile size, time the other knobs of bgt_tuning one at a time
+ * (raster_prims in {4, 8, 16}, bwd_dequeue in {1, 2, 4},
+ * chain_blocks_per_sm in {4, 8, 16}) and keep each fastest value; read the
+ * chosen tuple with bgt_get_tuning. Buffers as for bgt_render_fwd /
+ * bgt_render_bwd. */
 bgt_status bgt_autotune(bgt_handle *h, const bgt_scene *scene, const bgt_camera *cams, int n_views,
                         float *images, const float *d_images, const bgt_grads *grads, int iters,
                         int *best, float *ms_out, void *stream);
@@ -323,7 +353,8 @@ bgt_status bgt_subdivide(int degree, const bgt_scene *scene, const int *sel, int
  * depth, 26..0 Gaussian index); 6 per-tile
  * boundary ranges int64[tiles+1]; 7 sorted boundary keys uint64[Kb] (primitive << 32 | boundary index);
  * 8 final transmittance float[P]; 9 per-pixel count of list entries
- * processed int32[P]; 10 per-Gaussian gradients float[F][12];
+ * processed int32[P]; 10 per-Gaussian gradients float[F][12] (dl/dmu x, y,
+ * dl/dK a, b, c, dl/do, dl/dcolour r, g, b, 0, 0, 0);
  * 11 per-boundary-point gradients float[Nb][4]. `bytes` is the size of dst;
  * *written receives the bytes copied. Synchronizes `stream`. */
 bgt_status bgt_get_stage(bgt_handle *h, int which, void *dst, long long bytes, long long *written,

@@ -49,6 +49,12 @@ class Grads(ctypes.Structure):
                 ("log_scale", c_void_p), ("quat", c_void_p), ("sh", c_void_p)]
 
 
+class Tuning(ctypes.Structure):
+    """bgt_tuning: scheduling knobs of the batched launches."""
+    _fields_ = [("tile_size", c_int), ("raster_prims", c_int), ("bwd_dequeue", c_int),
+                ("chain_blocks_per_sm", c_int)]
+
+
 PRIMS_KEYS = ("ctrl", "color", "opacity", "r_b", "log_scale", "quat", "sh")
 
 
@@ -79,6 +85,8 @@ def _declare(L):
     L.bgt_get_tile_size.argtypes = [P]
     L.bgt_autotune.argtypes = [P, ctypes.POINTER(Scene), ctypes.POINTER(Camera), c_int, P, P, ctypes.POINTER(Grads),
                                c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_float), P]
+    L.bgt_get_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
+    L.bgt_set_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
     L.bgt_l1_loss_grad.argtypes = [P, P, c_ll, c_float, P, P, P]
     L.bgt_l2_dssim_loss_grad.argtypes = [P, P, c_int, P, c_float, c_float, P, P, P]
     L.bgt_prim_metrics.argtypes = [c_int, ctypes.POINTER(Scene), P, c_float, c_float, c_float, P, P, c_float, P,

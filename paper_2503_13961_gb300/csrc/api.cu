@@ -33,6 +33,8 @@ struct bgt_handle {
   int *h_status = nullptr;  // pinned
   cudaEvent_t staged = nullptr;
   int tile = 16;
+  // scheduling knobs of bgt_tuning other than the tile size
+  int raster_prims = 8, bwd_dequeue = 1, chain_bps = 8;
   // last forward
   bool fwd_valid = false;
   bgt::Params last{};
@@ -125,6 +127,7 @@ void carve(bgt_handle *h, char *base, size_t *total) {
   w.rec_prev = c.take<int>(w.rec_chunk_cap);
   w.rec_fill = c.take<int>((long long)w.fill_unit_cap * 32);
   w.blk_rec = c.take<int2>(8 * (long long)T + 8);  // warp blocks: at most 8 per tile at any tile size
+  w.walk_list = c.take<int>(8 * (long long)T + 8);
   w.gkeys = c.take<unsigned long long>(2 * K);   // second half: sort scratch
   w.bkeys = c.take<unsigned long long>(2 * Kb);  // second half: sort scratch
   w.bl_prim = c.take<int>(Kb);
@@ -230,6 +233,9 @@ bgt_status setup_call(bgt_handle *h, const bgt_scene *sc, const bgt_camera *cams
   p.ntex = R * (R + 1) / 2;
   p.sh_deg = sc->sh_degree;
   p.sh_k = (sc->sh_degree + 1) * (sc->sh_degree + 1) - 1;
+  p.raster_prims = h->raster_prims;
+  p.bwd_dequeue = h->bwd_dequeue;
+  p.chain_bps = h->chain_bps;
   return BGT_OK;
 }
 
@@ -300,8 +306,8 @@ cudaError_t enqueue_bwd(bgt_handle *h, const bgt::Params &p, const bgt::Scene &s
 std::string graph_key(const bgt::Params &p, const void *a, const void *b, const void *c, const void *d,
                       const void *e, const bgt_camera *cams, int n) {
   char buf[256];
-  snprintf(buf, sizeof(buf), "%p|%p|%p|%p|%p|%d|%d|%d|%d|%d|%d|%d|%d|", a, b, c, d, e, p.M, p.V, p.P, p.tiles,
-           p.tile, p.use_boundary, p.attr_res, p.sh_deg);
+  snprintf(buf, sizeof(buf), "%p|%p|%p|%p|%p|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|", a, b, c, d, e, p.M, p.V, p.P,
+           p.tiles, p.tile, p.use_boundary, p.attr_res, p.sh_deg, p.raster_prims, p.bwd_dequeue, p.chain_bps);
   std::string k(buf);
   for (int v = 0; v < n; v++) k += std::to_string(cams[v].width) + "x" + std::to_string(cams[v].height) + ",";
   // the parameters passed by value to kernels are part of the graph
@@ -372,8 +378,9 @@ bgt_status bgt_create(const bgt_config *cfg, bgt_handle **out) {
   h->Fcap = cfg->max_pixels;
   h->Kcap = cfg->max_pairs;
   h->Kbcap = cfg->max_boundary_pairs;
-  // default 32 per pixel, at least 4M (every resident warp holds a partly used fill chunk)
-  h->Bcap = cfg->max_blend_pairs > 0 ? cfg->max_blend_pairs : std::max(32 * cfg->max_pixels, 1ll << 22);
+  // default 8 per pixel, at least 4M (every resident warp holds a partly used fill chunk); warp
+  // blocks whose records do not fit are differentiated by re-walking their tile lists
+  h->Bcap = cfg->max_blend_pairs > 0 ? cfg->max_blend_pairs : std::max(8 * cfg->max_pixels, 1ll << 22);
   if (h->Bcap > (1ll << 31) - 1024) h->Bcap = (1ll << 31) - 1024;
   h->Vcap = cfg->max_views;
   h->Mcap = cfg->max_prims;
@@ -495,7 +502,6 @@ bgt_status bgt_sync_status(bgt_handle *h, void *stream) {
   cudaMemsetAsync(h->w.status, 0, sizeof(int), st);
   if (s & (bgt::kStatusPairOverflow | bgt::kStatusBoundaryOverflow | bgt::kStatusTileOverflow))
     return fail(h, BGT_ERR_CAPACITY, "device-side pair count exceeded its capacity");
-  if (s & bgt::kStatusBlendOverflow) return fail(h, BGT_ERR_CAPACITY, "blend records exceeded max_blend_pairs");
   if (s & bgt::kStatusNonFinite) return fail(h, BGT_ERR_NONFINITE, "non-finite projected Gaussian");
   if (s & bgt::kStatusBadPrim) return fail(h, BGT_ERR_STATE, "depth buffer held an invalid primitive id");
   return BGT_OK;
@@ -503,10 +509,10 @@ bgt_status bgt_sync_status(bgt_handle *h, void *stream) {
 
 const char *bgt_last_error(const bgt_handle *h) { return h ? h->err.c_str() : ""; }
 
-bgt_status bgt_get_counts(bgt_handle *h, long long out[7], void *stream) {
+bgt_status bgt_get_counts(bgt_handle *h, long long out[8], void *stream) {
   if (!h || !out) return BGT_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemcpyAsync(h->h_status + 4, h->w.counters, 10 * sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaMemcpyAsync(h->h_status + 4, h->w.counters, 11 * sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(h, e, "counter read");
   for (int i = 0; i < 4; i++) out[i] = h->h_status[4 + i];
@@ -514,6 +520,7 @@ bgt_status bgt_get_counts(bgt_handle *h, long long out[7], void *stream) {
   const int ppt = h->last.tile == 32 ? 4 : 1;
   out[5] = (long long)h->h_status[4 + bgt::kRecChunks] * bgt::kRecChunk;
   out[6] = (long long)h->h_status[4 + bgt::kFillChunks] * bgt::kFillChunk * ppt;
+  out[7] = h->h_status[4 + bgt::kWalkCount];
   return BGT_OK;
 }
 
@@ -561,41 +568,94 @@ bgt_status bgt_get_profile(bgt_handle *h, float ms[8], int *kernels_fwd, int *ke
   return BGT_OK;
 }
 
+bgt_status bgt_get_tuning(const bgt_handle *h, bgt_tuning *out) {
+  if (!h || !out) return BGT_ERR_INVALID_ARG;
+  out->tile_size = h->tile;
+  out->raster_prims = h->raster_prims;
+  out->bwd_dequeue = h->bwd_dequeue;
+  out->chain_blocks_per_sm = h->chain_bps;
+  return BGT_OK;
+}
+
+bgt_status bgt_set_tuning(bgt_handle *h, const bgt_tuning *t) {
+  if (!h || !t) return BGT_ERR_INVALID_ARG;
+  if ((t->tile_size != 8 && t->tile_size != 16 && t->tile_size != 32) || t->raster_prims < 1 ||
+      t->raster_prims > 64 || t->bwd_dequeue < 1 || t->bwd_dequeue > 8 || t->chain_blocks_per_sm < 1 ||
+      t->chain_blocks_per_sm > 32)
+    return fail(h, BGT_ERR_INVALID_ARG, "tuning value out of range");
+  if (t->tile_size != h->tile) h->fwd_valid = false;
+  h->tile = t->tile_size;
+  h->raster_prims = t->raster_prims;
+  h->bwd_dequeue = t->bwd_dequeue;
+  h->chain_bps = t->chain_blocks_per_sm;
+  return BGT_OK;
+}
+
+namespace {
+
+// ms per forward + backward pass of the handle's current scheduling (one
+// untimed pass first), timed with CUDA events on the stream
+bgt_status time_passes(bgt_handle *h, const bgt_scene *scene, const bgt_camera *cams, int n_views, float *images,
+                       const float *d_images, const bgt_grads *grads, int iters, void *stream, cudaEvent_t a,
+                       cudaEvent_t b, float *ms) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  h->fwd_valid = false;
+  bgt_status s = bgt_render_fwd(h, scene, cams, n_views, images, stream);
+  if (s == BGT_OK) s = bgt_render_bwd(h, scene, cams, n_views, d_images, grads, stream);
+  if (s != BGT_OK) return s;
+  cudaEventRecord(a, st);
+  for (int i = 0; i < iters && s == BGT_OK; i++) {
+    s = bgt_render_fwd(h, scene, cams, n_views, images, stream);
+    if (s == BGT_OK) s = bgt_render_bwd(h, scene, cams, n_views, d_images, grads, stream);
+  }
+  cudaEventRecord(b, st);
+  cudaEventSynchronize(b);
+  *ms = 0.f;
+  cudaEventElapsedTime(ms, a, b);
+  *ms /= iters;
+  if (s == BGT_OK) s = bgt_sync_status(h, stream);
+  return s;
+}
+
+}  // namespace
+
 bgt_status bgt_autotune(bgt_handle *h, const bgt_scene *scene, const bgt_camera *cams, int n_views, float *images,
                         const float *d_images, const bgt_grads *grads, int iters, int *best, float *ms_out,
                         void *stream) {
   if (!h || iters < 1) return BGT_ERR_INVALID_ARG;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int sizes[3] = {8, 16, 32};
-  float best_ms = 3e38f;
-  int best_t = h->tile;
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
   bgt_status s = BGT_OK;
+  // 1. tile size
+  const int sizes[3] = {8, 16, 32};
+  float best_ms = 3e38f;
+  int best_t = h->tile;
   for (int k = 0; k < 3 && s == BGT_OK; k++) {
     h->tile = sizes[k];
-    h->fwd_valid = false;
-    s = bgt_render_fwd(h, scene, cams, n_views, images, stream);  // warm-up
-    if (s == BGT_OK) s = bgt_render_bwd(h, scene, cams, n_views, d_images, grads, stream);
-    if (s != BGT_OK) break;
-    cudaEventRecord(a, st);
-    for (int i = 0; i < iters && s == BGT_OK; i++) {
-      s = bgt_render_fwd(h, scene, cams, n_views, images, stream);
-      if (s == BGT_OK) s = bgt_render_bwd(h, scene, cams, n_views, d_images, grads, stream);
-    }
-    cudaEventRecord(b, st);
-    cudaEventSynchronize(b);
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, a, b);
-    ms /= iters;
+    s = time_passes(h, scene, cams, n_views, images, d_images, grads, iters, stream, a, b, &ms);
     if (ms_out) ms_out[k] = ms;
-    if (ms < best_ms) { best_ms = ms; best_t = sizes[k]; }
-    if (s == BGT_OK) s = bgt_sync_status(h, stream);
+    if (s == BGT_OK && ms < best_ms) { best_ms = ms; best_t = sizes[k]; }
+  }
+  h->tile = best_t;
+  // 2. the work-queue knobs, one at a time at that tile size
+  int *knob[3] = {&h->raster_prims, &h->bwd_dequeue, &h->chain_bps};
+  const int values[3][3] = {{4, 8, 16}, {1, 2, 4}, {4, 8, 16}};
+  for (int q = 0; q < 3 && s == BGT_OK; q++) {
+    const int keep = *knob[q];
+    int best_v = keep;
+    float knob_ms = 3e38f;
+    for (int k = 0; k < 3 && s == BGT_OK; k++) {
+      *knob[q] = values[q][k];
+      float ms = 0.f;
+      s = time_passes(h, scene, cams, n_views, images, d_images, grads, iters, stream, a, b, &ms);
+      if (s == BGT_OK && ms < knob_ms) { knob_ms = ms; best_v = values[q][k]; }
+    }
+    *knob[q] = s == BGT_OK ? best_v : keep;
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  h->tile = best_t;
   h->fwd_valid = false;
   if (best) *best = best_t;
   return s;
@@ -710,6 +770,16 @@ __global__ void k_pack_gauss(bgt::Work w, int F, float *out) {
   o[8] = C.x; o[9] = C.y; o[10] = C.z; o[11] = w.g_depth[i];
 }
 
+__global__ void k_pack_ggrad(bgt::Work w, int F, float *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= F) return;
+  float gd[9];
+  bgt::gauss_grad_from_sums(w.gg + 12 * (size_t)i, w.gB[i], gd);
+  float *o = out + 12 * (size_t)i;
+  for (int k = 0; k < 9; k++) o[k] = gd[k];
+  o[9] = o[10] = o[11] = 0.f;
+}
+
 __global__ void k_pack_bnd(bgt::Work w, int Nb, float *out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Nb) return;
@@ -756,7 +826,7 @@ extern "C" {
 bgt_status bgt_get_stage(bgt_handle *h, int which, void *dst, long long bytes, long long *written, void *stream) {
   if (!h || !dst || bytes < 0) return BGT_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  long long cnt[7];
+  long long cnt[8];
   bgt_status s = bgt_get_counts(h, cnt, stream);
   if (s != BGT_OK) return s;
   const bgt::Params &p = h->last;
@@ -769,15 +839,17 @@ bgt_status bgt_get_stage(bgt_handle *h, int which, void *dst, long long bytes, l
     case 0: src = h->w.pid; need = 4 * P; break;
     case 1: src = h->w.puv; need = 8 * P; break;
     case 2:
-    case 3: {
-      const long long items = which == 2 ? F : Nb;
-      need = (which == 2 ? 48 : 32) * items;
+    case 3:
+    case 10: {
+      const long long items = which == 3 ? Nb : F;
+      need = (which == 3 ? 32 : 48) * items;
       if (need > bytes) return fail(h, BGT_ERR_CAPACITY, "destination too small");
       // pack through the (unused between calls) sort scratch of the Gaussian keys
       tmp = reinterpret_cast<float *>(h->w.gkeys + h->Kcap);
       if (need > 8 * h->Kcap) return fail(h, BGT_ERR_CAPACITY, "stage larger than scratch");
       if (items > 0) {
         if (which == 2) k_pack_gauss<<<(int)((items + 255) / 256), 256, 0, st>>>(h->w, (int)items, tmp);
+        else if (which == 10) k_pack_ggrad<<<(int)((items + 255) / 256), 256, 0, st>>>(h->w, (int)items, tmp);
         else k_pack_bnd<<<(int)((items + 255) / 256), 256, 0, st>>>(h->w, (int)items, tmp);
       }
       src = tmp;
@@ -789,7 +861,6 @@ bgt_status bgt_get_stage(bgt_handle *h, int which, void *dst, long long bytes, l
     case 7: src = h->w.bkeys; need = 8 * Kb; break;
     case 8: src = h->w.T_final; need = 4 * P; break;
     case 9: src = h->w.n_contrib; need = 4 * P; break;
-    case 10: src = h->w.gg; need = 48 * F; break;
     case 11: src = h->w.bg_grad; need = 16 * Nb; break;
     default: return fail(h, BGT_ERR_INVALID_ARG, "unknown stage");
   }

@@ -28,7 +28,7 @@ constexpr int kStatusBoundaryOverflow = 2;
 constexpr int kStatusTileOverflow = 4;
 constexpr int kStatusNonFinite = 8;
 constexpr int kStatusBadPrim = 16;
-constexpr int kStatusBlendOverflow = 32;  // the forward pass's blend records exceeded their capacity
+constexpr int kStatusBlendOverflow = 32;  // reserved (blend-record overflow falls back to a tile-list walk)
 
 // blend records (forward -> backward): headers in chunks of kRecChunk per warp
 // block, fill records in chunks of kFillChunk per warp
@@ -59,6 +59,9 @@ struct Params {
   int stats;                  // 1: blending kernels count their work units into Work::stats
   int attr_res, ntex;         // attribute maps: leg resolution R, texels R (R + 1) / 2
   int sh_deg, sh_k;           // SH colour: degree D, coefficients per channel (D + 1)^2 - 1
+  // scheduling (bgt_tuning): primitives per rasterizer warp and block, warp
+  // blocks per backward dequeue, persistent blocks per SM of the chain kernels
+  int raster_prims, bwd_dequeue, chain_bps;
 };
 
 struct Scene {                // device pointers, caller-owned
@@ -71,6 +74,22 @@ struct Grads {                // device pointers, caller-owned outputs
   float *log_scale, *quat;    // attribute-map texel gradients, nullable
   float *sh;                  // SH coefficient gradients, nullable
 };
+
+// Per-Gaussian gradient of the blending backward from the sums in Work::gg
+// and the Gaussian's conic K = (a, b, c) and opacity o: out = (dl/dmu x, y,
+// dl/dK a, b, c, dl/do, dl/dcolour r, g, b).
+__device__ inline void gauss_grad_from_sums(const float *gs, float4 Ko, float *out) {
+  const float o = Ko.w;
+  out[0] = o * (Ko.x * gs[0] + Ko.y * gs[1]);
+  out[1] = o * (Ko.y * gs[0] + Ko.z * gs[1]);
+  out[2] = -0.5f * o * gs[2];
+  out[3] = -o * gs[3];
+  out[4] = -0.5f * o * gs[4];
+  out[5] = gs[5];
+  out[6] = gs[6];
+  out[7] = gs[7];
+  out[8] = gs[8];
+}
 
 // Gaussian record (one per foreground pixel), three float4 per Gaussian:
 //   A = (off_x, off_y, bits(qx | qy << 16), support radius)
@@ -127,6 +146,8 @@ struct Work {
   int *rec_prev;              // [rec_chunk_cap] previous header chunk of the same warp block, -1
   int *rec_fill;              // [fill_unit_cap * 32] one unit = one plane of one fill record
   int2 *blk_rec;              // [warp blocks] last header chunk (-1 none, -2 overflow), records in it
+  int *walk_list;             // [warp blocks] blocks whose records overflowed (counters[kWalkCount] of them):
+                              // the backward re-walks their tile lists instead of replaying records
   int rec_chunk_cap, fill_unit_cap;
   // pairs
   unsigned long long *gkeys;  // [Kcap] depth key (FP32 bits << 5 | sub) << 27 | gaussian index
@@ -137,7 +158,10 @@ struct Work {
   float *T_final;             // [P]
   int *n_contrib;             // [P] tile-list position after the last composited pair
   // intermediate gradients
-  float *gg;                  // [Fcap][12]: dmu x,y; dK a,b,c; do; dcol r,g,b; pad
+  float *gg;                  // [Fcap][12] per-Gaussian sums of the blending backward over its composited
+                              // pairs, s = dl/dalpha w G of a pair, d = q - mu: s dx, s dy, s dx^2,
+                              // s dx dy, s dy^2, s (= dl/do), dl/dcolour r, g, b; pad (dl/dmu = o K (s d),
+                              // dl/dK = -o/2 (s dx^2, 2 s dx dy, s dy^2) are formed per Gaussian)
   float4 *bg_grad;            // [Fcap] (db x, db y, dsigma, 0)
   unsigned long long *stats;  // [8] work units of the last profiled call (see Stat)
   long long Fcap;
@@ -154,7 +178,7 @@ constexpr int kIndexBits = 27;  // Gaussian index field of a pair key (<= 134M G
 constexpr unsigned long long kIndexMask = (1ull << kIndexBits) - 1ull;
 
 enum Counter { kF = 0, kNb = 1, kK = 2, kKb = 3, kQueueFwd = 4, kQueueBwd = 5, kQueueSort = 6, kBigCount = 7,
-               kRecChunks = 8, kFillChunks = 9 };
+               kRecChunks = 8, kFillChunks = 9, kWalkCount = 10, kQueueWalk = 11 };
 
 // ---------------------------------------------------------------------------
 // small helpers

@@ -63,10 +63,13 @@ __global__ void __launch_bounds__(256) k_chain_gauss(Params p, Scene s, Work w, 
       const float4 q0 = reinterpret_cast<const float4 *>(gg)[0];
       const float4 q1 = reinterpret_cast<const float4 *>(gg)[1];
       const float4 q2 = reinterpret_cast<const float4 *>(gg)[2];
-      const float gmx = q0.x, gmy = q0.y, gKa = q0.z, gKb = q0.w, gKc = q1.x;
-      gop = q1.y;
-      gcol[0] = q1.z; gcol[1] = q1.w; gcol[2] = q2.x;
       const float4 Bq = w.gB[i];
+      const float sums[9] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x};
+      float gd[9];
+      gauss_grad_from_sums(sums, Bq, gd);
+      const float gmx = gd[0], gmy = gd[1], gKa = gd[2], gKb = gd[3], gKc = gd[4];
+      gop = gd[5];
+      gcol[0] = gd[6]; gcol[1] = gd[7]; gcol[2] = gd[8];
       g = __float_as_int(w.gC[i].w);
       const View vw = w.views[w.g_view[i]];
       const float2 uv = w.g_uv[i];
@@ -318,7 +321,10 @@ __global__ void k_l1_grad(const float *img, const float *tgt, long long n, float
 }  // namespace
 
 int launch_chain(const Params &p, const Scene &s, const Work &w, const Grads &g, cudaStream_t st) {
-  const int grid = 152 * 8;
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = (sms > 0 ? sms : 152) * p.chain_bps;
   dispatch_degree(p.n, [&](auto d) {
     k_chain_gauss<decltype(d)::value><<<grid, 256, 0, st>>>(p, s, w, g);
     k_chain_bnd<decltype(d)::value><<<grid, 256, 0, st>>>(p, s, w, g);

@@ -64,11 +64,18 @@ __device__ __forceinline__ float ex2(float x) {
   return y;
 }
 
-// G = exp(-1/2 (a dx^2 + 2 b dx dy + c dy^2)) evaluated as a power of two
-__device__ __forceinline__ float gauss(float dx, float dy, const float4 &Q) {
-  const float e = __fmaf_rn(Q.x, __fmul_rn(dx, dx), __fmul_rn(Q.z, __fmul_rn(dy, dy)));
-  const float f = __fmul_rn(Q.y, __fmul_rn(dx, dy));
-  return ex2(__fmaf_rn(e, -0.5f * kLog2e, __fmul_rn(-kLog2e, f)));
+// Conic (a, b, c) and opacity o of a Gaussian record, with the conic scaled
+// for the exponent: (-a/2, -b, -c/2) log2(e), so that G = 2^(a' dx^2 + b' dx dy
+// + c' dy^2). Forward and backward stage the same scaled values.
+__device__ __forceinline__ float4 scaled_conic(const float4 K) {
+  return make_float4(__fmul_rn(K.x, -0.5f * kLog2e), __fmul_rn(K.y, -kLog2e), __fmul_rn(K.z, -0.5f * kLog2e), K.w);
+}
+
+// G = exp(-1/2 (a dx^2 + 2 b dx dy + c dy^2)) = 2^(dx (a' dx + b' dy) + c' dy^2)
+// for a conic scaled by scaled_conic
+__device__ __forceinline__ float gauss(float dx, float dy, const float4 &Qs) {
+  const float t = __fmaf_rn(Qs.x, dx, __fmul_rn(Qs.y, dy));
+  return ex2(__fmaf_rn(dx, t, __fmul_rn(__fmul_rn(Qs.z, dy), dy)));
 }
 
 // A boundary record in the form the search uses: pixel coordinates of the
@@ -236,7 +243,7 @@ __device__ __forceinline__ unsigned stage_chunk(const Work &w, unsigned long lon
     hit = r >= 0.f && cx + r >= bx0 && cx - r <= bx1 && cy + r >= by0 && cy - r <= by1;
     if (hit) {
       sP[lane] = make_float4(gx, gy, A.x, A.y);
-      sQ[lane] = w.gB[gi];
+      sQ[lane] = scaled_conic(w.gB[gi]);
       sC[lane] = w.gC[gi];
       if (sG) sG[lane] = (int)gi;
     }
@@ -298,7 +305,8 @@ __device__ __forceinline__ int cache_find(int ckey, int g) {
 // (lane i holds the block's i-th pending header) and stored as one coalesced
 // chunk of kRecChunk; fill records come from chunks of kFillChunk units owned
 // by the warp across the blocks it blends. Running out of either capacity
-// raises kStatusBlendOverflow and marks the block's records invalid.
+// marks the block's records invalid and lists the block for the tile-list
+// walk of the backward pass.
 struct RecWriter {
   int chunk, last_n;  // the block's last stored header chunk (-1: none) and its headers
   int count;          // pending headers
@@ -313,10 +321,7 @@ struct RecWriter {
     ok = true;
   }
 
-  __device__ __forceinline__ void fail(const Work &w) {
-    ok = false;
-    if ((threadIdx.x & 31) == 0) atomicOr(w.status, kStatusBlendOverflow);
-  }
+  __device__ __forceinline__ void fail(const Work &) { ok = false; }
 
   // first unit of a new fill record of `units` planes, or -1
   __device__ __forceinline__ int new_fill(const Work &w, int units) {
@@ -365,7 +370,10 @@ struct RecWriter {
 
   __device__ __forceinline__ void end_block(const Work &w, int blk) {
     flush(w);
-    if ((threadIdx.x & 31) == 0) w.blk_rec[blk] = ok ? make_int2(chunk, last_n) : make_int2(-2, 0);
+    if ((threadIdx.x & 31) == 0) {
+      w.blk_rec[blk] = ok ? make_int2(chunk, last_n) : make_int2(-2, 0);
+      if (!ok) w.walk_list[atomicAdd(w.counters + kWalkCount, 1)] = blk;
+    }
   }
 };
 
@@ -547,41 +555,83 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float *v) {
   return c;
 }
 
-// Boundary-point gradients of one cache slot (primitive g). For every pixel
-// the slot's w = gamma (inside g) or 1 - gamma with gamma = 2^(rho - 1) of the
-// same boundary point b for all of g's Gaussians, so their dl/dw add up
-// (sum) before dl/drho = +-ln2 gamma sum is taken through rho = |q - b| / sigma:
-// drho/db = -(q - b) / (|q - b| sigma), drho/dsigma = -rho / sigma. brec and
-// bkeys are the tile's boundary list (records in search form after
-// to_search, keys holding the boundary point's index).
+// Backward of one composited pair (Gaussian with colour Cc at offset (dx, dy)
+// of the pixel from its mean, G, og = o G, w, raw = og w, alpha): T_{i+1} ->
+// T_i = T_{i+1} / (1 - alpha_i) in Tr, the colour behind the pair R updated
+// (R <- R + alpha_i (c_i - R)), and the per-Gaussian sums accumulated in acc:
+// with s = dl/dalpha w G (the pair's dl/do), acc[0..4] += s (dx, dy, dx^2,
+// dx dy, dy^2), acc[5] += s, acc[6..8] += T_i alpha_i dl/dC (the chain kernel
+// turns the moments into dl/dmu = o K (acc0, acc1) and dl/dK = -o/2 (acc2,
+// 2 acc3, acc4)). dl/dalpha_i = dl/dC . T_i (c_i - R_i) (the supplementary's
+// T_i c_i - S_i / (1 - alpha_i), without the 1 / (1 - alpha_i) amplification
+// of rounding). Returns dl/dw (0 when alpha is clamped at alpha_max).
+__device__ __forceinline__ float pair_backward(float dx, float dy, float G, float og, float wv, float raw, float alpha,
+                                               float alpha_max, const float4 &Cc, const float *dC, float &Tr, float *R,
+                                               float *acc) {
+  Tr = __fdividef(Tr, 1.0f - alpha);  // T_i
+  const float ta = Tr * alpha;
+  const float col[3] = {Cc.x, Cc.y, Cc.z};
+  float dl_da = 0.f;
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    acc[6 + c] = fmaf(ta, dC[c], acc[6 + c]);
+    const float d = col[c] - R[c];
+    dl_da = fmaf(dC[c], d, dl_da);
+    R[c] = fmaf(alpha, d, R[c]);
+  }
+  dl_da *= Tr;
+  if (raw >= alpha_max) return 0.f;  // clamped: alpha is constant
+  const float sg = dl_da * wv * G;
+  const float a = sg * dx, b = sg * dy;
+  acc[0] += a;
+  acc[1] += b;
+  acc[2] = fmaf(a, dx, acc[2]);
+  acc[3] = fmaf(a, dy, acc[3]);
+  acc[4] = fmaf(b, dy, acc[4]);
+  acc[5] += sg;
+  return dl_da * og;
+}
+
+// Boundary-point gradient of pixel (pxf, pyf) and boundary candidate bi of
+// the tile's list, given sum = the pixel's dl/dw over Gaussians of the
+// candidate's primitive (inside: the pixel belongs to it). w = gamma (inside)
+// or 1 - gamma with gamma = 2^(rho - 1), so dl/drho = +-ln2 gamma sum, taken
+// through rho = |q - b| / sigma: drho/db = -(q - b) / (|q - b| sigma),
+// drho/dsigma = -rho / sigma. brec and bkeys are the tile's boundary list
+// (records in pixel-relative form, keys holding the boundary point's index).
+__device__ __forceinline__ void boundary_grad(const float4 *brec, const unsigned long long *bkeys, float4 *bg_grad,
+                                              int bi, float sum, bool inside, float pxf, float pyf) {
+  const float LN2 = 0.69314718055994531f;
+  if (bi < 0 || sum == 0.f) return;
+  // rho and gamma with the operations of the forward search
+  const float4 rec = brec[bi];
+  const float4 b = to_search(rec);
+  const float isig = rec.w;
+  const float ex = __fsub_rn(__fsub_rn(pxf, b.x), b.z), ey = __fsub_rn(__fsub_rn(pyf, b.y), b.w);
+  const float r2 = __fmul_rn(__fmaf_rn(ex, ex, __fmul_rn(ey, ey)), __fmul_rn(isig, isig));
+  const float rho = sqrt_approx(r2);
+  if (!(rho > 0.f)) return;
+  const float gam = gamma_of(r2);
+  const float dl_drho = (inside ? LN2 : -LN2) * gam * sum;
+  const float s = dl_drho * isig * __frcp_rn(rho);  // (q - b) isig / rho is the unit direction
+  const unsigned bidx = (unsigned)(bkeys[bi] & 0xffffffffull);
+  float *gb = reinterpret_cast<float *>(bg_grad + bidx);
+  atomicAdd(gb + 0, -(ex * isig) * s);
+  atomicAdd(gb + 1, -(ey * isig) * s);
+  atomicAdd(gb + 2, -dl_drho * rho * isig);
+}
+
+// Boundary-point gradients of one cache slot (primitive g): for every pixel
+// all of g's Gaussians use the same boundary point, so their dl/dw were
+// summed (cacc) before the gradient is taken once per (pixel, slot).
 template <int PPT>
 __device__ __forceinline__ void flush_boundary(const float4 *brec, const unsigned long long *bkeys, float4 *bg_grad,
                                                const int *cb, const float *cacc, int g, const int *idq,
                                                const float *pxf, const float *pyf) {
-  const float LN2 = 0.69314718055994531f;
   const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int k = 0; k < PPT; k++) {
-    const int bi = cb[k * 32 + lane];
-    const float sum = cacc[k * 32 + lane];
-    if (bi < 0 || sum == 0.f) continue;
-    // rho and gamma with the operations of the forward search
-    const float4 rec = brec[bi];
-    const float4 b = to_search(rec);
-    const float isig = rec.w;
-    const float ex = __fsub_rn(__fsub_rn(pxf[k], b.x), b.z), ey = __fsub_rn(__fsub_rn(pyf[k], b.y), b.w);
-    const float r2 = __fmul_rn(__fmaf_rn(ex, ex, __fmul_rn(ey, ey)), __fmul_rn(isig, isig));
-    const float rho = sqrt_approx(r2);
-    if (!(rho > 0.f)) continue;
-    const float gam = gamma_of(r2);
-    const float dl_drho = ((idq[k] == g) ? LN2 : -LN2) * gam * sum;
-    const float s = dl_drho * isig * __frcp_rn(rho);  // (q - b) isig / rho is the unit direction
-    const unsigned bidx = (unsigned)(bkeys[bi] & 0xffffffffull);
-    float *gb = reinterpret_cast<float *>(bg_grad + bidx);
-    atomicAdd(gb + 0, -(ex * isig) * s);
-    atomicAdd(gb + 1, -(ey * isig) * s);
-    atomicAdd(gb + 2, -dl_drho * rho * isig);
-  }
+  for (int k = 0; k < PPT; k++)
+    boundary_grad(brec, bkeys, bg_grad, cb[k * 32 + lane], cacc[k * 32 + lane], idq[k] == g, pxf[k], pyf[k]);
 }
 
 // w (Eq. 6-7) at pixel (px, py) for the primitive whose most influential
@@ -617,150 +667,241 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
   auto &s_cb = sh.s_cb[warp];
   auto &s_cacc = sh.s_cacc[warp];
   const int items = p.tiles * NW;
-  int item = 0;
-  if (lane == 0) item = atomicAdd(w.counters + kQueueBwd, 1);
-  item = __shfl_sync(0xffffffffu, item, 0);
-  while (item < items) {
-    int next = 0;  // the next warp block, fetched while this one is processed
-    if (lane == 0) next = atomicAdd(w.counters + kQueueBwd, 1);
-    const int tile = item / NW, wb = item - tile * NW;
-    const int4 d = w.tile_desc[2 * tile];
-    const int x0 = d.y & 0xffff, y0 = (int)((unsigned)d.y >> 16);
-    const int W = d.z & 0xffff, H = (int)((unsigned)d.z >> 16);
-    const long long bs = w.tile_desc[2 * tile + 1].z;
-    const float4 *brec = w.bl_rec + bs;
-    const unsigned long long *bkeys = w.bkeys + bs;
-    const int2 br = w.blk_rec[item];
+  const int deq = p.bwd_dequeue;  // warp blocks per dequeue
+  int base = 0;
+  if (lane == 0) base = atomicAdd(w.counters + kQueueBwd, deq);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  while (base < items) {
+    int next = 0;  // the next warp blocks, fetched while these are processed
+    if (lane == 0) next = atomicAdd(w.counters + kQueueBwd, deq);
+    const int end = min(base + deq, items);
+    for (int item = base; item < end; item++) {
+      const int tile = item / NW, wb = item - tile * NW;
+      const int4 d = w.tile_desc[2 * tile];
+      const int x0 = d.y & 0xffff, y0 = (int)((unsigned)d.y >> 16);
+      const int W = d.z & 0xffff, H = (int)((unsigned)d.z >> 16);
+      const long long bs = w.tile_desc[2 * tile + 1].z;
+      const float4 *brec = w.bl_rec + bs;
+      const unsigned long long *bkeys = w.bkeys + bs;
+      const int2 br = w.blk_rec[item];
 
+      float Tr[PPT], R[PPT][3], dC[PPT][3], pxf[PPT], pyf[PPT];
+      int idq[PPT];
+#pragma unroll
+      for (int k = 0; k < PPT; k++) {
+        int lx, ly;
+        lane_pixel<T>(wb, lane, k, lx, ly);
+        const int px = x0 + lx, py = y0 + ly;
+        pxf[k] = (float)px;
+        pyf[k] = (float)py;
+        idq[k] = -1;
+        Tr[k] = 1.f;
+        R[k][0] = R[k][1] = R[k][2] = 0.f;
+        dC[k][0] = dC[k][1] = dC[k][2] = 0.f;
+        if (br.x >= 0 && px < W && py < H) {
+          const int pix = d.w + py * W + px;
+          idq[k] = w.pid[pix];
+          Tr[k] = w.T_final[pix];
+#pragma unroll
+          for (int c = 0; c < 3; c++) {
+            dC[k][c] = dimage[3 * (size_t)pix + c];
+            R[k][c] = p.bg[c];
+          }
+        }
+      }
+      unsigned n_comp = 0, n_rec = 0;
+      int ckey = -2, cnext = 0;
+      int chunk = br.x, n = br.y;
+      while (chunk >= 0) {
+        const int prev = w.rec_prev[chunk];
+        // stage the chunk's records: headers and their Gaussians
+        if (lane < n) {
+          const uint4 h = w.rec_hdr[(size_t)chunk * kRecChunk + lane];
+          const float4 A = w.gA[h.x];
+          const unsigned qxy = __float_as_uint(A.z);
+          sH[lane] = h;
+          sP[lane] = make_float4((float)(int)(qxy & 0xffffu), (float)(int)(qxy >> 16), A.x, A.y);
+          sQ[lane] = scaled_conic(w.gB[h.x]);
+          sC[lane] = w.gC[h.x];
+        }
+        __syncwarp();
+        for (int r = n - 1; r >= 0; r--) {
+          const uint4 h = sH[r];
+          const bool mine = (h.y >> lane) & 1u;
+          const int rk = (int)h.w;
+          const float4 P = sP[r], Q = sQ[r], Cc = sC[r];
+          const int g = __float_as_int(Cc.w);
+          n_rec++;
+          // w of (pixel, g): from the cache slot, filled from g's fill record
+          int slot = 0;
+          if (p.use_boundary) {
+            slot = cache_find(ckey, g);
+            if (slot < 0) {  // warp-uniform miss: flush the evicted slot, take in g
+              slot = cnext;
+              cnext = (cnext + 1 == S) ? 0 : cnext + 1;
+              const int old = __shfl_sync(0xffffffffu, ckey, slot);
+              if (old >= 0)
+                flush_boundary<PPT>(brec, bkeys, w.bg_grad, &s_cb[slot][0][0], &s_cacc[slot][0][0], old, idq, pxf, pyf);
+#pragma unroll
+              for (int k = 0; k < PPT; k++) {
+                const int bi = (int)h.z >= 0 ? w.rec_fill[(size_t)((int)h.z + k) * 32 + lane] : -1;
+                s_cw[slot][k][lane] = w_from_candidate(brec, bi, pxf[k], pyf[k], idq[k] == g);
+                s_cb[slot][k][lane] = bi;
+                s_cacc[slot][k][lane] = 0.f;
+              }
+              if (lane == slot) ckey = g;
+            }
+          }
+          float acc[9];
+#pragma unroll
+          for (int q = 0; q < 9; q++) acc[q] = 0.f;
+          float dl_dw = 0.f;
+#pragma unroll
+          for (int k = 0; k < PPT; k++) {
+            if (k != rk || !mine) continue;
+            n_comp++;
+            const float dx = __fsub_rn(__fsub_rn(pxf[k], P.x), P.z), dy = __fsub_rn(__fsub_rn(pyf[k], P.y), P.w);
+            const float G = gauss(dx, dy, Q);
+            const float og = __fmul_rn(Q.w, G);
+            const float wv = p.use_boundary ? s_cw[slot][k][lane] : 1.0f;
+            const float raw = __fmul_rn(og, wv);
+            const float alpha = fminf(p.alpha_max, raw);
+            dl_dw = pair_backward(dx, dy, G, og, wv, raw, alpha, p.alpha_max, Cc, dC[k], Tr[k], R[k], acc);
+          }
+          if (p.use_boundary && mine) s_cacc[slot][rk][lane] += dl_dw;
+          // per-Gaussian sums (see pair_backward); slots 0-7 by reduce-scatter
+          // (lanes 4m hold slot m), slot 8 by a butterfly
+          const float part = warp_reduce_scatter8(acc);
+          const float s8 = warp_sum(acc[8]);
+          float *gg = w.gg + 12 * (size_t)h.x;
+          const int gslot = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+          if ((lane & 3) == 0 && part != 0.f) atomicAdd(gg + gslot, part);
+          if (lane == 1 && s8 != 0.f) atomicAdd(gg + 8, s8);
+        }
+        __syncwarp();
+        chunk = prev;
+        n = kRecChunk;
+      }
+      if (p.use_boundary) {
+        for (int sl = 0; sl < S; sl++) {
+          const int old = __shfl_sync(0xffffffffu, ckey, sl);
+          if (old >= 0)
+            flush_boundary<PPT>(brec, bkeys, w.bg_grad, &s_cb[sl][0][0], &s_cacc[sl][0][0], old, idq, pxf, pyf);
+        }
+      }
+      if (p.stats) flush_stats(w.stats, kBwdSupport, n_comp, n_comp, 0u, n_rec);
+    }
+    base = __shfl_sync(0xffffffffu, next, 0);
+  }
+}
+
+// Backward pass of the warp blocks whose blend records did not fit (listed
+// by the forward pass): each warp re-walks its block's tile list back to
+// front from the last composited entry of its pixels. Every decision of the
+// forward (support, w by the same Eq. 6 search over the tile's boundary
+// list, alpha, the alpha_min cut) is retaken with the forward's operations,
+// so exactly the forward's composited pairs are visited; T_i = T_{i+1} /
+// (1 - alpha_i) and the gradients follow as in the record replay. Boundary
+// gradients are added per pair (the most influential boundary point of the
+// pair's search).
+template <int T>
+__global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd_walk(Params p, Work w, const float *dimage) {
+  using Cfg = TileCfg<T>;
+  constexpr int PPT = Cfg::PPT, NW = Cfg::NW;
+  const int lane = threadIdx.x & 31;
+  const int nwalk = w.counters[kWalkCount];
+  for (;;) {
+    int q = 0;
+    if (lane == 0) q = atomicAdd(w.counters + kQueueWalk, 1);
+    q = __shfl_sync(0xffffffffu, q, 0);
+    if (q >= nwalk) break;
+    const int item = w.walk_list[q];
+    const int tile = item / NW, wb = item - tile * NW;
+    const TileInfo ti = tile_info(p, w, tile);
+    BList bl;
+    bl.n = (int)ti.bn;
+    bl.glob = w.bl_rec + ti.bs;
+    bl.cached = false;
+    bl.prim = w.bl_prim + ti.bs;
+    bl.loc = nullptr;
+    bl.isig = nullptr;
+    const float4 *brec = w.bl_rec + ti.bs;
+    const unsigned long long *bkeys = w.bkeys + ti.bs;
     float Tr[PPT], R[PPT][3], dC[PPT][3], pxf[PPT], pyf[PPT];
-    int idq[PPT];
+    int idq[PPT], nlast[PPT];
+    int emax = 0;
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
       int lx, ly;
       lane_pixel<T>(wb, lane, k, lx, ly);
-      const int px = x0 + lx, py = y0 + ly;
+      const int px = ti.x0 + lx, py = ti.y0 + ly;
       pxf[k] = (float)px;
       pyf[k] = (float)py;
       idq[k] = -1;
+      nlast[k] = 0;
       Tr[k] = 1.f;
       R[k][0] = R[k][1] = R[k][2] = 0.f;
       dC[k][0] = dC[k][1] = dC[k][2] = 0.f;
-      if (br.x >= 0 && px < W && py < H) {
-        const int pix = d.w + py * W + px;
+      if (px < ti.W && py < ti.H) {
+        const int pix = ti.pix_off + py * ti.W + px;
         idq[k] = w.pid[pix];
         Tr[k] = w.T_final[pix];
+        nlast[k] = w.n_contrib[pix];
 #pragma unroll
         for (int c = 0; c < 3; c++) {
           dC[k][c] = dimage[3 * (size_t)pix + c];
           R[k][c] = p.bg[c];
         }
       }
+      emax = max(emax, nlast[k]);
     }
-    unsigned n_comp = 0, n_rec = 0;
-    int ckey = -2, cnext = 0;
-    int chunk = br.x, n = br.y;
-    while (chunk >= 0) {
-      const int prev = w.rec_prev[chunk];
-      // stage the chunk's records: headers and their Gaussians
-      if (lane < n) {
-        const uint4 h = w.rec_hdr[(size_t)chunk * kRecChunk + lane];
-        const float4 A = w.gA[h.x];
-        const unsigned qxy = __float_as_uint(A.z);
-        sH[lane] = h;
-        sP[lane] = make_float4((float)(int)(qxy & 0xffffu), (float)(int)(qxy >> 16), A.x, A.y);
-        sQ[lane] = w.gB[h.x];
-        sC[lane] = w.gC[h.x];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    const unsigned long long *gkeys = w.gkeys + ti.gs;
+    for (int e = emax - 1; e >= 0; e--) {
+      const unsigned gi = (unsigned)(gkeys[e] & kIndexMask);
+      const float4 A = w.gA[gi];
+      const unsigned qxy = __float_as_uint(A.z);
+      const float4 P = make_float4((float)(int)(qxy & 0xffffu), (float)(int)(qxy >> 16), A.x, A.y);
+      const float4 Q = scaled_conic(w.gB[gi]), Cc = w.gC[gi];
+      const int g = __float_as_int(Cc.w);
+      float og[PPT], Gk[PPT];
+      bool cand[PPT];
+      bool anyc = false;
+#pragma unroll
+      for (int k = 0; k < PPT; k++) {
+        const float dx = __fsub_rn(__fsub_rn(pxf[k], P.x), P.z), dy = __fsub_rn(__fsub_rn(pyf[k], P.y), P.w);
+        Gk[k] = gauss(dx, dy, Q);
+        og[k] = __fmul_rn(Q.w, Gk[k]);
+        cand[k] = e < nlast[k] && A.w >= 0.f && og[k] >= p.alpha_min;
+        anyc = anyc || cand[k];
       }
-      __syncwarp();
-      for (int r = n - 1; r >= 0; r--) {
-        const uint4 h = sH[r];
-        const bool mine = (h.y >> lane) & 1u;
-        const int rk = (int)h.w;
-        const float4 P = sP[r], Q = sQ[r], Cc = sC[r];
-        const int g = __float_as_int(Cc.w);
-        n_rec++;
-        // w of (pixel, g): from the cache slot, filled from g's fill record
-        int slot = 0;
-        if (p.use_boundary) {
-          slot = cache_find(ckey, g);
-          if (slot < 0) {  // warp-uniform miss: flush the evicted slot, take in g
-            slot = cnext;
-            cnext = (cnext + 1 == S) ? 0 : cnext + 1;
-            const int old = __shfl_sync(0xffffffffu, ckey, slot);
-            if (old >= 0)
-              flush_boundary<PPT>(brec, bkeys, w.bg_grad, &s_cb[slot][0][0], &s_cacc[slot][0][0], old, idq, pxf, pyf);
+      if (!__any_sync(0xffffffffu, anyc)) continue;
+      int lo = 0, hi = 0;
+      if (p.use_boundary) warp_equal_range(bl.prim, bl.n, g, lo, hi);
+      float acc[9];
 #pragma unroll
-            for (int k = 0; k < PPT; k++) {
-              const int bi = (int)h.z >= 0 ? w.rec_fill[(size_t)((int)h.z + k) * 32 + lane] : -1;
-              s_cw[slot][k][lane] = w_from_candidate(brec, bi, pxf[k], pyf[k], idq[k] == g);
-              s_cb[slot][k][lane] = bi;
-              s_cacc[slot][k][lane] = 0.f;
-            }
-            if (lane == slot) ckey = g;
-          }
-        }
-        float acc[9];
+      for (int c = 0; c < 9; c++) acc[c] = 0.f;
 #pragma unroll
-        for (int q = 0; q < 9; q++) acc[q] = 0.f;
-        float dl_dw = 0.f;
-#pragma unroll
-        for (int k = 0; k < PPT; k++) {
-          if (k != rk || !mine) continue;
-          n_comp++;
-          const float dx = __fsub_rn(__fsub_rn(pxf[k], P.x), P.z), dy = __fsub_rn(__fsub_rn(pyf[k], P.y), P.w);
-          const float G = gauss(dx, dy, Q);
-          const float og = __fmul_rn(Q.w, G);
-          const float wv = p.use_boundary ? s_cw[slot][k][lane] : 1.0f;
-          const float raw = __fmul_rn(og, wv);
-          const float alpha = fminf(p.alpha_max, raw);
-          const float oma = 1.0f - alpha;
-          Tr[k] = __fdividef(Tr[k], oma);  // T_i
-          const float ta = Tr[k] * alpha;
-          // dl/dalpha_i = dl/dC . (T_i c_i - S_i / (1 - alpha_i)) with
-          // S_i / (1 - alpha_i) = T_i R_i, R <- alpha_i c_i + (1 - alpha_i) R:
-          // the form T_i (c_i - R_i) avoids amplifying rounding by 1 / (1 - alpha_i)
-          float dl_da = 0.f;
-          const float col[3] = {Cc.x, Cc.y, Cc.z};
-#pragma unroll
-          for (int c = 0; c < 3; c++) {
-            acc[6 + c] += ta * dC[k][c];
-            dl_da += dC[k][c] * (col[c] - R[k][c]);
-            R[k][c] = alpha * col[c] + oma * R[k][c];
-          }
-          dl_da *= Tr[k];
-          if (raw >= p.alpha_max) continue;  // clamped: alpha is constant
-          acc[5] += dl_da * wv * G;
-          dl_dw = dl_da * Q.w * G;
-          const float dl_dpow = dl_da * og * wv;
-          acc[2] += dl_dpow * (-0.5f * dx * dx);
-          acc[3] += dl_dpow * (-dx * dy);
-          acc[4] += dl_dpow * (-0.5f * dy * dy);
-          acc[0] += dl_dpow * (Q.x * dx + Q.y * dy);
-          acc[1] += dl_dpow * (Q.y * dx + Q.z * dy);
-        }
-        if (p.use_boundary && mine) s_cacc[slot][rk][lane] += dl_dw;
-        // gradient slots: 0 dmu x, 1 dmu y, 2-4 dK, 5 do, 6-8 dcol; slots 0-7
-        // by reduce-scatter (lanes 4m hold slot m), slot 8 by a butterfly
-        const float part = warp_reduce_scatter8(acc);
-        const float s8 = warp_sum(acc[8]);
-        float *gg = w.gg + 12 * (size_t)h.x;
-        const int gslot = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-        if ((lane & 3) == 0 && part != 0.f) atomicAdd(gg + gslot, part);
-        if (lane == 1 && s8 != 0.f) atomicAdd(gg + 8, s8);
+      for (int k = 0; k < PPT; k++) {
+        int best = -1;
+        unsigned ncand = 0;
+        const float wv = p.use_boundary ? w_search<2>(bl, lo, hi, pxf[k], pyf[k], idq[k] == g, best, ncand) : 1.0f;
+        if (!cand[k]) continue;
+        const float raw = __fmul_rn(og[k], wv);
+        const float alpha = fminf(p.alpha_max, raw);
+        if (alpha < p.alpha_min) continue;
+        const float dx = __fsub_rn(__fsub_rn(pxf[k], P.x), P.z), dy = __fsub_rn(__fsub_rn(pyf[k], P.y), P.w);
+        const float dl_dw = pair_backward(dx, dy, Gk[k], og[k], wv, raw, alpha, p.alpha_max, Cc, dC[k], Tr[k], R[k], acc);
+        if (p.use_boundary) boundary_grad(brec, bkeys, w.bg_grad, best, dl_dw, idq[k] == g, pxf[k], pyf[k]);
       }
-      __syncwarp();
-      chunk = prev;
-      n = kRecChunk;
+      const float part = warp_reduce_scatter8(acc);
+      const float s8 = warp_sum(acc[8]);
+      float *gg = w.gg + 12 * (size_t)gi;
+      const int gslot = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+      if ((lane & 3) == 0 && part != 0.f) atomicAdd(gg + gslot, part);
+      if (lane == 1 && s8 != 0.f) atomicAdd(gg + 8, s8);
     }
-    if (p.use_boundary) {
-      for (int sl = 0; sl < S; sl++) {
-        const int old = __shfl_sync(0xffffffffu, ckey, sl);
-        if (old >= 0)
-          flush_boundary<PPT>(brec, bkeys, w.bg_grad, &s_cb[sl][0][0], &s_cacc[sl][0][0], old, idq, pxf, pyf);
-      }
-    }
-    if (p.stats) flush_stats(w.stats, kBwdSupport, n_comp, n_comp, 0u, n_rec);
-    item = __shfl_sync(0xffffffffu, next, 0);
   }
 }
 
@@ -775,9 +916,13 @@ int launch_fwd_t(const Params &p, const Work &w, float *image, cudaStream_t st, 
 template <int T>
 int launch_bwd_t(const Params &p, const Work &w, const float *dimage, cudaStream_t st, int sms) {
   int grid = p.tiles < sms * 8 ? p.tiles : sms * 8;
-  if (grid > 0)
+  if (grid > 0) {
     k_composite_bwd<T><<<grid, TileCfg<T>::NT, sizeof(BwdShared<T>), st>>>(p, w, dimage);
-  return grid > 0 ? 1 : 0;
+    // warp blocks whose records overflowed (none in the common case: the
+    // kernel reads the count and returns)
+    k_composite_bwd_walk<T><<<sms * 2, TileCfg<T>::NT, 0, st>>>(p, w, dimage);
+  }
+  return grid > 0 ? 2 : 0;
 }
 
 template <int T>
@@ -820,6 +965,7 @@ int launch_composite_fwd(const Params &p, const Work &w, float *image, cudaStrea
 
 int launch_composite_bwd(const Params &p, const Work &w, const float *dimage, cudaStream_t st) {
   cudaMemsetAsync(w.counters + kQueueBwd, 0, sizeof(int), st);
+  cudaMemsetAsync(w.counters + kQueueWalk, 0, sizeof(int), st);
   const int sms = num_sms();
   if (p.tile == 8) return launch_bwd_t<8>(p, w, dimage, st, sms);
   if (p.tile == 32) return launch_bwd_t<32>(p, w, dimage, st, sms);

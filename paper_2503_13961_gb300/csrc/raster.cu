@@ -26,7 +26,6 @@ namespace bgt {
 namespace {
 
 constexpr int kRasterWarps = 4;
-constexpr int kPrimsPerWarp = 8;  // primitives each warp rasterizes per block (amortises the tables)
 constexpr int kMaxVerts = (kMaxTess + 1) * (kMaxTess + 2) / 2;
 constexpr int kSpan32 = 32000;    // box spans (1/256 px) below which edge functions fit 32 bits
 
@@ -239,7 +238,8 @@ __global__ void k_resolve(Params p, Scene s, Work w) {
 
 int launch_raster(const Params &p, const Scene &s, const Work &w, cudaStream_t st) {
   if (p.V == 0 || p.M == 0) return 0;
-  const int per_block = kRasterWarps * kPrimsPerWarp;
+  // each warp rasterizes p.raster_prims primitives per block (amortises the tables)
+  const int per_block = kRasterWarps * p.raster_prims;
   const dim3 grid((unsigned)((p.M + per_block - 1) / per_block), (unsigned)p.V);
   dispatch_degree(p.n, [&](auto d) { k_raster<decltype(d)::value><<<grid, kRasterWarps * 32, 0, st>>>(p, s, w); });
   return 1;

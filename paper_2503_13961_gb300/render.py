@@ -180,7 +180,8 @@ class Renderer:
     max_pairs / max_boundary_pairs ((Gaussian, tile) and (boundary point,
     tile) pairs; default 8 per pixel), max_blend_pairs (composited
     (pixel, Gaussian) pairs the forward records for the backward; default
-    32 per pixel). Options: tess_level L, tile_size
+    8 per pixel; blocks whose records do not fit are re-walked by the
+    backward). Options: tess_level L, tile_size
     (8/16/32), use_boundary (False = the paper's "w/o B" ablation), graph
     (capture forward / backward in CUDA graphs) and the blending cutoffs.
     """
@@ -265,10 +266,10 @@ class Renderer:
         return int(self.lib.bgt_sync_status(self.h, _stream(stream)))
 
     def counts(self, stream=None):
-        out = (ctypes.c_longlong * 7)()
+        out = (ctypes.c_longlong * 8)()
         self._check(self.lib.bgt_get_counts(self.h, out, _stream(stream)))
         return {"F": out[0], "Nb": out[1], "K": out[2], "Kb": out[3], "tiles": out[4], "rec_headers": out[5],
-                "rec_fill_units": out[6]}
+                "rec_fill_units": out[6], "walked_blocks": out[7]}
 
     def set_tile_size(self, t):
         self._check(self.lib.bgt_set_tile_size(self.h, int(t)))
@@ -276,6 +277,25 @@ class Renderer:
     @property
     def tile_size(self):
         return int(self.lib.bgt_get_tile_size(self.h))
+
+    TUNING_KEYS = ("tile_size", "raster_prims", "bwd_dequeue", "chain_blocks_per_sm")
+
+    def tuning(self):
+        """The scheduling of the handle (bgt_tuning) as a dict."""
+        t = _abi.Tuning()
+        self._check(self.lib.bgt_get_tuning(self.h, ctypes.byref(t)))
+        return {k: int(getattr(t, k)) for k in self.TUNING_KEYS}
+
+    def set_tuning(self, **knobs):
+        """Change scheduling knobs (tile_size, raster_prims, bwd_dequeue,
+        chain_blocks_per_sm); images do not depend on them."""
+        cur = self.tuning()
+        unknown = set(knobs) - set(cur)
+        if unknown:
+            raise ValueError(f"unknown tuning knobs {sorted(unknown)}")
+        cur.update(knobs)
+        t = _abi.Tuning(*(int(cur[k]) for k in self.TUNING_KEYS))
+        self._check(self.lib.bgt_set_tuning(self.h, ctypes.byref(t)))
 
     def autotune(self, scene, cams, images, d_images, grads, iters=3, stream=None):
         best = ctypes.c_int(0)

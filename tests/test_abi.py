@@ -29,7 +29,7 @@ def test_struct_fields_follow_the_header():
     from paper_2503_13961_gb300 import _abi
     text = open(os.path.join(ROOT, "include", "bgt.h")).read()
     for struct, cls in (("bgt_config", _abi.Config), ("bgt_camera", _abi.Camera), ("bgt_scene", _abi.Scene),
-                        ("bgt_grads", _abi.Grads), ("bgt_prims", _abi.Prims)):
+                        ("bgt_grads", _abi.Grads), ("bgt_prims", _abi.Prims), ("bgt_tuning", _abi.Tuning)):
         body = re.search(r"typedef struct \{([^{}]*)\}\s*" + struct + ";", text).group(1)
         body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
         fields = []

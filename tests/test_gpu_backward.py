@@ -123,22 +123,28 @@ def test_gradients_multiview_batch_small_boundary_scale(oracle, scenes):
     assert np.abs(ref["r_b"]).max() > 0
 
 
-def test_dense_tiles_room_crop(oracle, scenes):
+@pytest.mark.parametrize("blend_cap", [0, 1])
+def test_dense_tiles_room_crop(oracle, scenes, blend_cap):
     """Config 5 (100,000 degree-3 triangles, opacity Beta(5,1)): a 96^2 crop of
     a view whose near surfaces give Gaussians of ~16 px support. Its tiles hold
     up to ~8,800 (Gaussian, tile) pairs (the long-segment sort in global
     memory), pixels walk ~450 list entries and reach the transmittance stop,
     and the blend records run to many headers per pixel. Image (stable pixels)
-    and gradients against the oracle."""
+    and gradients against the oracle, with the default record capacity and
+    with none at all (every warp block re-walks its tile list)."""
     from tests.gpu_util import FWD_TOL, compare_images
     sc, cams = scenes.config_scene(5)
     crop = scenes.crop_camera(cams[5], 640, 192, 96, 96)
-    rd = make_renderer(sc, [crop], pairs_per_px=64)
+    rd = make_renderer(sc, [crop], pairs_per_px=64, max_blend_pairs=blend_cap)
     g, got, ref, inter, _ = _run(oracle, sc, [crop], seed=6, renderer=rd)
     counts = rd.counts()
     ranges = rd.stage("g_ranges")
     assert int(np.diff(ranges).max()) > 4096  # the global-memory radix sort of long tile lists ran
     assert counts["rec_headers"] > 96 * 96, counts
+    if blend_cap:
+        assert counts["walked_blocks"] >= 6 * 6 * 8 - 1, counts  # (at most one chunk fits)
+    else:
+        assert counts["walked_blocks"] == 0, counts
     ref_img = oracle.render(sc, crop)
     err, unstable = compare_images(g["images"][0], ref_img, ref_img["flags"], oracle)
     assert err < FWD_TOL, err
@@ -146,6 +152,29 @@ def test_dense_tiles_room_crop(oracle, scenes):
     for k in ("ctrl", "color", "opacity", "r_b"):
         if np.abs(ref[k]).max() == 0:
             continue
+        _assert_close(got[k], ref[k], k)
+
+
+@pytest.mark.parametrize("cap", [1, 3000])
+def test_blend_record_overflow_falls_back_to_tile_walk(oracle, scenes, cap):
+    """max_blend_pairs below what the forward composites: the warp blocks
+    whose records do not fit are listed by the forward and the backward
+    re-walks their tile lists (retaking the forward's decisions) instead of
+    replaying records; no error is raised and the gradients still match the
+    oracle. cap = 1: every block walks; cap = 3000: some blocks replay, the
+    rest walk."""
+    sc, cams = scenes.tiny_scene("ico1", noise=0.04, size=(90, 70), r_b=0.04)
+    rd = make_renderer(sc, cams, max_blend_pairs=cap)
+    _, got, ref, _, _ = _run(oracle, sc, cams, seed=7, renderer=rd)
+    # warp blocks (8 x 4 pixels at tile 16) holding a composited pixel (T < 1)
+    T = rd.stage("T").reshape(70, 90)
+    cells = np.zeros(((70 + 3) // 4, (90 + 7) // 8), bool)
+    ys, xs = np.nonzero(T < 1.0)
+    cells[ys // 4, xs // 8] = True
+    blocks = int(cells.sum())
+    walked = rd.counts()["walked_blocks"]
+    assert (walked >= blocks - 1) if cap == 1 else (0 < walked < blocks), (walked, blocks)
+    for k in ("ctrl", "color", "opacity", "r_b"):
         _assert_close(got[k], ref[k], k)
 
 
