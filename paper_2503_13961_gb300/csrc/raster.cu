@@ -183,55 +183,74 @@ __global__ void __launch_bounds__(kRasterWarps * 32, N <= 2 ? 8 : 6) k_raster(Pa
   }
 }
 
+// Resolve: the winning key of each pixel -> I_id and perspective-correct
+// I_uv. Persistent blocks tabulate the lattice Bernstein weights once (the
+// raster's table, same operations) and recompute the winning flat triangle's
+// three vertices from it with the primitive's control points in registers.
 template <int N>
-__global__ void k_resolve(Params p, Scene s, Work w) {
-  const int pix = blockIdx.x * blockDim.x + threadIdx.x;
-  if (pix >= p.P) return;
-  const unsigned long long key = w.zbuf[pix];
-  if (key == ~0ull) {
-    w.pid[pix] = -1;
-    w.puv[pix] = make_float2(0.f, 0.f);
-    return;
-  }
-  const int view = find_view(w.view_pix_off, p.V, pix);
-  const View vw = w.views[view];
+__global__ void __launch_bounds__(256) k_resolve(Params p, Scene s, Work w) {
+  constexpr int NCP = (N + 1) * (N + 2) / 2;
+  __shared__ float sB[kMaxVerts * NCP];
   const int L = p.L, nsub = 2 * L * L;
-  const unsigned int gid = (unsigned int)(key & 0xffffffffu);
-  const int prim = (int)(gid / (unsigned int)nsub);
-  const int sid = (int)(gid - (unsigned int)prim * (unsigned int)nsub);
-  if (prim >= p.M) {
-    atomicOr(w.status, kStatusBadPrim);
-    w.pid[pix] = -1;
-    return;
-  }
-  const float *cp = s.ctrl + (size_t)prim * p.ncp * 3;
-  int va[3], vb[3];
-  subtri_verts(L, sid, va, vb);
-  RVert r[3];
+  const int NV = (L + 1) * (L + 2) / 2;
+  for (int vi = threadIdx.x; vi < NV; vi += blockDim.x) {
+    int a, b;
+    slot_to_ab(vi, L, a, b);
+    float Bw[NCP];
+    lattice_bernstein<N>(lattice_frac(a, L), lattice_frac(b, L), lattice_frac(L - a - b, L), Bw);
 #pragma unroll
-  for (int c = 0; c < 3; c++) r[c] = raster_vertex<N>(cp, va[c], vb[c], L, vw, p.near_z);
-  long long area2 = edge_fn(r[0].X, r[0].Y, r[1].X, r[1].Y, r[2].X, r[2].Y);
-  if (area2 < 0) {
-    RVert t = r[1]; r[1] = r[2]; r[2] = t;
-    int x = va[1]; va[1] = va[2]; va[2] = x;
-    x = vb[1]; vb[1] = vb[2]; vb[2] = x;
-    area2 = -area2;
+    for (int t = 0; t < NCP; t++) sB[vi * NCP + t] = Bw[t];
   }
-  const int local = pix - vw.pix_off;
-  const int qy = local / vw.W, qx = local - qy * vw.W;
-  const int Px = qx * 256, Py = qy * 256;
-  const long long e0 = edge_fn(r[1].X, r[1].Y, r[2].X, r[2].Y, Px, Py);
-  const long long e1 = edge_fn(r[2].X, r[2].Y, r[0].X, r[0].Y, Px, Py);
-  const long long e2 = edge_fn(r[0].X, r[0].Y, r[1].X, r[1].Y, Px, Py);
-  const float af = (float)area2;
-  const float w0 = ((float)e0 / af) / r[0].Z;
-  const float w1 = ((float)e1 / af) / r[1].Z;
-  const float w2 = ((float)e2 / af) / r[2].Z;
-  const float ws = (w0 + w1) + w2;
-  const float u = (w0 * (float)va[0] + w1 * (float)va[1] + w2 * (float)va[2]) / (ws * (float)L);
-  const float v = (w0 * (float)vb[0] + w1 * (float)vb[1] + w2 * (float)vb[2]) / (ws * (float)L);
-  w.pid[pix] = prim;
-  w.puv[pix] = make_float2(u, v);
+  __syncthreads();
+  for (int pix = blockIdx.x * blockDim.x + threadIdx.x; pix < p.P; pix += gridDim.x * blockDim.x) {
+    const unsigned long long key = w.zbuf[pix];
+    if (key == ~0ull) {
+      w.pid[pix] = -1;
+      w.puv[pix] = make_float2(0.f, 0.f);
+      continue;
+    }
+    const unsigned int gid = (unsigned int)(key & 0xffffffffu);
+    const int prim = (int)(gid / (unsigned int)nsub);
+    const int sid = (int)(gid - (unsigned int)prim * (unsigned int)nsub);
+    if (prim >= p.M) {
+      atomicOr(w.status, kStatusBadPrim);
+      w.pid[pix] = -1;
+      continue;
+    }
+    const int view = find_view(w.view_pix_off, p.V, pix);
+    const View &vw = w.views[view];
+    const float *cp = s.ctrl + (size_t)prim * NCP * 3;
+    float c[3 * NCP];
+#pragma unroll
+    for (int k = 0; k < 3 * NCP; k++) c[k] = __ldg(cp + k);
+    int va[3], vb[3];
+    subtri_verts(L, sid, va, vb);
+    RVert r[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) r[k] = vertex_from_weights<N>(sB + vslot(va[k], vb[k], L) * NCP, c, vw, p.near_z);
+    long long area2 = edge_fn(r[0].X, r[0].Y, r[1].X, r[1].Y, r[2].X, r[2].Y);
+    if (area2 < 0) {
+      RVert t = r[1]; r[1] = r[2]; r[2] = t;
+      int x = va[1]; va[1] = va[2]; va[2] = x;
+      x = vb[1]; vb[1] = vb[2]; vb[2] = x;
+      area2 = -area2;
+    }
+    const int local = pix - vw.pix_off;
+    const int qy = local / vw.W, qx = local - qy * vw.W;
+    const int Px = qx * 256, Py = qy * 256;
+    const long long e0 = edge_fn(r[1].X, r[1].Y, r[2].X, r[2].Y, Px, Py);
+    const long long e1 = edge_fn(r[2].X, r[2].Y, r[0].X, r[0].Y, Px, Py);
+    const long long e2 = edge_fn(r[0].X, r[0].Y, r[1].X, r[1].Y, Px, Py);
+    const float af = (float)area2;
+    const float w0 = ((float)e0 / af) / r[0].Z;
+    const float w1 = ((float)e1 / af) / r[1].Z;
+    const float w2 = ((float)e2 / af) / r[2].Z;
+    const float ws = (w0 + w1) + w2;
+    const float u = (w0 * (float)va[0] + w1 * (float)va[1] + w2 * (float)va[2]) / (ws * (float)L);
+    const float v = (w0 * (float)vb[0] + w1 * (float)vb[1] + w2 * (float)vb[2]) / (ws * (float)L);
+    w.pid[pix] = prim;
+    w.puv[pix] = make_float2(u, v);
+  }
 }
 
 }  // namespace
@@ -247,7 +266,11 @@ int launch_raster(const Params &p, const Scene &s, const Work &w, cudaStream_t s
 
 int launch_resolve(const Params &p, const Scene &s, const Work &w, cudaStream_t st) {
   if (p.P == 0) return 0;
-  dispatch_degree(p.n, [&](auto d) { k_resolve<decltype(d)::value><<<(p.P + 255) / 256, 256, 0, st>>>(p, s, w); });
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = min((p.P + 255) / 256, (sms > 0 ? sms : 152) * 8);
+  dispatch_degree(p.n, [&](auto d) { k_resolve<decltype(d)::value><<<blocks, 256, 0, st>>>(p, s, w); });
   return 1;
 }
 
