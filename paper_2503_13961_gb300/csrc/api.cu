@@ -91,6 +91,7 @@ void carve(bgt_handle *h, char *base, size_t *total) {
   w.T_final = c.take<float>(P);
   w.n_contrib = c.take<int>(P);
   w.blk_cnt = c.take<int>(2 * (long long)h->nblk_cap);
+  w.blk_off = c.take<long long>(2 * ((long long)h->nblk_cap + 1));
   w.counters = c.take<int>(16);
   w.stats = c.take<unsigned long long>(8);
   w.status = c.take<int>(1);
@@ -117,8 +118,9 @@ void carve(bgt_handle *h, char *base, size_t *total) {
   w.b_tcount = c.take<int>(T + 1);
   w.b_tstart = c.take<long long>(T + 1);
   w.b_tfill = c.take<int>(T + 1);
-  w.scan_aux = c.take<long long>(2 * (T / 4096 + 4));
-  w.scan_aux2 = w.scan_aux ? w.scan_aux + (T / 4096 + 4) : nullptr;
+  const long long naux = std::max<long long>(T, h->nblk_cap) / 4096 + 4;
+  w.scan_aux = c.take<long long>(2 * naux);
+  w.scan_aux2 = w.scan_aux ? w.scan_aux + naux : nullptr;
   w.big_list = c.take<int>(2 * (long long)T + 2);
   w.tile_desc = c.take<int4>(2 * (long long)T + 2);
   w.rec_chunk_cap = (int)(h->Bcap / 2 / bgt::kRecChunk + 1);
@@ -386,7 +388,7 @@ bgt_status bgt_create(const bgt_config *cfg, bgt_handle **out) {
   h->Mcap = cfg->max_prims;
   // tiles of all views at the smallest tile size: sum (W/8+1)(H/8+1) <= P (1/64 + 1/8) + 2 V
   h->Tcap = (int)(h->Pcap * 9 / 64 + 2ll * h->Vcap + 1);
-  h->nblk_cap = (int)((h->Pcap + 1023) / 1024);
+  h->nblk_cap = (int)((h->Pcap + 127) / 128);  // warp chunks of 128 pixels (sub-primitive generation)
   size_t total = 0;
   carve(h, nullptr, &total);
   cudaError_t e = cudaMalloc(&h->arena, total);

@@ -108,7 +108,8 @@ struct Work {
   unsigned long long *vis_seen;  // [M] views (bit v - v0) a primitive owns pixels in, for the visibility measures
   float2 *puv;                // [P] I_uv (u, v)
   int *pix_gidx;              // [P] gaussian index of a foreground pixel, else -1
-  int *blk_cnt;               // [2][nblk] per-block foreground / boundary counts
+  int *blk_cnt;               // [2][nblk] foreground / boundary pixels per warp chunk of 128 pixels
+  long long *blk_off;         // [2][nblk + 1] their exclusive prefix sums (totals last)
   int *counters;              // [16] F, Nb, K, Kb, queue heads...
   int *status;                // [1]
   // per primitive
@@ -131,7 +132,7 @@ struct Work {
   int *g_tcount, *g_tfill;    // [tiles + 1] per-tile pair counts / fill cursors
   int *b_tcount, *b_tfill;
   long long *g_tstart, *b_tstart;  // [tiles + 1] exclusive prefix sums (64-bit: no wrap)
-  long long *scan_aux, *scan_aux2; // scratch of the two tile-count scans
+  long long *scan_aux, *scan_aux2; // scratch of the two tile-count (and chunk-count) scans
   int *big_list;              // [2 tiles] segments too long for one warp to sort
   int4 *tile_desc;            // [2 tiles] (view, x0 | y0 << 16, W | H << 16, view pixel offset),
                               // (Gaussian list start, length, boundary list start, length)

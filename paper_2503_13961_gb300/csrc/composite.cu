@@ -383,13 +383,12 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_compos
   constexpr int NT = Cfg::NT, PPT = Cfg::PPT, S = Cfg::SLOTS_FWD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto &sh = *reinterpret_cast<FwdShared<T> *>(smem_raw);
-  auto &sP = sh.sP;
-  auto &sQ = sh.sQ;
-  auto &sC = sh.sC;
-  auto &sG = sh.sG;
-  auto &s_cw = sh.s_cw;
   auto &s_tile = sh.s_tile;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // this warp's staging slots and primitive cache (w per slot, plane and lane)
+  float4 *sP = sh.sP[warp], *sQ = sh.sQ[warp], *sC = sh.sC[warp];
+  int *sG = sh.sG[warp];
+  float *cw = &sh.s_cw[warp][0][0][0];
   RecWriter rw;
   rw.fill = rw.fill_end = 0;
   if (threadIdx.x == 0) s_tile = atomicAdd(w.counters + kQueueFwd, 1);
@@ -438,11 +437,11 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_compos
       if (__all_sync(0xffffffffu, alldone)) break;
       const unsigned long long key = knext;
       if (c0 + 32 + lane < gn) knext = gkeys[c0 + 32 + lane];  // prefetch the next chunk's keys
-      unsigned mask = stage_chunk(w, key, c0 + lane < gn, bx0, bx1, by0, by1, sP[warp], sQ[warp], sC[warp], sG[warp]);
+      unsigned mask = stage_chunk(w, key, c0 + lane < gn, bx0, bx1, by0, by1, sP, sQ, sC, sG);
       while (mask) {
         const int l = __ffs(mask) - 1;
         mask &= mask - 1;
-        const float4 P = sP[warp][l], Q = sQ[warp][l];
+        const float4 P = sP[l], Q = sQ[l];
         float og[PPT];
         bool cand[PPT];
         bool anyc = false;
@@ -456,7 +455,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_compos
         }
         if (!__any_sync(0xffffffffu, anyc)) continue;
         n_visit++;
-        const float4 Cc = sC[warp][l];
+        const float4 Cc = sC[l];
         const int g = __float_as_int(Cc.w);
         int slot = cache_find(ckey, g);
         if (slot < 0) {  // warp-uniform miss: every lane searches, coherently
@@ -470,7 +469,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_compos
 #pragma unroll
           for (int k = 0; k < PPT; k++) {
             int best = -1;
-            s_cw[warp][slot][k][lane] = p.use_boundary
+            cw[(slot * PPT + k) * 32 + lane] = p.use_boundary
                 ? w_search<2>(bl, lo, hi, pxf[k], pyf[k], idq[k] == g, best, n_cand) : 1.0f;
             if (f >= 0) w.rec_fill[(size_t)(f + k) * 32 + lane] = best;
           }
@@ -479,34 +478,32 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_compos
             cfill = f;
           }
         }
+        // compositing without branches: a pixel composites when it is a
+        // candidate, alpha >= alpha_min and T would stay >= t_stop; the pair
+        // that would take T below t_stop ends the pixel's list
         bool comp[PPT];
 #pragma unroll
         for (int k = 0; k < PPT; k++) {
-          comp[k] = false;
-          if (!cand[k]) continue;
-          n_sup++;
-          const float alpha = fminf(p.alpha_max, __fmul_rn(og[k], s_cw[warp][slot][k][lane]));
-          if (alpha < p.alpha_min) continue;
+          const float alpha = fminf(p.alpha_max, __fmul_rn(og[k], cw[(slot * PPT + k) * 32 + lane]));
           const float testT = __fmul_rn(Tr[k], __fsub_rn(1.0f, alpha));
-          if (testT < p.t_stop) {
-            done[k] = true;
-            continue;
-          }
-          const float ta = __fmul_rn(Tr[k], alpha);
+          const bool ok = cand[k] && alpha >= p.alpha_min;
+          const bool stop = ok && testT < p.t_stop;
+          comp[k] = ok && !stop;
+          done[k] = done[k] || stop;
+          const float ta = comp[k] ? __fmul_rn(Tr[k], alpha) : 0.0f;
           C[k][0] = __fmaf_rn(ta, Cc.x, C[k][0]);
           C[k][1] = __fmaf_rn(ta, Cc.y, C[k][1]);
           C[k][2] = __fmaf_rn(ta, Cc.z, C[k][2]);
-          Tr[k] = testT;
-          last[k] = c0 + l + 1;
-          comp[k] = true;
-          n_comp++;
+          Tr[k] = comp[k] ? testT : Tr[k];
+          last[k] = comp[k] ? c0 + l + 1 : last[k];
+          n_sup += cand[k];
+          n_comp += comp[k];
         }
         // record the pixels composited for the backward pass
-        const int fill = __shfl_sync(0xffffffffu, cfill, slot);
 #pragma unroll
         for (int k = 0; k < PPT; k++) {
           const unsigned cm = __ballot_sync(0xffffffffu, comp[k]);
-          if (cm) rw.put(w, (unsigned)sG[warp][l], cm, fill, k);
+          if (cm) rw.put(w, (unsigned)sG[l], cm, __shfl_sync(0xffffffffu, cfill, slot), k);
         }
       }
       __syncwarp();

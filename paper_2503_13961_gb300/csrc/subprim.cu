@@ -10,10 +10,11 @@
 // different id) also yield a boundary point b = projection of the same S_q
 // with radius sigma = k_b fx r_b / z.
 //
-// Gaussians and boundary points are compacted in global pixel order with a
-// two-pass block scan (count, scan of block counts, generate), so indices do
-// not depend on scheduling. Each record counts its screen tiles into
-// per-tile counters for the binning pass.
+// Gaussians and boundary points are compacted in global pixel order: a count
+// pass per warp chunk of 128 pixels, exclusive scans of the chunk counts, and
+// the generation pass in which every warp compacts its chunk with ballots
+// (no block barrier), so indices do not depend on scheduling. Each record
+// counts its screen tiles into per-tile counters for the binning pass.
 #include "bgt_internal.cuh"
 
 namespace bgt {
@@ -21,8 +22,9 @@ namespace bgt {
 namespace {
 
 constexpr int kGenThreads = 256;
-constexpr int kGenRounds = 4;  // pixels per thread; block covers 1024 pixels
-constexpr int kGenPixels = kGenThreads * kGenRounds;
+constexpr int kGenRounds = 4;                  // pixels per lane: a warp chunk covers 128 pixels
+constexpr int kChunk = 32 * kGenRounds;
+constexpr int kGenWarps = kGenThreads / 32;
 
 // foreground / boundary flags of global pixel `pix`
 __device__ inline void pixel_flags(const Params &p, const Work &w, int pix, bool &fg, bool &bnd,
@@ -42,84 +44,30 @@ __device__ inline void pixel_flags(const Params &p, const Work &w, int pix, bool
         (y > 0 && w.pid[pix - W] != id) || (y < H - 1 && w.pid[pix + W] != id);
 }
 
+// foreground and boundary pixels of each warp chunk of 128 pixels
 __global__ void __launch_bounds__(kGenThreads) k_count(Params p, Work w) {
-  __shared__ int s_cnt[2][kGenThreads / 32];
-  const int base = blockIdx.x * kGenPixels;
+  const int lane = threadIdx.x & 31;
+  const int chunk = blockIdx.x * kGenWarps + (threadIdx.x >> 5);
+  if (chunk >= w.nblk) return;
   int cf = 0, cb = 0;
+#pragma unroll
   for (int r = 0; r < kGenRounds; r++) {
     bool fg, bnd;
     int view;
-    pixel_flags(p, w, base + r * kGenThreads + threadIdx.x, fg, bnd, view);
-    cf += fg;
-    cb += bnd;
+    pixel_flags(p, w, chunk * kChunk + r * 32 + lane, fg, bnd, view);
+    cf += __popc(__ballot_sync(0xffffffffu, fg));
+    cb += __popc(__ballot_sync(0xffffffffu, bnd));
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    cf += __shfl_xor_sync(0xffffffffu, cf, o);
-    cb += __shfl_xor_sync(0xffffffffu, cb, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    s_cnt[0][threadIdx.x >> 5] = cf;
-    s_cnt[1][threadIdx.x >> 5] = cb;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int a = 0, b = 0;
-    for (int i = 0; i < kGenThreads / 32; i++) {
-      a += s_cnt[0][i];
-      b += s_cnt[1][i];
-    }
-    w.blk_cnt[blockIdx.x] = a;
-    w.blk_cnt[w.nblk + blockIdx.x] = b;
+  if (lane == 0) {
+    w.blk_cnt[chunk] = cf;
+    w.blk_cnt[w.nblk + chunk] = cb;
   }
 }
 
-// exclusive scan of the two block-count arrays in one block; totals -> F, Nb
-__global__ void __launch_bounds__(1024) k_scan_blocks(Work w, int nblk) {
-  __shared__ int s_w[2][32];
-  __shared__ int s_carry[2];
-  if (threadIdx.x < 2) s_carry[threadIdx.x] = 0;
-  __syncthreads();
-  for (int base = 0; base < nblk; base += 1024) {
-    const int i = base + threadIdx.x;
-    int v0 = i < nblk ? w.blk_cnt[i] : 0;
-    int v1 = i < nblk ? w.blk_cnt[w.nblk + i] : 0;
-    int x0 = v0, x1 = v1;
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y0 = __shfl_up_sync(0xffffffffu, x0, o);
-      const int y1 = __shfl_up_sync(0xffffffffu, x1, o);
-      if (lane >= o) { x0 += y0; x1 += y1; }
-    }
-    if (lane == 31) { s_w[0][wp] = x0; s_w[1][wp] = x1; }
-    __syncthreads();
-    if (wp == 0) {
-      int a = s_w[0][lane], b = s_w[1][lane];
-      for (int o = 1; o < 32; o <<= 1) {
-        const int ya = __shfl_up_sync(0xffffffffu, a, o);
-        const int yb = __shfl_up_sync(0xffffffffu, b, o);
-        if (lane >= o) { a += ya; b += yb; }
-      }
-      s_w[0][lane] = a;
-      s_w[1][lane] = b;
-    }
-    __syncthreads();
-    const int pre0 = (wp ? s_w[0][wp - 1] : 0) + x0 - v0 + s_carry[0];
-    const int pre1 = (wp ? s_w[1][wp - 1] : 0) + x1 - v1 + s_carry[1];
-    if (i < nblk) {
-      w.blk_cnt[i] = pre0;
-      w.blk_cnt[w.nblk + i] = pre1;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      s_carry[0] += s_w[0][31];
-      s_carry[1] += s_w[1][31];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    w.counters[kF] = s_carry[0];
-    w.counters[kNb] = s_carry[1];
-  }
+// F and Nb: the totals of the two chunk scans
+__global__ void k_totals(Work w) {
+  w.counters[kF] = (int)w.blk_off[w.nblk];
+  w.counters[kNb] = (int)w.blk_off[2 * w.nblk + 1];
 }
 
 __device__ inline void count_tiles(int *cnt, int tile_off, int tiles_x, uint2 rect) {
@@ -141,44 +89,37 @@ __device__ inline uint2 tile_rect(float cx, float cy, float rx, float ry, const 
 
 template <int N>
 __global__ void __launch_bounds__(kGenThreads) k_generate(Params p, Scene s, Work w) {
-  __shared__ int s_wf[kGenThreads / 32], s_wb[kGenThreads / 32];
-  // the block's foreground pixels in pixel order: pixel, view, boundary index (-1)
-  __shared__ int s_pix[kGenPixels], s_view[kGenPixels], s_bi[kGenPixels];
+  // each warp's foreground pixels in pixel order: pixel, view, boundary index (-1)
+  __shared__ int s_pix[kGenWarps][kChunk], s_view[kGenWarps][kChunk], s_bi[kGenWarps][kChunk];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  const int base_f0 = w.blk_cnt[blockIdx.x];
-  int nf = 0, base_b = w.blk_cnt[w.nblk + blockIdx.x];
-  const int base = blockIdx.x * kGenPixels;
+  const int chunk = blockIdx.x * kGenWarps + wp;
+  if (chunk >= w.nblk) return;
+  const int base_f0 = (int)w.blk_off[chunk];
+  const int base_b0 = (int)w.blk_off[w.nblk + 1 + chunk];
+  const unsigned lt = (1u << lane) - 1u;
+  int nf = 0, nb = 0;
   // compaction: ranks in pixel order give the Gaussian and boundary indices
+#pragma unroll
   for (int r = 0; r < kGenRounds; r++) {
-    const int pix = base + r * kGenThreads + threadIdx.x;
+    const int pix = chunk * kChunk + r * 32 + lane;
     bool fg, bnd;
     int view;
     pixel_flags(p, w, pix, fg, bnd, view);
     const unsigned mf = __ballot_sync(0xffffffffu, fg), mb = __ballot_sync(0xffffffffu, bnd);
-    const unsigned lt = (1u << lane) - 1u;
-    if (lane == 0) { s_wf[wp] = __popc(mf); s_wb[wp] = __popc(mb); }
-    __syncthreads();
-    int off_f = nf, off_b = base_b, tot_f = 0, tot_b = 0;
-    for (int i = 0; i < kGenThreads / 32; i++) {
-      if (i < wp) { off_f += s_wf[i]; off_b += s_wb[i]; }
-      tot_f += s_wf[i];
-      tot_b += s_wb[i];
-    }
-    __syncthreads();
-    nf += tot_f;
-    base_b += tot_b;
-    const int lf = off_f + __popc(mf & lt);
+    const int lf = nf + __popc(mf & lt);
     if (pix < p.P) w.pix_gidx[pix] = fg ? base_f0 + lf : -1;
     if (fg) {
-      s_pix[lf] = pix;
-      s_view[lf] = view;
-      s_bi[lf] = bnd ? off_b + __popc(mb & lt) : -1;
+      s_pix[wp][lf] = pix;
+      s_view[wp][lf] = view;
+      s_bi[wp][lf] = bnd ? base_b0 + nb + __popc(mb & lt) : -1;
     }
+    nf += __popc(mf);
+    nb += __popc(mb);
   }
-  __syncthreads();
-  // sub-primitives of the foreground pixels, all threads busy
-  for (int j = threadIdx.x; j < nf; j += kGenThreads) {
-    const int pix = s_pix[j], view = s_view[j], bi = s_bi[j];
+  __syncwarp();
+  // sub-primitives of the chunk's foreground pixels
+  for (int j = lane; j < nf; j += 32) {
+    const int pix = s_pix[wp][j], view = s_view[wp][j], bi = s_bi[wp][j];
     const bool bnd = bi >= 0;
     const int gi = base_f0 + j;
     const View vw = w.views[view];
@@ -334,19 +275,26 @@ __global__ void __launch_bounds__(256) k_sh_color(Params p, Scene s, Work w) {
 }
 
 int launch_generate(const Params &p, const Scene &s, const Work &w, cudaStream_t st) {
-  const int nblk = (p.P + kGenPixels - 1) / kGenPixels;
-  if (nblk == 0) {
+  const int nchunk = (p.P + kChunk - 1) / kChunk;
+  if (nchunk == 0) {
     cudaMemsetAsync(w.counters, 0, 2 * sizeof(int), st);
     return 0;
   }
-  k_count<<<nblk, kGenThreads, 0, st>>>(p, w);
-  k_scan_blocks<<<1, 1024, 0, st>>>(w, nblk);
-  dispatch_degree(p.n, [&](auto d) { k_generate<decltype(d)::value><<<nblk, kGenThreads, 0, st>>>(p, s, w); });
+  Work wc = w;
+  wc.nblk = nchunk;  // chunks of this call (the arrays hold the capacity's)
+  const int blocks = (nchunk + kGenWarps - 1) / kGenWarps;
+  k_count<<<blocks, kGenThreads, 0, st>>>(p, wc);
+  int k = 1;
+  k += launch_exclusive_scan(wc.blk_cnt, wc.blk_off, nchunk, wc.scan_aux, st);
+  k += launch_exclusive_scan(wc.blk_cnt + nchunk, wc.blk_off + nchunk + 1, nchunk, wc.scan_aux2, st);
+  k_totals<<<1, 1, 0, st>>>(wc);
+  dispatch_degree(p.n, [&](auto d) { k_generate<decltype(d)::value><<<blocks, kGenThreads, 0, st>>>(p, s, wc); });
+  k += 2;
   if (p.sh_deg > 0) {
     dispatch_degree(p.n, [&](auto d) { k_sh_color<decltype(d)::value><<<152 * 8, 256, 0, st>>>(p, s, w); });
-    return 4;
+    k++;
   }
-  return 3;
+  return k;
 }
 
 }  // namespace bgt

@@ -140,10 +140,10 @@ def test_dense_tiles_room_crop(oracle, scenes, blend_cap):
     counts = rd.counts()
     ranges = rd.stage("g_ranges")
     assert int(np.diff(ranges).max()) > 4096  # the global-memory radix sort of long tile lists ran
-    assert counts["rec_headers"] > 96 * 96, counts
     if blend_cap:
         assert counts["walked_blocks"] >= 6 * 6 * 8 - 1, counts  # (at most one chunk fits)
     else:
+        assert counts["rec_headers"] > 96 * 96, counts  # more than one record per pixel
         assert counts["walked_blocks"] == 0, counts
     ref_img = oracle.render(sc, crop)
     err, unstable = compare_images(g["images"][0], ref_img, ref_img["flags"], oracle)
