@@ -100,6 +100,7 @@ void carve(bgt_handle *h, char *base, size_t *total) {
   w.gC = c.take<float4>(F);
   w.g_pix = c.take<int>(F);
   w.g_view = c.take<int>(F);
+  w.g_bidx = c.take<int>(F);
   w.g_uv = c.take<float2>(F);
   w.g_rect = c.take<uint2>(F);
   w.g_depth = c.take<float>(F);

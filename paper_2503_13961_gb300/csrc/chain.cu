@@ -10,8 +10,9 @@
 //   dl/dJ = dl/d(JW) W^T, J depends on t; dl/dS_q = W^T dl/dt.
 // Boundary point b = projection of S_b, sigma = k_b fx r_b / z_b.
 // Control-point, colour and opacity gradients of consecutive Gaussians (which
-// mostly share a primitive, being compacted in pixel order) are summed with a
-// warp-segmented scan before one atomic per run.
+// mostly share a primitive, being compacted in pixel order) are summed per
+// run of equal primitive through shared memory before one atomic per run and
+// value.
 #include "bgt_internal.cuh"
 
 namespace bgt {
@@ -31,24 +32,46 @@ __device__ inline void camera_point_f32(const float *cp, float u, float v, const
   for (int r = 0; r < 3; r++) t[r] = vw.R[3 * r] * S[0] + vw.R[3 * r + 1] * S[1] + vw.R[3 * r + 2] * S[2] + vw.t[r];
 }
 
-// scatter sum_run B[a] * v[c] into dst[(g * m + a) * 3 + c] (runs of equal g)
-template <int m>
-__device__ inline void scatter_cp(float *dst, int g, const float *B, const float *v, const Seg &sg, bool active) {
+// Per-primitive sums of NV values per lane over the warp's runs of lanes with
+// equal key (the primitive; -1 for lanes with nothing to add), one atomic per
+// (run, value): each lane writes its values to its row of the warp's shared
+// memory `sw` (32 rows of NV | 1 floats: the odd stride keeps the row writes
+// and the column reads free of bank conflicts), then lane j adds column j
+// over the rows of each run and adds the sum to dst(key, j).
+template <int NV, class Dst>
+__device__ __forceinline__ void scatter_runs(float *sw, const float *v, int key, Dst dst) {
+  constexpr int NS = NV | 1;
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int a = 0; a < m; a++)
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-      const float s = seg_sum(active ? B[a] * v[c] : 0.f, sg);
-      if (sg.tail && active && s != 0.f) atomicAdd(dst + ((size_t)g * m + a) * 3 + c, s);
+  for (int j = 0; j < NV; j++) sw[lane * NS + j] = v[j];
+  const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+  unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != key);
+  __syncwarp();
+  while (heads) {
+    const int start = __ffs(heads) - 1;
+    heads &= heads - 1;
+    const int end = heads ? __ffs(heads) - 1 : 32;
+    const int g = __shfl_sync(0xffffffffu, key, start);
+    if (g < 0) continue;
+    for (int j = lane; j < NV; j += 32) {
+      float sum = 0.f;
+      for (int r = start; r < end; r++) sum += sw[r * NS + j];
+      if (sum != 0.f) atomicAdd(dst(g, j), sum);
     }
+  }
+  __syncwarp();
 }
+
+constexpr int kChainWarps = 8;
 
 template <int N>
 __global__ void __launch_bounds__(256) k_chain_gauss(Params p, Scene s, Work w, Grads out) {
+  constexpr int m = SurfPoint<N>::M;
+  __shared__ float s_rows[kChainWarps][32 * ((3 * m + 1) | 1)];
+  float *sw = s_rows[threadIdx.x >> 5];
   const int F = w.counters[kF];
   const int lane = threadIdx.x & 31;
   const int warps_total = gridDim.x * (blockDim.x >> 5);
-  constexpr int m = SurfPoint<N>::M;
   for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < F; base += warps_total * 32) {
     const int i = base + lane;
     bool active = i < F;
@@ -171,11 +194,25 @@ __global__ void __launch_bounds__(256) k_chain_gauss(Params p, Scene s, Work w, 
     const bool nz = active && (gS[0] != 0.f || gS[1] != 0.f || gS[2] != 0.f || gcol[0] != 0.f ||
                                gcol[1] != 0.f || gcol[2] != 0.f || gop != 0.f);
     if (!__any_sync(0xffffffffu, nz)) continue;
-    const Seg sg = seg_info(nz ? g : -1 - lane);
-    scatter_cp<m>(out.ctrl, g, B, gS, sg, nz);
-    scatter_cp<m>(out.color, g, B, gcol, sg, nz);
-    const float so = seg_sum(nz ? gop : 0.f, sg);
-    if (sg.tail && nz && so != 0.f) atomicAdd(out.opacity + g, so);
+    {
+      // control points and opacity, then colour control points (Eq. 3, 4: dl/dp = sum B dl/dS)
+      float v[3 * m + 1];
+#pragma unroll
+      for (int a = 0; a < m; a++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) v[3 * a + c] = nz ? B[a] * gS[c] : 0.f;
+      v[3 * m] = nz ? gop : 0.f;
+      float *gctrl = out.ctrl, *gopa = out.opacity;
+      scatter_runs<3 * m + 1>(sw, v, nz ? g : -1, [&](int gg, int j) {
+        return j < 3 * m ? gctrl + (size_t)gg * 3 * m + j : gopa + gg;
+      });
+#pragma unroll
+      for (int a = 0; a < m; a++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) v[3 * a + c] = nz ? B[a] * gcol[c] : 0.f;
+      float *gcolor = out.color;
+      scatter_runs<3 * m>(sw, v, nz ? g : -1, [&](int gg, int j) { return gcolor + (size_t)gg * 3 * m + j; });
+    }
     if (out.log_scale || out.quat) {
       // the map texels of the interpolation, with their weights; runs of equal
       // (primitive, texel) are summed before one atomic each
@@ -211,6 +248,8 @@ __global__ void __launch_bounds__(256) k_chain_gauss(Params p, Scene s, Work w, 
 // the control points with the Bernstein weights (Eq. 3).
 template <int N>
 __global__ void __launch_bounds__(256) k_chain_sh(Params p, Scene s, Work w, Grads out) {
+  __shared__ float s_rows[kChainWarps][32 * ((3 * SurfPoint<N>::M) | 1)];
+  float *sw = s_rows[threadIdx.x >> 5];
   const int F = w.counters[kF];
   const int lane = threadIdx.x & 31;
   const int warps_total = gridDim.x * (blockDim.x >> 5);
@@ -252,8 +291,16 @@ __global__ void __launch_bounds__(256) k_chain_sh(Params p, Scene s, Work w, Gra
     }
     const bool nz = active && (gcol[0] != 0.f || gcol[1] != 0.f || gcol[2] != 0.f);
     if (!__any_sync(0xffffffffu, nz)) continue;
+    {
+      float v[3 * m];
+#pragma unroll
+      for (int a = 0; a < m; a++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) v[3 * a + c] = nz ? B[a] * gS[c] : 0.f;
+      float *gctrl = out.ctrl;
+      scatter_runs<3 * m>(sw, v, nz ? g : -1, [&](int gg, int j) { return gctrl + (size_t)gg * 3 * m + j; });
+    }
     const Seg sg = seg_info(nz ? g : -1 - lane);
-    scatter_cp<m>(out.ctrl, g, B, gS, sg, nz);
     if (out.sh) {
 #pragma unroll
       for (int k = 0; k < 15; k++) {
@@ -270,10 +317,12 @@ __global__ void __launch_bounds__(256) k_chain_sh(Params p, Scene s, Work w, Gra
 
 template <int N>
 __global__ void __launch_bounds__(256) k_chain_bnd(Params p, Scene s, Work w, Grads out) {
+  constexpr int m = SurfPoint<N>::M;
+  __shared__ float s_rows[kChainWarps][32 * ((3 * m + 1) | 1)];
+  float *sw = s_rows[threadIdx.x >> 5];
   const int Nb = w.counters[kNb];
   const int lane = threadIdx.x & 31;
   const int warps_total = gridDim.x * (blockDim.x >> 5);
-  constexpr int m = SurfPoint<N>::M;
   for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < Nb; base += warps_total * 32) {
     const int i = base + lane;
     bool nz = false;
@@ -300,10 +349,16 @@ __global__ void __launch_bounds__(256) k_chain_bnd(Params p, Scene s, Work w, Gr
       }
     }
     if (!__any_sync(0xffffffffu, nz)) continue;
-    const Seg sg = seg_info(nz ? g : -1 - lane);
-    scatter_cp<m>(out.ctrl, g, B, gS, sg, nz);
-    const float sr = seg_sum(nz ? grb : 0.f, sg);
-    if (sg.tail && nz && sr != 0.f) atomicAdd(out.r_b + g, sr);
+    float v[3 * m + 1];
+#pragma unroll
+    for (int a = 0; a < m; a++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) v[3 * a + c] = nz ? B[a] * gS[c] : 0.f;
+    v[3 * m] = nz ? grb : 0.f;
+    float *gctrl = out.ctrl, *grbp = out.r_b;
+    scatter_runs<3 * m + 1>(sw, v, nz ? g : -1, [&](int gg, int j) {
+      return j < 3 * m ? gctrl + (size_t)gg * 3 * m + j : grbp + gg;
+    });
   }
 }
 

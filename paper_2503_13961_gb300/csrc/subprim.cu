@@ -11,10 +11,14 @@
 // with radius sigma = k_b fx r_b / z.
 //
 // Gaussians and boundary points are compacted in global pixel order: a count
-// pass per warp chunk of 128 pixels, exclusive scans of the chunk counts, and
-// the generation pass in which every warp compacts its chunk with ballots
-// (no block barrier), so indices do not depend on scheduling. Each record
-// counts its screen tiles into per-tile counters for the binning pass.
+// pass per warp chunk of 128 pixels, exclusive scans of the chunk counts, a
+// compaction pass in which every warp writes its chunk's foreground pixels
+// (pixel, view, boundary index) at their ranks with ballots, and the
+// generation pass with one thread per Gaussian; indices do not depend on
+// scheduling. Each record counts its screen tiles into per-tile counters for
+// the binning pass.
+#include <algorithm>
+
 #include "bgt_internal.cuh"
 
 namespace bgt {
@@ -87,18 +91,15 @@ __device__ inline uint2 tile_rect(float cx, float cy, float rx, float ry, const 
   return make_uint2((unsigned)x0 | ((unsigned)y0 << 16), (unsigned)x1 | ((unsigned)y1 << 16));
 }
 
-template <int N>
-__global__ void __launch_bounds__(kGenThreads) k_generate(Params p, Scene s, Work w) {
-  // each warp's foreground pixels in pixel order: pixel, view, boundary index (-1)
-  __shared__ int s_pix[kGenWarps][kChunk], s_view[kGenWarps][kChunk], s_bi[kGenWarps][kChunk];
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  const int chunk = blockIdx.x * kGenWarps + wp;
+// compaction: each warp writes its chunk's foreground pixels at their ranks in
+// pixel order (the Gaussian and boundary indices)
+__global__ void __launch_bounds__(kGenThreads) k_compact(Params p, Work w) {
+  const int lane = threadIdx.x & 31;
+  const int chunk = blockIdx.x * kGenWarps + (threadIdx.x >> 5);
   if (chunk >= w.nblk) return;
-  const int base_f0 = (int)w.blk_off[chunk];
-  const int base_b0 = (int)w.blk_off[w.nblk + 1 + chunk];
+  int nf = (int)w.blk_off[chunk];
+  int nb = (int)w.blk_off[w.nblk + 1 + chunk];
   const unsigned lt = (1u << lane) - 1u;
-  int nf = 0, nb = 0;
-  // compaction: ranks in pixel order give the Gaussian and boundary indices
 #pragma unroll
   for (int r = 0; r < kGenRounds; r++) {
     const int pix = chunk * kChunk + r * 32 + lane;
@@ -106,22 +107,25 @@ __global__ void __launch_bounds__(kGenThreads) k_generate(Params p, Scene s, Wor
     int view;
     pixel_flags(p, w, pix, fg, bnd, view);
     const unsigned mf = __ballot_sync(0xffffffffu, fg), mb = __ballot_sync(0xffffffffu, bnd);
-    const int lf = nf + __popc(mf & lt);
-    if (pix < p.P) w.pix_gidx[pix] = fg ? base_f0 + lf : -1;
+    const int gi = nf + __popc(mf & lt);
+    if (pix < p.P) w.pix_gidx[pix] = fg ? gi : -1;
     if (fg) {
-      s_pix[wp][lf] = pix;
-      s_view[wp][lf] = view;
-      s_bi[wp][lf] = bnd ? base_b0 + nb + __popc(mb & lt) : -1;
+      w.g_pix[gi] = pix;
+      w.g_view[gi] = view;
+      w.g_bidx[gi] = bnd ? nb + __popc(mb & lt) : -1;
     }
     nf += __popc(mf);
     nb += __popc(mb);
   }
-  __syncwarp();
-  // sub-primitives of the chunk's foreground pixels
-  for (int j = lane; j < nf; j += 32) {
-    const int pix = s_pix[wp][j], view = s_view[wp][j], bi = s_bi[wp][j];
+}
+
+// one thread per Gaussian (sub-primitive) and boundary point
+template <int N>
+__global__ void __launch_bounds__(kGenThreads) k_generate(Params p, Scene s, Work w) {
+  const int F = w.counters[kF];
+  for (int gi = blockIdx.x * blockDim.x + threadIdx.x; gi < F; gi += gridDim.x * blockDim.x) {
+    const int pix = w.g_pix[gi], view = w.g_view[gi], bi = w.g_bidx[gi];
     const bool bnd = bi >= 0;
-    const int gi = base_f0 + j;
     const View vw = w.views[view];
     const int prim = w.pid[pix];
     const float2 uv = w.puv[pix];
@@ -205,8 +209,6 @@ __global__ void __launch_bounds__(kGenThreads) k_generate(Params p, Scene s, Wor
     w.gB[gi] = make_float4(Ka, Kb, Kc, o);
     w.gC[gi] = make_float4(col[0], col[1], col[2], __int_as_float(prim));
     w.g_depth[gi] = tz;
-    w.g_pix[gi] = pix;
-    w.g_view[gi] = view;
     w.g_uv[gi] = uv;
     w.g_rect[gi] = rect;
     w.g_dsub[gi] = dsub;
@@ -288,8 +290,14 @@ int launch_generate(const Params &p, const Scene &s, const Work &w, cudaStream_t
   k += launch_exclusive_scan(wc.blk_cnt, wc.blk_off, nchunk, wc.scan_aux, st);
   k += launch_exclusive_scan(wc.blk_cnt + nchunk, wc.blk_off + nchunk + 1, nchunk, wc.scan_aux2, st);
   k_totals<<<1, 1, 0, st>>>(wc);
-  dispatch_degree(p.n, [&](auto d) { k_generate<decltype(d)::value><<<blocks, kGenThreads, 0, st>>>(p, s, wc); });
-  k += 2;
+  k_compact<<<blocks, kGenThreads, 0, st>>>(p, wc);
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // one thread per Gaussian over a persistent grid (F is known on the device only)
+  const int gblocks = std::min((p.P + kGenThreads - 1) / kGenThreads, (sms > 0 ? sms : 152) * 8);
+  dispatch_degree(p.n, [&](auto d) { k_generate<decltype(d)::value><<<gblocks, kGenThreads, 0, st>>>(p, s, wc); });
+  k += 3;
   if (p.sh_deg > 0) {
     dispatch_degree(p.n, [&](auto d) { k_sh_color<decltype(d)::value><<<152 * 8, 256, 0, st>>>(p, s, w); });
     k++;

@@ -84,6 +84,23 @@ def test_bin_sort_large_tiles(oracle, scenes, n, low, high):
     assert any(low < x <= high for x in lengths), lengths
 
 
+def test_bin_sort_register_bitonic_tiles(oracle, scenes):
+    # tiles of 33..64, 65..128 and 129..256 keys (one warp, 2, 4 or 8 keys per
+    # lane in registers) and 257..512 keys (one warp, radix in shared memory)
+    W, H = 64, 64
+    seen = []
+    for seed, n in ((21, 150), (22, 400), (23, 900), (24, 1800)):
+        g = scenes.random_gaussians(seed, W, H, n, radius_px=(1.0, 4.0))
+        rd = _renderer(W, H, n, 16)
+        res = rd.bin_sort(g, W, H)
+        rd.sync_status()
+        ptr, idx = oracle.pixel_lists(g, W, H)
+        seen += _check_lists(g, W, H, 16, res["ranges"], res["keys"], ptr, idx, oracle.DEFAULTS["alpha_min"])
+        rd.close()
+    for lo, hi in ((32, 64), (64, 128), (128, 256), (256, 512)):
+        assert any(lo < m <= hi for m in seen), (lo, hi, seen)
+
+
 def test_bin_sort_mid_size_tiles(oracle, scenes):
     # tiles of 513..1024 keys (one warp, shared memory) and 1025..4096 keys
     # (one block, shared memory) in the same call
