@@ -252,7 +252,7 @@ __device__ void radix_global(unsigned long long *keys, unsigned long long *tmp, 
 }
 
 constexpr int kWarpSortCap = 1024;  // keys a single warp sorts in its own shared memory
-constexpr int kRadixMin = 257;     // segments from this length sort by radix in shared memory
+constexpr int kRadixMin = 129;     // segments from this length sort by radix, shorter ones by bitonic network
 // per warp: the keys (kWarpSortCap) and 256 radix bins
 constexpr int kTileSortSmem = (kSortThreads / 32) * (kWarpSortCap * (int)sizeof(unsigned long long) + 256 * 4);
 
@@ -367,56 +367,10 @@ __device__ __forceinline__ void warp_radix_smem(unsigned long long *sk, unsigned
   }
 }
 
-// Bitonic sort of keys[0, n) (n <= 32 R) by one warp in registers: element
-// i = lane R + r sits in register r of its lane, so the exchanges of distance
-// j < R stay inside a lane and the longer ones take one 64-bit shuffle per
-// register; missing elements are padded with the largest key.
-template <int R>
-__device__ __forceinline__ void warp_bitonic_regs(unsigned long long *keys, int n, int lane) {
-  constexpr int N = 32 * R;
-  unsigned long long x[R];
-#pragma unroll
-  for (int r = 0; r < R; r++) {
-    const int i = lane * R + r;
-    x[r] = i < n ? keys[i] : ~0ull;
-  }
-#pragma unroll
-  for (int k = 2; k <= N; k <<= 1) {
-#pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      if (j < R) {
-#pragma unroll
-        for (int r = 0; r < R; r++) {
-          if (r & j) continue;
-          const int rp = r | j;
-          const bool asc = ((lane * R + r) & k) == 0;
-          const unsigned long long a = x[r], b = x[rp];
-          const bool swap = (a > b) == asc;
-          x[r] = swap ? b : a;
-          x[rp] = swap ? a : b;
-        }
-      } else {
-#pragma unroll
-        for (int r = 0; r < R; r++) {
-          const int i = lane * R + r;
-          const unsigned long long other = __shfl_xor_sync(0xffffffffu, x[r], j / R);
-          const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
-          x[r] = keep_min ? (x[r] < other ? x[r] : other) : (x[r] < other ? other : x[r]);
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < R; r++) {
-    const int i = lane * R + r;
-    if (i < n) keys[i] = x[r];
-  }
-}
-
 // Warps take segments from a queue. Up to 32 keys: bitonic sort across the
-// lanes' registers; up to 256: bitonic sort with 2, 4 or 8 keys per lane in
-// registers; up to kWarpSortCap: radix sort in the warp's shared memory;
-// longer segments are appended to a list for k_tile_sort_big.
+// lanes' registers; up to kWarpSortCap: bitonic sort (up to 128 keys) or
+// radix sort in the warp's shared memory; longer segments are appended to a
+// list for k_tile_sort_big.
 __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Params p, Work w, int *big_list) {
   extern __shared__ __align__(16) unsigned long long s_sort[];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
@@ -449,12 +403,6 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Params p, Work w, in
           key = (lower == up) ? (key < other ? key : other) : (key < other ? other : key);
         }
       if (lane < n) keys[lane] = key;
-    } else if (n <= 64) {
-      warp_bitonic_regs<2>(keys, n, lane);
-    } else if (n <= 128) {
-      warp_bitonic_regs<4>(keys, n, lane);
-    } else if (n <= 256) {
-      warp_bitonic_regs<8>(keys, n, lane);
     } else if (n > 32) {
       int N = 64;
       while (N < n) N <<= 1;

@@ -44,11 +44,11 @@ struct TileCfg {
   static constexpr int WPR = T / WX;         // warp blocks per tile row
   // primitive cache per warp (fully associative, FIFO): slot keys one per lane
   static constexpr int SLOTS_FWD = (PPT == 1) ? 16 : 8;
-  static constexpr int SLOTS_BWD = (PPT == 1) ? 12 : 4;
+  static constexpr int SLOTS_BWD = (PPT == 1) ? 6 : 4;
   // resident blocks per SM the kernels are compiled for (their shared memory
   // allows this many; the register budget follows)
   static constexpr int MINB_FWD = (T == 8) ? 6 : (T == 16) ? 4 : 2;
-  static constexpr int MINB_BWD = (T == 8) ? 6 : (T == 16) ? 4 : 2;
+  static constexpr int MINB_BWD = (T == 8) ? 6 : (T == 16) ? 3 : 2;
 };
 
 template <int T>
@@ -292,6 +292,12 @@ struct BwdShared {
   float s_cw[Cfg::NW][S][Cfg::PPT][32];  // w of the slot's primitive per pixel
   int s_cb[Cfg::NW][S][Cfg::PPT][32];    // the slot's boundary candidate per pixel (-1: none)
   float s_cacc[Cfg::NW][S][Cfg::PPT][32];  // sum of dl/dw over the slot's Gaussians per pixel
+  // one pixel per lane: per-pair values of the last 16 records (row = record,
+  // column = pixel, stride 33) and dl/dC of the warp block's pixels
+  static constexpr int TR = (Cfg::PPT == 1) ? 16 : 1;
+  float s_sg[Cfg::NW][TR][33];  // s = dl/dalpha w G of the pair (0 if not composited or clamped)
+  float s_ta[Cfg::NW][TR][33];  // T alpha of the pair
+  float4 s_dc[Cfg::NW][(Cfg::PPT == 1) ? 32 : 1];
 };
 
 // Warp-wide lookup of primitive g in the warp's cache: lane s < SLOTS holds
@@ -562,23 +568,27 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float *v) {
 // 2 acc3, acc4)). dl/dalpha_i = dl/dC . T_i (c_i - R_i) (the supplementary's
 // T_i c_i - S_i / (1 - alpha_i), without the 1 / (1 - alpha_i) amplification
 // of rounding). Returns dl/dw (0 when alpha is clamped at alpha_max).
-__device__ __forceinline__ float pair_backward(float dx, float dy, float G, float og, float wv, float raw, float alpha,
-                                               float alpha_max, const float4 &Cc, const float *dC, float &Tr, float *R,
-                                               float *acc) {
+__device__ __forceinline__ float pair_values(float G, float og, float wv, float raw, float alpha, float alpha_max,
+                                             const float4 &Cc, const float *dC, float &Tr, float *R, float &sg,
+                                             float &ta) {
   Tr = __fdividef(Tr, 1.0f - alpha);  // T_i
-  const float ta = Tr * alpha;
+  ta = Tr * alpha;
   const float col[3] = {Cc.x, Cc.y, Cc.z};
   float dl_da = 0.f;
 #pragma unroll
   for (int c = 0; c < 3; c++) {
-    acc[6 + c] = fmaf(ta, dC[c], acc[6 + c]);
     const float d = col[c] - R[c];
     dl_da = fmaf(dC[c], d, dl_da);
     R[c] = fmaf(alpha, d, R[c]);
   }
   dl_da *= Tr;
+  sg = 0.f;
   if (raw >= alpha_max) return 0.f;  // clamped: alpha is constant
-  const float sg = dl_da * wv * G;
+  sg = dl_da * wv * G;
+  return dl_da * og;
+}
+
+__device__ __forceinline__ void add_pair_sums(float sg, float ta, float dx, float dy, const float *dC, float *acc) {
   const float a = sg * dx, b = sg * dy;
   acc[0] += a;
   acc[1] += b;
@@ -586,7 +596,17 @@ __device__ __forceinline__ float pair_backward(float dx, float dy, float G, floa
   acc[3] = fmaf(a, dy, acc[3]);
   acc[4] = fmaf(b, dy, acc[4]);
   acc[5] += sg;
-  return dl_da * og;
+#pragma unroll
+  for (int c = 0; c < 3; c++) acc[6 + c] = fmaf(ta, dC[c], acc[6 + c]);
+}
+
+__device__ __forceinline__ float pair_backward(float dx, float dy, float G, float og, float wv, float raw, float alpha,
+                                               float alpha_max, const float4 &Cc, const float *dC, float &Tr, float *R,
+                                               float *acc) {
+  float sg, ta;
+  const float dl_dw = pair_values(G, og, wv, raw, alpha, alpha_max, Cc, dC, Tr, R, sg, ta);
+  add_pair_sums(sg, ta, dx, dy, dC, acc);
+  return dl_dw;
 }
 
 // Boundary-point gradient of pixel (pxf, pyf) and boundary candidate bi of
@@ -709,6 +729,10 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
       unsigned n_comp = 0, n_rec = 0;
       int ckey = -2, cnext = 0;
       int chunk = br.x, n = br.y;
+      // one pixel per lane: the block origin and dl/dC of every pixel, for the
+      // per-Gaussian sums taken record by record over the block's pixels
+      const float wx0 = (float)(x0 + (wb % Cfg::WPR) * Cfg::WX), wy0 = (float)(y0 + (wb / Cfg::WPR) * Cfg::WY);
+      if constexpr (PPT == 1) sh.s_dc[warp][lane] = make_float4(dC[0][0], dC[0][1], dC[0][2], 0.f);
       while (chunk >= 0) {
         const int prev = w.rec_prev[chunk];
         // stage the chunk's records: headers and their Gaussians
@@ -749,31 +773,80 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
               if (lane == slot) ckey = g;
             }
           }
-          float acc[9];
+          if constexpr (PPT == 1) {
+            // the pair's values go to row r % 16 of the warp's transposition rows;
+            // every 16 records, lane i (and i + 16, for the other half of the
+            // pixels) sums record i's values over the block's pixels: the
+            // per-Gaussian sums without a warp reduction per record
+            float sg = 0.f, ta = 0.f, dl_dw = 0.f;
+            if (mine) {
+              n_comp++;
+              const float dx = __fsub_rn(__fsub_rn(pxf[0], P.x), P.z), dy = __fsub_rn(__fsub_rn(pyf[0], P.y), P.w);
+              const float G = gauss(dx, dy, Q);
+              const float og = __fmul_rn(Q.w, G);
+              const float wv = p.use_boundary ? s_cw[slot][0][lane] : 1.0f;
+              const float raw = __fmul_rn(og, wv);
+              const float alpha = fminf(p.alpha_max, raw);
+              dl_dw = pair_values(G, og, wv, raw, alpha, p.alpha_max, Cc, dC[0], Tr[0], R[0], sg, ta);
+              if (p.use_boundary) s_cacc[slot][0][lane] += dl_dw;
+            }
+            sh.s_sg[warp][r & 15][lane] = sg;
+            sh.s_ta[warp][r & 15][lane] = ta;
+            if ((r & 15) == 0) {
+              __syncwarp();
+              const int i = lane & 15, half = lane >> 4, rec = r + i;
+              float acc[9];
 #pragma unroll
-          for (int q = 0; q < 9; q++) acc[q] = 0.f;
-          float dl_dw = 0.f;
+              for (int q = 0; q < 9; q++) acc[q] = 0.f;
+              if (rec < n) {
+                const float4 Pm = sP[rec];
+                const float bxm = __fsub_rn(__fsub_rn(wx0, Pm.x), Pm.z), bym = __fsub_rn(__fsub_rn(wy0, Pm.y), Pm.w);
 #pragma unroll
-          for (int k = 0; k < PPT; k++) {
-            if (k != rk || !mine) continue;
-            n_comp++;
-            const float dx = __fsub_rn(__fsub_rn(pxf[k], P.x), P.z), dy = __fsub_rn(__fsub_rn(pyf[k], P.y), P.w);
-            const float G = gauss(dx, dy, Q);
-            const float og = __fmul_rn(Q.w, G);
-            const float wv = p.use_boundary ? s_cw[slot][k][lane] : 1.0f;
-            const float raw = __fmul_rn(og, wv);
-            const float alpha = fminf(p.alpha_max, raw);
-            dl_dw = pair_backward(dx, dy, G, og, wv, raw, alpha, p.alpha_max, Cc, dC[k], Tr[k], R[k], acc);
+                for (int j = 0; j < 16; j++) {
+                  const int l = half * 16 + j;
+                  const float4 dc = sh.s_dc[warp][l];
+                  const float dcv[3] = {dc.x, dc.y, dc.z};
+                  add_pair_sums(sh.s_sg[warp][i][l], sh.s_ta[warp][i][l], bxm + (float)(l & 7), bym + (float)(l >> 3),
+                                dcv, acc);
+                }
+              }
+#pragma unroll
+              for (int q = 0; q < 9; q++) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 16);
+              if (rec < n && half == 0) {
+                float *gg = w.gg + 12 * (size_t)sH[rec].x;
+#pragma unroll
+                for (int q = 0; q < 9; q++)
+                  if (acc[q] != 0.f) atomicAdd(gg + q, acc[q]);
+              }
+              __syncwarp();
+            }
+          } else {
+            float acc[9];
+#pragma unroll
+            for (int q = 0; q < 9; q++) acc[q] = 0.f;
+            float dl_dw = 0.f;
+#pragma unroll
+            for (int k = 0; k < PPT; k++) {
+              if (k != rk || !mine) continue;
+              n_comp++;
+              const float dx = __fsub_rn(__fsub_rn(pxf[k], P.x), P.z), dy = __fsub_rn(__fsub_rn(pyf[k], P.y), P.w);
+              const float G = gauss(dx, dy, Q);
+              const float og = __fmul_rn(Q.w, G);
+              const float wv = p.use_boundary ? s_cw[slot][k][lane] : 1.0f;
+              const float raw = __fmul_rn(og, wv);
+              const float alpha = fminf(p.alpha_max, raw);
+              dl_dw = pair_backward(dx, dy, G, og, wv, raw, alpha, p.alpha_max, Cc, dC[k], Tr[k], R[k], acc);
+            }
+            if (p.use_boundary && mine) s_cacc[slot][rk][lane] += dl_dw;
+            // per-Gaussian sums (see pair_backward); slots 0-7 by reduce-scatter
+            // (lanes 4m hold slot m), slot 8 by a butterfly
+            const float part = warp_reduce_scatter8(acc);
+            const float s8 = warp_sum(acc[8]);
+            float *gg = w.gg + 12 * (size_t)h.x;
+            const int gslot = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+            if ((lane & 3) == 0 && part != 0.f) atomicAdd(gg + gslot, part);
+            if (lane == 1 && s8 != 0.f) atomicAdd(gg + 8, s8);
           }
-          if (p.use_boundary && mine) s_cacc[slot][rk][lane] += dl_dw;
-          // per-Gaussian sums (see pair_backward); slots 0-7 by reduce-scatter
-          // (lanes 4m hold slot m), slot 8 by a butterfly
-          const float part = warp_reduce_scatter8(acc);
-          const float s8 = warp_sum(acc[8]);
-          float *gg = w.gg + 12 * (size_t)h.x;
-          const int gslot = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-          if ((lane & 3) == 0 && part != 0.f) atomicAdd(gg + gslot, part);
-          if (lane == 1 && s8 != 0.f) atomicAdd(gg + 8, s8);
         }
         __syncwarp();
         chunk = prev;

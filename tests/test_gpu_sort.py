@@ -84,9 +84,9 @@ def test_bin_sort_large_tiles(oracle, scenes, n, low, high):
     assert any(low < x <= high for x in lengths), lengths
 
 
-def test_bin_sort_register_bitonic_tiles(oracle, scenes):
-    # tiles of 33..64, 65..128 and 129..256 keys (one warp, 2, 4 or 8 keys per
-    # lane in registers) and 257..512 keys (one warp, radix in shared memory)
+def test_bin_sort_warp_sized_tiles(oracle, scenes):
+    # tiles of 33..64, 65..128 keys (one warp, bitonic network in shared
+    # memory) and 129..256, 257..512 keys (one warp, radix in shared memory)
     W, H = 64, 64
     seen = []
     for seed, n in ((21, 150), (22, 400), (23, 900), (24, 1800)):
