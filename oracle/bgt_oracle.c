@@ -227,7 +227,10 @@ static int subtri_exists(int L, int s) {
 }
 
 /* Rasterize every flat triangle of every primitive with a z-buffer of
- * 64-bit keys (float bits of the interpolated depth << 32 | sub-triangle id).
+ * 64-bit keys (complement of the float bits of the interpolated 1/z << 32 |
+ * sub-triangle id): 1/z is affine in screen space, so at a covered pixel it is
+ * sum(e_i / z_i) / area2 with the exact edge functions e_i; the nearest surface
+ * has the largest 1/z and, complemented, the smallest key.
  * out_key receives the winning key per pixel (~0 for background); out_id the
  * primitive (-1 background); out_uv the perspective-correct (u, v) in FP64
  * from the exact edge functions of the winning triangle. If `ztest` is 0,
@@ -285,12 +288,11 @@ int bgto_raster(int n, int M, const float *ctrl, int L, const float *cam, int W,
           if (out_cover) out_cover[p]++;
           if (!ztest) continue;
           float af = (float)area2;
-          float l0 = (float)e0 / af, l1 = (float)e1 / af, l2 = (float)e2 / af;
-          float sd = l0 * v0.iz;
-          sd = fmaf(l1, v1.iz, sd);
-          sd = fmaf(l2, v2.iz, sd);
-          float z = 1.0f / sd;
-          uint64_t key = ((uint64_t)fbits(z) << 32) | gid;
+          float sd = (float)e0 * v0.iz;
+          sd = fmaf((float)e1, v1.iz, sd);
+          sd = fmaf((float)e2, v2.iz, sd);
+          float inv_z = sd / af;
+          uint64_t key = ((uint64_t)(~fbits(inv_z)) << 32) | gid;
           if (key < zb[p]) zb[p] = key;
         }
     }

@@ -383,7 +383,9 @@ struct RecWriter {
   }
 };
 
-template <int T>
+// STATS: count the work units of bench.py's roofline (a separate instantiation,
+// launched only when profiling, so the production kernel carries no counters)
+template <int T, bool STATS>
 __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_composite_fwd(Params p, Work w, float *image) {
   using Cfg = TileCfg<T>;
   constexpr int NT = Cfg::NT, PPT = Cfg::PPT, S = Cfg::SLOTS_FWD;
@@ -460,7 +462,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_compos
           anyc = anyc || cand[k];
         }
         if (!__any_sync(0xffffffffu, anyc)) continue;
-        n_visit++;
+        if constexpr (STATS) n_visit++;
         const float4 Cc = sC[l];
         const int g = __float_as_int(Cc.w);
         int slot = cache_find(ckey, g);
@@ -470,7 +472,9 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_compos
           int lo = 0, hi = 0, f = -1;
           if (p.use_boundary) {
             warp_equal_range(bl.prim, bl.n, g, lo, hi);
-            f = rw.new_fill(w, PPT);
+            // a primitive without boundary points in the tile has w = 1 inside and
+            // 0 outside: no fill record (the backward reads -1 the same way)
+            if (hi > lo) f = rw.new_fill(w, PPT);
           }
 #pragma unroll
           for (int k = 0; k < PPT; k++) {
@@ -502,8 +506,10 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_compos
           C[k][2] = __fmaf_rn(ta, Cc.z, C[k][2]);
           Tr[k] = comp[k] ? testT : Tr[k];
           last[k] = comp[k] ? c0 + l + 1 : last[k];
-          n_sup += cand[k];
-          n_comp += comp[k];
+          if constexpr (STATS) {
+            n_sup += cand[k];
+            n_comp += comp[k];
+          }
         }
         // record the pixels composited for the backward pass
 #pragma unroll
@@ -525,7 +531,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_compos
         w.n_contrib[pix[k]] = last[k];
       }
     }
-    if (p.stats) flush_stats(w.stats, kFwdSupport, n_sup, n_comp, n_cand, n_visit);
+    if constexpr (STATS) flush_stats(w.stats, kFwdSupport, n_sup, n_comp, n_cand, n_visit);
     __syncthreads();  // the staged boundary list is free again
   }
 }
@@ -671,7 +677,7 @@ __device__ __forceinline__ float w_from_candidate(const float4 *brec, int bi, fl
 // R <- alpha_i c_i + (1 - alpha_i) R. Per record, the per-Gaussian gradient is
 // reduced over the warp; boundary-point gradients are summed per (pixel,
 // primitive) in a cache slot and flushed on eviction and at the block's end.
-template <int T>
+template <int T, bool STATS>
 __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_composite_bwd(Params p, Work w, const float *dimage) {
   using Cfg = TileCfg<T>;
   constexpr int PPT = Cfg::PPT, S = Cfg::SLOTS_BWD, NW = Cfg::NW;
@@ -752,7 +758,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
           const int rk = (int)h.w;
           const float4 P = sP[r], Q = sQ[r], Cc = sC[r];
           const int g = __float_as_int(Cc.w);
-          n_rec++;
+          if constexpr (STATS) n_rec++;
           // w of (pixel, g): from the cache slot, filled from g's fill record
           int slot = 0;
           if (p.use_boundary) {
@@ -780,7 +786,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
             // per-Gaussian sums without a warp reduction per record
             float sg = 0.f, ta = 0.f, dl_dw = 0.f;
             if (mine) {
-              n_comp++;
+              if constexpr (STATS) n_comp++;
               const float dx = __fsub_rn(__fsub_rn(pxf[0], P.x), P.z), dy = __fsub_rn(__fsub_rn(pyf[0], P.y), P.w);
               const float G = gauss(dx, dy, Q);
               const float og = __fmul_rn(Q.w, G);
@@ -828,7 +834,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
 #pragma unroll
             for (int k = 0; k < PPT; k++) {
               if (k != rk || !mine) continue;
-              n_comp++;
+              if constexpr (STATS) n_comp++;
               const float dx = __fsub_rn(__fsub_rn(pxf[k], P.x), P.z), dy = __fsub_rn(__fsub_rn(pyf[k], P.y), P.w);
               const float G = gauss(dx, dy, Q);
               const float og = __fmul_rn(Q.w, G);
@@ -859,7 +865,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
             flush_boundary<PPT>(brec, bkeys, w.bg_grad, &s_cb[sl][0][0], &s_cacc[sl][0][0], old, idq, pxf, pyf);
         }
       }
-      if (p.stats) flush_stats(w.stats, kBwdSupport, n_comp, n_comp, 0u, n_rec);
+      if constexpr (STATS) flush_stats(w.stats, kBwdSupport, n_comp, n_comp, 0u, n_rec);
     }
     base = __shfl_sync(0xffffffffu, next, 0);
   }
@@ -978,8 +984,10 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd_walk(Params p,
 template <int T>
 int launch_fwd_t(const Params &p, const Work &w, float *image, cudaStream_t st, int sms) {
   int grid = p.tiles < sms * 8 ? p.tiles : sms * 8;
-  if (grid > 0)
-    k_composite_fwd<T><<<grid, TileCfg<T>::NT, sizeof(FwdShared<T>), st>>>(p, w, image);
+  if (grid > 0) {
+    if (p.stats) k_composite_fwd<T, true><<<grid, TileCfg<T>::NT, sizeof(FwdShared<T>), st>>>(p, w, image);
+    else k_composite_fwd<T, false><<<grid, TileCfg<T>::NT, sizeof(FwdShared<T>), st>>>(p, w, image);
+  }
   return grid > 0 ? 1 : 0;
 }
 
@@ -987,7 +995,8 @@ template <int T>
 int launch_bwd_t(const Params &p, const Work &w, const float *dimage, cudaStream_t st, int sms) {
   int grid = p.tiles < sms * 8 ? p.tiles : sms * 8;
   if (grid > 0) {
-    k_composite_bwd<T><<<grid, TileCfg<T>::NT, sizeof(BwdShared<T>), st>>>(p, w, dimage);
+    if (p.stats) k_composite_bwd<T, true><<<grid, TileCfg<T>::NT, sizeof(BwdShared<T>), st>>>(p, w, dimage);
+    else k_composite_bwd<T, false><<<grid, TileCfg<T>::NT, sizeof(BwdShared<T>), st>>>(p, w, dimage);
     // warp blocks whose records overflowed (none in the common case: the
     // kernel reads the count and returns)
     k_composite_bwd_walk<T><<<sms * 2, TileCfg<T>::NT, 0, st>>>(p, w, dimage);
@@ -995,14 +1004,20 @@ int launch_bwd_t(const Params &p, const Work &w, const float *dimage, cudaStream
   return grid > 0 ? 2 : 0;
 }
 
-template <int T>
-cudaError_t configure_t() {
-  cudaError_t e = cudaFuncSetAttribute(k_composite_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <int T, bool STATS>
+cudaError_t configure_ts() {
+  cudaError_t e = cudaFuncSetAttribute(k_composite_fwd<T, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sizeof(FwdShared<T>));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_composite_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_composite_bwd<T, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(BwdShared<T>));
   return e;
+}
+
+template <int T>
+cudaError_t configure_t() {
+  cudaError_t e = configure_ts<T, false>();
+  return e == cudaSuccess ? configure_ts<T, true>() : e;
 }
 
 int num_sms() {

@@ -3,8 +3,10 @@
 // of a uniform barycentric lattice whose vertices are exact evaluations of
 // Eq. 1; each flat triangle is rasterized against pixel centres with exact
 // 64-bit edge functions on a 1/256-pixel grid, and the nearest one per pixel
-// is kept by a 64-bit atomicMin on (depth bits << 32 | sub-triangle id). The
-// resolve pass turns the winning key into I_id and perspective-correct I_uv.
+// is kept by a 64-bit atomicMin on (~bits(1/z) << 32 | sub-triangle id), 1/z
+// the perspective-correct interpolation sum(e_i / z_i) / area2 (the nearest
+// surface has the largest 1/z). The resolve pass turns the winning key into
+// I_id and perspective-correct I_uv.
 //
 // Grid: one block row per view (blockIdx.y), warps take primitives of that
 // view. Per block, the Bernstein weights of the (L+1)(L+2)/2 lattice vertices
@@ -15,9 +17,7 @@
 // before any edge function, and the pixel centres of the box are walked with
 // incrementally updated edge functions, in 32-bit integers when the box is
 // under 125 px (exact: every product stays below 2^30) and in 64-bit ones
-// otherwise. Covered pixels are queued per warp in shared memory and their
-// depth tests (four IEEE divisions and a 64-bit atomicMin) run afterwards on
-// all lanes, instead of on the few lanes of a divergent walk that cover. Every operation that decides coverage or the depth order is an
+// otherwise. Every operation that decides coverage or the depth order is an
 // explicit IEEE-rounded intrinsic, so the result is reproducible bit for bit.
 #include <climits>
 
@@ -46,29 +46,16 @@ __device__ inline void slot_to_ab(int vi, int L, int &a, int &b) {
 __device__ __forceinline__ float to_f32(int x) { return __int2float_rn(x); }
 __device__ __forceinline__ float to_f32(long long x) { return __ll2float_rn(x); }
 
-// A covered pixel of a flat triangle, queued for the depth test: the edge
-// functions as rounded floats, the doubled area, the reciprocal depths of the
-// vertices, the pixel (view-local index) and the sub-triangle id.
-struct Covered {
-  float4 a;  // (e0, e1, e2, area2) as floats
-  float4 b;  // (1/z0, 1/z1, 1/z2, bits(pixel))
-  unsigned gid;
-};
-
-constexpr int kQCap = 96;  // covered pixels queued per warp before the test runs inline
-
-// depth test of one covered pixel: the interpolated depth 1 / sum(l_i / z_i)
-// with l_i = e_i / area2, every operation IEEE-rounded
+// depth test of one covered pixel: the interpolated 1/z = sum(e_i / z_i) /
+// area2, every operation IEEE-rounded; the key complements its bits so that
+// the nearest surface has the smallest key
 __device__ __forceinline__ void depth_test(float f0, float f1, float f2, float af, const float *IZ, int pix,
                                            unsigned gid, unsigned long long *zb) {
-  const float l0 = __fdiv_rn(f0, af);
-  const float l1 = __fdiv_rn(f1, af);
-  const float l2 = __fdiv_rn(f2, af);
-  float sd = __fmul_rn(l0, IZ[0]);
-  sd = __fmaf_rn(l1, IZ[1], sd);
-  sd = __fmaf_rn(l2, IZ[2], sd);
-  const float z = __fdiv_rn(1.0f, sd);
-  atomicMin(zb + pix, ((unsigned long long)__float_as_uint(z) << 32) | (unsigned long long)gid);
+  float sd = __fmul_rn(f0, IZ[0]);
+  sd = __fmaf_rn(f1, IZ[1], sd);
+  sd = __fmaf_rn(f2, IZ[2], sd);
+  const float inv_z = __fdiv_rn(sd, af);
+  atomicMin(zb + pix, ((unsigned long long)(~__float_as_uint(inv_z)) << 32) | (unsigned long long)gid);
 }
 
 // Pixel centres of the box [px0, px1] x [py0, py1] inside the flat triangle
@@ -76,12 +63,11 @@ __device__ __forceinline__ void depth_test(float f0, float f1, float f2, float a
 // t0..t2 of the edges 1-2, 2-0, 0-1): edge functions (b - a) x (P - a) start
 // at the box corner and step by their constant differences; I is int when
 // every value stays below 2^31 (box span < kSpan32), else long long. Covered
-// pixels go to the warp's queue (q, count qn), so that the depth tests later
-// run on all lanes; when the queue is full the test runs here.
+// pixels take the depth test.
 template <typename I>
 __device__ __forceinline__ void raster_box(const int *X, const int *Y, const float *IZ, bool t0, bool t1, bool t2,
                                            float af, int px0, int px1, int py0, int py1, unsigned gid,
-                                           unsigned long long *zb, int W, Covered *q, int *qn) {
+                                           unsigned long long *zb, int W) {
   const I a0 = (I)(X[2] - X[1]), b0 = (I)(Y[2] - Y[1]);
   const I a1 = (I)(X[0] - X[2]), b1 = (I)(Y[0] - Y[2]);
   const I a2 = (I)(X[1] - X[0]), b2 = (I)(Y[1] - Y[0]);
@@ -95,15 +81,7 @@ __device__ __forceinline__ void raster_box(const int *X, const int *Y, const flo
     I e0 = r0, e1 = r1, e2 = r2;
     for (int px = px0; px <= px1; px++) {
       if ((e0 > 0 || (e0 == 0 && t0)) && (e1 > 0 || (e1 == 0 && t1)) && (e2 > 0 || (e2 == 0 && t2))) {
-        const int pix = py * W + px;
-        const int slot = atomicAdd(qn, 1);
-        if (slot < kQCap) {
-          q[slot].a = make_float4(to_f32(e0), to_f32(e1), to_f32(e2), af);
-          q[slot].b = make_float4(IZ[0], IZ[1], IZ[2], __int_as_float(pix));
-          q[slot].gid = gid;
-        } else {
-          depth_test(to_f32(e0), to_f32(e1), to_f32(e2), af, IZ, pix, gid, zb);
-        }
+        depth_test(to_f32(e0), to_f32(e1), to_f32(e2), af, IZ, py * W + px, gid, zb);
       }
       e0 -= sx0;
       e1 -= sx1;
@@ -116,17 +94,14 @@ __device__ __forceinline__ void raster_box(const int *X, const int *Y, const flo
 }
 
 template <int N>
-__global__ void __launch_bounds__(kRasterWarps * 32, N <= 2 ? 7 : 5) k_raster(Params p, Scene s, Work w) {
+__global__ void __launch_bounds__(kRasterWarps * 32, N <= 2 ? 8 : 6) k_raster(Params p, Scene s, Work w) {
   constexpr int NCP = (N + 1) * (N + 2) / 2;
   __shared__ float sB[kMaxVerts * NCP];  // Bernstein weights of the lattice vertices
   __shared__ int2 s_tri[kMaxTess * kMaxTess];  // vertex slots (8 bits each) and sub-triangle id
   __shared__ int sX[kRasterWarps][kMaxVerts];
   __shared__ int sY[kRasterWarps][kMaxVerts];
   __shared__ float sIZ[kRasterWarps][kMaxVerts];
-  __shared__ Covered s_q[kRasterWarps][kQCap];  // covered pixels waiting for the depth test
-  __shared__ int s_qn[kRasterWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) s_qn[warp] = 0;
   const int L = p.L;
   const int NV = (L + 1) * (L + 2) / 2;
   const int up_count = L * (L + 1) / 2;
@@ -207,20 +182,10 @@ __global__ void __launch_bounds__(kRasterWarps * 32, N <= 2 ? 7 : 5) k_raster(Pa
       const float af = __ll2float_rn(area2);
       const unsigned gid = (unsigned)prim * (unsigned)nsub + (unsigned)tri.y;
       if (xmax - xmin < kSpan32 && ymax - ymin < kSpan32)
-        raster_box<int>(X, Y, IZ, t0, t1, t2, af, px0, px1, py0, py1, gid, zb, W, s_q[warp], &s_qn[warp]);
+        raster_box<int>(X, Y, IZ, t0, t1, t2, af, px0, px1, py0, py1, gid, zb, W);
       else
-        raster_box<long long>(X, Y, IZ, t0, t1, t2, af, px0, px1, py0, py1, gid, zb, W, s_q[warp], &s_qn[warp]);
+        raster_box<long long>(X, Y, IZ, t0, t1, t2, af, px0, px1, py0, py1, gid, zb, W);
     }
-    __syncwarp();
-    // the queued depth tests of this primitive, one per lane
-    const int nq = min(s_qn[warp], kQCap);
-    for (int i = lane; i < nq; i += 32) {
-      const Covered c = s_q[warp][i];
-      const float IZc[3] = {c.b.x, c.b.y, c.b.z};
-      depth_test(c.a.x, c.a.y, c.a.z, c.a.w, IZc, __float_as_int(c.b.w), c.gid, zb);
-    }
-    __syncwarp();
-    if (lane == 0) s_qn[warp] = 0;
     __syncwarp();
   }
 }
