@@ -178,7 +178,10 @@ bgt_status bgt_set_tile_size(bgt_handle *h, int tile_size);
 int bgt_get_tile_size(const bgt_handle *h);
 
 /* Per-stage timing: when on, forward and backward record CUDA events on their
- * stream between stages (also inside captured graphs). bgt_get_profile
+ * stream between stages (also inside captured graphs); on = 1 also has the
+ * blending kernels count their work units (a build of them with counters,
+ * slightly slower), on = 2 times the kernels of the normal step without
+ * counting, on = 0 turns profiling off (BGT_ERR_INVALID_ARG otherwise). bgt_get_profile
  * waits for the last backward and returns device milliseconds of the last
  * forward + backward: ms[0] clears + per-primitive prep, [1] tessellation +
  * raster, [2] resolve, [3] sub-primitive generation, [4] binning + sort,

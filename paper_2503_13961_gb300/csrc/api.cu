@@ -44,8 +44,9 @@ struct bgt_handle {
   // graphs
   cudaGraphExec_t g_fwd = nullptr, g_bwd = nullptr;
   std::string g_fwd_key, g_bwd_key;
-  // profiling: events between stages, kernels enqueued per pass
-  bool profiling = false;
+  // profiling: events between stages, kernels enqueued per pass; count_units:
+  // the blending kernels also count their work units (their counting build)
+  bool profiling = false, count_units = false;
   cudaEvent_t prof[12] = {};
   int kernels_fwd = 0, kernels_bwd = 0;
   std::string err;
@@ -231,7 +232,7 @@ bgt_status setup_call(bgt_handle *h, const bgt_scene *sc, const bgt_camera *cams
   p.bg[0] = sc->bg[0]; p.bg[1] = sc->bg[1]; p.bg[2] = sc->bg[2];
   p.max_pairs = h->Kcap;
   p.max_bpairs = h->Kbcap;
-  p.stats = h->profiling ? 1 : 0;
+  p.stats = h->count_units ? 1 : 0;
   p.attr_res = R;
   p.ntex = R * (R + 1) / 2;
   p.sh_deg = sc->sh_degree;
@@ -444,7 +445,7 @@ bgt_status bgt_render_fwd(bgt_handle *h, const bgt_scene *scene, const bgt_camer
   if ((h->cfg.flags & BGT_FLAG_GRAPH) && st != nullptr) {
     const std::string key = graph_key(p, scene->ctrl, scene->color, scene->opacity, scene->r_b, images, cams, n_views) +
                             std::to_string((size_t)scene->quat) + std::to_string((size_t)scene->log_scale) +
-                            std::to_string((size_t)scene->sh) + (h->profiling ? "P" : "-");
+                            std::to_string((size_t)scene->sh) + (h->profiling ? "P" : "-") + (h->count_units ? "U" : "-");
     e = run_graph(&h->g_fwd, &h->g_fwd_key, key, st, [&]() { return enqueue_fwd(h, p, sc, images, st); });
   } else {
     e = enqueue_fwd(h, p, sc, images, st);
@@ -486,7 +487,7 @@ bgt_status bgt_render_bwd(bgt_handle *h, const bgt_scene *scene, const bgt_camer
     const std::string key = graph_key(p, scene->ctrl, d_images, grads->ctrl, grads->color, grads->opacity, cams,
                                       n_views) + std::to_string((size_t)grads->r_b) +
                             std::to_string((size_t)grads->log_scale) + std::to_string((size_t)grads->quat) +
-                            std::to_string((size_t)grads->sh) + (h->profiling ? "P" : "-");
+                            std::to_string((size_t)grads->sh) + (h->profiling ? "P" : "-") + (h->count_units ? "U" : "-");
     e = run_graph(&h->g_bwd, &h->g_bwd_key, key, st, [&]() { return enqueue_bwd(h, p, sc, d_images, g, st); });
   } else {
     e = enqueue_bwd(h, p, sc, d_images, g, st);
@@ -544,7 +545,9 @@ bgt_status bgt_set_profiling(bgt_handle *h, int on) {
       if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventCreate");
     }
   }
+  if (on < 0 || on > 2) return fail(h, BGT_ERR_INVALID_ARG, "profiling mode must be 0, 1 or 2");
   h->profiling = on != 0;
+  h->count_units = on == 1;
   return BGT_OK;
 }
 

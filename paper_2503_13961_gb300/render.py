@@ -308,8 +308,11 @@ class Renderer:
 
     STAGES = ("prep", "raster", "resolve", "generate", "binning", "composite_fwd", "composite_bwd", "chain")
 
-    def set_profiling(self, on=True):
-        self._check(self.lib.bgt_set_profiling(self.h, 1 if on else 0))
+    def set_profiling(self, on=True, count_units=True):
+        """Stage events on (`on`); with count_units the blending kernels also
+        count their work units (their counting build), else the step's own
+        kernels are timed."""
+        self._check(self.lib.bgt_set_profiling(self.h, (1 if count_units else 2) if on else 0))
 
     UNITS = ("fwd_support", "fwd_composited", "fwd_candidates", "fwd_warp_visits", "bwd_support",
              "bwd_composited", "bwd_candidates", "bwd_warp_visits")

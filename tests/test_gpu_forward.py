@@ -192,6 +192,32 @@ def test_batch_equals_single_views(scenes):
         assert np.array_equal(single, batch[k])
 
 
+def test_stage_profile_and_work_units(scenes):
+    """Stage events with and without the blending kernels' counting build:
+    the same images either way, work units only from the counting build,
+    and an unknown mode rejected."""
+    import torch
+    from paper_2503_13961_gb300 import render as R
+    sc, cams = scenes.tiny_scene("ico1", noise=0.04, size=(96, 80), r_b=0.03)
+    rd = make_renderer(sc, cams)
+    dev = R.scene_to_device(sc)
+    imgs = []
+    for count in (True, False):
+        rd.set_profiling(True, count_units=count)
+        img = rd.forward(dev, cams).clone()
+        rd.backward(dev, cams, torch.ones_like(img) / img.numel())
+        torch.cuda.synchronize()
+        ms, kf, kb, units = rd.profile()
+        assert all(v >= 0.0 for v in ms.values()) and ms["composite_fwd"] > 0.0 and kf > 0 and kb > 0
+        if count:
+            assert units["fwd_composited"] > 0 and units["fwd_composited"] == units["bwd_composited"]
+        imgs.append(img)
+    assert torch.equal(imgs[0], imgs[1])
+    assert rd.lib.bgt_set_profiling(rd.h, 3) == 1
+    rd.set_profiling(False)
+    rd.sync_status()
+
+
 def test_graph_replay_matches_direct(scenes):
     import torch
     from paper_2503_13961_gb300 import render as R
