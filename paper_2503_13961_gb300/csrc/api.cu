@@ -102,6 +102,7 @@ void carve(bgt_handle *h, char *base, size_t *total) {
   w.g_pix = c.take<int>(F);
   w.g_view = c.take<int>(F);
   w.g_bidx = c.take<int>(F);
+  w.g_prim = c.take<int>(F);
   w.g_uv = c.take<float2>(F);
   w.g_rect = c.take<uint2>(F);
   w.g_depth = c.take<float>(F);

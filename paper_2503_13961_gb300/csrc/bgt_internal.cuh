@@ -118,6 +118,7 @@ struct Work {
   int *g_pix;                 // [Fcap] global pixel index
   int *g_view;                // [Fcap]
   int *g_bidx;                // [Fcap] boundary point of the Gaussian's pixel, -1 if not in B
+  int *g_prim;                // [Fcap] primitive of the Gaussian's pixel (I_id)
   float2 *g_uv;               // [Fcap]
   uint2 *g_rect;              // [Fcap] tile rect x0 | y0 << 16, x1 | y1 << 16 (view-local tiles)
   float *g_depth;             // [Fcap] camera depth (FP32)

@@ -98,6 +98,19 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const int *in, long 
   if (base < n && base + kScanItems >= n) out[n] = run;
 }
 
+// a slot in tile t's segment: the active lanes of the warp that want one in
+// the same tile share one atomic (consecutive Gaussians mostly share tiles);
+// the order inside a segment is set by the sort that follows
+__device__ __forceinline__ int tile_slot(int *fill, int t) {
+  const int lane = threadIdx.x & 31;
+  const unsigned peers = __match_any_sync(__activemask(), t);
+  const int leader = __ffs(peers) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(fill + t, __popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  return base + __popc(peers & ((1u << lane) - 1u));
+}
+
 __device__ inline void emit_rect(unsigned long long *keys, int *fill, const long long *start, long long cap,
                                  int tile_off, int tiles_x, uint2 rect, unsigned long long hi,
                                  unsigned lo) {
@@ -105,7 +118,7 @@ __device__ inline void emit_rect(unsigned long long *keys, int *fill, const long
   for (int ty = y0; ty <= y1; ty++)
     for (int tx = x0; tx <= x1; tx++) {
       const int t = tile_off + ty * tiles_x + tx;
-      const long long pos = start[t] + atomicAdd(fill + t, 1);
+      const long long pos = start[t] + tile_slot(fill, t);
       if (pos >= 0 && pos < cap) keys[pos] = hi | (unsigned long long)lo;
     }
 }
@@ -251,7 +264,8 @@ __device__ void radix_global(unsigned long long *keys, unsigned long long *tmp, 
   __syncthreads();
 }
 
-constexpr int kWarpSortCap = 1024;  // keys a single warp sorts in its own shared memory
+constexpr int kWarpSortCap = 512;  // keys a single warp sorts in its own shared memory (occupancy:
+                                   // 16 keys per lane in registers, 36 KB of shared memory per block)
 constexpr int kRadixMin = 129;     // segments from this length sort by radix, shorter ones by bitonic network
 // per warp: the keys (kWarpSortCap) and 256 radix bins
 constexpr int kTileSortSmem = (kSortThreads / 32) * (kWarpSortCap * (int)sizeof(unsigned long long) + 256 * 4);
@@ -371,7 +385,7 @@ __device__ __forceinline__ void warp_radix_smem(unsigned long long *sk, unsigned
 // lanes' registers; up to kWarpSortCap: bitonic sort (up to 128 keys) or
 // radix sort in the warp's shared memory; longer segments are appended to a
 // list for k_tile_sort_big.
-__global__ void __launch_bounds__(kSortThreads) k_tile_sort(Params p, Work w, int *big_list) {
+__global__ void __launch_bounds__(kSortThreads, 3) k_tile_sort(Params p, Work w, int *big_list) {
   extern __shared__ __align__(16) unsigned long long s_sort[];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const bool g_over = w.g_tstart[p.tiles] > p.max_pairs, b_over = w.b_tstart[p.tiles] > p.max_bpairs;
@@ -470,7 +484,7 @@ cudaError_t configure_binning() {
 }
 
 int launch_bin_sort_only(const Params &p, const Work &w, cudaStream_t st) {
-  k_emit<<<4 * 152, 256, 0, st>>>(p, w);
+  k_emit<<<16 * 152, 256, 0, st>>>(p, w);
   if (p.tiles <= 0) return 1;
   cudaMemsetAsync(w.counters + kQueueSort, 0, 2 * sizeof(int), st);
   k_tile_sort<<<3 * 152, kSortThreads, kTileSortSmem, st>>>(p, w, w.big_list);

@@ -74,10 +74,18 @@ __global__ void k_totals(Work w) {
   w.counters[kNb] = (int)w.blk_off[2 * w.nblk + 1];
 }
 
+// one count per tile of the rect; the active lanes of the warp that count the
+// same tile add their counts with one atomic (consecutive Gaussians mostly
+// share tiles)
 __device__ inline void count_tiles(int *cnt, int tile_off, int tiles_x, uint2 rect) {
+  const int lane = threadIdx.x & 31;
   const int x0 = rect.x & 0xffff, y0 = rect.x >> 16, x1 = rect.y & 0xffff, y1 = rect.y >> 16;
   for (int ty = y0; ty <= y1; ty++)
-    for (int tx = x0; tx <= x1; tx++) atomicAdd(cnt + tile_off + ty * tiles_x + tx, 1);
+    for (int tx = x0; tx <= x1; tx++) {
+      const int t = tile_off + ty * tiles_x + tx;
+      const unsigned peers = __match_any_sync(__activemask(), t);
+      if (lane == __ffs(peers) - 1) atomicAdd(cnt + t, __popc(peers));
+    }
 }
 
 // tile rect of the pixel box [cx - rx, cx + rx] x [cy - ry, cy + ry]; empty -> x0 > x1
@@ -113,6 +121,8 @@ __global__ void __launch_bounds__(kGenThreads) k_compact(Params p, Work w) {
       w.g_pix[gi] = pix;
       w.g_view[gi] = view;
       w.g_bidx[gi] = bnd ? nb + __popc(mb & lt) : -1;
+      w.g_prim[gi] = w.pid[pix];
+      w.g_uv[gi] = w.puv[pix];
     }
     nf += __popc(mf);
     nb += __popc(mb);
@@ -124,11 +134,10 @@ template <int N>
 __global__ void __launch_bounds__(kGenThreads) k_generate(Params p, Scene s, Work w) {
   const int F = w.counters[kF];
   for (int gi = blockIdx.x * blockDim.x + threadIdx.x; gi < F; gi += gridDim.x * blockDim.x) {
-    const int pix = w.g_pix[gi], view = w.g_view[gi], bi = w.g_bidx[gi];
+    const int pix = w.g_pix[gi], view = w.g_view[gi], bi = w.g_bidx[gi], prim = w.g_prim[gi];
+    const float2 uv = w.g_uv[gi];
     const bool bnd = bi >= 0;
     const View vw = w.views[view];
-    const int prim = w.pid[pix];
-    const float2 uv = w.puv[pix];
     const int local = pix - vw.pix_off;
     const int qy = local / vw.W, qx = local - qy * vw.W;
     const float *cp = s.ctrl + (size_t)prim * p.ncp * 3;
@@ -209,7 +218,6 @@ __global__ void __launch_bounds__(kGenThreads) k_generate(Params p, Scene s, Wor
     w.gB[gi] = make_float4(Ka, Kb, Kc, o);
     w.gC[gi] = make_float4(col[0], col[1], col[2], __int_as_float(prim));
     w.g_depth[gi] = tz;
-    w.g_uv[gi] = uv;
     w.g_rect[gi] = rect;
     w.g_dsub[gi] = dsub;
     float4 *ggz = reinterpret_cast<float4 *>(w.gg + 12 * (size_t)gi);

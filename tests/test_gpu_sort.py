@@ -86,7 +86,7 @@ def test_bin_sort_large_tiles(oracle, scenes, n, low, high):
 
 def test_bin_sort_warp_sized_tiles(oracle, scenes):
     # tiles of 33..64, 65..128 keys (one warp, bitonic network in shared
-    # memory) and 129..256, 257..512 keys (one warp, radix in shared memory)
+    # memory) and 129..256, 257..512 keys (one warp, radix sort)
     W, H = 64, 64
     seen = []
     for seed, n in ((21, 150), (22, 400), (23, 900), (24, 1800)):
@@ -102,8 +102,8 @@ def test_bin_sort_warp_sized_tiles(oracle, scenes):
 
 
 def test_bin_sort_mid_size_tiles(oracle, scenes):
-    # tiles of 513..1024 keys (one warp, shared memory) and 1025..4096 keys
-    # (one block, shared memory) in the same call
+    # tiles of 513..1024 and 1025..4096 keys (one block, bitonic network in
+    # shared memory) in the same call
     W, H, n = 40, 36, 2000
     g = scenes.random_gaussians(7, W, H, n, radius_px=(2.0, 5.0))
     rd = _renderer(W, H, n, 32)
