@@ -193,19 +193,19 @@ def stage_bytes(stage, c, M, ncp, V):
 
 
 # DRAM bytes (read + write) per composited pair of the blending kernels, from one
-# ncu capture of four 1024^2 views, valid only for the kernel source they were
-# measured on (else traffic: null)
-BLEND_TRAFFIC = {"source_sha256": "a94eb491f9d2d0fe7e79ba9500e43337c7c2eaa2ced6ca010bb02e317178329d",
-                 "composite_fwd": (132.1e6 + 154.3e6) / 50625814, "composite_bwd": (297.4e6 + 40.7e6) / 50625814}
+# ncu capture of four 1024^2 views (profiles/composite_blend_views1024x4.md),
+# valid only for the kernel source they were measured on (else traffic: null)
+BLEND_TRAFFIC = {"source_sha256": "481457d7f15612ede7007265ef41c570cb3a93a00065887f8d5960100920f5e9",
+                 "composite_fwd": (132303360 + 154140672) / 50625814,
+                 "composite_bwd": (292152320 + 42065152) / 50625814}
 
 
 # Warp instructions per warp visit of the blending kernels (a visit: one warp,
-# one listed Gaussian forward; one replayed record backward), from one ncu
-# capture of four 1024^2 views: both kernels keep the instruction issue slots
-# 80-85 % busy, so issue is the ceiling that binds them; same source check as
-# the traffic
+# one listed Gaussian forward; one replayed record backward), from the same
+# capture; the forward keeps the issue slots ~80 % busy, so issue is the
+# ceiling that binds it; same source check as the traffic
 BLEND_ISSUE = {"source_sha256": BLEND_TRAFFIC["source_sha256"],
-               "composite_fwd": 780578445 / 5419084, "composite_bwd": 911759901 / 4948871}
+               "composite_fwd": 735800302 / 5419084, "composite_bwd": 548180225 / 4948871}
 
 
 def _blend_source_matches():
