@@ -78,32 +78,25 @@ __device__ __forceinline__ float gauss(float dx, float dy, const float4 &Qs) {
   return ex2(__fmaf_rn(dx, t, __fmul_rn(__fmul_rn(Qs.z, dy), dy)));
 }
 
-// A boundary record in the form the search uses: pixel coordinates of the
-// boundary pixel as exact floats and the offset of b from its centre, so that
-// q - b = (q - qb) - off takes one exact and one rounded subtraction whatever
-// the tile (images do not depend on the tile size).
-__device__ __forceinline__ float4 to_search(const float4 rec) {
+// A boundary record in the form the search uses, relative to the 32 x 32 pixel
+// cell (cx, cy) holding the tile (cells do not depend on the tile size, so
+// neither do images): (x, y, 1/sigma^2, 1/sigma) with x = (qx_b - cx) +
+// off_x, the first difference exact. For a pixel at (pxr, pyr) = (px - cx,
+// py - cy) (exact), q - b = (pxr - x, pyr - y).
+__device__ __forceinline__ float4 cell_record(const float4 rec, int cx, int cy) {
   const unsigned qxy = __float_as_uint(rec.x);
-  return make_float4((float)(int)(qxy & 0xffffu), (float)(int)(qxy >> 16), rec.y, rec.z);
+  return make_float4(__fadd_rn((float)((int)(qxy & 0xffffu) - cx), rec.y),
+                     __fadd_rn((float)((int)(qxy >> 16) - cy), rec.z), __fmul_rn(rec.w, rec.w), rec.w);
 }
 
 // the tile's boundary candidates, sorted by (primitive, index)
 struct BList {
   const int *prim;
-  const float4 *loc;   // search-form records in shared memory (if cached)
-  const float *isig;   // 1 / sigma in shared memory (if cached)
+  const float4 *loc;   // cell-relative records in shared memory (if cached)
   const float4 *glob;  // pixel-relative records in global memory
-  int n;
+  int n, cx, cy;       // candidates; the cell of the tile
   bool cached;
-  __device__ __forceinline__ float4 get(int i, float &is) const {
-    if (cached) {
-      is = isig[i];
-      return loc[i];
-    }
-    const float4 r = glob[i];
-    is = r.w;
-    return to_search(r);
-  }
+  __device__ __forceinline__ float4 get(int i) const { return cached ? loc[i] : cell_record(glob[i], cx, cy); }
 };
 
 __device__ __forceinline__ float sqrt_approx(float x) {
@@ -141,31 +134,34 @@ __device__ __forceinline__ void warp_equal_range(const int *prim, int n, int g, 
   hi = b + __popc(__ballot_sync(0xffffffffu, vb <= g));
 }
 
-// |q - b|^2 / sigma^2 for boundary candidate i at pixel (pxf, pyf)
-__device__ __forceinline__ float cand_r2(const BList &bl, int i, float pxf, float pyf) {
-  float is;
-  const float4 b = bl.get(i, is);
-  const float dx = __fsub_rn(__fsub_rn(pxf, b.x), b.z), dy = __fsub_rn(__fsub_rn(pyf, b.y), b.w);
-  return __fmul_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)), __fmul_rn(is, is));
+// |q - b|^2 / sigma^2 of a cell-relative record b at the cell-relative pixel (pxr, pyr)
+__device__ __forceinline__ float rec_r2(const float4 &b, float pxr, float pyr) {
+  const float dx = __fsub_rn(pxr, b.x), dy = __fsub_rn(pyr, b.y);
+  return __fmul_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)), b.z);
+}
+
+// |q - b|^2 / sigma^2 for boundary candidate i at the cell-relative pixel (pxr, pyr)
+__device__ __forceinline__ float cand_r2(const BList &bl, int i, float pxr, float pyr) {
+  return rec_r2(bl.get(i), pxr, pyr);
 }
 
 // gamma = min(2^(rho - 1), 1) (Eq. 7) for rho^2 = r2 < 1
 __device__ __forceinline__ float gamma_of(float r2) { return ex2(__fsub_rn(sqrt_approx(r2), 1.0f)); }
 
-// Eq. 6-7 at pixel (px, py) for primitive g, whose boundary candidates are
+// Eq. 6-7 at the cell-relative pixel (pxr, pyr) for primitive g, whose boundary candidates are
 // [lo, hi): gamma* = min over g's boundary points of min(2^(rho - 1), 1),
 // rho = |q - b| / sigma_b; w = gamma* inside g, 1 - gamma* outside.
 // best: the first candidate of least rho if rho < 1, else -1. U candidates
 // are evaluated per iteration (instruction-level parallelism vs registers).
 template <int U>
-__device__ __forceinline__ float w_search(const BList &bl, int lo, int hi, float pxf, float pyf, bool inside,
+__device__ __forceinline__ float w_search(const BList &bl, int lo, int hi, float pxr, float pyr, bool inside,
                                           int &best, unsigned &cands) {
   float r2min = 3.0e38f;
   best = -1;
   for (int i = lo; i < hi; i += U) {
     float r[U];
 #pragma unroll
-    for (int u = 0; u < U; u++) r[u] = cand_r2(bl, min(i + u, hi - 1), pxf, pyf);
+    for (int u = 0; u < U; u++) r[u] = cand_r2(bl, min(i + u, hi - 1), pxr, pyr);
 #pragma unroll
     for (int u = 0; u < U; u++)
       if (r[u] < r2min) {  // a repeated last candidate never replaces itself
@@ -204,23 +200,21 @@ __device__ inline TileInfo tile_info(const Params &p, const Work &w, int tile) {
 }
 
 template <int NT>
-__device__ __forceinline__ BList load_boundary(const TileInfo &ti, const Work &w, int *s_bprim, float4 *s_bloc,
-                                               float *s_bisig) {
+__device__ __forceinline__ BList load_boundary(const TileInfo &ti, const Work &w, int *s_bprim, float4 *s_bloc) {
   BList bl;
   bl.n = (int)ti.bn;
   bl.glob = w.bl_rec + ti.bs;
+  bl.cx = ti.x0 & ~31;
+  bl.cy = ti.y0 & ~31;
   bl.cached = ti.bn <= kBCap;
   if (bl.cached) {
     for (int i = threadIdx.x; i < ti.bn; i += NT) {
-      const float4 r = w.bl_rec[ti.bs + i];
       s_bprim[i] = w.bl_prim[ti.bs + i];
-      s_bloc[i] = to_search(r);
-      s_bisig[i] = r.w;
+      s_bloc[i] = cell_record(w.bl_rec[ti.bs + i], bl.cx, bl.cy);
     }
   }
   bl.prim = bl.cached ? s_bprim : w.bl_prim + ti.bs;
   bl.loc = s_bloc;
-  bl.isig = s_bisig;
   return bl;
 }
 
@@ -279,7 +273,6 @@ struct FwdShared {
   float s_cw[Cfg::NW][S][Cfg::PPT][32];  // cached w per slot and pixel
   int sG[Cfg::NW][32];
   int s_bprim[kBCap];
-  float s_bisig[kBCap];
   int s_tile;
 };
 
@@ -405,7 +398,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_compos
     const int tile = s_tile;
     if (tile >= p.tiles) break;
     const TileInfo ti = tile_info(p, w, tile);
-    const BList bl = load_boundary<NT>(ti, w, sh.s_bprim, sh.s_bloc, sh.s_bisig);
+    const BList bl = load_boundary<NT>(ti, w, sh.s_bprim, sh.s_bloc);
     __syncthreads();  // boundary list staged, s_tile read by every thread
     // the next tile, fetched while this one is blended
     if (threadIdx.x == 0) s_tile = atomicAdd(w.counters + kQueueFwd, 1);
@@ -414,7 +407,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_compos
     const float bx0 = (float)wx, bx1 = (float)(wx + Cfg::WX - 1);
     const float by0 = (float)wy, by1 = (float)(wy + Cfg::WY - 1);
 
-    float C[PPT][3], Tr[PPT], pxf[PPT], pyf[PPT];
+    float C[PPT][3], Tr[PPT], pxf[PPT], pyf[PPT], pxr[PPT], pyr[PPT];
     int last[PPT], idq[PPT], pix[PPT];
     bool done[PPT];
     unsigned n_sup = 0, n_comp = 0, n_cand = 0, n_visit = 0;
@@ -427,6 +420,8 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_compos
       const int px = ti.x0 + lx, py = ti.y0 + ly;
       pxf[k] = (float)px;
       pyf[k] = (float)py;
+      pxr[k] = (float)(px - bl.cx);
+      pyr[k] = (float)(py - bl.cy);
       const bool inside = px < ti.W && py < ti.H;
       pix[k] = inside ? ti.pix_off + py * ti.W + px : -1;
       done[k] = !inside;
@@ -480,7 +475,7 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_FWD) k_compos
           for (int k = 0; k < PPT; k++) {
             int best = -1;
             cw[(slot * PPT + k) * 32 + lane] = p.use_boundary
-                ? w_search<2>(bl, lo, hi, pxf[k], pyf[k], idq[k] == g, best, n_cand) : 1.0f;
+                ? w_search<2>(bl, lo, hi, pxr[k], pyr[k], idq[k] == g, best, n_cand) : 1.0f;
             if (f >= 0) w.rec_fill[(size_t)(f + k) * 32 + lane] = best;
           }
           if (lane == slot) {
@@ -615,23 +610,23 @@ __device__ __forceinline__ float pair_backward(float dx, float dy, float G, floa
   return dl_dw;
 }
 
-// Boundary-point gradient of pixel (pxf, pyf) and boundary candidate bi of
-// the tile's list, given sum = the pixel's dl/dw over Gaussians of the
-// candidate's primitive (inside: the pixel belongs to it). w = gamma (inside)
-// or 1 - gamma with gamma = 2^(rho - 1), so dl/drho = +-ln2 gamma sum, taken
-// through rho = |q - b| / sigma: drho/db = -(q - b) / (|q - b| sigma),
-// drho/dsigma = -rho / sigma. brec and bkeys are the tile's boundary list
-// (records in pixel-relative form, keys holding the boundary point's index).
+// Boundary-point gradient of the cell-relative pixel (pxr, pyr) (cell (cx,
+// cy)) and boundary candidate bi of the tile's list, given sum = the pixel's
+// dl/dw over Gaussians of the candidate's primitive (inside: the pixel
+// belongs to it). w = gamma (inside) or 1 - gamma with gamma = 2^(rho - 1),
+// so dl/drho = +-ln2 gamma sum, taken through rho = |q - b| / sigma:
+// drho/db = -(q - b) / (|q - b| sigma), drho/dsigma = -rho / sigma. brec and
+// bkeys are the tile's boundary list (records in pixel-relative form, keys
+// holding the boundary point's index).
 __device__ __forceinline__ void boundary_grad(const float4 *brec, const unsigned long long *bkeys, float4 *bg_grad,
-                                              int bi, float sum, bool inside, float pxf, float pyf) {
+                                              int bi, float sum, bool inside, float pxr, float pyr, int cx, int cy) {
   const float LN2 = 0.69314718055994531f;
   if (bi < 0 || sum == 0.f) return;
   // rho and gamma with the operations of the forward search
-  const float4 rec = brec[bi];
-  const float4 b = to_search(rec);
-  const float isig = rec.w;
-  const float ex = __fsub_rn(__fsub_rn(pxf, b.x), b.z), ey = __fsub_rn(__fsub_rn(pyf, b.y), b.w);
-  const float r2 = __fmul_rn(__fmaf_rn(ex, ex, __fmul_rn(ey, ey)), __fmul_rn(isig, isig));
+  const float4 b = cell_record(brec[bi], cx, cy);
+  const float isig = b.w;
+  const float ex = __fsub_rn(pxr, b.x), ey = __fsub_rn(pyr, b.y);
+  const float r2 = __fmul_rn(__fmaf_rn(ex, ex, __fmul_rn(ey, ey)), b.z);
   const float rho = sqrt_approx(r2);
   if (!(rho > 0.f)) return;
   const float gam = gamma_of(r2);
@@ -650,23 +645,22 @@ __device__ __forceinline__ void boundary_grad(const float4 *brec, const unsigned
 template <int PPT>
 __device__ __forceinline__ void flush_boundary(const float4 *brec, const unsigned long long *bkeys, float4 *bg_grad,
                                                const int *cb, const float *cacc, int g, const int *idq,
-                                               const float *pxf, const float *pyf) {
+                                               const float *pxr, const float *pyr, int cx, int cy) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int k = 0; k < PPT; k++)
-    boundary_grad(brec, bkeys, bg_grad, cb[k * 32 + lane], cacc[k * 32 + lane], idq[k] == g, pxf[k], pyf[k]);
+    boundary_grad(brec, bkeys, bg_grad, cb[k * 32 + lane], cacc[k * 32 + lane], idq[k] == g, pxr[k], pyr[k], cx,
+                  cy);
 }
 
-// w (Eq. 6-7) at pixel (px, py) for the primitive whose most influential
-// boundary point is candidate bi of the tile's list (-1: none within rho < 1),
-// with the operations of the forward search, so the value is bit-identical
-__device__ __forceinline__ float w_from_candidate(const float4 *brec, int bi, float pxf, float pyf, bool inside) {
+// w (Eq. 6-7) at the cell-relative pixel (pxr, pyr) for the primitive whose
+// most influential boundary point is candidate bi of the tile's list (-1: none
+// within rho < 1), with the operations of the forward search, so the value is
+// bit-identical
+__device__ __forceinline__ float w_from_candidate(const float4 *brec, int bi, float pxr, float pyr, int cx, int cy,
+                                                  bool inside) {
   if (bi < 0) return inside ? 1.0f : 0.0f;
-  const float4 rec = brec[bi];
-  const float4 b = to_search(rec);
-  const float dx = __fsub_rn(__fsub_rn(pxf, b.x), b.z), dy = __fsub_rn(__fsub_rn(pyf, b.y), b.w);
-  const float r2 = __fmul_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)), __fmul_rn(rec.w, rec.w));
-  const float gamma = gamma_of(r2);
+  const float gamma = gamma_of(rec_r2(cell_record(brec[bi], cx, cy), pxr, pyr));
   return inside ? gamma : __fsub_rn(1.0f, gamma);
 }
 
@@ -708,7 +702,8 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
       const unsigned long long *bkeys = w.bkeys + bs;
       const int2 br = w.blk_rec[item];
 
-      float Tr[PPT], R[PPT][3], dC[PPT][3], pxf[PPT], pyf[PPT];
+      const int cx = x0 & ~31, cy = y0 & ~31;  // the tile's cell (boundary records are cell-relative)
+      float Tr[PPT], R[PPT][3], dC[PPT][3], pxf[PPT], pyf[PPT], pxr[PPT], pyr[PPT];
       int idq[PPT];
 #pragma unroll
       for (int k = 0; k < PPT; k++) {
@@ -717,6 +712,8 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
         const int px = x0 + lx, py = y0 + ly;
         pxf[k] = (float)px;
         pyf[k] = (float)py;
+        pxr[k] = (float)(px - cx);
+        pyr[k] = (float)(py - cy);
         idq[k] = -1;
         Tr[k] = 1.f;
         R[k][0] = R[k][1] = R[k][2] = 0.f;
@@ -768,11 +765,12 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
               cnext = (cnext + 1 == S) ? 0 : cnext + 1;
               const int old = __shfl_sync(0xffffffffu, ckey, slot);
               if (old >= 0)
-                flush_boundary<PPT>(brec, bkeys, w.bg_grad, &s_cb[slot][0][0], &s_cacc[slot][0][0], old, idq, pxf, pyf);
+                flush_boundary<PPT>(brec, bkeys, w.bg_grad, &s_cb[slot][0][0], &s_cacc[slot][0][0], old, idq, pxr,
+                                    pyr, cx, cy);
 #pragma unroll
               for (int k = 0; k < PPT; k++) {
                 const int bi = (int)h.z >= 0 ? w.rec_fill[(size_t)((int)h.z + k) * 32 + lane] : -1;
-                s_cw[slot][k][lane] = w_from_candidate(brec, bi, pxf[k], pyf[k], idq[k] == g);
+                s_cw[slot][k][lane] = w_from_candidate(brec, bi, pxr[k], pyr[k], cx, cy, idq[k] == g);
                 s_cb[slot][k][lane] = bi;
                 s_cacc[slot][k][lane] = 0.f;
               }
@@ -862,7 +860,8 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
         for (int sl = 0; sl < S; sl++) {
           const int old = __shfl_sync(0xffffffffu, ckey, sl);
           if (old >= 0)
-            flush_boundary<PPT>(brec, bkeys, w.bg_grad, &s_cb[sl][0][0], &s_cacc[sl][0][0], old, idq, pxf, pyf);
+            flush_boundary<PPT>(brec, bkeys, w.bg_grad, &s_cb[sl][0][0], &s_cacc[sl][0][0], old, idq, pxr, pyr, cx,
+                                cy);
         }
       }
       if constexpr (STATS) flush_stats(w.stats, kBwdSupport, n_comp, n_comp, 0u, n_rec);
@@ -897,13 +896,14 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd_walk(Params p,
     BList bl;
     bl.n = (int)ti.bn;
     bl.glob = w.bl_rec + ti.bs;
+    bl.cx = ti.x0 & ~31;
+    bl.cy = ti.y0 & ~31;
     bl.cached = false;
     bl.prim = w.bl_prim + ti.bs;
     bl.loc = nullptr;
-    bl.isig = nullptr;
     const float4 *brec = w.bl_rec + ti.bs;
     const unsigned long long *bkeys = w.bkeys + ti.bs;
-    float Tr[PPT], R[PPT][3], dC[PPT][3], pxf[PPT], pyf[PPT];
+    float Tr[PPT], R[PPT][3], dC[PPT][3], pxf[PPT], pyf[PPT], pxr[PPT], pyr[PPT];
     int idq[PPT], nlast[PPT];
     int emax = 0;
 #pragma unroll
@@ -913,6 +913,8 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd_walk(Params p,
       const int px = ti.x0 + lx, py = ti.y0 + ly;
       pxf[k] = (float)px;
       pyf[k] = (float)py;
+      pxr[k] = (float)(px - bl.cx);
+      pyr[k] = (float)(py - bl.cy);
       idq[k] = -1;
       nlast[k] = 0;
       Tr[k] = 1.f;
@@ -962,14 +964,15 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd_walk(Params p,
       for (int k = 0; k < PPT; k++) {
         int best = -1;
         unsigned ncand = 0;
-        const float wv = p.use_boundary ? w_search<2>(bl, lo, hi, pxf[k], pyf[k], idq[k] == g, best, ncand) : 1.0f;
+        const float wv = p.use_boundary ? w_search<2>(bl, lo, hi, pxr[k], pyr[k], idq[k] == g, best, ncand) : 1.0f;
         if (!cand[k]) continue;
         const float raw = __fmul_rn(og[k], wv);
         const float alpha = fminf(p.alpha_max, raw);
         if (alpha < p.alpha_min) continue;
         const float dx = __fsub_rn(__fsub_rn(pxf[k], P.x), P.z), dy = __fsub_rn(__fsub_rn(pyf[k], P.y), P.w);
         const float dl_dw = pair_backward(dx, dy, Gk[k], og[k], wv, raw, alpha, p.alpha_max, Cc, dC[k], Tr[k], R[k], acc);
-        if (p.use_boundary) boundary_grad(brec, bkeys, w.bg_grad, best, dl_dw, idq[k] == g, pxf[k], pyf[k]);
+        if (p.use_boundary)
+          boundary_grad(brec, bkeys, w.bg_grad, best, dl_dw, idq[k] == g, pxr[k], pyr[k], bl.cx, bl.cy);
       }
       const float part = warp_reduce_scatter8(acc);
       const float s8 = warp_sum(acc[8]);
