@@ -137,6 +137,8 @@ void carve(bgt_handle *h, char *base, size_t *total) {
   w.bkeys = c.take<unsigned long long>(2 * Kb);  // second half: sort scratch
   w.bl_prim = c.take<int>(Kb);
   w.bl_rec = c.take<float4>(Kb);
+  w.prim_cov = c.take<float>(6 * (long long)h->Mcap);
+  w.prim_gcov = c.take<float>(6 * (long long)h->Mcap);
   w.gg = c.take<float>(12 * F);
   w.bg_grad = c.take<float4>(F);
   w.Fcap = F;
@@ -276,6 +278,7 @@ cudaError_t enqueue_fwd(bgt_handle *h, const bgt::Params &p, const bgt::Scene &s
   mark(h, 2, st);
   k += bgt::launch_resolve(p, s, w, st);
   mark(h, 3, st);
+  k += bgt::launch_prim_cov(p, s, w, st);
   k += bgt::launch_generate(p, s, w, st);
   mark(h, 4, st);
   k += bgt::launch_binning(p, w, st);
@@ -299,6 +302,7 @@ cudaError_t enqueue_bwd(bgt_handle *h, const bgt::Params &p, const bgt::Scene &s
     if (g.log_scale) cudaMemsetAsync(g.log_scale, 0, sizeof(float) * 3 * (size_t)p.M * p.ntex, st);
     if (g.quat) cudaMemsetAsync(g.quat, 0, sizeof(float) * 4 * (size_t)p.M * p.ntex, st);
     if (g.sh && p.sh_k > 0) cudaMemsetAsync(g.sh, 0, sizeof(float) * 3 * (size_t)p.M * p.sh_k, st);
+    if (p.attr_res == 1 && (g.log_scale || g.quat)) cudaMemsetAsync(w.prim_gcov, 0, sizeof(float) * 6 * (size_t)p.M, st);
   }
   int k = bgt::launch_composite_bwd(p, w, dimg, st);
   mark(h, 8, st);

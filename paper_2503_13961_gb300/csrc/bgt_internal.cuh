@@ -161,6 +161,8 @@ struct Work {
   float *T_final;             // [P]
   int *n_contrib;             // [P] tile-list position after the last composited pair
   // intermediate gradients
+  float *prim_cov;            // [Mcap][6] Sigma3D per primitive (maps of leg resolution 1): xx xy xz yy yz zz
+  float *prim_gcov;           // [Mcap][6] dl/dSigma3D per primitive, summed over its Gaussians (same order)
   float *gg;                  // [Fcap][12] per-Gaussian sums of the blending backward over its composited
                               // pairs, s = dl/dalpha w G of a pair, d = q - mu: s dx, s dy, s dx^2,
                               // s dx dy, s dy^2, s (= dl/do), dl/dcolour r, g, b; pad (dl/dmu = o K (s d),
@@ -437,6 +439,44 @@ __device__ inline void cov3d_f32(const float *q, const float *ls, float *S6, flo
     for (int j = i; j < 3; j++) S6[k++] = Mx[3 * i] * Mx[3 * j] + Mx[3 * i + 1] * Mx[3 * j + 1] + Mx[3 * i + 2] * Mx[3 * j + 2];
 }
 
+// dl/d(log scales) and dl/d(raw quaternion) of Sigma3D = M M^T, M = R(q / |q|)
+// diag(exp(ls)), from G3 = dl/dSigma3D (symmetric, row-major 3 x 3), with
+// Rm = R(q / |q|) and sc = exp(ls) of cov3d_f32: dl/dM = 2 G3 M,
+// dl/dls_c = exp(ls_c) sum_r dM_rc R_rc, dl/dR_rc = dM_rc exp(ls_c), then
+// through the normalisation of q
+__device__ inline void cov_grad_to_attrs(const float *qa, const float *G3, const float *Rm, const float *sc3,
+                                         float *gls, float *gq) {
+  float GR[9];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    float ds = 0.f;
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+      float dm = 0.f;
+#pragma unroll
+      for (int k = 0; k < 3; k++) dm += 2.f * G3[3 * r + k] * Rm[3 * k + c] * sc3[c];
+      GR[3 * r + c] = dm * sc3[c];
+      ds += dm * Rm[3 * r + c];
+    }
+    gls[c] = ds * sc3[c];
+  }
+  const float nq = rsqrtf(qa[0] * qa[0] + qa[1] * qa[1] + qa[2] * qa[2] + qa[3] * qa[3]);
+  const float r = qa[0] * nq, x = qa[1] * nq, y = qa[2] * nq, z = qa[3] * nq;
+  float h[4];
+  h[0] = 2.f * (-z * GR[1] + y * GR[2] + z * GR[3] - x * GR[5] - y * GR[6] + x * GR[7]);
+  h[1] = 2.f * (-2.f * x * GR[4] + y * GR[1] + z * GR[2] + y * GR[3] - r * GR[5] + z * GR[6] + r * GR[7] -
+                2.f * x * GR[8]);
+  h[2] = 2.f * (-2.f * y * GR[0] + x * GR[1] + r * GR[2] + x * GR[3] + z * GR[5] - r * GR[6] + z * GR[7] -
+                2.f * y * GR[8]);
+  h[3] = 2.f * (-2.f * z * GR[0] - r * GR[1] + x * GR[2] + r * GR[3] - 2.f * z * GR[4] + y * GR[5] + x * GR[6] +
+                y * GR[7]);
+  const float dot = r * h[0] + x * h[1] + y * h[2] + z * h[3];
+  gq[0] = (h[0] - r * dot) * nq;
+  gq[1] = (h[1] - x * dot) * nq;
+  gq[2] = (h[2] - y * dot) * nq;
+  gq[3] = (h[3] - z * dot) * nq;
+}
+
 // ---------------------------------------------------------------------------
 // View-dependent colour: real spherical harmonics of bands 1..D (D <= 3) at a
 // unit direction (x, y, z), in the Cartesian forms that the associated
@@ -652,6 +692,7 @@ cudaError_t configure_binning();    // the same for the per-tile sort
 int launch_composite_fwd(const Params &p, const Work &w, float *image, cudaStream_t st);
 int launch_composite_bwd(const Params &p, const Work &w, const float *dimage, cudaStream_t st);
 int launch_chain(const Params &p, const Scene &s, const Work &w, const Grads &g, cudaStream_t st);
+int launch_prim_cov(const Params &p, const Scene &s, const Work &w, cudaStream_t st);
 int launch_l1_grad(const float *img, const float *target, long long n, float scale, float *dimg,
                    float *loss, cudaStream_t st);
 int launch_l2_dssim_grad(const float *img, const float *gt, int n_views, const int *sizes, float lambda,

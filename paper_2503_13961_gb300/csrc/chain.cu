@@ -67,7 +67,7 @@ constexpr int kChainWarps = 8;
 template <int N>
 __global__ void __launch_bounds__(256) k_chain_gauss(Params p, Scene s, Work w, Grads out) {
   constexpr int m = SurfPoint<N>::M;
-  __shared__ float s_rows[kChainWarps][32 * ((3 * m + 1) | 1)];
+  __shared__ float s_rows[kChainWarps][32 * ((3 * m + 7) | 1)];
   float *sw = s_rows[threadIdx.x >> 5];
   const int F = w.counters[kF];
   const int lane = threadIdx.x & 31;
@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(256) k_chain_gauss(Params p, Scene s, Work w, 
     int g = -1;
     float gS[3] = {0.f, 0.f, 0.f}, gcol[3] = {0.f, 0.f, 0.f}, gop = 0.f;
     float gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};  // map gradients (interpolated attrs)
+    float gc6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dl/dSigma3D (xx xy xz yy yz zz), leg resolution 1
     int tex[3] = {0, 0, 0};
     float tw[3] = {0.f, 0.f, 0.f};
     float B[m];
@@ -119,49 +120,31 @@ __global__ void __launch_bounds__(256) k_chain_gauss(Params p, Scene s, Work w, 
           T1[k] = j11 * vw.R[3 + k] + j12 * vw.R[6 + k];
         }
         // Sigma3D from the attribute maps at I_uv (Eq. 5), as in the forward
+        // (the primitive's own with maps of leg resolution 1)
         float qa[4], lsa[3], Rm[9], sc3[3], S3[6];
-        gauss_attrs(s.quat, s.log_scale, p.attr_res, p.ntex, g, uv.x, uv.y, qa, lsa, tex, tw);
-        cov3d_f32(qa, lsa, S3, Rm, sc3);
+        if (p.attr_res == 1) {
+#pragma unroll
+          for (int k = 0; k < 6; k++) S3[k] = w.prim_cov[6 * (size_t)g + k];
+        } else {
+          gauss_attrs(s.quat, s.log_scale, p.attr_res, p.ntex, g, uv.x, uv.y, qa, lsa, tex, tw);
+          cov3d_f32(qa, lsa, S3, Rm, sc3);
+        }
         const float Sg[9] = {S3[0], S3[1], S3[2], S3[1], S3[3], S3[4], S3[2], S3[4], S3[5]};
         if (out.log_scale || out.quat) {
-          // dl/dSigma3D = T^T dl/dSigma2D T; Sigma3D = M M^T, M = R(q) diag(exp(s)):
-          // dl/dM = 2 dl/dSigma3D M, dl/ds_c = exp(s_c) sum_r dM_rc R_rc,
-          // dl/dR_rc = dM_rc exp(s_c), then through the normalised quaternion
+          // dl/dSigma3D = T^T dl/dSigma2D T (symmetric): summed per primitive
+          // for maps of leg resolution 1 (taken to the texel once per
+          // primitive), else through the Gaussian's interpolated attributes
           float G3[9];
 #pragma unroll
           for (int a = 0; a < 3; a++)
 #pragma unroll
             for (int b = 0; b < 3; b++)
               G3[3 * a + b] = GS00 * T0[a] * T0[b] + GS01 * (T0[a] * T1[b] + T1[a] * T0[b]) + GS11 * T1[a] * T1[b];
-          float GR[9];
-#pragma unroll
-          for (int c = 0; c < 3; c++) {
-            float ds = 0.f;
-#pragma unroll
-            for (int r = 0; r < 3; r++) {
-              float dm = 0.f;
-#pragma unroll
-              for (int k = 0; k < 3; k++) dm += 2.f * G3[3 * r + k] * Rm[3 * k + c] * sc3[c];
-              GR[3 * r + c] = dm * sc3[c];
-              ds += dm * Rm[3 * r + c];
-            }
-            gls[c] = ds * sc3[c];
+          if (p.attr_res == 1) {
+            gc6[0] = G3[0]; gc6[1] = G3[1]; gc6[2] = G3[2]; gc6[3] = G3[4]; gc6[4] = G3[5]; gc6[5] = G3[8];
+          } else {
+            cov_grad_to_attrs(qa, G3, Rm, sc3, gls, gq);
           }
-          const float nq = rsqrtf(qa[0] * qa[0] + qa[1] * qa[1] + qa[2] * qa[2] + qa[3] * qa[3]);
-          const float r = qa[0] * nq, x = qa[1] * nq, y = qa[2] * nq, z = qa[3] * nq;
-          float h[4];
-          h[0] = 2.f * (-z * GR[1] + y * GR[2] + z * GR[3] - x * GR[5] - y * GR[6] + x * GR[7]);
-          h[1] = 2.f * (-2.f * x * GR[4] + y * GR[1] + z * GR[2] + y * GR[3] - r * GR[5] + z * GR[6] + r * GR[7] -
-                        2.f * x * GR[8]);
-          h[2] = 2.f * (-2.f * y * GR[0] + x * GR[1] + r * GR[2] + x * GR[3] + z * GR[5] - r * GR[6] + z * GR[7] -
-                        2.f * y * GR[8]);
-          h[3] = 2.f * (-2.f * z * GR[0] - r * GR[1] + x * GR[2] + r * GR[3] - 2.f * z * GR[4] + y * GR[5] +
-                        x * GR[6] + y * GR[7]);
-          const float dot = r * h[0] + x * h[1] + y * h[2] + z * h[3];
-          gq[0] = (h[0] - r * dot) * nq;
-          gq[1] = (h[1] - x * dot) * nq;
-          gq[2] = (h[2] - y * dot) * nq;
-          gq[3] = (h[3] - z * dot) * nq;
         }
         float TS0[3], TS1[3];
 #pragma unroll
@@ -194,18 +177,29 @@ __global__ void __launch_bounds__(256) k_chain_gauss(Params p, Scene s, Work w, 
     const bool nz = active && (gS[0] != 0.f || gS[1] != 0.f || gS[2] != 0.f || gcol[0] != 0.f ||
                                gcol[1] != 0.f || gcol[2] != 0.f || gop != 0.f);
     if (!__any_sync(0xffffffffu, nz)) continue;
+    const bool per_prim_cov = p.attr_res == 1 && (out.log_scale || out.quat);
     {
-      // control points and opacity, then colour control points (Eq. 3, 4: dl/dp = sum B dl/dS)
-      float v[3 * m + 1];
+      // control points, opacity and (leg resolution 1) dl/dSigma3D, then colour
+      // control points (Eq. 3, 4: dl/dp = sum B dl/dS)
+      float v[3 * m + 7];
 #pragma unroll
       for (int a = 0; a < m; a++)
 #pragma unroll
         for (int c = 0; c < 3; c++) v[3 * a + c] = nz ? B[a] * gS[c] : 0.f;
       v[3 * m] = nz ? gop : 0.f;
-      float *gctrl = out.ctrl, *gopa = out.opacity;
-      scatter_runs<3 * m + 1>(sw, v, nz ? g : -1, [&](int gg, int j) {
-        return j < 3 * m ? gctrl + (size_t)gg * 3 * m + j : gopa + gg;
-      });
+      float *gctrl = out.ctrl, *gopa = out.opacity, *gcov = w.prim_gcov;
+      if (per_prim_cov) {
+#pragma unroll
+        for (int k = 0; k < 6; k++) v[3 * m + 1 + k] = nz ? gc6[k] : 0.f;
+        scatter_runs<3 * m + 7>(sw, v, nz ? g : -1, [&](int gg, int j) {
+          return j < 3 * m ? gctrl + (size_t)gg * 3 * m + j
+                           : (j == 3 * m ? gopa + gg : gcov + 6 * (size_t)gg + (j - 3 * m - 1));
+        });
+      } else {
+        scatter_runs<3 * m + 1>(sw, v, nz ? g : -1, [&](int gg, int j) {
+          return j < 3 * m ? gctrl + (size_t)gg * 3 * m + j : gopa + gg;
+        });
+      }
 #pragma unroll
       for (int a = 0; a < m; a++)
 #pragma unroll
@@ -213,7 +207,7 @@ __global__ void __launch_bounds__(256) k_chain_gauss(Params p, Scene s, Work w, 
       float *gcolor = out.color;
       scatter_runs<3 * m>(sw, v, nz ? g : -1, [&](int gg, int j) { return gcolor + (size_t)gg * 3 * m + j; });
     }
-    if (out.log_scale || out.quat) {
+    if ((out.log_scale || out.quat) && !per_prim_cov) {
       // the map texels of the interpolation, with their weights; runs of equal
       // (primitive, texel) are summed before one atomic each
       const bool nm = active && (gls[0] != 0.f || gls[1] != 0.f || gls[2] != 0.f || gq[0] != 0.f ||
@@ -375,6 +369,29 @@ __global__ void k_l1_grad(const float *img, const float *tgt, long long n, float
 
 }  // namespace
 
+// maps of leg resolution 1: dl/dSigma3D summed over a primitive's Gaussians
+// taken to its one rotation and scaling texel (linear in dl/dSigma3D, so the
+// sum of the per-Gaussian terms)
+__global__ void k_prim_attr_grad(Params p, Scene s, Work w, Grads out) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= p.M) return;
+  const float *gc = w.prim_gcov + 6 * (size_t)m;
+  const float G3[9] = {gc[0], gc[1], gc[2], gc[1], gc[3], gc[4], gc[2], gc[4], gc[5]};
+  float qa[4], ls[3], Rm[9], sc3[3], S3[6], gls[3], gq[4];
+#pragma unroll
+  for (int k = 0; k < 4; k++) qa[k] = s.quat[4 * (size_t)m + k];
+#pragma unroll
+  for (int k = 0; k < 3; k++) ls[k] = s.log_scale[3 * (size_t)m + k];
+  cov3d_f32(qa, ls, S3, Rm, sc3);
+  cov_grad_to_attrs(qa, G3, Rm, sc3, gls, gq);
+  if (out.log_scale)
+#pragma unroll
+    for (int k = 0; k < 3; k++) out.log_scale[3 * (size_t)m + k] = gls[k];
+  if (out.quat)
+#pragma unroll
+    for (int k = 0; k < 4; k++) out.quat[4 * (size_t)m + k] = gq[k];
+}
+
 int launch_chain(const Params &p, const Scene &s, const Work &w, const Grads &g, cudaStream_t st) {
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
@@ -385,7 +402,12 @@ int launch_chain(const Params &p, const Scene &s, const Work &w, const Grads &g,
     k_chain_bnd<decltype(d)::value><<<grid, 256, 0, st>>>(p, s, w, g);
     if (p.sh_deg > 0) k_chain_sh<decltype(d)::value><<<grid, 256, 0, st>>>(p, s, w, g);
   });
-  return p.sh_deg > 0 ? 3 : 2;
+  int k = p.sh_deg > 0 ? 3 : 2;
+  if (p.attr_res == 1 && (g.log_scale || g.quat) && p.M > 0) {
+    k_prim_attr_grad<<<(p.M + 255) / 256, 256, 0, st>>>(p, s, w, g);
+    k++;
+  }
+  return k;
 }
 
 int launch_l1_grad(const float *img, const float *target, long long n, float scale, float *dimg, float *loss,

@@ -168,9 +168,13 @@ __global__ void __launch_bounds__(kGenThreads) k_generate(Params p, Scene s, Wor
       T0[k] = j00 * vw.R[k] + j02 * vw.R[6 + k];
       T1[k] = j11 * vw.R[3 + k] + j12 * vw.R[6 + k];
     }
-    // Sigma3D from the attribute maps interpolated at I_uv (Eq. 5)
+    // Sigma3D from the attribute maps interpolated at I_uv (Eq. 5); maps of leg
+    // resolution 1 hold one texel, so Sigma3D is the primitive's
     float S3[6];
-    {
+    if (p.attr_res == 1) {
+#pragma unroll
+      for (int k = 0; k < 6; k++) S3[k] = w.prim_cov[6 * (size_t)prim + k];
+    } else {
       float qa[4], ls[3], Rm[9], sc3[3], tw[3];
       int tex[3];
       gauss_attrs(s.quat, s.log_scale, p.attr_res, p.ntex, prim, uv.x, uv.y, qa, ls, tex, tw);
@@ -282,6 +286,27 @@ __global__ void __launch_bounds__(256) k_sh_color(Params p, Scene s, Work w) {
     }
     w.gC[i] = C;
   }
+}
+
+// Sigma3D of every primitive whose rotation / scaling maps hold one texel
+// (leg resolution 1), shared by its Gaussians
+__global__ void k_prim_cov(Params p, Scene s, Work w) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= p.M) return;
+  float qa[4], ls[3], Rm[9], sc3[3], S3[6];
+#pragma unroll
+  for (int k = 0; k < 4; k++) qa[k] = s.quat[4 * (size_t)m + k];
+#pragma unroll
+  for (int k = 0; k < 3; k++) ls[k] = s.log_scale[3 * (size_t)m + k];
+  cov3d_f32(qa, ls, S3, Rm, sc3);
+#pragma unroll
+  for (int k = 0; k < 6; k++) w.prim_cov[6 * (size_t)m + k] = S3[k];
+}
+
+int launch_prim_cov(const Params &p, const Scene &s, const Work &w, cudaStream_t st) {
+  if (p.attr_res != 1 || p.M == 0) return 0;
+  k_prim_cov<<<(p.M + 255) / 256, 256, 0, st>>>(p, s, w);
+  return 1;
 }
 
 int launch_generate(const Params &p, const Scene &s, const Work &w, cudaStream_t st) {
