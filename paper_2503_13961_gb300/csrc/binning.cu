@@ -308,11 +308,13 @@ __device__ __forceinline__ void warp_bitonic_smem(unsigned long long *sk, int N,
 }
 
 // Stable LSD radix sort (8-bit digits) of sk[0, n) (n <= kWarpSortCap) by
-// one warp: the keys sit in registers, key i in lane i % 32, slot i / 32; each
-// pass histograms the digit into `bins`, scans it and scatters the keys back
-// to sk in order, ranking equal digits of a round with a match; digits that
-// are equal over the whole segment are skipped.
-__device__ __forceinline__ void warp_radix_smem(unsigned long long *sk, unsigned *bins, int n, int lane) {
+// one warp on the key bits from lo_shift up: the keys sit in registers, key i
+// in lane i % 32, slot i / 32; each pass histograms the digit into `bins`,
+// scans it and scatters the keys back to sk in order, ranking equal digits of
+// a round with a match; digits that are equal over the whole segment are
+// skipped. Keys equal above lo_shift keep their input order.
+__device__ __forceinline__ void warp_radix_smem(unsigned long long *sk, unsigned *bins, int n, int lane,
+                                                int lo_shift) {
   constexpr int R = kWarpSortCap / 32;
   const int rounds = (n + 31) >> 5;
   const unsigned lt = (1u << lane) - 1u;
@@ -333,7 +335,7 @@ __device__ __forceinline__ void warp_radix_smem(unsigned long long *sk, unsigned
     vand &= __shfl_xor_sync(0xffffffffu, vand, o);
   }
   const unsigned long long varying = vor ^ vand;
-  for (int shift = 0; shift < 64; shift += 8) {
+  for (int shift = lo_shift; shift < 64; shift += 8) {
     if (((varying >> shift) & 0xffull) == 0ull) continue;
     for (int d = lane; d < 256; d += 32) bins[d] = 0u;
     __syncwarp();
@@ -422,8 +424,20 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_tile_sort(Params p, Work w,
       while (N < n) N <<= 1;
       for (int i = lane; i < N; i += 32) sk[i] = i < n ? keys[i] : ~0ull;
       __syncwarp();
-      if (n >= kRadixMin) warp_radix_smem(sk, bins, n, lane);
-      else warp_bitonic_smem(sk, N, lane);
+      if (n < kRadixMin) {
+        warp_bitonic_smem(sk, N, lane);
+      } else if (bnd) {
+        warp_radix_smem(sk, bins, n, lane, 0);
+      } else {
+        // Gaussian keys by their depth bits only (the index below them just
+        // breaks ties); a tie left in emission order is rare and then the
+        // full keys go through the bitonic network, so the order is the
+        // (tile, depth, index) order either way
+        warp_radix_smem(sk, bins, n, lane, kIndexBits);
+        bool tie = false;
+        for (int i = lane; i + 1 < n; i += 32) tie |= ((sk[i] ^ sk[i + 1]) >> kIndexBits) == 0ull;
+        if (__any_sync(0xffffffffu, tie)) warp_bitonic_smem(sk, N, lane);
+      }
       for (int i = lane; i < n; i += 32) keys[i] = sk[i];
       __syncwarp();
     }
