@@ -9,16 +9,19 @@
 // I_id and perspective-correct I_uv.
 //
 // Grid: one block row per view (blockIdx.y), warps take primitives of that
-// view. Per block, the Bernstein weights of the (L+1)(L+2)/2 lattice vertices
-// and the vertex slots of the L^2 flat triangles are tabulated once in shared
-// memory. Per primitive, the lanes evaluate its lattice vertices from the
-// table and its control points (held in registers) into shared memory; then
-// each lane rasterizes its flat triangles: an empty pixel box is rejected
-// before any edge function, and the pixel centres of the box are walked with
-// incrementally updated edge functions, in 32-bit integers when the box is
-// under 125 px (exact: every product stays below 2^30) and in 64-bit ones
-// otherwise. Every operation that decides coverage or the depth order is an
-// explicit IEEE-rounded intrinsic, so the result is reproducible bit for bit.
+// view two at a time. Per block, the Bernstein weights of the (L+1)(L+2)/2
+// lattice vertices and the vertex slots of the L^2 flat triangles are
+// tabulated once in shared memory. Per pair of primitives, the lanes evaluate
+// the lattice vertices of both from the table and their control points (in
+// shared memory) into shared memory (2 x 45 vertices at L = 8 fill three
+// rounds of 32 lanes where one primitive alone leaves the second of two
+// rounds mostly idle); then each lane rasterizes its flat triangles: an empty
+// pixel box is rejected before any edge function, and the pixel centres of the
+// box are walked in one loop with incrementally updated edge functions, in
+// 32-bit integers when the box is under 125 px (exact: every product stays
+// below 2^30) and in 64-bit ones otherwise. Every operation that decides
+// coverage or the depth order is an explicit IEEE-rounded intrinsic, so the
+// result is reproducible bit for bit.
 #include <climits>
 
 #include "bgt_internal.cuh"
@@ -61,7 +64,8 @@ __device__ __forceinline__ void depth_test(float f0, float f1, float f2, float a
 // Pixel centres of the box [px0, px1] x [py0, py1] inside the flat triangle
 // (X, Y, IZ) (counter-clockwise after the swap, area2 > 0, fill-rule flags
 // t0..t2 of the edges 1-2, 2-0, 0-1): edge functions (b - a) x (P - a) start
-// at the box corner and step by their constant differences; I is int when
+// at the box corner and step by their constant differences, row by row in one
+// loop (lanes with boxes of different shapes stay in step); I is int when
 // every value stays below 2^31 (box span < kSpan32), else long long. Covered
 // pixels take the depth test.
 template <typename I>
@@ -77,19 +81,29 @@ __device__ __forceinline__ void raster_box(const int *X, const int *Y, const flo
   I r2 = a2 * (I)(Py0 - Y[0]) - b2 * (I)(Px0 - X[0]);
   const I sx0 = b0 * (I)256, sx1 = b1 * (I)256, sx2 = b2 * (I)256;  // per pixel step in x (subtracted)
   const I sy0 = a0 * (I)256, sy1 = a1 * (I)256, sy2 = a2 * (I)256;  // per pixel step in y (added)
-  for (int py = py0; py <= py1; py++) {
-    I e0 = r0, e1 = r1, e2 = r2;
-    for (int px = px0; px <= px1; px++) {
-      if ((e0 > 0 || (e0 == 0 && t0)) && (e1 > 0 || (e1 == 0 && t1)) && (e2 > 0 || (e2 == 0 && t2))) {
-        depth_test(to_f32(e0), to_f32(e1), to_f32(e2), af, IZ, py * W + px, gid, zb);
-      }
+  // one loop over the box's pixel centres, row by row
+  const int n = (px1 - px0 + 1) * (py1 - py0 + 1);
+  I e0 = r0, e1 = r1, e2 = r2;
+  int px = px0, pix = py0 * W + px0;
+  for (int k = 0; k < n; k++) {
+    if ((e0 > 0 || (e0 == 0 && t0)) && (e1 > 0 || (e1 == 0 && t1)) && (e2 > 0 || (e2 == 0 && t2)))
+      depth_test(to_f32(e0), to_f32(e1), to_f32(e2), af, IZ, pix, gid, zb);
+    if (px < px1) {
+      px++;
+      pix++;
       e0 -= sx0;
       e1 -= sx1;
       e2 -= sx2;
+    } else {
+      r0 += sy0;
+      r1 += sy1;
+      r2 += sy2;
+      e0 = r0;
+      e1 = r1;
+      e2 = r2;
+      pix += W - (px1 - px0);
+      px = px0;
     }
-    r0 += sy0;
-    r1 += sy1;
-    r2 += sy2;
   }
 }
 
@@ -98,9 +112,10 @@ __global__ void __launch_bounds__(kRasterWarps * 32, N <= 2 ? 8 : 6) k_raster(Pa
   constexpr int NCP = (N + 1) * (N + 2) / 2;
   __shared__ float sB[kMaxVerts * NCP];  // Bernstein weights of the lattice vertices
   __shared__ int2 s_tri[kMaxTess * kMaxTess];  // vertex slots (8 bits each) and sub-triangle id
-  __shared__ int sX[kRasterWarps][kMaxVerts];
-  __shared__ int sY[kRasterWarps][kMaxVerts];
-  __shared__ float sIZ[kRasterWarps][kMaxVerts];
+  __shared__ int sX[kRasterWarps][2 * kMaxVerts];
+  __shared__ int sY[kRasterWarps][2 * kMaxVerts];
+  __shared__ float sIZ[kRasterWarps][2 * kMaxVerts];
+  __shared__ __align__(16) float sC[kRasterWarps][2][3 * NCP + 2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int L = p.L;
   const int NV = (L + 1) * (L + 2) / 2;
@@ -136,18 +151,25 @@ __global__ void __launch_bounds__(kRasterWarps * 32, N <= 2 ? 8 : 6) k_raster(Pa
   const View vw = w.views[blockIdx.y];
   const int W = vw.W, H = vw.H;
   unsigned long long *zb = w.zbuf + vw.pix_off;
-  for (int prim = blockIdx.x * kRasterWarps + warp; prim < p.M; prim += gridDim.x * kRasterWarps) {
-    const float *cp = s.ctrl + (size_t)prim * NCP * 3;
-    float c[3 * NCP];
-#pragma unroll
-    for (int k = 0; k < 3 * NCP; k++) c[k] = __ldg(cp + k);
-    for (int vi = lane; vi < NV; vi += 32) {
-      const RVert r = vertex_from_weights<N>(sB + vi * NCP, c, vw, p.near_z);
+  const int stride = gridDim.x * kRasterWarps;
+  for (int prim0 = blockIdx.x * kRasterWarps + warp; prim0 < p.M; prim0 += 2 * stride) {
+    const int nitem = prim0 + stride < p.M ? 2 : 1;
+    for (int k = lane; k < nitem * 3 * NCP; k += 32) {
+      const int it = k >= 3 * NCP;
+      sC[warp][it][k - it * 3 * NCP] = __ldg(s.ctrl + (size_t)(prim0 + it * stride) * NCP * 3 + (k - it * 3 * NCP));
+    }
+    __syncwarp();
+    for (int vi = lane; vi < nitem * NV; vi += 32) {
+      const int it = vi >= NV;
+      const RVert r = vertex_from_weights<N>(sB + (vi - it * NV) * NCP, sC[warp][it], vw, p.near_z);
       sX[warp][vi] = r.valid ? r.X : INT_MIN;
       sY[warp][vi] = r.Y;
       sIZ[warp][vi] = r.iz;
     }
     __syncwarp();
+    for (int it = 0; it < nitem; it++) {
+    const int prim = prim0 + it * stride;
+    const int vb = it * NV;
     for (int ti = lane; ti < L * L; ti += 32) {
       const int2 tri = s_tri[ti];
       int X[3], Y[3];
@@ -155,7 +177,7 @@ __global__ void __launch_bounds__(kRasterWarps * 32, N <= 2 ? 8 : 6) k_raster(Pa
       bool ok = true;
 #pragma unroll
       for (int k = 0; k < 3; k++) {
-        const int sl = (tri.x >> (8 * k)) & 0xff;
+        const int sl = vb + ((tri.x >> (8 * k)) & 0xff);
         X[k] = sX[warp][sl];
         Y[k] = sY[warp][sl];
         IZ[k] = sIZ[warp][sl];
@@ -185,6 +207,7 @@ __global__ void __launch_bounds__(kRasterWarps * 32, N <= 2 ? 8 : 6) k_raster(Pa
         raster_box<int>(X, Y, IZ, t0, t1, t2, af, px0, px1, py0, py1, gid, zb, W);
       else
         raster_box<long long>(X, Y, IZ, t0, t1, t2, af, px0, px1, py0, py1, gid, zb, W);
+    }
     }
     __syncwarp();
   }
