@@ -121,7 +121,7 @@ void carve(bgt_handle *h, char *base, size_t *total) {
   w.b_tcount = c.take<int>(T + 1);
   w.b_tstart = c.take<long long>(T + 1);
   w.b_tfill = c.take<int>(T + 1);
-  const long long naux = std::max<long long>(T, h->nblk_cap) / 4096 + 4;
+  const long long naux = std::max<long long>(std::max<long long>(T, h->nblk_cap), h->Mcap) / 4096 + 4;
   w.scan_aux = c.take<long long>(2 * naux);
   w.scan_aux2 = w.scan_aux ? w.scan_aux + naux : nullptr;
   w.big_list = c.take<int>(2 * (long long)T + 2);
@@ -141,6 +141,12 @@ void carve(bgt_handle *h, char *base, size_t *total) {
   w.prim_gcov = c.take<float>(6 * (long long)h->Mcap);
   w.gg = c.take<float>(12 * F);
   w.bg_grad = c.take<float4>(F);
+  w.prim_gcnt = c.take<int>(h->Mcap);
+  w.prim_bcnt = c.take<int>(h->Mcap);
+  w.prim_gseg = c.take<long long>((long long)h->Mcap + 1);
+  w.prim_bseg = c.take<long long>((long long)h->Mcap + 1);
+  w.pg_rec = c.take<float4>(4 * F);
+  w.pb_rec = c.take<float4>(2 * F);
   w.Fcap = F;
   w.nblk = h->nblk_cap;
   w.views = h->d_views;
@@ -302,7 +308,6 @@ cudaError_t enqueue_bwd(bgt_handle *h, const bgt::Params &p, const bgt::Scene &s
     if (g.log_scale) cudaMemsetAsync(g.log_scale, 0, sizeof(float) * 3 * (size_t)p.M * p.ntex, st);
     if (g.quat) cudaMemsetAsync(g.quat, 0, sizeof(float) * 4 * (size_t)p.M * p.ntex, st);
     if (g.sh && p.sh_k > 0) cudaMemsetAsync(g.sh, 0, sizeof(float) * 3 * (size_t)p.M * p.sh_k, st);
-    if (p.attr_res == 1 && (g.log_scale || g.quat)) cudaMemsetAsync(w.prim_gcov, 0, sizeof(float) * 6 * (size_t)p.M, st);
   }
   int k = bgt::launch_composite_bwd(p, w, dimg, st);
   mark(h, 8, st);

@@ -168,6 +168,12 @@ struct Work {
                               // s dx dy, s dy^2, s (= dl/do), dl/dcolour r, g, b; pad (dl/dmu = o K (s d),
                               // dl/dK = -o/2 (s dx^2, 2 s dx dy, s dy^2) are formed per Gaussian)
   float4 *bg_grad;            // [Fcap] (db x, db y, dsigma, 0)
+  // per-primitive gradient records of the chain rule: each Gaussian's and
+  // each boundary point's dl/dS (and the rest) in its primitive's segment
+  int *prim_gcnt, *prim_bcnt;     // [Mcap] records per primitive, then fill counters
+  long long *prim_gseg, *prim_bseg;  // [Mcap + 1] segment starts
+  float4 *pg_rec;             // [Fcap][4] Gaussian: (dl/dS, dl/do), (dl/dc, u), (v, dl/dSigma3D xx xy xz), (yy yz zz, 0)
+  float4 *pb_rec;             // [Fcap][2] boundary point: (dl/dS, dl/dr_b), (u, v, 0, 0)
   unsigned long long *stats;  // [8] work units of the last profiled call (see Stat)
   long long Fcap;
   int nblk;

@@ -9,10 +9,15 @@
 //   dl/dSigma2D = -K (dl/dK) K, dl/d(JW) = 2 dl/dSigma2D (JW) Sigma3D,
 //   dl/dJ = dl/d(JW) W^T, J depends on t; dl/dS_q = W^T dl/dt.
 // Boundary point b = projection of S_b, sigma = k_b fx r_b / z_b.
-// Control-point, colour and opacity gradients of consecutive Gaussians (which
-// mostly share a primitive, being compacted in pixel order) are summed per
-// run of equal primitive through shared memory before one atomic per run and
-// value.
+// Two passes take these to the primitives: pass one (one thread per Gaussian,
+// one per boundary point) computes dl/dS_q and the other per-record
+// gradients and writes them, with the record's (u, v), into its primitive's
+// segment of a record array (segments from a count and a scan over the
+// primitives); pass two sums each primitive's records with their Bernstein
+// weights. A primitive covers a few pixels of a view, so records in pixel
+// order change primitive every two or so; grouped, a primitive's records of
+// all views are contiguous and its sums take a few atomics instead of one
+// per short run and value.
 #include "bgt_internal.cuh"
 
 namespace bgt {
@@ -67,8 +72,6 @@ constexpr int kChainWarps = 8;
 template <int N>
 __global__ void __launch_bounds__(256) k_chain_gauss(Params p, Scene s, Work w, Grads out) {
   constexpr int m = SurfPoint<N>::M;
-  __shared__ float s_rows[kChainWarps][32 * ((3 * m + 7) | 1)];
-  float *sw = s_rows[threadIdx.x >> 5];
   const int F = w.counters[kF];
   const int lane = threadIdx.x & 31;
   const int warps_total = gridDim.x * (blockDim.x >> 5);
@@ -82,6 +85,7 @@ __global__ void __launch_bounds__(256) k_chain_gauss(Params p, Scene s, Work w, 
     int tex[3] = {0, 0, 0};
     float tw[3] = {0.f, 0.f, 0.f};
     float B[m];
+    float2 uv = make_float2(0.f, 0.f);
     if (active) {
       const float *gg = w.gg + 12 * (size_t)i;
       const float4 q0 = reinterpret_cast<const float4 *>(gg)[0];
@@ -94,9 +98,9 @@ __global__ void __launch_bounds__(256) k_chain_gauss(Params p, Scene s, Work w, 
       const float gmx = gd[0], gmy = gd[1], gKa = gd[2], gKb = gd[3], gKc = gd[4];
       gop = gd[5];
       gcol[0] = gd[6]; gcol[1] = gd[7]; gcol[2] = gd[8];
-      g = __float_as_int(w.gC[i].w);
+      g = w.g_prim[i];
       const View vw = w.views[w.g_view[i]];
-      const float2 uv = w.g_uv[i];
+      uv = w.g_uv[i];
       float t[3];
       camera_point_f32<N>(s.ctrl + (size_t)g * m * 3, uv.x, uv.y, vw, B, t);
       const bool any = gmx != 0.f || gmy != 0.f || gKa != 0.f || gKb != 0.f || gKc != 0.f;
@@ -174,38 +178,20 @@ __global__ void __launch_bounds__(256) k_chain_gauss(Params p, Scene s, Work w, 
         for (int k = 0; k < 3; k++) gS[k] = vw.R[k] * gt0 + vw.R[3 + k] * gt1 + vw.R[6 + k] * gt2;
       }
     }
-    const bool nz = active && (gS[0] != 0.f || gS[1] != 0.f || gS[2] != 0.f || gcol[0] != 0.f ||
-                               gcol[1] != 0.f || gcol[2] != 0.f || gop != 0.f);
-    if (!__any_sync(0xffffffffu, nz)) continue;
     const bool per_prim_cov = p.attr_res == 1 && (out.log_scale || out.quat);
-    {
-      // control points, opacity and (leg resolution 1) dl/dSigma3D, then colour
-      // control points (Eq. 3, 4: dl/dp = sum B dl/dS)
-      float v[3 * m + 7];
-#pragma unroll
-      for (int a = 0; a < m; a++)
-#pragma unroll
-        for (int c = 0; c < 3; c++) v[3 * a + c] = nz ? B[a] * gS[c] : 0.f;
-      v[3 * m] = nz ? gop : 0.f;
-      float *gctrl = out.ctrl, *gopa = out.opacity, *gcov = w.prim_gcov;
-      if (per_prim_cov) {
-#pragma unroll
-        for (int k = 0; k < 6; k++) v[3 * m + 1 + k] = nz ? gc6[k] : 0.f;
-        scatter_runs<3 * m + 7>(sw, v, nz ? g : -1, [&](int gg, int j) {
-          return j < 3 * m ? gctrl + (size_t)gg * 3 * m + j
-                           : (j == 3 * m ? gopa + gg : gcov + 6 * (size_t)gg + (j - 3 * m - 1));
-        });
-      } else {
-        scatter_runs<3 * m + 1>(sw, v, nz ? g : -1, [&](int gg, int j) {
-          return j < 3 * m ? gctrl + (size_t)gg * 3 * m + j : gopa + gg;
-        });
-      }
-#pragma unroll
-      for (int a = 0; a < m; a++)
-#pragma unroll
-        for (int c = 0; c < 3; c++) v[3 * a + c] = nz ? B[a] * gcol[c] : 0.f;
-      float *gcolor = out.color;
-      scatter_runs<3 * m>(sw, v, nz ? g : -1, [&](int gg, int j) { return gcolor + (size_t)gg * 3 * m + j; });
+    // the Gaussian's record in its primitive's segment (the per-primitive sum
+    // takes it to the control points, colour control points and opacity)
+    if (active) {
+      const unsigned peers = __match_any_sync(__activemask(), g);
+      const int leader = __ffs(peers) - 1;
+      int b0 = 0;
+      if (lane == leader) b0 = atomicAdd(w.prim_gcnt + g, __popc(peers));
+      b0 = __shfl_sync(peers, b0, leader);
+      float4 *r = w.pg_rec + 4 * (w.prim_gseg[g] + b0 + __popc(peers & ((1u << lane) - 1u)));
+      r[0] = make_float4(gS[0], gS[1], gS[2], gop);
+      r[1] = make_float4(gcol[0], gcol[1], gcol[2], uv.x);
+      r[2] = make_float4(uv.y, gc6[0], gc6[1], gc6[2]);
+      r[3] = make_float4(gc6[3], gc6[4], gc6[5], __int_as_float(g));
     }
     if ((out.log_scale || out.quat) && !per_prim_cov) {
       // the map texels of the interpolation, with their weights; runs of equal
@@ -258,7 +244,7 @@ __global__ void __launch_bounds__(256) k_chain_sh(Params p, Scene s, Work w, Gra
       gcol[0] = gg[6];
       gcol[1] = gg[7];
       gcol[2] = gg[8];
-      g = __float_as_int(w.gC[i].w);
+      g = w.g_prim[i];
       const View vw = w.views[w.g_view[i]];
       const float2 uv = w.g_uv[i];
       float t[3], dv[3];
@@ -312,47 +298,318 @@ __global__ void __launch_bounds__(256) k_chain_sh(Params p, Scene s, Work w, Gra
 template <int N>
 __global__ void __launch_bounds__(256) k_chain_bnd(Params p, Scene s, Work w, Grads out) {
   constexpr int m = SurfPoint<N>::M;
-  __shared__ float s_rows[kChainWarps][32 * ((3 * m + 1) | 1)];
-  float *sw = s_rows[threadIdx.x >> 5];
   const int Nb = w.counters[kNb];
   const int lane = threadIdx.x & 31;
   const int warps_total = gridDim.x * (blockDim.x >> 5);
   for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < Nb; base += warps_total * 32) {
     const int i = base + lane;
-    bool nz = false;
-    int g = -1;
+    if (i >= Nb) continue;
+    const int g = w.b_prim[i];
+    const float2 uv = w.b_uv[i];
     float gS[3] = {0.f, 0.f, 0.f}, grb = 0.f;
-    float B[m];
-    if (i < Nb) {
-      const float4 gb = w.bg_grad[i];
-      nz = gb.x != 0.f || gb.y != 0.f || gb.z != 0.f;
-      if (nz) {
-        g = w.b_prim[i];
-        const View vw = w.views[w.b_view[i]];
-        const float2 uv = w.b_uv[i];
-        float t[3];
-        camera_point_f32<N>(s.ctrl + (size_t)g * m * 3, uv.x, uv.y, vw, B, t);
-        const float tz = w.b_z[i], sigma = w.b_sigma[i];
-        const float iz = 1.0f / tz, iz2 = iz * iz;
-        const float gt0 = gb.x * vw.fx * iz;
-        const float gt1 = gb.y * vw.fy * iz;
-        const float gt2 = -gb.x * vw.fx * t[0] * iz2 - gb.y * vw.fy * t[1] * iz2 - gb.z * sigma * iz;
-        grb = gb.z * p.k_b * vw.fx * iz;
+    const float4 gb = w.bg_grad[i];
+    if (gb.x != 0.f || gb.y != 0.f || gb.z != 0.f) {
+      const View vw = w.views[w.b_view[i]];
+      float t[3], B[m];
+      camera_point_f32<N>(s.ctrl + (size_t)g * m * 3, uv.x, uv.y, vw, B, t);
+      const float tz = w.b_z[i], sigma = w.b_sigma[i];
+      const float iz = 1.0f / tz, iz2 = iz * iz;
+      const float gt0 = gb.x * vw.fx * iz;
+      const float gt1 = gb.y * vw.fy * iz;
+      const float gt2 = -gb.x * vw.fx * t[0] * iz2 - gb.y * vw.fy * t[1] * iz2 - gb.z * sigma * iz;
+      grb = gb.z * p.k_b * vw.fx * iz;
 #pragma unroll
-        for (int k = 0; k < 3; k++) gS[k] = vw.R[k] * gt0 + vw.R[3 + k] * gt1 + vw.R[6 + k] * gt2;
+      for (int k = 0; k < 3; k++) gS[k] = vw.R[k] * gt0 + vw.R[3 + k] * gt1 + vw.R[6 + k] * gt2;
+    }
+    // the boundary point's record in its primitive's segment
+    const unsigned peers = __match_any_sync(__activemask(), g);
+    const int leader = __ffs(peers) - 1;
+    int b0 = 0;
+    if (lane == leader) b0 = atomicAdd(w.prim_bcnt + g, __popc(peers));
+    b0 = __shfl_sync(peers, b0, leader);
+    float4 *r = w.pb_rec + 2 * (w.prim_bseg[g] + b0 + __popc(peers & ((1u << lane) - 1u)));
+    r[0] = make_float4(gS[0], gS[1], gS[2], grb);
+    r[1] = make_float4(uv.x, uv.y, __int_as_float(g), 0.f);
+  }
+}
+
+// records per primitive: its Gaussians and its boundary points; the lanes of
+// a warp with the same primitive add their count with one atomic
+__global__ void k_prim_count(Work w) {
+  const int F = w.counters[kF], Nb = w.counters[kNb];
+  const int lane = threadIdx.x & 31;
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < F + Nb; i += stride) {
+    const bool gs = i < F;
+    const int g = gs ? w.g_prim[i] : w.b_prim[i - F];
+    const unsigned peers = __match_any_sync(__activemask(), gs ? g : -1 - g);
+    if (lane == __ffs(peers) - 1) atomicAdd((gs ? w.prim_gcnt : w.prim_bcnt) + g, __popc(peers));
+  }
+}
+
+constexpr int kSumCols = 15;   // staged row: dl/dS (3), dl/do, dl/dc (3), dl/dSigma3D (6), dl/dr_b, primitive
+constexpr int kSumChunk = 256; // records per work item of the per-primitive sums
+
+// Per-primitive sums of the records, which pass one left grouped by primitive:
+// dl/dp_a = sum_q B_a(u_q, v_q) dl/dS_q over the primitive's Gaussians and
+// boundary points (Eq. 3, supplementary), dl/dc_a = sum B_a dl/dc_q (Eq. 4),
+// dl/do, dl/dr_b and dl/dSigma3D as plain sums. Warps take chunks of
+// kSumChunk records (Gaussian records, then boundary records) and stage 32 at
+// a time in shared memory with their Bernstein weights; lane j owns outputs
+// j, j + 32, ... (3m control-point, 3m colour values, opacity, r_b, 6
+// Sigma3D) and sums them along the run of the current primitive, adding the
+// run's sum with one atomic when the primitive changes and at the chunk's end.
+template <int N>
+__global__ void __launch_bounds__(256) k_prim_sum(Params p, Work w, Grads out, int with_cov) {
+  constexpr int m = SurfPoint<N>::M;
+  constexpr int RS = (kSumCols + m) | 1;  // row stride (odd: conflict-free row writes)
+  constexpr int NO = 6 * m + 8;           // outputs
+  constexpr int NQ = (NO + 31) / 32;
+  __shared__ float s_rows[kChainWarps][32 * RS];
+  float *rows = s_rows[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const int F = w.counters[kF], Nb = w.counters[kNb];
+  // this lane's outputs: value column, Bernstein column (-1: weight 1) and destination
+  int vcol[NQ], bcol[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; q++) {
+    const int j = q * 32 + lane;
+    vcol[q] = -1;
+    bcol[q] = -1;
+    if (j < 3 * m) {
+      vcol[q] = j % 3;
+      bcol[q] = kSumCols + j / 3;
+    } else if (j < 6 * m) {
+      vcol[q] = 4 + (j - 3 * m) % 3;
+      bcol[q] = kSumCols + (j - 3 * m) / 3;
+    } else if (j == 6 * m) {
+      vcol[q] = 3;
+    } else if (j == 6 * m + 1) {
+      vcol[q] = 13;
+    } else if (j < NO && with_cov) {
+      vcol[q] = 7 + (j - 6 * m - 2);
+    }
+  }
+  auto flush = [&](int g, const float *acc) {
+#pragma unroll
+    for (int q = 0; q < NQ; q++) {
+      const int j = q * 32 + lane;
+      if (vcol[q] < 0 || acc[q] == 0.f) continue;
+      float *dst = j < 3 * m ? out.ctrl + (size_t)g * 3 * m + j
+                   : j < 6 * m ? out.color + (size_t)g * 3 * m + (j - 3 * m)
+                   : j == 6 * m ? out.opacity + g
+                   : j == 6 * m + 1 ? out.r_b + g
+                   : w.prim_gcov + 6 * (size_t)g + (j - 6 * m - 2);
+      atomicAdd(dst, acc[q]);
+    }
+  };
+  const long long ng = (F + kSumChunk - 1) / kSumChunk, nchunks = ng + (Nb + kSumChunk - 1) / kSumChunk;
+  const int warps_total = gridDim.x * (blockDim.x >> 5);
+  for (long long ck = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ck < nchunks; ck += warps_total) {
+    const bool bnd = ck >= ng;
+    const long long r0 = (bnd ? ck - ng : ck) * kSumChunk;
+    const long long r1 = min(r0 + kSumChunk, (long long)(bnd ? Nb : F));
+    float acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; q++) acc[q] = 0.f;
+    int gcur = -1;
+    // this lane's record of the round, loaded one round ahead
+    float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra, rc = ra, rd = ra;
+    auto load = [&](long long c) {
+      if (c + lane < r1) {
+        if (!bnd) {
+          const float4 *r = w.pg_rec + 4 * (c + lane);
+          ra = r[0]; rb = r[1]; rc = r[2]; rd = r[3];
+        } else {
+          const float4 *r = w.pb_rec + 2 * (c + lane);
+          ra = r[0]; rb = r[1];
+        }
+      }
+    };
+    load(r0);
+    for (long long c0 = r0; c0 < r1; c0 += 32) {
+      float *row = rows + lane * RS;
+      float val[kSumCols];
+#pragma unroll
+      for (int k = 0; k < kSumCols; k++) val[k] = 0.f;
+      float u = 0.f, v = 0.f;
+      if (c0 + lane < r1) {
+        if (!bnd) {
+          val[0] = ra.x; val[1] = ra.y; val[2] = ra.z; val[3] = ra.w;
+          val[4] = rb.x; val[5] = rb.y; val[6] = rb.z;
+          val[7] = rc.y; val[8] = rc.z; val[9] = rc.w;
+          val[10] = rd.x; val[11] = rd.y; val[12] = rd.z; val[14] = rd.w;
+          u = rb.w;
+          v = rc.x;
+        } else {
+          val[0] = ra.x; val[1] = ra.y; val[2] = ra.z; val[13] = ra.w; val[14] = rb.z;
+          u = rb.x;
+          v = rb.y;
+        }
+      }
+      load(c0 + 32);
+      float B[m];
+      bernstein_f32<N>(u, v, B);
+#pragma unroll
+      for (int k = 0; k < kSumCols; k++) row[k] = val[k];
+#pragma unroll
+      for (int a = 0; a < m; a++) row[kSumCols + a] = B[a];
+      const int nr = (int)min(32ll, r1 - c0);
+      // the round's runs of equal primitive (rows are sorted by primitive):
+      // each run is summed without a per-row test, the previous run flushed
+      // when the primitive changes
+      const int gl = __float_as_int(val[14]);
+      const int gp = __shfl_up_sync(0xffffffffu, gl, 1);
+      unsigned heads = __ballot_sync(0xffffffffu, lane < nr && (lane == 0 || gp != gl));
+      __syncwarp();
+      while (heads) {
+        const int s0 = __ffs(heads) - 1;
+        heads &= heads - 1;
+        const int s1 = heads ? __ffs(heads) - 1 : nr;
+        const int g = __float_as_int(rows[s0 * RS + 14]);
+        if (g != gcur) {
+          if (gcur >= 0) flush(gcur, acc);
+#pragma unroll
+          for (int q = 0; q < NQ; q++) acc[q] = 0.f;
+          gcur = g;
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+          if (vcol[q] < 0) continue;
+          float sum = acc[q];
+          if (s1 - s0 == 32) {
+            if (bcol[q] >= 0) {
+#pragma unroll
+              for (int r = 0; r < 32; r++) sum = fmaf(rows[r * RS + bcol[q]], rows[r * RS + vcol[q]], sum);
+            } else {
+#pragma unroll
+              for (int r = 0; r < 32; r++) sum += rows[r * RS + vcol[q]];
+            }
+          } else if (bcol[q] >= 0) {
+            for (int r = s0; r < s1; r++) sum = fmaf(rows[r * RS + bcol[q]], rows[r * RS + vcol[q]], sum);
+          } else {
+            for (int r = s0; r < s1; r++) sum += rows[r * RS + vcol[q]];
+          }
+          acc[q] = sum;
+        }
+      }
+      __syncwarp();
+    }
+    if (gcur >= 0) flush(gcur, acc);
+  }
+}
+
+// The per-primitive sums of k_prim_sum for degrees whose outputs fit in
+// registers (6m + 8 <= 44 at degree 2): lane i owns record slot i of each
+// round of 32 and adds its record's weighted values to its own 6m + 8
+// accumulators over the rounds of a run of equal primitive; when the
+// primitive changes (and at the chunk's end) a reduce-scatter over the warp
+// (shuffle butterfly, 62 exchanges) leaves outputs 2i and 2i + 1 in lane i,
+// which adds them with one atomic each. Same sums as k_prim_sum, with a
+// shuffle exchange per run instead of a shared-memory pass per round.
+template <int N>
+__global__ void __launch_bounds__(256, 2) k_prim_sum_reg(Params p, Work w, Grads out) {
+  constexpr int m = SurfPoint<N>::M;
+  constexpr int NO = 6 * m + 8;
+  static_assert(NO <= 64, "outputs beyond two per lane");
+  const int lane = threadIdx.x & 31;
+  const int F = w.counters[kF], Nb = w.counters[kNb];
+  float acc[64];
+  auto reduce_flush = [&](int g) {
+#pragma unroll
+    for (int off = 16, H = 32; off > 0; off >>= 1, H >>= 1) {
+      const bool hb = (lane & off) != 0;
+#pragma unroll
+      for (int i = 0; i < H; i++) {
+        const float send = hb ? acc[i] : acc[i + H];
+        const float keep = hb ? acc[i + H] : acc[i];
+        acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
       }
     }
-    if (!__any_sync(0xffffffffu, nz)) continue;
-    float v[3 * m + 1];
 #pragma unroll
-    for (int a = 0; a < m; a++)
+    for (int i = 0; i < 2; i++) {
+      const int j = 2 * lane + i;
+      if (j < NO && acc[i] != 0.f) {
+        float *dst = j < 3 * m ? out.ctrl + (size_t)g * 3 * m + j
+                     : j < 6 * m ? out.color + (size_t)g * 3 * m + (j - 3 * m)
+                     : j == 6 * m ? out.opacity + g
+                     : j == 6 * m + 1 ? out.r_b + g
+                     : w.prim_gcov + 6 * (size_t)g + (j - 6 * m - 2);
+        atomicAdd(dst, acc[i]);
+      }
+    }
 #pragma unroll
-      for (int c = 0; c < 3; c++) v[3 * a + c] = nz ? B[a] * gS[c] : 0.f;
-    v[3 * m] = nz ? grb : 0.f;
-    float *gctrl = out.ctrl, *grbp = out.r_b;
-    scatter_runs<3 * m + 1>(sw, v, nz ? g : -1, [&](int gg, int j) {
-      return j < 3 * m ? gctrl + (size_t)gg * 3 * m + j : grbp + gg;
-    });
+    for (int i = 0; i < 64; i++) acc[i] = 0.f;
+  };
+  const long long ng = (F + kSumChunk - 1) / kSumChunk, nchunks = ng + (Nb + kSumChunk - 1) / kSumChunk;
+  const int warps_total = gridDim.x * (blockDim.x >> 5);
+  for (long long ck = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ck < nchunks; ck += warps_total) {
+    const bool bnd = ck >= ng;
+    const long long r0 = (bnd ? ck - ng : ck) * kSumChunk;
+    const long long r1 = min(r0 + kSumChunk, (long long)(bnd ? Nb : F));
+#pragma unroll
+    for (int i = 0; i < 64; i++) acc[i] = 0.f;
+    int gcur = -1;
+    float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra, rc = ra, rd = ra;
+    auto load = [&](long long c) {
+      if (c + lane < r1) {
+        if (!bnd) {
+          const float4 *r = w.pg_rec + 4 * (c + lane);
+          ra = r[0]; rb = r[1]; rc = r[2]; rd = r[3];
+        } else {
+          const float4 *r = w.pb_rec + 2 * (c + lane);
+          ra = r[0]; rb = r[1];
+        }
+      }
+    };
+    load(r0);
+    for (long long c0 = r0; c0 < r1; c0 += 32) {
+      const bool valid = c0 + lane < r1;
+      // dl/dS, dl/do, dl/dc, dl/dSigma3D, dl/dr_b, u, v and the primitive
+      float gS[3] = {ra.x, ra.y, ra.z}, gop = 0.f, gc[3] = {0.f, 0.f, 0.f}, gv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      float grb = 0.f, u, v;
+      int gl;
+      if (!bnd) {
+        gop = ra.w;
+        gc[0] = rb.x; gc[1] = rb.y; gc[2] = rb.z;
+        gv[0] = rc.y; gv[1] = rc.z; gv[2] = rc.w; gv[3] = rd.x; gv[4] = rd.y; gv[5] = rd.z;
+        u = rb.w;
+        v = rc.x;
+        gl = __float_as_int(rd.w);
+      } else {
+        grb = ra.w;
+        u = rb.x;
+        v = rb.y;
+        gl = __float_as_int(rb.z);
+      }
+      if (!valid) gl = -1;
+      load(c0 + 32);
+      float B[m];
+      bernstein_f32<N>(u, v, B);
+      bool consumed = !valid;
+      for (;;) {
+        if (!consumed && gl == gcur) {
+#pragma unroll
+          for (int a = 0; a < m; a++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+              acc[3 * a + c] = fmaf(B[a], gS[c], acc[3 * a + c]);
+              acc[3 * m + 3 * a + c] = fmaf(B[a], gc[c], acc[3 * m + 3 * a + c]);
+            }
+          acc[6 * m] += gop;
+          acc[6 * m + 1] += grb;
+#pragma unroll
+          for (int k = 0; k < 6; k++) acc[6 * m + 2 + k] += gv[k];
+          consumed = true;
+        }
+        const unsigned rest = __ballot_sync(0xffffffffu, !consumed);
+        if (!rest) break;
+        // the round holds the start of the next primitive's run
+        if (gcur >= 0) reduce_flush(gcur);
+        gcur = __shfl_sync(0xffffffffu, gl, __ffs(rest) - 1);
+      }
+    }
+    if (gcur >= 0) reduce_flush(gcur);
   }
 }
 
@@ -397,12 +654,31 @@ int launch_chain(const Params &p, const Scene &s, const Work &w, const Grads &g,
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = (sms > 0 ? sms : 152) * p.chain_bps;
+  int k = 0;
+  const int with_cov = p.attr_res == 1 && (g.log_scale || g.quat);
+  if (p.M > 0) {
+    // segments of the per-primitive records
+    cudaMemsetAsync(w.prim_gcnt, 0, sizeof(int) * (size_t)p.M, st);
+    cudaMemsetAsync(w.prim_bcnt, 0, sizeof(int) * (size_t)p.M, st);
+    k_prim_count<<<(sms > 0 ? sms : 152) * 8, 256, 0, st>>>(w);
+    k += 1 + launch_exclusive_scan(w.prim_gcnt, w.prim_gseg, p.M, w.scan_aux, st);
+    k += launch_exclusive_scan(w.prim_bcnt, w.prim_bseg, p.M, w.scan_aux2, st);
+    cudaMemsetAsync(w.prim_gcnt, 0, sizeof(int) * (size_t)p.M, st);  // now the fill counters
+    cudaMemsetAsync(w.prim_bcnt, 0, sizeof(int) * (size_t)p.M, st);
+    if (with_cov) cudaMemsetAsync(w.prim_gcov, 0, sizeof(float) * 6 * (size_t)p.M, st);
+  }
   dispatch_degree(p.n, [&](auto d) {
     k_chain_gauss<decltype(d)::value><<<grid, 256, 0, st>>>(p, s, w, g);
     k_chain_bnd<decltype(d)::value><<<grid, 256, 0, st>>>(p, s, w, g);
+    if (p.M > 0) {
+      if constexpr (SurfPoint<decltype(d)::value>::M <= 6)
+        k_prim_sum_reg<decltype(d)::value><<<(sms > 0 ? sms : 152) * 2, 256, 0, st>>>(p, w, g);
+      else
+        k_prim_sum<decltype(d)::value><<<(sms > 0 ? sms : 152) * 4, 256, 0, st>>>(p, w, g, with_cov);
+    }
     if (p.sh_deg > 0) k_chain_sh<decltype(d)::value><<<grid, 256, 0, st>>>(p, s, w, g);
   });
-  int k = p.sh_deg > 0 ? 3 : 2;
+  k += (p.sh_deg > 0 ? 3 : 2) + (p.M > 0 ? 1 : 0);
   if (p.attr_res == 1 && (g.log_scale || g.quat) && p.M > 0) {
     k_prim_attr_grad<<<(p.M + 255) / 256, 256, 0, st>>>(p, s, w, g);
     k++;
