@@ -189,7 +189,7 @@ constexpr int kIndexBits = 27;  // Gaussian index field of a pair key (<= 134M G
 constexpr unsigned long long kIndexMask = (1ull << kIndexBits) - 1ull;
 
 enum Counter { kF = 0, kNb = 1, kK = 2, kKb = 3, kQueueFwd = 4, kQueueBwd = 5, kQueueSort = 6, kBigCount = 7,
-               kRecChunks = 8, kFillChunks = 9, kWalkCount = 10, kQueueWalk = 11 };
+               kRecChunks = 8, kFillChunks = 9, kWalkCount = 10, kQueueWalk = 11, kMidCount = 12 };
 
 // ---------------------------------------------------------------------------
 // small helpers

@@ -266,9 +266,12 @@ __device__ void radix_global(unsigned long long *keys, unsigned long long *tmp, 
 
 constexpr int kWarpSortCap = 512;  // keys a single warp sorts in its own shared memory (occupancy:
                                    // 16 keys per lane in registers, 36 KB of shared memory per block)
+constexpr int kMidSortCap = 1024;  // longer segments up to this: one warp each in k_tile_sort_mid
+                                   // (32 keys per lane, 72 KB of shared memory per block)
 constexpr int kRadixMin = 129;     // segments from this length sort by radix, shorter ones by bitonic network
 // per warp: the keys (kWarpSortCap) and 256 radix bins
 constexpr int kTileSortSmem = (kSortThreads / 32) * (kWarpSortCap * (int)sizeof(unsigned long long) + 256 * 4);
+constexpr int kTileSortMidSmem = (kSortThreads / 32) * (kMidSortCap * (int)sizeof(unsigned long long) + 256 * 4);
 
 __device__ inline void segment_bounds(const Params &p, const Work &w, int item, bool &bnd, long long &s0,
                                       long long &s1) {
@@ -307,15 +310,15 @@ __device__ __forceinline__ void warp_bitonic_smem(unsigned long long *sk, int N,
     }
 }
 
-// Stable LSD radix sort (8-bit digits) of sk[0, n) (n <= kWarpSortCap) by
+// Stable LSD radix sort (8-bit digits) of sk[0, n) (n <= 32 R) by
 // one warp on the key bits from lo_shift up: the keys sit in registers, key i
 // in lane i % 32, slot i / 32; each pass histograms the digit into `bins`,
 // scans it and scatters the keys back to sk in order, ranking equal digits of
 // a round with a match; digits that are equal over the whole segment are
 // skipped. Keys equal above lo_shift keep their input order.
+template <int R>  // n <= 32 R
 __device__ __forceinline__ void warp_radix_smem(unsigned long long *sk, unsigned *bins, int n, int lane,
                                                 int lo_shift) {
-  constexpr int R = kWarpSortCap / 32;
   const int rounds = (n + 31) >> 5;
   const unsigned lt = (1u << lane) - 1u;
   unsigned long long key[R];
@@ -383,6 +386,24 @@ __device__ __forceinline__ void warp_radix_smem(unsigned long long *sk, unsigned
   }
 }
 
+// A segment staged in sk[0, n) (padded with ~0 to the power of two N) sorted
+// by one warp: boundary keys by radix on all bits; Gaussian keys by their
+// depth bits only (the index below them just breaks ties), and when a tie is
+// left in emission order (rare) the full keys go through the bitonic network,
+// so the order is the (tile, depth, index) order either way.
+template <int R>
+__device__ __forceinline__ void warp_sort_segment(unsigned long long *sk, unsigned *bins, int n, int N, bool bnd,
+                                                  int lane) {
+  if (bnd) {
+    warp_radix_smem<R>(sk, bins, n, lane, 0);
+    return;
+  }
+  warp_radix_smem<R>(sk, bins, n, lane, kIndexBits);
+  bool tie = false;
+  for (int i = lane; i + 1 < n; i += 32) tie |= ((sk[i] ^ sk[i + 1]) >> kIndexBits) == 0ull;
+  if (__any_sync(0xffffffffu, tie)) warp_bitonic_smem(sk, N, lane);
+}
+
 // Warps take segments from a queue. Up to 32 keys: bitonic sort across the
 // lanes' registers; up to kWarpSortCap: bitonic sort (up to 128 keys) or
 // radix sort in the warp's shared memory; longer segments are appended to a
@@ -405,8 +426,11 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_tile_sort(Params p, Work w,
     if (bnd ? b_over : g_over) continue;  // unwritten slots: nothing to sort
     const int n = (int)(s1 - s0);
     unsigned long long *keys = (bnd ? w.bkeys : w.gkeys) + s0;
-    if (n > kWarpSortCap) {
-      if (lane == 0) big_list[atomicAdd(w.counters + kQueueSort + 1, 1)] = item;
+    if (n > kWarpSortCap) {  // listed for k_tile_sort_mid (from the top of the list) or k_tile_sort_big
+      if (lane == 0) {
+        if (n <= kMidSortCap) big_list[2 * p.tiles + 1 - atomicAdd(w.counters + kMidCount, 1)] = item;
+        else big_list[atomicAdd(w.counters + kQueueSort + 1, 1)] = item;
+      }
       continue;
     }
     if (n > 1 && n <= 32) {
@@ -424,20 +448,8 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_tile_sort(Params p, Work w,
       while (N < n) N <<= 1;
       for (int i = lane; i < N; i += 32) sk[i] = i < n ? keys[i] : ~0ull;
       __syncwarp();
-      if (n < kRadixMin) {
-        warp_bitonic_smem(sk, N, lane);
-      } else if (bnd) {
-        warp_radix_smem(sk, bins, n, lane, 0);
-      } else {
-        // Gaussian keys by their depth bits only (the index below them just
-        // breaks ties); a tie left in emission order is rare and then the
-        // full keys go through the bitonic network, so the order is the
-        // (tile, depth, index) order either way
-        warp_radix_smem(sk, bins, n, lane, kIndexBits);
-        bool tie = false;
-        for (int i = lane; i + 1 < n; i += 32) tie |= ((sk[i] ^ sk[i + 1]) >> kIndexBits) == 0ull;
-        if (__any_sync(0xffffffffu, tie)) warp_bitonic_smem(sk, N, lane);
-      }
+      if (n < kRadixMin) warp_bitonic_smem(sk, N, lane);
+      else warp_sort_segment<kWarpSortCap / 32>(sk, bins, n, N, bnd, lane);
       for (int i = lane; i < n; i += 32) keys[i] = sk[i];
       __syncwarp();
     }
@@ -445,6 +457,31 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_tile_sort(Params p, Work w,
       __syncwarp();
       gather_boundary(w, s0, s1, lane, 32);
     }
+  }
+}
+
+// Segments of kWarpSortCap + 1 .. kMidSortCap keys (listed from the top of
+// big_list): one warp each, as in k_tile_sort with 32 keys per lane.
+__global__ void __launch_bounds__(kSortThreads, 2) k_tile_sort_mid(Params p, Work w, const int *big_list) {
+  extern __shared__ __align__(16) unsigned long long s_mid[];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  unsigned long long *sk = s_mid + wp * kMidSortCap;
+  unsigned *bins = reinterpret_cast<unsigned *>(s_mid + (kSortThreads / 32) * kMidSortCap) + wp * 256;
+  const int nmid = w.counters[kMidCount];
+  for (int it = blockIdx.x * (kSortThreads / 32) + wp; it < nmid; it += gridDim.x * (kSortThreads / 32)) {
+    bool bnd;
+    long long s0, s1;
+    segment_bounds(p, w, big_list[2 * p.tiles + 1 - it], bnd, s0, s1);
+    const int n = (int)(s1 - s0);
+    unsigned long long *keys = (bnd ? w.bkeys : w.gkeys) + s0;
+    int N = 64;
+    while (N < n) N <<= 1;
+    for (int i = lane; i < N; i += 32) sk[i] = i < n ? keys[i] : ~0ull;
+    __syncwarp();
+    warp_sort_segment<kMidSortCap / 32>(sk, bins, n, N, bnd, lane);
+    for (int i = lane; i < n; i += 32) keys[i] = sk[i];
+    __syncwarp();
+    if (bnd) gather_boundary(w, s0, s1, lane, 32);
   }
 }
 
@@ -494,16 +531,21 @@ int launch_exclusive_scan(const int *in, long long *out, int n, long long *aux, 
 }
 
 cudaError_t configure_binning() {
-  return cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSortSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSortSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tile_sort_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSortMidSmem);
+  return e;
 }
 
 int launch_bin_sort_only(const Params &p, const Work &w, cudaStream_t st) {
   k_emit<<<16 * 152, 256, 0, st>>>(p, w);
   if (p.tiles <= 0) return 1;
   cudaMemsetAsync(w.counters + kQueueSort, 0, 2 * sizeof(int), st);
+  cudaMemsetAsync(w.counters + kMidCount, 0, sizeof(int), st);
   k_tile_sort<<<3 * 152, kSortThreads, kTileSortSmem, st>>>(p, w, w.big_list);
+  k_tile_sort_mid<<<2 * 152, kSortThreads, kTileSortMidSmem, st>>>(p, w, w.big_list);
   k_tile_sort_big<<<4 * 152, kSortThreads, 0, st>>>(p, w, w.big_list, w.gkeys + p.max_pairs, w.bkeys + p.max_bpairs);
-  return 3;
+  return 4;
 }
 
 int launch_binning(const Params &p, const Work &w, cudaStream_t st) {
