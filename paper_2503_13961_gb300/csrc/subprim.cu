@@ -30,22 +30,60 @@ constexpr int kGenRounds = 4;                  // pixels per lane: a warp chunk 
 constexpr int kChunk = 32 * kGenRounds;
 constexpr int kGenWarps = kGenThreads / 32;
 
-// foreground / boundary flags of global pixel `pix`
-__device__ inline void pixel_flags(const Params &p, const Work &w, int pix, bool &fg, bool &bnd,
-                                   int &view) {
+// A warp chunk of kChunk pixels from `first`: its view when the whole chunk
+// lies in one view (the usual case: one search and one division per chunk),
+// with the view's size and the column and row of `first`; view = -1 otherwise.
+struct ChunkPos {
+  int view, W, H, x0, y0;
+};
+
+__device__ inline ChunkPos chunk_pos(const Params &p, const Work &w, int first) {
+  ChunkPos c{-1, 1, 1, 0, 0};
+  if (first >= p.P) return c;
+  const int v = find_view(w.view_pix_off, p.V, first);
+  if (min(first + kChunk, p.P) > __ldg(w.view_pix_off + v + 1)) return c;
+  c.view = v;
+  c.W = __ldg(&w.views[v].W);
+  c.H = __ldg(&w.views[v].H);
+  const int local = first - __ldg(w.view_pix_off + v);
+  c.y0 = local / c.W;
+  c.x0 = local - c.y0 * c.W;
+  return c;
+}
+
+// foreground / boundary flags of global pixel `pix`, the k-th of its chunk
+__device__ inline void pixel_flags(const Params &p, const Work &w, int pix, int k, const ChunkPos &cp, bool &fg,
+                                   bool &bnd, int &view) {
   fg = false;
   bnd = false;
   view = 0;
   if (pix >= p.P) return;
+  int W, H, x, y;
+  if (cp.view >= 0) {
+    view = cp.view;
+    W = cp.W;
+    H = cp.H;
+    x = cp.x0 + k;
+    y = cp.y0;
+    if (x >= W) {  // the chunk wraps to the following row(s)
+      y += x / W;
+      x -= (x / W) * W;
+    }
+  } else {
+    view = find_view(w.view_pix_off, p.V, pix);
+    W = __ldg(&w.views[view].W);
+    H = __ldg(&w.views[view].H);
+    const int local = pix - __ldg(w.view_pix_off + view);
+    y = local / W;
+    x = local - y * W;
+  }
+  // the pixel and its 4-neighbours, loaded together (clamped to the pixel
+  // itself where a neighbour lies outside the view)
   const int id = w.pid[pix];
-  if (id < 0) return;
-  fg = true;
-  view = find_view(w.view_pix_off, p.V, pix);
-  const int W = __ldg(&w.views[view].W), H = __ldg(&w.views[view].H);
-  const int local = pix - __ldg(&w.views[view].pix_off);
-  const int y = local / W, x = local - y * W;
-  bnd = (x > 0 && w.pid[pix - 1] != id) || (x < W - 1 && w.pid[pix + 1] != id) ||
-        (y > 0 && w.pid[pix - W] != id) || (y < H - 1 && w.pid[pix + W] != id);
+  const int il = w.pid[x > 0 ? pix - 1 : pix], ir = w.pid[x < W - 1 ? pix + 1 : pix];
+  const int iu = w.pid[y > 0 ? pix - W : pix], idn = w.pid[y < H - 1 ? pix + W : pix];
+  fg = id >= 0;
+  bnd = fg && (il != id || ir != id || iu != id || idn != id);
 }
 
 // foreground and boundary pixels of each warp chunk of 128 pixels
@@ -54,11 +92,12 @@ __global__ void __launch_bounds__(kGenThreads) k_count(Params p, Work w) {
   const int chunk = blockIdx.x * kGenWarps + (threadIdx.x >> 5);
   if (chunk >= w.nblk) return;
   int cf = 0, cb = 0;
+  const ChunkPos cp = chunk_pos(p, w, chunk * kChunk);
 #pragma unroll
   for (int r = 0; r < kGenRounds; r++) {
     bool fg, bnd;
     int view;
-    pixel_flags(p, w, chunk * kChunk + r * 32 + lane, fg, bnd, view);
+    pixel_flags(p, w, chunk * kChunk + r * 32 + lane, r * 32 + lane, cp, fg, bnd, view);
     cf += __popc(__ballot_sync(0xffffffffu, fg));
     cb += __popc(__ballot_sync(0xffffffffu, bnd));
   }
@@ -108,12 +147,13 @@ __global__ void __launch_bounds__(kGenThreads) k_compact(Params p, Work w) {
   int nf = (int)w.blk_off[chunk];
   int nb = (int)w.blk_off[w.nblk + 1 + chunk];
   const unsigned lt = (1u << lane) - 1u;
+  const ChunkPos cp = chunk_pos(p, w, chunk * kChunk);
 #pragma unroll
   for (int r = 0; r < kGenRounds; r++) {
     const int pix = chunk * kChunk + r * 32 + lane;
     bool fg, bnd;
     int view;
-    pixel_flags(p, w, pix, fg, bnd, view);
+    pixel_flags(p, w, pix, r * 32 + lane, cp, fg, bnd, view);
     const unsigned mf = __ballot_sync(0xffffffffu, fg), mb = __ballot_sync(0xffffffffu, bnd);
     const int gi = nf + __popc(mf & lt);
     if (pix < p.P) w.pix_gidx[pix] = fg ? gi : -1;
