@@ -390,8 +390,9 @@ def run_ours(args):
     M, ncp = sc["ctrl"].shape[0], sc["ctrl"].shape[1]
     n = int(sc["degree"])
     ppp = 32 if args.workload == "room8" else 6  # pair capacity per pixel (the room is dense)
+    bpp = 24 if args.workload == "room8" else 0   # blend records per pixel (0: the default, 8)
     rd = R.Renderer(degree=n, max_prims=M, max_views=V, max_pixels=P, max_pairs=ppp * P, max_boundary_pairs=ppp * P,
-                    tile_size=16, graph=True)
+                    max_blend_pairs=bpp * P, tile_size=16, graph=True)
     dev = R.scene_to_device(sc)
     stream = torch.cuda.Stream()
     gen = torch.Generator(device="cuda").manual_seed(1234 + rank)
@@ -444,7 +445,7 @@ def run_ours(args):
     # timing the step's own kernels; one more pass with the blending kernels'
     # counting build gives their work units
     prof_rd = R.Renderer(degree=n, max_prims=M, max_views=V, max_pixels=P, max_pairs=ppp * P,
-                         max_boundary_pairs=ppp * P, tile_size=rd.tile_size, graph=False)
+                         max_boundary_pairs=ppp * P, max_blend_pairs=bpp * P, tile_size=rd.tile_size, graph=False)
     prof_rd.set_tuning(**rd.tuning())
     stage_ms = {}
     units = {}
@@ -659,8 +660,9 @@ def run_plain(rd_ctx, args):
     M = sc["ctrl"].shape[0]
     Pmax = max(c["width"] * c["height"] for c in cams)
     ppp = 32 if args.workload == "room8" else 6
+    bpp = 24 if args.workload == "room8" else 0
     rd = R.Renderer(degree=int(sc["degree"]), max_prims=M, max_views=1, max_pixels=Pmax, max_pairs=ppp * Pmax,
-                    max_boundary_pairs=ppp * Pmax, tile_size=16, graph=False)
+                    max_boundary_pairs=ppp * Pmax, max_blend_pairs=bpp * Pmax, tile_size=16, graph=False)
     bufs = []
     gen = torch.Generator(device="cuda").manual_seed(99)
     with torch.cuda.stream(stream):

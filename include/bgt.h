@@ -61,8 +61,8 @@ typedef struct {
   long long max_pairs;          /* capacity: (Gaussian, tile) pairs per call */
   long long max_boundary_pairs; /* capacity: (boundary point, tile) pairs per call */
   long long max_blend_pairs;    /* capacity: (pixel, Gaussian) pairs the forward pass composites
-                                   per call, recorded for the backward pass: headers get 1/2,
-                                   fill records 1/32 of it; 0 = 8 per pixel, at least 2^22.
+                                   per call, recorded for the backward pass: headers get 3/4,
+                                   fill records 1/64 of it; 0 = 8 per pixel, at least 2^22.
                                    Warp blocks whose records do not fit are differentiated by
                                    re-walking their tile lists (bgt_get_counts out[7]): not an
                                    error, only slower */
@@ -164,8 +164,8 @@ const char *bgt_last_error(const bgt_handle *h);
 /* Counts of the last forward, after a synchronize: out[0] = foreground
  * pixels F (= Gaussians), out[1] = boundary points |B|, out[2] = Gaussian
  * tile pairs K, out[3] = boundary tile pairs Kb, out[4] = total tiles,
- * out[5] = blend-record header slots taken (capacity max_blend_pairs / 2),
- * out[6] = blend fill-record units taken (capacity max_blend_pairs / 32),
+ * out[5] = blend-record header slots taken (capacity 3/4 max_blend_pairs),
+ * out[6] = blend fill-record units taken (capacity max_blend_pairs / 64),
  * out[7] = warp blocks (32 pixels, 128 at tile 32) whose records did not
  * fit: the backward pass re-walks their tile lists instead of replaying
  * records (same gradients, slower); taken slots beyond a capacity were not

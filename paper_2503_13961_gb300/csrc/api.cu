@@ -126,8 +126,10 @@ void carve(bgt_handle *h, char *base, size_t *total) {
   w.scan_aux2 = w.scan_aux ? w.scan_aux + naux : nullptr;
   w.big_list = c.take<int>(2 * (long long)T + 2);
   w.tile_desc = c.take<int4>(2 * (long long)T + 2);
-  w.rec_chunk_cap = (int)(h->Bcap / 2 / bgt::kRecChunk + 1);
-  w.fill_unit_cap = (int)(h->Bcap / 32 + bgt::kFillChunk * 4 * 1024);
+  // headers 3/4 of the capacity, fill units 1/64 (fills are per primitive-cache miss: ~1 in 13
+  // headers on the 64-view scene, ~1 in 200 on dense tiles)
+  w.rec_chunk_cap = (int)(h->Bcap / 4 * 3 / bgt::kRecChunk + 1);
+  w.fill_unit_cap = (int)(h->Bcap / 64 + bgt::kFillChunk * 4 * 1024);
   w.rec_hdr = c.take<uint4>((long long)w.rec_chunk_cap * bgt::kRecChunk);
   w.rec_prev = c.take<int>(w.rec_chunk_cap);
   w.rec_fill = c.take<int>((long long)w.fill_unit_cap * 32);

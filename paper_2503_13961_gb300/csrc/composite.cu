@@ -876,14 +876,24 @@ __global__ void __launch_bounds__(TileCfg<T>::NT, TileCfg<T>::MINB_BWD) k_compos
 // forward (support, w by the same Eq. 6 search over the tile's boundary
 // list, alpha, the alpha_min cut) is retaken with the forward's operations,
 // so exactly the forward's composited pairs are visited; T_i = T_{i+1} /
-// (1 - alpha_i) and the gradients follow as in the record replay. Boundary
-// gradients are added per pair (the most influential boundary point of the
-// pair's search).
+// (1 - alpha_i) and the gradients follow as in the record replay. As in the
+// forward, the list is staged 32 entries at a time and culled against the
+// warp's block with one ballot, and w of (pixel, primitive) is kept per
+// primitive in a small per-warp cache (the same search, so the same values).
+// Boundary gradients are added per pair (the most influential boundary point
+// of the pair's search).
 template <int T>
 __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd_walk(Params p, Work w, const float *dimage) {
   using Cfg = TileCfg<T>;
   constexpr int PPT = Cfg::PPT, NW = Cfg::NW;
-  const int lane = threadIdx.x & 31;
+  constexpr int kWalkSlots = PPT == 1 ? 8 : 2;  // primitive cache slots per warp (static shared memory)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ float4 s_P[NW][32], s_Q[NW][32], s_C[NW][32];
+  __shared__ int s_G[NW][32];
+  __shared__ float s_ww[NW][kWalkSlots][PPT][32];  // w of the slot's primitive per pixel
+  __shared__ int s_wb[NW][kWalkSlots][PPT][32];    // its most influential boundary candidate
+  float4 *sP = s_P[warp], *sQ = s_Q[warp], *sC = s_C[warp];
+  int *sG = s_G[warp];
   const int nwalk = w.counters[kWalkCount];
   for (;;) {
     int q = 0;
@@ -936,12 +946,21 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd_walk(Params p,
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
     const unsigned long long *gkeys = w.gkeys + ti.gs;
-    for (int e = emax - 1; e >= 0; e--) {
-      const unsigned gi = (unsigned)(gkeys[e] & kIndexMask);
-      const float4 A = w.gA[gi];
-      const unsigned qxy = __float_as_uint(A.z);
-      const float4 P = make_float4((float)(int)(qxy & 0xffffu), (float)(int)(qxy >> 16), A.x, A.y);
-      const float4 Q = scaled_conic(w.gB[gi]), Cc = w.gC[gi];
+    // the warp's pixel block: entries whose support box misses it have no
+    // candidate pixel there (the box holds every pixel with o G >= alpha_min)
+    const int wx = ti.x0 + (wb % Cfg::WPR) * Cfg::WX, wy = ti.y0 + (wb / Cfg::WPR) * Cfg::WY;
+    const float bx0 = (float)wx, bx1 = (float)(wx + Cfg::WX - 1);
+    const float by0 = (float)wy, by1 = (float)(wy + Cfg::WY - 1);
+    int ckey = -2, cnext = 0;  // lane s: primitive of cache slot s (w and best per pixel in shared memory)
+    for (int c0 = ((emax - 1) >> 5) << 5; c0 >= 0; c0 -= 32) {
+      const bool valid = c0 + lane < emax;
+      unsigned mask = stage_chunk(w, valid ? gkeys[c0 + lane] : 0ull, valid, bx0, bx1, by0, by1, sP, sQ, sC, sG);
+      while (mask) {  // back to front
+      const int l = 31 - __clz(mask);
+      mask &= ~(1u << l);
+      const int e = c0 + l;
+      const unsigned gi = (unsigned)sG[l];
+      const float4 P = sP[l], Q = sQ[l], Cc = sC[l];
       const int g = __float_as_int(Cc.w);
       float og[PPT], Gk[PPT];
       bool cand[PPT];
@@ -951,20 +970,37 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd_walk(Params p,
         const float dx = __fsub_rn(__fsub_rn(pxf[k], P.x), P.z), dy = __fsub_rn(__fsub_rn(pyf[k], P.y), P.w);
         Gk[k] = gauss(dx, dy, Q);
         og[k] = __fmul_rn(Q.w, Gk[k]);
-        cand[k] = e < nlast[k] && A.w >= 0.f && og[k] >= p.alpha_min;
+        cand[k] = e < nlast[k] && og[k] >= p.alpha_min;
         anyc = anyc || cand[k];
       }
       if (!__any_sync(0xffffffffu, anyc)) continue;
-      int lo = 0, hi = 0;
-      if (p.use_boundary) warp_equal_range(bl.prim, bl.n, g, lo, hi);
+      // w of (pixel, g) by the forward's search, kept per primitive in a cache slot
+      int slot = 0;
+      if (p.use_boundary) {
+        slot = cache_find(ckey, g);
+        if (slot < 0) {
+          slot = cnext;
+          cnext = (cnext + 1 == kWalkSlots) ? 0 : cnext + 1;
+          int lo = 0, hi = 0;
+          warp_equal_range(bl.prim, bl.n, g, lo, hi);
+#pragma unroll
+          for (int k = 0; k < PPT; k++) {
+            int best = -1;
+            unsigned ncand = 0;
+            s_ww[warp][slot][k][lane] = w_search<2>(bl, lo, hi, pxr[k], pyr[k], idq[k] == g, best, ncand);
+            s_wb[warp][slot][k][lane] = best;
+          }
+          if (lane == slot) ckey = g;
+          __syncwarp();
+        }
+      }
       float acc[9];
 #pragma unroll
       for (int c = 0; c < 9; c++) acc[c] = 0.f;
 #pragma unroll
       for (int k = 0; k < PPT; k++) {
-        int best = -1;
-        unsigned ncand = 0;
-        const float wv = p.use_boundary ? w_search<2>(bl, lo, hi, pxr[k], pyr[k], idq[k] == g, best, ncand) : 1.0f;
+        const int best = p.use_boundary ? s_wb[warp][slot][k][lane] : -1;
+        const float wv = p.use_boundary ? s_ww[warp][slot][k][lane] : 1.0f;
         if (!cand[k]) continue;
         const float raw = __fmul_rn(og[k], wv);
         const float alpha = fminf(p.alpha_max, raw);
@@ -980,6 +1016,8 @@ __global__ void __launch_bounds__(TileCfg<T>::NT) k_composite_bwd_walk(Params p,
       const int gslot = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
       if ((lane & 3) == 0 && part != 0.f) atomicAdd(gg + gslot, part);
       if (lane == 1 && s8 != 0.f) atomicAdd(gg + 8, s8);
+      }
+      __syncwarp();
     }
   }
 }

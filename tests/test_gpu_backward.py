@@ -180,6 +180,20 @@ def test_blend_record_overflow_falls_back_to_tile_walk(oracle, scenes, cap):
         _assert_close(got[k], ref[k], k)
 
 
+@pytest.mark.parametrize("tile", [8, 32])
+def test_tile_walk_at_other_tile_sizes(oracle, scenes, tile):
+    """Every warp block re-walks its tile list (max_blend_pairs = 1) at tile 8
+    (one pixel per lane, two warps per tile) and tile 32 (four pixels per
+    lane, the walk's two-slot primitive cache): gradients against the
+    oracle."""
+    sc, cams = scenes.tiny_scene("ico1", noise=0.04, size=(90, 70), r_b=0.04)
+    rd = make_renderer(sc, cams, tile=tile, max_blend_pairs=1)
+    _, got, ref, _, _ = _run(oracle, sc, cams, seed=8, renderer=rd)
+    assert rd.counts()["walked_blocks"] > 0
+    for k in ("ctrl", "color", "opacity", "r_b"):
+        _assert_close(got[k], ref[k], k)
+
+
 def test_gradients_without_boundary_term(oracle, scenes):
     sc, cams = scenes.tiny_scene("ico1", noise=0.04, size=(64, 60), r_b=0.04)
     _, got, ref, _, _ = _run(oracle, sc, cams, use_boundary=False)
