@@ -406,8 +406,8 @@ __device__ __forceinline__ void warp_sort_segment(unsigned long long *sk, unsign
 
 // Warps take segments from a queue. Up to 32 keys: bitonic sort across the
 // lanes' registers; up to kWarpSortCap: bitonic sort (up to 128 keys) or
-// radix sort in the warp's shared memory; longer segments are appended to a
-// list for k_tile_sort_big.
+// radix sort in the warp's shared memory; longer segments are listed for
+// k_tile_sort_mid (up to kMidSortCap keys) or k_tile_sort_big.
 __global__ void __launch_bounds__(kSortThreads, 3) k_tile_sort(Params p, Work w, int *big_list) {
   extern __shared__ __align__(16) unsigned long long s_sort[];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
@@ -485,8 +485,9 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_tile_sort_mid(Params p, Wor
   }
 }
 
-// Segments longer than one warp's capacity: one block each (bitonic in
-// shared memory up to kSortCap keys, stable radix sort in global memory beyond).
+// Segments longer than kMidSortCap: one block each (bitonic in shared memory
+// up to kSortCap keys, stable radix sort in global memory beyond; a block
+// radix sort in shared memory measured slower on dense tiles).
 __global__ void __launch_bounds__(kSortThreads) k_tile_sort_big(Params p, Work w, const int *big_list,
                                                                unsigned long long *gtmp, unsigned long long *btmp) {
   __shared__ unsigned long long s_keys[kSortCap];
