@@ -408,7 +408,7 @@ def run_ours(args):
     if args.tile:
         rd.set_tile_size(args.tile)
     else:
-        _, tune_ms = rd.autotune(dev, cams, images, dimg, grads, iters=2, stream=stream)
+        _, tune_ms = rd.autotune(dev, cams, images, dimg, grads, iters=5, stream=stream)  # 5 passes per candidate: the knobs differ by 1-3 %
 
     def step():
         rd.forward(dev, cams, images, stream=stream)
