@@ -68,10 +68,24 @@ __device__ __forceinline__ void scatter_runs(float *sw, const float *v, int key,
 }
 
 constexpr int kChainWarps = 8;
+constexpr int kStagedViews = 64;  // cameras a chain block keeps in shared memory
+
+// the call's first kStagedViews cameras copied to shared memory, so that a
+// thread reads the fields it uses instead of holding a 128-byte View in
+// registers; returns how many were staged
+__device__ inline int stage_views(const Params &p, const Work &w, View *s_views) {
+  const int nsv = p.V < kStagedViews ? p.V : kStagedViews;
+  for (int v = threadIdx.x; v < nsv * (int)(sizeof(View) / 4); v += blockDim.x)
+    reinterpret_cast<int *>(s_views)[v] = reinterpret_cast<const int *>(w.views)[v];
+  __syncthreads();
+  return nsv;
+}
 
 template <int N>
 __global__ void __launch_bounds__(256) k_chain_gauss(Params p, Scene s, Work w, Grads out) {
   constexpr int m = SurfPoint<N>::M;
+  __shared__ View s_views[kStagedViews];
+  const int nsv = stage_views(p, w, s_views);
   const int F = w.counters[kF];
   const int lane = threadIdx.x & 31;
   const int warps_total = gridDim.x * (blockDim.x >> 5);
@@ -99,7 +113,8 @@ __global__ void __launch_bounds__(256) k_chain_gauss(Params p, Scene s, Work w, 
       gop = gd[5];
       gcol[0] = gd[6]; gcol[1] = gd[7]; gcol[2] = gd[8];
       g = w.g_prim[i];
-      const View vw = w.views[w.g_view[i]];
+      const int vi = w.g_view[i];
+      const View &vw = vi < nsv ? s_views[vi] : w.views[vi];
       uv = w.g_uv[i];
       float t[3];
       camera_point_f32<N>(s.ctrl + (size_t)g * m * 3, uv.x, uv.y, vw, B, t);
@@ -298,6 +313,8 @@ __global__ void __launch_bounds__(256) k_chain_sh(Params p, Scene s, Work w, Gra
 template <int N>
 __global__ void __launch_bounds__(256) k_chain_bnd(Params p, Scene s, Work w, Grads out) {
   constexpr int m = SurfPoint<N>::M;
+  __shared__ View s_views[kStagedViews];
+  const int nsv = stage_views(p, w, s_views);
   const int Nb = w.counters[kNb];
   const int lane = threadIdx.x & 31;
   const int warps_total = gridDim.x * (blockDim.x >> 5);
@@ -309,7 +326,8 @@ __global__ void __launch_bounds__(256) k_chain_bnd(Params p, Scene s, Work w, Gr
     float gS[3] = {0.f, 0.f, 0.f}, grb = 0.f;
     const float4 gb = w.bg_grad[i];
     if (gb.x != 0.f || gb.y != 0.f || gb.z != 0.f) {
-      const View vw = w.views[w.b_view[i]];
+      const int vi = w.b_view[i];
+      const View &vw = vi < nsv ? s_views[vi] : w.views[vi];
       float t[3], B[m];
       camera_point_f32<N>(s.ctrl + (size_t)g * m * 3, uv.x, uv.y, vw, B, t);
       const float tz = w.b_z[i], sigma = w.b_sigma[i];
