@@ -148,7 +148,13 @@ __global__ void __launch_bounds__(kRasterWarps * 32, N <= 2 ? 8 : 6) k_raster(Pa
     s_tri[ti] = make_int2(vslot(va[0], vb[0], L) | (vslot(va[1], vb[1], L) << 8) | (vslot(va[2], vb[2], L) << 16), sid);
   }
   __syncthreads();
-  const View vw = w.views[blockIdx.y];
+  // the block row's camera in shared memory, its fields read where used
+  // (held in registers it costs spills at the 64-register budget)
+  __shared__ View s_view;
+  if (threadIdx.x < (int)(sizeof(View) / 4))
+    reinterpret_cast<int *>(&s_view)[threadIdx.x] = reinterpret_cast<const int *>(w.views + blockIdx.y)[threadIdx.x];
+  __syncthreads();
+  const View &vw = s_view;
   const int W = vw.W, H = vw.H;
   unsigned long long *zb = w.zbuf + vw.pix_off;
   const int stride = gridDim.x * kRasterWarps;
