@@ -223,9 +223,10 @@ bgt_status bgt_set_tuning(bgt_handle *h, const bgt_tuning *t);
  * return it in *best (ms per pass of each size in ms_out[3] if non-NULL);
  * then, at that tile size, time the other knobs of bgt_tuning one at a time
  * (raster_prims in {4, 8, 16}, bwd_dequeue in {1, 2, 4},
- * chain_blocks_per_sm in {4, 8, 16}) and keep each fastest value; read the
- * chosen tuple with bgt_get_tuning. Buffers as for bgt_render_fwd /
- * bgt_render_bwd. */
+ * chain_blocks_per_sm in {4, 8, 16}) and keep each fastest value. The
+ * candidates of each knob are timed in two interleaved rounds, each keeping
+ * its faster time. Read the chosen tuple with bgt_get_tuning. Buffers as for
+ * bgt_render_fwd / bgt_render_bwd. */
 bgt_status bgt_autotune(bgt_handle *h, const bgt_scene *scene, const bgt_camera *cams, int n_views,
                         float *images, const float *d_images, const bgt_grads *grads, int iters,
                         int *best, float *ms_out, void *stream);

@@ -299,6 +299,18 @@ def test_l1_loss_helper(scenes):
     torch.cuda.synchronize()
     assert torch.allclose(d, 0.5 * torch.sign(a - b))
     assert torch.allclose(loss, 0.5 * (a - b).abs().sum(), rtol=1e-5)
+    # a ragged length (the four-value loop's tail) and arrays one float off a
+    # 16-byte boundary (the one-value loop only)
+    for off in (0, 1):
+        buf_a = torch.rand(3 * 1001 + off, device="cuda")
+        buf_b = torch.rand(3 * 1001 + off, device="cuda")
+        a, b = buf_a[off:], buf_b[off:]
+        dbuf = torch.empty(3 * 1001 + off, device="cuda")
+        loss = torch.zeros(1, device="cuda")
+        d = rd.l1_loss_grad(a, b, 0.25, d_images=dbuf[off:], loss=loss)
+        torch.cuda.synchronize()
+        assert torch.equal(d, 0.25 * torch.sign(a - b)), off
+        assert torch.allclose(loss, 0.25 * (a - b).abs().sum(), rtol=1e-5), off
     del R
 
 

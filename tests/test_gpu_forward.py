@@ -146,6 +146,32 @@ def test_tile_size_does_not_change_images(scenes):
     assert np.array_equal(imgs[0], imgs[1]) and np.array_equal(imgs[1], imgs[2])
 
 
+def test_autotune_picks_candidate_values_and_keeps_images(scenes):
+    """bgt_autotune on two crops of the config-4 scene: every knob of the
+    chosen tuple is one of its candidates, the per-tile-size times are
+    positive, and the images after tuning are bit-identical to those of the
+    default scheduling."""
+    import torch
+    from paper_2503_13961_gb300 import render as R
+    sc, cams = scenes.config_scene(4)
+    crops = [scenes.crop_camera(cams[1], 100, 100, 150, 130), scenes.crop_camera(cams[2], 0, 0, 77, 201)]
+    dev = R.scene_to_device(sc)
+    P = sum(c["width"] * c["height"] for c in crops)
+    rd = make_renderer(sc, crops)
+    ref = rd.forward(dev, crops).clone()
+    images = torch.empty((P, 3), device="cuda")
+    dl = torch.full((P, 3), 1e-3, device="cuda")
+    grads = {k: torch.empty_like(dev[k]) for k in R.GRAD_KEYS if k in dev}
+    best, ms = rd.autotune(dev, crops, images, dl, grads, iters=1)
+    rd.sync_status()
+    t = rd.tuning()
+    assert best in (8, 16, 32) and t["tile_size"] == best, (best, t)
+    assert t["raster_prims"] in (4, 8, 16) and t["bwd_dequeue"] in (1, 2, 4), t
+    assert t["chain_blocks_per_sm"] in (4, 8, 16), t
+    assert all(v > 0 for v in ms.values()), ms
+    assert torch.equal(rd.forward(dev, crops), ref)
+
+
 def test_scheduling_knobs_do_not_change_images(scenes):
     """Every knob of bgt_tuning (tile size, primitives per rasterizer warp,
     warp blocks per backward dequeue, chain-kernel blocks per SM) leaves the
