@@ -1040,7 +1040,7 @@ int launch_bwd_t(const Params &p, const Work &w, const float *dimage, cudaStream
     else k_composite_bwd<T, false><<<grid, TileCfg<T>::NT, sizeof(BwdShared<T>), st>>>(p, w, dimage);
     // warp blocks whose records overflowed (none in the common case: the
     // kernel reads the count and returns)
-    k_composite_bwd_walk<T><<<sms * 2, TileCfg<T>::NT, 0, st>>>(p, w, dimage);
+    k_composite_bwd_walk<T><<<sms * 3, TileCfg<T>::NT, 0, st>>>(p, w, dimage);  // 3 blocks per SM by registers
   }
   return grid > 0 ? 2 : 0;
 }
