@@ -408,7 +408,13 @@ def run_ours(args):
     if args.tile:
         rd.set_tile_size(args.tile)
     else:
-        _, tune_ms = rd.autotune(dev, cams, images, dimg, grads, iters=5, stream=stream)  # 5 passes per candidate: the knobs differ by 1-3 %
+        # the tuner times the step's backward with the L1 gradient of one
+        # forward (zero gradients would skip the backward's atomics); 5 passes
+        # per candidate: the knobs differ by 1-3 %
+        with torch.cuda.stream(stream):
+            rd.forward(dev, cams, images, stream=stream)
+            rd.l1_loss_grad(images, target, scale, dimg, torch.zeros(1, device="cuda"), stream=stream)
+        _, tune_ms = rd.autotune(dev, cams, images, dimg, grads, iters=5, stream=stream)
 
     def step():
         rd.forward(dev, cams, images, stream=stream)
