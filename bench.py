@@ -195,9 +195,9 @@ def stage_bytes(stage, c, M, ncp, V):
 # DRAM bytes (read + write) per composited pair of the blending kernels, from one
 # ncu capture of four 1024^2 views (profiles/composite_blend_views1024x4.md),
 # valid only for the kernel source they were measured on (else traffic: null)
-BLEND_TRAFFIC = {"source_sha256": "cc2780c8cf49e302ca40ff1189e6c55b059b5b70ada73b41ad7d4b5726e03b29",
-                 "composite_fwd": (131679744 + 153734656) / 50625814,
-                 "composite_bwd": (292571904 + 40398848) / 50625814}
+BLEND_TRAFFIC = {"source_sha256": "31926f2fd2cc1a5d3a82528a9d09ede5a53636275ce296cf8d2a83e72afeef5b",
+                 "composite_fwd": (131572480 + 153608192) / 50625814,
+                 "composite_bwd": (292371712 + 40375552) / 50625814}
 
 
 # Warp instructions per warp visit of the blending kernels (a visit: one warp,
@@ -205,7 +205,7 @@ BLEND_TRAFFIC = {"source_sha256": "cc2780c8cf49e302ca40ff1189e6c55b059b5b70ada73
 # capture; the forward keeps the issue slots ~80 % busy, so issue is the
 # ceiling that binds it; same source check as the traffic
 BLEND_ISSUE = {"source_sha256": BLEND_TRAFFIC["source_sha256"],
-               "composite_fwd": 681557896 / 5419084, "composite_bwd": 552831143 / 4948871}
+               "composite_fwd": 681557800 / 5419084, "composite_bwd": 552831143 / 4948871}
 
 
 def _blend_source_matches():
